@@ -1,0 +1,250 @@
+/*
+ * nnmg.h - C ABI of the GB300-native non-nested geometric multigrid library.
+ *
+ * The library solves the Poisson problem -lap u = f, u = 0 on the Dirichlet boundary,
+ * discretised by continuous Lagrange P1/P2 elements on simplicial meshes (triangles,
+ * tetrahedra), with the V-cycle of Chen & Wells, "Multigrid on unstructured meshes with
+ * regions of low quality cells" (arXiv:2402.12947):
+ *   - non-nested levels Omega_1 (finest) .. Omega_L, interpolation prolongation
+ *     [P_l]_ij = phi_j^(l+1)(x_i), R_l = P_l^T, Galerkin A_{l+1} = P_l^T A_l P_l (Sec. 2);
+ *   - the global-local combined smoother S_gc (Sec. 4.2): local residual correction S_c on
+ *     the patches around low-quality cells (Sec. 4.1, Alg. 2, patches per Sec. 4.4), a
+ *     Jacobi-preconditioned Chebyshev global smoother S_g (Sec. 3.2) with the adjusted
+ *     largest eigenvalue (Sec. 5), then S_c again;
+ *   - the V-cycle of Alg. 1 and, as in Sec. 6.2, CG preconditioned by one V-cycle.
+ *
+ * Conventions shared by every call:
+ *   - Levels are numbered 0 (finest, the paper's Omega_1) .. L-1 (coarsest).
+ *   - Vectors live on the free DoFs of a level, in the library's numbering: vertices in
+ *     the caller's vertex order, then (P2) one DoF per edge with edges in lexicographic
+ *     order of their sorted vertex pair; Dirichlet DoFs are removed, order kept. Local
+ *     DoF order inside a cell: vertices, then edges (0,1),(0,2),(1,2) in 2D and
+ *     (0,1),(0,2),(0,3),(1,2),(1,3),(2,3) in 3D.
+ *   - Dirichlet DoFs: vertices on a boundary facet (a facet of exactly one cell) allowed
+ *     by the optional vertex mask; an edge DoF is Dirichlet when its edge lies in a
+ *     boundary facet and both of its vertices are Dirichlet.
+ *   - Pointers named *_dev are device pointers (cudaMalloc / PyTorch CUDA memory) owned
+ *     by the caller; *_host pointers are host memory owned by the caller. The library
+ *     copies every host input it keeps; the hierarchy owns all device memory it allocates.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Compute calls are asynchronous on that stream unless stated otherwise.
+ *   - Every call returns an mg_status code; on failure, mg_last_error(h) (or
+ *     mg_last_error(NULL) after a failed setup) returns a message. Nothing aborts the
+ *     process and no call traps the GPU.
+ *   - Index limits: free DoFs and nonzeros per level must be < 2^31.
+ */
+#ifndef NNMG_H
+#define NNMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum mg_status {
+  MG_OK = 0,
+  MG_ERR_INVALID_ARG = 1,     /* bad pointer, size, level index or option */
+  MG_ERR_DEGENERATE_CELL = 2, /* a cell of zero volume (gamma = 0) */
+  MG_ERR_POINT_LOCATION = 3,  /* a fine DoF point lies in no coarse cell (tolerance 1e-12) */
+  MG_ERR_NOT_SPD = 4,         /* a patch matrix or the coarsest matrix failed Cholesky */
+  MG_ERR_NO_CONVERGENCE = 5,  /* maxit reached; the info struct is still filled */
+  MG_ERR_BREAKDOWN = 6,       /* CG breakdown: p^T A p <= 0 or a non-finite scalar */
+  MG_ERR_OOM = 7,             /* device or host allocation failed */
+  MG_ERR_CUDA = 8,            /* a CUDA runtime error (message has the CUDA text) */
+  MG_ERR_TIMEOUT = 9,         /* a bounded device-side wait gave up */
+  MG_ERR_NO_DEVICE = 10       /* compute call on a hierarchy built with host_only = 1 */
+};
+
+/* Smoother order (option `smoother`). */
+enum mg_smoother {
+  MG_SMOOTHER_SANDWICH = 0,          /* S_c, S_g, S_c on both sides (Sec. 4.2) */
+  MG_SMOOTHER_GLOBAL_THEN_LOCAL = 1, /* pre: S_g then S_c; post: S_c then S_g */
+  MG_SMOOTHER_GLOBAL = 2             /* S_g only (no local correction) */
+};
+
+/* Arithmetic of the V-cycle (option `precision`). */
+enum mg_precision {
+  MG_PREC_FP64 = 0,   /* everything in FP64 */
+  MG_PREC_MIXED = 1   /* V-cycle SpMVs/transfers/Chebyshev in FP32 (int32 indices) inside
+                         FP64 CG; patch solves, patch residuals and the coarsest solve FP64 */
+};
+
+typedef struct mg_hierarchy mg_hierarchy_t;
+
+/* One mesh level (Sec. 2: a triangulation Omega_l of the same domain; levels need not be
+ * nested but must share the boundary). coords [nv*dim] (x,y[,z] per vertex), cells
+ * [nc*(dim+1)] vertex ids (either orientation). dirichlet_vertex_mask [nv] or NULL (NULL:
+ * the whole boundary is Dirichlet). All host memory, copied by mg_setup. */
+typedef struct mg_mesh_t {
+  int32_t dim;            /* 2 or 3 */
+  int32_t reserved;
+  int64_t nv;
+  int64_t nc;
+  const double* coords;
+  const int32_t* cells;
+  const uint8_t* dirichlet_vertex_mask;
+} mg_mesh_t;
+
+/* Options; fill with mg_default_options() and change fields. */
+typedef struct mg_options_t {
+  int32_t cheb_degree;     /* A-applications per Chebyshev smoother application (2) */
+  int32_t nu;              /* smoother applications before and after the coarse correction (1) */
+  int32_t patch_layers;    /* vertex-layer extensions of Omega_b into Omega_B (1, Eq. identify) */
+  int32_t smoother;        /* enum mg_smoother (SANDWICH) */
+  int32_t adjusted_lambda; /* 1: lambda_max of A_gg (Sec. 5); 0: of the whole operator (1) */
+  int32_t precision;       /* enum mg_precision (FP64) */
+  int32_t host_only;       /* 1: build the hierarchy on the host only (exports work, compute
+                              calls return MG_ERR_NO_DEVICE) (0) */
+  int32_t eig_maxit;       /* Lanczos step limit for lambda_max (600) */
+  double lmin_ratio;       /* lambda_min = lmin_ratio * lambda_max (0.1, Sec. 3.2) */
+  double lmax_safety;      /* lambda_max is multiplied by this factor (1.0) */
+  double eig_tol;          /* Lanczos residual tolerance relative to lambda_max (1e-8) */
+  const double* lambda_override; /* [L-1] host array of lambda_max per level, or NULL */
+  int32_t use_graph;       /* 1: mg_solve runs as one CUDA graph with a device-side
+                              convergence test (conditional while node) (1) */
+  int32_t local_levels_mask; /* bit l set: local correction on level l (-1 = all) */
+  double quality_threshold;  /* set by mg_setup from its argument; ignored by mg_setup_csr */
+  int32_t sell_sigma;      /* rows sorted by length within windows of this many rows before
+                              SELL-32 slicing (1 = no sorting) (1) */
+  int32_t reserved[5];
+} mg_options_t;
+
+/* Result of a solve. */
+typedef struct mg_solve_info_t {
+  int32_t iterations;        /* CG iterations (= V-cycle applications) */
+  int32_t converged;         /* 1 if the recurrence residual reached rtol */
+  double rel_residual;       /* ||r_k||_2 / ||b||_2 of the recurrence residual */
+  double true_rel_residual;  /* ||b - A x||_2 / ||b||_2 recomputed in FP64 at exit */
+} mg_solve_info_t;
+
+/* CSR matrix handed to mg_setup_csr (host memory, copied). */
+typedef struct mg_csr_t {
+  int64_t nrows;
+  int64_t ncols;
+  const int32_t* rowptr;   /* [nrows+1], rowptr[0] = 0 */
+  const int32_t* colidx;   /* [nnz], sorted within each row */
+  const double* values;    /* [nnz] */
+} mg_csr_t;
+
+/* ---- set-up and teardown ------------------------------------------------------------ */
+
+/* Default options (see the field comments). */
+void mg_default_options(mg_options_t* opt);
+
+/* Build the hierarchy from mesh levels (Sec. 2, Sec. 4.4, Sec. 5, Sec. 6): P1/P2 stiffness
+ * on level 0; per level gamma = d R_I / R_C (Eq. radius_ratio, read as normalised to 1
+ * for the regular simplex), Omega_b = {gamma < quality_threshold}, Omega_B by
+ * patch_layers vertex extensions, patches B_d = vertex-connected components (free DoFs,
+ * ascending, patches ordered by their smallest DoF); P_l by point location of the fine
+ * DoF points in the coarse mesh; A_{l+1} = P_l^T A_l P_l; patch matrices A[B_d,B_d] and
+ * the coarsest matrix factored by Cholesky (FP64); lambda_max of D^-1 A_l by Lanczos.
+ * levels: host array [L] (L >= 2), degree 1 or 2. On success *out owns the hierarchy.
+ * Errors: INVALID_ARG, DEGENERATE_CELL, POINT_LOCATION, NOT_SPD, OOM, CUDA. */
+int mg_setup(const mg_mesh_t* levels, int32_t L, int32_t degree, double quality_threshold,
+             const mg_options_t* opt, mg_hierarchy_t** out);
+
+/* Build a hierarchy from algebraic data: A[L] level operators (SPD, square), P[L-1] with
+ * P[l] mapping level l+1 to level l (nrows = n_l, ncols = n_{l+1}; R_l = P_l^T),
+ * patch_ptr[l] ([np_l+1]) / patch_dofs[l] (disjoint DoF sets) per level (NULL = none),
+ * lambda_max per level through opt->lambda_override (required). No Galerkin product is
+ * formed: A[l] is used as given. Same ownership and errors as mg_setup. */
+int mg_setup_csr(const mg_csr_t* A, const mg_csr_t* P, int32_t L,
+                 const int32_t* const* patch_ptr, const int32_t* const* patch_dofs,
+                 const int32_t* num_patches, const mg_options_t* opt, mg_hierarchy_t** out);
+
+/* Free a hierarchy and all memory it owns (NULL is allowed). Synchronises the device. */
+void mg_free(mg_hierarchy_t* h);
+
+/* Message of the last failed call on h (NULL: of the last failed setup in this thread). */
+const char* mg_last_error(const mg_hierarchy_t* h);
+
+/* ---- queries and exports (host memory; work on host_only hierarchies) --------------- */
+
+int32_t mg_num_levels(const mg_hierarchy_t* h);
+int64_t mg_num_dofs(const mg_hierarchy_t* h, int32_t level);        /* free DoFs n_l */
+int64_t mg_level_nnz(const mg_hierarchy_t* h, int32_t level);       /* nnz of A_l */
+int64_t mg_transfer_nnz(const mg_hierarchy_t* h, int32_t level);    /* nnz of P_l (l < L-1) */
+/* Number of patches and total patch DoFs on a level. */
+int mg_num_patches(const mg_hierarchy_t* h, int32_t level, int32_t* num, int64_t* total_dofs);
+
+/* A_l as CSR into caller arrays rowptr[n+1], colidx[nnz], values[nnz]. */
+int mg_export_level(const mg_hierarchy_t* h, int32_t level, int32_t* rowptr, int32_t* colidx, double* values);
+/* P_l (level l+1 -> l) as CSR: rowptr[n_l+1], colidx/values[nnz]. */
+int mg_export_transfer(const mg_hierarchy_t* h, int32_t level, int32_t* rowptr, int32_t* colidx, double* values);
+/* Patches of a level: ptr[num+1], dofs[total] (free DoF ids). */
+int mg_export_patches(const mg_hierarchy_t* h, int32_t level, int32_t* ptr, int32_t* dofs);
+/* lambda_max of D^-1 A_l, unadjusted and adjusted (Sec. 5), as estimated at setup (0 when
+ * an override was given), and the value the smoother uses. */
+int mg_eigs(const mg_hierarchy_t* h, int32_t level, double* lmax, double* lmax_adj, double* lmax_used);
+/* Interpolation point of each free DoF: out[n_l*dim] (geometric hierarchies only). */
+int mg_dof_coords(const mg_hierarchy_t* h, int32_t level, double* out);
+/* gamma per cell of a level's mesh: out[nc] (geometric hierarchies only). */
+int mg_cell_quality(const mg_hierarchy_t* h, int32_t level, double* out);
+/* b_i = int f phi_i for a constant f on the free DoFs of level 0: out[n_0] host. */
+int mg_load_constant(const mg_hierarchy_t* h, double f, double* out_host);
+
+/* ---- the hot path (device vectors, FP64 at the boundary) ---------------------------- */
+
+/* One V-cycle of Alg. 1 in place: x_dev (initial guess in, new iterate out) for
+ * A_0 x = b, b_dev/x_dev [n_0] FP64. In MIXED precision the cycle computes the correction
+ * for the residual in FP32 (x += V(b - A x)). */
+int mg_vcycle(mg_hierarchy_t* h, const double* b_dev, double* x_dev, void* stream);
+
+/* V-cycle-preconditioned CG (Sec. 6.2) from x = 0 until ||r||_2/||b||_2 <= rtol or maxit
+ * iterations; x_dev receives the solution. Blocks until the solve has finished and fills
+ * *info (may be NULL). Returns MG_OK, MG_ERR_NO_CONVERGENCE or MG_ERR_BREAKDOWN. */
+int mg_solve(mg_hierarchy_t* h, const double* b_dev, double* x_dev, double rtol, int32_t maxit,
+             mg_solve_info_t* info, void* stream);
+
+/* mg_solve with host vectors: copies b_host in, solves, copies the solution to x_host. */
+int mg_solve_host(mg_hierarchy_t* h, const double* b_host, double* x_host, double rtol,
+                  int32_t maxit, mg_solve_info_t* info, void* stream);
+
+/* Stationary multigrid (Sec. 6.1): repeated V-cycles from x_dev until ||b-Ax||/||b|| <=
+ * rtol or maxit cycles. Blocks; fills *info. */
+int mg_solve_stationary(mg_hierarchy_t* h, const double* b_dev, double* x_dev, double rtol,
+                        int32_t maxit, mg_solve_info_t* info, void* stream);
+
+/* Solve n independent problems (their own hierarchies, all FP64 at the boundary) with the
+ * V-cycles of all problems interleaved on the device (one stream per problem, joined
+ * back to `stream`). Blocks; info[n] may be NULL. Returns the first non-OK status. */
+int mg_solve_batch(mg_hierarchy_t* const* hs, const double* const* b_dev, double* const* x_dev,
+                   int32_t n, double rtol, int32_t maxit, mg_solve_info_t* info, void* stream);
+
+/* ---- single steps of the hot path (device vectors in the hierarchy's V-cycle type:
+ *      FP64 in FP64 mode; FP32 in MIXED mode is not exposed) -------------------------- */
+
+/* y = A_l x. */
+int mg_apply_A(mg_hierarchy_t* h, int32_t level, const double* x_dev, double* y_dev, void* stream);
+/* One Chebyshev smoother application S_g of cheb_degree steps on level l, in place. */
+int mg_chebyshev(mg_hierarchy_t* h, int32_t level, const double* b_dev, double* x_dev, void* stream);
+/* One local correction S_c on level l (Alg. 2), in place. */
+int mg_local_correction(mg_hierarchy_t* h, int32_t level, const double* b_dev, double* x_dev, void* stream);
+/* One combined smoother application on level l (post = 0: pre-smoothing order), in place. */
+int mg_smooth(mg_hierarchy_t* h, int32_t level, int32_t post, const double* b_dev, double* x_dev, void* stream);
+/* r = b - A_l x and bc = R_l r (Eq. 4); r_dev [n_l], bc_dev [n_{l+1}]. */
+int mg_residual_restrict(mg_hierarchy_t* h, int32_t level, const double* b_dev, const double* x_dev,
+                         double* r_dev, double* bc_dev, void* stream);
+/* x_l += P_l xc (Alg. 1, coarse-grid correction); xc_dev [n_{l+1}], x_dev [n_l]. */
+int mg_prolong_correct(mg_hierarchy_t* h, int32_t level, const double* xc_dev, double* x_dev, void* stream);
+/* x = A_{L-1}^{-1} b on the coarsest level (direct solve). */
+int mg_coarse_solve(mg_hierarchy_t* h, const double* b_dev, double* x_dev, void* stream);
+
+/* Time `reps` back-to-back launches of the fine-level fused Chebyshev SpMV kernel with CUDA
+ * events on `stream`; returns the mean duration in ms and the kernel's algorithmic bytes
+ * per launch (matrix once, vectors once). Vectors are the hierarchy's own work buffers. */
+int mg_time_smoother_kernel(mg_hierarchy_t* h, int32_t reps, void* stream, double* ms_per_launch,
+                            double* bytes_per_launch);
+
+/* Device bytes held by the hierarchy. */
+int64_t mg_device_bytes(const mg_hierarchy_t* h);
+/* Number of kernel launches of one V-cycle, and of one CG iteration (V-cycle included). */
+int mg_launch_counts(const mg_hierarchy_t* h, int32_t* per_vcycle, int32_t* per_cg_iteration);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NNMG_H */

@@ -7,19 +7,19 @@ Builds, for meshes Omega_1 (finest) .. Omega_L (coarsest), per Sec. 2 and Sec. 6
     with A^{[d]} = A_l[B_d, B_d] factored by dense Cholesky (smoother.LocalSolver);
   * lambda_max of D^{-1}A_l (adjusted per Sec. 5 by default), lambda_min = lmin_ratio
     lambda_max; the option ``lambda_override`` injects given values instead;
-  * a dense Cholesky factor of the coarsest operator (the "direct solver" of Alg. 1).
+  * a dense Cholesky factor of the coarsest operator (the "direct solver" of Alg. 1),
+    with the semi-definite reading of ``smoother.DirectSolver``.
 """
 from __future__ import annotations
 
 from dataclasses import dataclass, field
 
 import numpy as np
-import scipy.linalg as sla
 import scipy.sparse as sp
 
 from . import eig as _eig
 from . import fem, patches as _patches, quality, transfer
-from .smoother import LocalSolver
+from .smoother import DirectSolver, LocalSolver
 
 
 @dataclass
@@ -51,7 +51,7 @@ class Hierarchy:
     cheb_degree: int = 2
     nu: int = 1
     order: str = "sandwich"
-    coarse: tuple | None = None
+    coarse: DirectSolver | None = None
 
     @property
     def L(self) -> int:
@@ -92,7 +92,7 @@ def build(meshes, degree: int, threshold: float = 0.1, layers: int = 1, adjusted
             lev.lmax_adj = _eig.adjusted_lambda_max(lev.A, lev.patches) if lev.patches else lev.lmax_unadj
             lev.lmax = lev.lmax_adj if adjusted else lev.lmax_unadj
         lev.lmin = lmin_ratio * lev.lmax
-    coarse = sla.cho_factor(levels[-1].A.toarray(), lower=True)
+    coarse = DirectSolver(levels[-1].A.toarray())
     return Hierarchy(levels=levels, degree=degree, cheb_degree=cheb_degree, nu=nu, order=order,
                      coarse=coarse)
 
@@ -110,5 +110,5 @@ def from_matrices(As, Ps, patches, lmax, cheb_degree=2, nu=1, order="sandwich", 
             lev.lmin = lmin_ratio * lev.lmax
         lev.local = LocalSolver(lev.A, lev.patches)
         levels.append(lev)
-    coarse = sla.cho_factor(levels[-1].A.toarray(), lower=True)
+    coarse = DirectSolver(levels[-1].A.toarray())
     return Hierarchy(levels=levels, degree=0, cheb_degree=cheb_degree, nu=nu, order=order, coarse=coarse)

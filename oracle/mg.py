@@ -19,7 +19,6 @@ local correction restores the iteration count of the high-quality hierarchy.
 from __future__ import annotations
 
 import numpy as np
-import scipy.linalg as sla
 
 from .hierarchy import Hierarchy
 from .smoother import smooth
@@ -28,7 +27,7 @@ from .smoother import smooth
 def vcycle(H: Hierarchy, b: np.ndarray, x: np.ndarray | None = None, l: int = 0) -> np.ndarray:
     lev = H.levels[l]
     if l == H.L - 1:
-        return sla.cho_solve(H.coarse, b)
+        return H.coarse.solve(b)
     x = np.zeros_like(b) if x is None else x.copy()
     for _ in range(H.nu):
         x = smooth(lev.A, lev.dinv, b, x, lev.lmax, lev.lmin, H.cheb_degree, lev.local, H.order, post=False)

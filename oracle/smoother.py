@@ -11,7 +11,12 @@ so that the error is multiplied by T_k((theta - D^{-1}A)/delta) / T_k(theta/delt
 
 S_c, Sec. 4.1 (Eqs. local_system .. local_update, Alg. 2): with one residual r = b - A x,
 x += sum_d I_d (I_d^T A I_d)^{-1} I_d^T r, each local system solved directly (dense
-Cholesky).
+Cholesky). Reading for semi-definite blocks: on coarse levels built from degenerate cells
+P can lose column rank, so a Galerkin block P^T A P may be singular (its residuals are
+still consistent: orthogonal to P's null space). The direct method is a Cholesky in
+which a pivot at or below 1e-10 of its original diagonal marks that DoF as dependent on
+the previous ones; dependent DoFs get a zero correction and the others are solved
+exactly. For SPD blocks nothing is dropped and this is the plain Cholesky solve.
 
 S_gc, Sec. 4.2: the sandwich S_c, then S_g, then S_c; the explicit form is
 S_gc = 2 S_c - S_c A S_c + (I - S_c A) S_g (I - A S_c).
@@ -56,15 +61,46 @@ def chebyshev(A: sp.csr_matrix, dinv: np.ndarray, b: np.ndarray, x: np.ndarray,
     return x
 
 
+DROP_TOL = 1e-10
+
+
+def dependent_dofs(Ad: np.ndarray) -> np.ndarray:
+    """Column-by-column Cholesky of a symmetric positive semi-definite matrix; returns the
+    mask of DoFs whose pivot is <= DROP_TOL times their diagonal (dependent DoFs)."""
+    n = Ad.shape[0]
+    L = np.zeros_like(Ad)
+    drop = np.zeros(n, dtype=bool)
+    for j in range(n):
+        s = Ad[j, j] - L[j, :j] @ L[j, :j]
+        if not Ad[j, j] > 0 or s < -DROP_TOL * Ad[j, j]:
+            raise np.linalg.LinAlgError("matrix is not positive semi-definite")
+        if s <= DROP_TOL * Ad[j, j]:
+            drop[j] = True
+            continue
+        L[j, j] = np.sqrt(s)
+        L[j + 1:, j] = (Ad[j + 1:, j] - L[j + 1:, :j] @ L[j, :j]) / L[j, j]
+    return drop
+
+
+class DirectSolver:
+    """Direct solve with a dense SPD (or consistent semi-definite) matrix, see module doc."""
+
+    def __init__(self, Ad: np.ndarray):
+        self.keep = ~dependent_dofs(Ad)
+        self.factor = sla.cho_factor(Ad[np.ix_(self.keep, self.keep)], lower=True)
+
+    def solve(self, r: np.ndarray) -> np.ndarray:
+        e = np.zeros_like(r)
+        e[self.keep] = sla.cho_solve(self.factor, r[self.keep])
+        return e
+
+
 class LocalSolver:
-    """Dense Cholesky factors of A^{[d]} = A[B_d, B_d] for each patch (Sec. 4.1)."""
+    """Direct solvers for A^{[d]} = A[B_d, B_d] of each patch (Sec. 4.1)."""
 
     def __init__(self, A: sp.csr_matrix, patches: list[np.ndarray]):
         self.patches = patches
-        self.factors = []
-        for B in patches:
-            Ad = A[B][:, B].toarray()
-            self.factors.append(sla.cho_factor(Ad, lower=True))
+        self.factors = [DirectSolver(A[B][:, B].toarray()) for B in patches]
 
     def apply(self, A: sp.csr_matrix, b: np.ndarray, x: np.ndarray) -> np.ndarray:
         if not self.patches:
@@ -72,7 +108,7 @@ class LocalSolver:
         r = b - A @ x
         x = x.copy()
         for B, fac in zip(self.patches, self.factors):
-            x[B] += sla.cho_solve(fac, r[B])
+            x[B] += fac.solve(r[B])
         return x
 
 

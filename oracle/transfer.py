@@ -11,6 +11,12 @@ the largest cell diameter of x_i, which contains every cell that can hold x_i. B
 values are taken at the raw barycentric coordinates; entries with |value| < 1e-14 are
 dropped; columns are the coarse free DoFs (Dirichlet columns vanish with g = 0).
 
+Reading for degenerate coarse cells: a coarse basis function can vanish at every fine
+interpolation point (e.g. the P2 edge DoF of a needle edge much shorter than the fine
+mesh size), leaving an empty column of P and an empty row/column of P^T A P. Such a DoF
+cannot influence the fine level; it is kept in the numbering with a unit diagonal, so it
+is decoupled and always receives a zero correction (equivalent to removing it).
+
 Pinned by tests/test_oracle_transfer.py: identical meshes give P = I; P reproduces any
 polynomial of degree <= p exactly; rows of the all-DoF P sum to 1; the Galerkin operator
 is symmetric positive definite and equals the dense triple product.
@@ -95,7 +101,10 @@ def prolongation(fine: DofMap, coarse_coords: np.ndarray, coarse_cells: np.ndarr
 
 
 def galerkin(A: sp.csr_matrix, P: sp.csr_matrix) -> sp.csr_matrix:
-    """A_{l+1} = P^T A P."""
+    """A_{l+1} = P^T A P, with a unit diagonal on coarse DoFs that P never reaches."""
     Ac = (P.T @ (A @ P)).tocsr()
+    unreached = np.flatnonzero(np.diff(P.tocsc().indptr) == 0)
+    if len(unreached):
+        Ac = (Ac + sp.csr_matrix((np.ones(len(unreached)), (unreached, unreached)), shape=Ac.shape)).tocsr()
     Ac.sort_indices()
     return Ac

@@ -1,0 +1,1291 @@
+// nnmg C ABI: hierarchy set-up, device residency, the V-cycle schedule and MG-PCG.
+//
+// Schedule of one V-cycle (Alg. 1 of Chen & Wells, zero initial guess on every level):
+//   level l < L-1: nu x S (pre), r_l = b_l - A_l x_l, b_{l+1} = R_l r_l (x_{l+1} = 0),
+//                  recurse, x_l += P_l x_{l+1}, nu x S (post)
+//   level L-1:     x = A^{-1} b with the dense inverse (FP64)
+// where S is the combined smoother of Sec. 4.2: S_c, cheb_degree fused Chebyshev steps,
+// S_c (sandwich), or the global-then-local / global-only variants.
+// MG-PCG (Sec. 6.2) keeps x, r, p, q, z and every scalar in FP64; in MIXED precision the
+// V-cycle runs on FP32 copies of the operators (int32 indices) and of r, while the patch
+// residuals and solves and the coarsest solve stay FP64.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <type_traits>
+
+#include "internal.hpp"
+#include "kernels.cuh"
+
+namespace nnmg {
+
+namespace {
+
+thread_local std::string g_setup_error;
+
+// Phase timer for set-up, printed to stderr when the environment sets NNMG_VERBOSE.
+struct PhaseTimer {
+  bool on = std::getenv("NNMG_VERBOSE") != nullptr;
+  std::chrono::steady_clock::time_point t = std::chrono::steady_clock::now();
+  void mark(const std::string& what) {
+    if (!on) return;
+    auto now = std::chrono::steady_clock::now();
+    std::fprintf(stderr, "[nnmg setup] %-28s %8.3f s\n", what.c_str(),
+                 std::chrono::duration<double>(now - t).count());
+    t = now;
+  }
+};
+
+#define CK(x)                                                                                            \
+  do {                                                                                                   \
+    cudaError_t e_ = (x);                                                                                \
+    if (e_ != cudaSuccess)                                                                               \
+      throw Error(e_ == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA,                            \
+                  std::string(#x) + ": " + cudaGetErrorString(e_));                                      \
+  } while (0)
+
+// Device allocations owned by one hierarchy (zero-filled on allocation).
+struct DevMem {
+  std::vector<void*> ptrs;
+  int64_t bytes = 0;
+  template <typename T>
+  T* alloc(size_t n) {
+    if (n == 0) return nullptr;
+    void* p = nullptr;
+    CK(cudaMalloc(&p, n * sizeof(T)));
+    ptrs.push_back(p);
+    bytes += (int64_t)(n * sizeof(T));
+    CK(cudaMemset(p, 0, n * sizeof(T)));
+    return (T*)p;
+  }
+  template <typename T>
+  T* upload(const T* src, size_t n) {
+    T* p = alloc<T>(n);
+    if (p) CK(cudaMemcpy(p, src, n * sizeof(T), cudaMemcpyHostToDevice));
+    return p;
+  }
+  template <typename T>
+  T* upload(const std::vector<T>& v) {
+    return upload(v.data(), v.size());
+  }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+    bytes = 0;
+  }
+};
+
+// Host CSR -> device SELL-32 (values converted to T).
+template <typename T>
+SellMat<T> make_sell(const Csr& A, DevMem& mem) {
+  SellMat<T> S;
+  S.nrows = (int32_t)A.nrows;
+  S.ncols = (int32_t)A.ncols;
+  S.nnz = A.nnz();
+  S.nslices = (int32_t)((A.nrows + 31) / 32);
+  std::vector<int64_t> off(S.nslices + 1, 0);
+  for (int32_t s = 0; s < S.nslices; ++s) {
+    int32_t w = 0;
+    for (int64_t r = (int64_t)s * 32; r < std::min<int64_t>(A.nrows, (int64_t)s * 32 + 32); ++r)
+      w = std::max(w, A.rp[r + 1] - A.rp[r]);
+    off[s + 1] = off[s] + 32 * (int64_t)w;
+  }
+  S.padded = off[S.nslices];
+  std::vector<int32_t> col(S.padded, 0);
+  std::vector<T> val(S.padded, T(0));
+  parallel_for(S.nslices, [&](int64_t lo, int64_t hi) {
+    for (int64_t s = lo; s < hi; ++s) {
+      int64_t w = (off[s + 1] - off[s]) / 32;
+      for (int lane = 0; lane < 32; ++lane) {
+        int64_t r = s * 32 + lane;
+        int32_t len = r < A.nrows ? A.rp[r + 1] - A.rp[r] : 0;
+        int32_t pad_col = len > 0 ? A.ci[A.rp[r + 1] - 1] : 0;
+        for (int64_t j = 0; j < w; ++j) {
+          int64_t o = off[s] + j * 32 + lane;
+          if (j < len) {
+            col[o] = A.ci[A.rp[r] + j];
+            val[o] = (T)A.v[A.rp[r] + j];
+          } else {
+            col[o] = pad_col;
+          }
+        }
+      }
+    }
+  });
+  S.off = mem.upload(off);
+  S.col = mem.upload(col);
+  S.val = mem.upload(val);
+  return S;
+}
+
+template <typename T>
+struct DevLevel {
+  int n = 0;
+  SellMat<T> A, P, R;
+  T *dinv = nullptr, *b = nullptr, *x = nullptr, *xt = nullptr, *d = nullptr, *res = nullptr;
+  std::vector<double> cd, cr;
+  // local correction
+  int np = 0, nt = 0, nitems = 0, max_patch = 0;
+  int32_t *pdofs = nullptr, *pptr = nullptr, *prp = nullptr, *pci = nullptr;
+  double* pv = nullptr;
+  int64_t* inv_off = nullptr;
+  double *inv = nullptr, *rbuf = nullptr;
+  PatchItem* items = nullptr;
+};
+
+}  // namespace
+
+// The V-cycle in one arithmetic type T (double or float).
+template <typename T>
+struct Engine {
+  std::vector<DevLevel<T>> lv;
+  int cheb_k = 2, nu = 1, order = MG_SMOOTHER_SANDWICH;
+  uint32_t local_mask = 0xffffffffu;
+  // coarsest level
+  int nc = 0, kchunk = 256;
+  double *Xc = nullptr, *cpart = nullptr;
+  int launches = 0;
+
+  bool local_on(int l) const {
+    return lv[l].np > 0 && order != MG_SMOOTHER_GLOBAL && ((local_mask >> std::min(l, 31)) & 1u);
+  }
+  void cheb(int l, cudaStream_t s) {
+    DevLevel<T>& L = lv[l];
+    T *xa = L.x, *xb = L.xt;
+    for (int j = 0; j < cheb_k; ++j) {
+      sell_cheb<T>(L.A, xa, L.b, L.dinv, L.d, xb, L.cd[j], L.cr[j], j == 0, s);
+      ++launches;
+      std::swap(xa, xb);
+    }
+    if (xa != L.x) {
+      CK(cudaMemcpyAsync(L.x, xa, sizeof(T) * L.n, cudaMemcpyDeviceToDevice, s));
+      ++launches;
+    }
+  }
+  void local(int l, cudaStream_t s) {
+    DevLevel<T>& L = lv[l];
+    patch_residual<T>(L.nt, L.pdofs, L.prp, L.pci, L.pv, L.b, L.x, L.rbuf, s);
+    patch_solve<T>(L.nitems, L.items, L.pptr, L.pdofs, L.inv_off, L.inv, L.rbuf, L.x, L.max_patch, s);
+    launches += 2;
+  }
+  void smooth(int l, bool post, cudaStream_t s) {
+    if (!local_on(l)) {
+      cheb(l, s);
+      return;
+    }
+    if (order == MG_SMOOTHER_SANDWICH) {
+      local(l, s);
+      cheb(l, s);
+      local(l, s);
+    } else if (!post) {
+      cheb(l, s);
+      local(l, s);
+    } else {
+      local(l, s);
+      cheb(l, s);
+    }
+  }
+  void coarse(cudaStream_t s) {
+    DevLevel<T>& L = lv.back();
+    dense_solve<T>(nc, Xc, L.b, L.x, cpart, kchunk, s);
+    launches += 2;
+  }
+  void residual_restrict(int l, cudaStream_t s) {
+    DevLevel<T>& L = lv[l];
+    DevLevel<T>& C = lv[l + 1];
+    sell_resid<T>(L.A, L.x, L.b, L.res, s);
+    sell_restrict<T>(L.R, L.res, C.b, C.x, s);
+    launches += 2;
+  }
+  void prolong(int l, cudaStream_t s) {
+    sell_prolong<T>(lv[l].P, lv[l + 1].x, lv[l].x, s);
+    ++launches;
+  }
+  void cycle(int l, cudaStream_t s) {
+    if (l == (int)lv.size() - 1) {
+      coarse(s);
+      return;
+    }
+    for (int k = 0; k < nu; ++k) smooth(l, false, s);
+    residual_restrict(l, s);
+    cycle(l + 1, s);
+    prolong(l, s);
+    for (int k = 0; k < nu; ++k) smooth(l, true, s);
+  }
+};
+
+}  // namespace nnmg
+
+using namespace nnmg;
+
+struct mg_hierarchy {
+  mg_options_t opt{};
+  int L = 0, degree = 0;
+  bool geometric = false, device = false;
+  std::vector<LevelH> host;
+  std::vector<double> fine_load_unit;  // b for f = 1 (geometric only)
+  std::vector<int64_t> ncells;
+  std::string err;
+  // device
+  DevMem mem;
+  std::unique_ptr<Engine<double>> e64;
+  std::unique_ptr<Engine<float>> e32;
+  SellMat<double> A0;  // fine operator in FP64 for the CG recurrence
+  int n0 = 0;
+  double *cb = nullptr, *cx = nullptr, *cr = nullptr, *cp = nullptr, *cq = nullptr, *cz = nullptr, *part = nullptr;
+  CgState* st = nullptr;
+  CgState* hst = nullptr;  // pinned
+  int nparts = 1, ap_parts = 1;
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t own_stream = nullptr;
+  int launches_vcycle = 0, launches_iter = 0;
+  int64_t dropped_dofs = 0;  // DoFs excluded as dependent by the dense direct solves
+
+  bool mixed() const { return opt.precision == MG_PREC_MIXED; }
+  template <typename F>
+  void with_engine(F&& f) {
+    if (e64) f(*e64);
+    else f(*e32);
+  }
+  ~mg_hierarchy() {
+    if (device) cudaDeviceSynchronize();
+    if (graph) cudaGraphExecDestroy(graph);
+    if (own_stream) cudaStreamDestroy(own_stream);
+    if (hst) cudaFreeHost(hst);
+    mem.release();
+  }
+};
+
+namespace nnmg {
+namespace {
+
+void validate_options(const mg_options_t& o) {
+  if (o.cheb_degree < 1 || o.cheb_degree > 16) throw Error(MG_ERR_INVALID_ARG, "cheb_degree must be in [1, 16]");
+  if (o.nu < 1 || o.nu > 16) throw Error(MG_ERR_INVALID_ARG, "nu must be in [1, 16]");
+  if (o.patch_layers < 0 || o.patch_layers > 8) throw Error(MG_ERR_INVALID_ARG, "patch_layers must be in [0, 8]");
+  if (o.smoother < 0 || o.smoother > 2) throw Error(MG_ERR_INVALID_ARG, "unknown smoother order");
+  if (o.precision < 0 || o.precision > 1) throw Error(MG_ERR_INVALID_ARG, "unknown precision");
+  if (!(o.lmin_ratio > 0 && o.lmin_ratio < 1)) throw Error(MG_ERR_INVALID_ARG, "lmin_ratio must be in (0, 1)");
+  if (!(o.lmax_safety > 0)) throw Error(MG_ERR_INVALID_ARG, "lmax_safety must be positive");
+}
+
+// Chebyshev coefficients per step: d = cd d + cr D^{-1} r (Sec. 3.2 three-term recurrence).
+void cheb_coefficients(double lmax, double lmin, int k, std::vector<double>& cd, std::vector<double>& cr) {
+  double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta, rho = 1.0 / sigma;
+  cd.assign(1, 0.0);
+  cr.assign(1, 1.0 / theta);
+  for (int j = 1; j < k; ++j) {
+    double rn = 1.0 / (2.0 * sigma - rho);
+    cd.push_back(rn * rho);
+    cr.push_back(2.0 * rn / delta);
+    rho = rn;
+  }
+}
+
+// Everything after the operators are known: diagonals, patch inverses, eigenvalues,
+// coarsest inverse, then (unless host_only) the device upload and the solve graph.
+void finish_setup(mg_hierarchy* h) {
+  const mg_options_t& o = h->opt;
+  const int L = h->L;
+  PhaseTimer tm;
+  for (int l = 0; l < L; ++l) {
+    LevelH& lv = h->host[l];
+    const int64_t n = lv.A.nrows;
+    if (n == 0) throw Error(MG_ERR_INVALID_ARG, "level " + std::to_string(l) + " has no free DoFs");
+    lv.dinv.resize(n);
+    for (int64_t i = 0; i < n; ++i) {
+      double dg = 0;
+      for (int32_t k = lv.A.rp[i]; k < lv.A.rp[i + 1]; ++k)
+        if (lv.A.ci[k] == i) dg = lv.A.v[k];
+      if (!(dg > 0)) throw Error(MG_ERR_NOT_SPD, "level " + std::to_string(l) + ": non-positive diagonal at " + std::to_string(i));
+      lv.dinv[i] = 1.0 / dg;
+    }
+    if (l == L - 1) continue;
+    const int64_t np = (int64_t)lv.patch_ptr.size() - 1;
+    // eigenvalues (Sec. 3.2 / Sec. 5)
+    if (o.lambda_override) {
+      lv.lmax = o.lambda_override[l];
+      if (!(lv.lmax > 0)) throw Error(MG_ERR_INVALID_ARG, "lambda_override must be positive");
+    } else {
+      int it = 0;
+      lv.lmax_unadj = lanczos_lmax(lv.A, nullptr, o.eig_tol, o.eig_maxit, &it);
+      lv.lanczos_iters = it;
+      if (np > 0) {
+        std::vector<uint8_t> keep(n, 1);
+        for (int32_t f : lv.patch_dofs) keep[f] = 0;
+        lv.lmax_adj = lanczos_lmax(lv.A, keep.data(), o.eig_tol, o.eig_maxit, &it);
+        lv.lanczos_iters += it;
+      } else {
+        lv.lmax_adj = lv.lmax_unadj;
+      }
+      tm.mark("lanczos L" + std::to_string(l) + " (" + std::to_string(lv.lanczos_iters) + " it)");
+      lv.lmax = o.adjusted_lambda ? lv.lmax_adj : lv.lmax_unadj;
+      lv.lmax *= o.lmax_safety;
+    }
+    lv.lmin = o.lmin_ratio * lv.lmax;
+  }
+  const int64_t ncoarse = h->host[L - 1].A.nrows;
+  if (ncoarse > 20000) throw Error(MG_ERR_INVALID_ARG, "coarsest level too large for the dense direct solve (> 20000 DoFs)");
+  if (o.host_only) return;
+
+  // ---- device upload ----
+  int dev_count = 0;
+  if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0) throw Error(MG_ERR_NO_DEVICE, "no CUDA device");
+  h->device = true;
+  DevMem& mem = h->mem;
+  int max_patch = 0;
+  // All dense blocks (every patch matrix A[B_d, B_d] of every level and the coarsest A)
+  // are inverted together on the device by the batched Gauss-Jordan sweep.
+  struct Blk {
+    int level, patch;
+    int32_t n;
+  };
+  std::vector<Blk> blks;
+  for (int l = 0; l + 1 < L; ++l) {
+    const LevelH& lv = h->host[l];
+    for (int64_t p = 0; p + 1 < (int64_t)lv.patch_ptr.size(); ++p)
+      blks.push_back({l, (int)p, lv.patch_ptr[p + 1] - lv.patch_ptr[p]});
+  }
+  blks.push_back({L - 1, -1, (int32_t)ncoarse});
+  std::vector<int> order(blks.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return blks[a].n > blks[b].n; });
+  GjBatch gj;
+  gj.nmat = (int)blks.size();
+  std::vector<int64_t> boff(blks.size()), bvoff(blks.size());  // by block id
+  std::vector<int64_t> soff, svoff;                              // by sorted position
+  int64_t mtot = 0, vtot = 0;
+  for (int id : order) {
+    boff[id] = mtot;
+    bvoff[id] = vtot;
+    gj.hn.push_back(blks[id].n);
+    soff.push_back(mtot);
+    svoff.push_back(vtot);
+    mtot += (int64_t)blks[id].n * blks[id].n;
+    vtot += blks[id].n;
+  }
+  gj.max_n = gj.hn.empty() ? 0 : gj.hn[0];
+  {
+    std::vector<double> Mh(mtot), d0(vtot);
+    parallel_for((int64_t)blks.size(), [&](int64_t lo, int64_t hi) {
+      for (int64_t id = lo; id < hi; ++id) {
+        const Blk& bk = blks[id];
+        const LevelH& lv = h->host[bk.level];
+        std::vector<int32_t> all;
+        const int32_t* idx;
+        if (bk.patch >= 0) {
+          idx = &lv.patch_dofs[lv.patch_ptr[bk.patch]];
+        } else {
+          all.resize(bk.n);
+          for (int32_t i = 0; i < bk.n; ++i) all[i] = i;
+          idx = all.data();
+        }
+        std::vector<double> D = dense_submatrix(lv.A, idx, bk.n);
+        std::copy(D.begin(), D.end(), Mh.begin() + boff[id]);
+        for (int32_t i = 0; i < bk.n; ++i) d0[bvoff[id] + i] = D[(int64_t)i * bk.n + i];
+      }
+    });
+    gj.M = mem.upload(Mh);
+    gj.diag0 = mem.upload(d0);
+  }
+  gj.n = mem.upload(gj.hn);
+  gj.off = mem.upload(soff);
+  gj.voff = mem.upload(svoff);
+  gj.rowk = mem.alloc<double>(vtot);
+  gj.colk = mem.alloc<double>(vtot);
+  gj.pinv = mem.alloc<double>(gj.nmat);
+  gj.drop = mem.alloc<int32_t>(gj.nmat);
+  gj.bad = mem.alloc<int32_t>(gj.nmat);
+  gj.ndrop = mem.alloc<int32_t>(gj.nmat);
+  batched_spsd_inverse(gj, 0);
+  check_launch("batched dense inverse");
+  {
+    std::vector<int32_t> bad(gj.nmat), nd(gj.nmat);
+    CK(cudaMemcpy(bad.data(), gj.bad, sizeof(int32_t) * gj.nmat, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(nd.data(), gj.ndrop, sizeof(int32_t) * gj.nmat, cudaMemcpyDeviceToHost));
+    for (int sp = 0; sp < gj.nmat; ++sp) {
+      const Blk& bk = blks[order[sp]];
+      if (bad[sp])
+        throw Error(MG_ERR_NOT_SPD, bk.patch >= 0 ? "level " + std::to_string(bk.level) + ": patch " +
+                                                        std::to_string(bk.patch) + " is not positive semi-definite"
+                                                  : std::string("coarsest operator is not positive semi-definite"));
+      h->dropped_dofs += nd[sp];
+    }
+  }
+  tm.mark("batched inverse (" + std::to_string(gj.nmat) + " blocks, max n " + std::to_string(gj.max_n) + ")");
+  std::vector<std::vector<int64_t>> level_inv_off(L);
+  for (size_t id = 0; id < blks.size(); ++id)
+    if (blks[id].patch >= 0) level_inv_off[blks[id].level].push_back(boff[id]);
+  const double* coarse_inv = gj.M + boff[blks.size() - 1];
+  auto upload_engine = [&](auto* eng, auto tag) {
+    using T = decltype(tag);
+    eng->cheb_k = o.cheb_degree;
+    eng->nu = o.nu;
+    eng->order = o.smoother;
+    eng->local_mask = (uint32_t)o.local_levels_mask;
+    eng->lv.resize(L);
+    for (int l = 0; l < L; ++l) {
+      LevelH& H = h->host[l];
+      DevLevel<T>& D = eng->lv[l];
+      D.n = (int)H.A.nrows;
+      D.A = make_sell<T>(H.A, mem);
+      if (l < L - 1) {
+        D.P = make_sell<T>(H.P, mem);
+        D.R = make_sell<T>(H.R, mem);
+        std::vector<T> dv(H.dinv.begin(), H.dinv.end());
+        D.dinv = mem.upload(dv);
+        cheb_coefficients(H.lmax, H.lmin, o.cheb_degree, D.cd, D.cr);
+        D.xt = mem.alloc<T>(D.n);
+        D.d = mem.alloc<T>(D.n);
+        D.res = mem.alloc<T>(D.n);
+        // patches
+        D.np = (int)H.patch_ptr.size() - 1;
+        if (D.np > 0) {
+          D.nt = (int)H.patch_dofs.size();
+          D.pdofs = mem.upload(H.patch_dofs);
+          D.pptr = mem.upload(H.patch_ptr);
+          std::vector<int32_t> prp(D.nt + 1, 0), pci;
+          std::vector<double> pv;
+          std::vector<PatchItem> items;
+          for (int t = 0; t < D.nt; ++t) {
+            int32_t r = H.patch_dofs[t];
+            for (int32_t k = H.A.rp[r]; k < H.A.rp[r + 1]; ++k) pci.push_back(H.A.ci[k]), pv.push_back(H.A.v[k]);
+            prp[t + 1] = (int32_t)pci.size();
+          }
+          for (int p = 0; p < D.np; ++p) {
+            int m = H.patch_ptr[p + 1] - H.patch_ptr[p];
+            D.max_patch = std::max(D.max_patch, m);
+            for (int r0 = 0; r0 < m; r0 += kBlock) items.push_back({p, r0});
+          }
+          if (D.max_patch > 27000) throw Error(MG_ERR_INVALID_ARG, "patch larger than 27000 DoFs");
+          max_patch = std::max(max_patch, D.max_patch);
+          D.nitems = (int)items.size();
+          D.prp = mem.upload(prp);
+          D.pci = mem.upload(pci);
+          D.pv = mem.upload(pv);
+          D.inv_off = mem.upload(level_inv_off[l]);
+          D.inv = gj.M;
+          D.rbuf = mem.alloc<double>(D.nt);
+          D.items = mem.upload(items);
+        }
+      }
+      bool fine_shared = (l == 0) && std::is_same<T, double>::value;
+      if (!fine_shared) {
+        D.b = mem.alloc<T>(D.n);
+        D.x = mem.alloc<T>(D.n);
+      }
+    }
+    eng->nc = (int)ncoarse;
+    eng->kchunk = 256;
+    int rowblocks = (eng->nc + kBlock - 1) / kBlock;
+    int want_chunks = std::max(1, (2 * 152 + rowblocks - 1) / rowblocks);
+    eng->kchunk = std::max(64, std::min(1024, ((eng->nc + want_chunks - 1) / want_chunks + 63) / 64 * 64));
+    eng->Xc = const_cast<double*>(coarse_inv);
+    eng->cpart = mem.alloc<double>((size_t)dense_chunks(eng->nc, eng->kchunk) * eng->nc);
+  };
+  h->n0 = (int)h->host[0].A.nrows;
+  const int n0 = h->n0;
+  h->cb = mem.alloc<double>(n0);
+  h->cx = mem.alloc<double>(n0);
+  h->cr = mem.alloc<double>(n0);
+  h->cp = mem.alloc<double>(n0);
+  h->cq = mem.alloc<double>(n0);
+  h->cz = mem.alloc<double>(n0);
+  h->nparts = cg_parts(n0);
+  h->ap_parts = sell_blocks(n0);
+  h->part = mem.alloc<double>(std::max(h->nparts, h->ap_parts));
+  h->st = mem.alloc<CgState>(1);
+  CK(cudaMallocHost(&h->hst, sizeof(CgState)));
+  std::memset(h->hst, 0, sizeof(CgState));
+  if (h->mixed()) {
+    h->e32.reset(new Engine<float>());
+    upload_engine(h->e32.get(), float());
+    h->A0 = make_sell<double>(h->host[0].A, mem);
+  } else {
+    h->e64.reset(new Engine<double>());
+    upload_engine(h->e64.get(), double());
+    h->e64->lv[0].b = h->cr;  // the V-cycle of CG reads r and writes z in place
+    h->e64->lv[0].x = h->cz;
+    h->A0 = h->e64->lv[0].A;
+  }
+  if (max_patch > 0) patch_solve_setup(max_patch);
+  CK(cudaDeviceSynchronize());
+  tm.mark("device upload");
+}
+
+}  // namespace
+}  // namespace nnmg
+
+// ---- CG orchestration -------------------------------------------------------------------
+
+namespace nnmg {
+namespace {
+
+template <typename T>
+struct CgRunner {
+  mg_hierarchy* h;
+  Engine<T>& e;
+  T* vb() { return e.lv[0].b; }
+  T* vx() { return e.lv[0].x; }
+  int launches = 0;
+
+  void tail(cudaStream_t s, unsigned long long cond) {
+    int na = 0;
+    sell_ap(h->A0, h->cp, h->cq, h->part, &na, s);
+    cg_finish(na, h->part, h->st, FIN_PQ, 0, s);
+    cg_update<T>(h->n0, h->st, h->cp, h->cq, h->cx, h->cr, vb(), vx(), h->part, s);
+    cg_finish(h->nparts, h->part, h->st, FIN_RR, cond, s);
+    launches += 4;
+  }
+  void head(cudaStream_t s, unsigned long long cond) {
+    cg_init<T>(h->n0, h->cb, h->cr, h->cx, vb(), vx(), h->part, s);
+    cg_finish(h->nparts, h->part, h->st, FIN_BB, 0, s);
+    e.launches = 0;
+    e.cycle(0, s);
+    cg_dotz<T>(h->n0, h->cr, vx(), h->cz, h->cp, true, h->part, s);
+    cg_finish(h->nparts, h->part, h->st, FIN_RZ0, 0, s);
+    launches += 4 + e.launches;
+    tail(s, cond);
+  }
+  void body(cudaStream_t s, unsigned long long cond) {
+    e.launches = 0;
+    e.cycle(0, s);
+    cg_dotz<T>(h->n0, h->cr, vx(), h->cz, h->cp, false, h->part, s);
+    cg_finish(h->nparts, h->part, h->st, FIN_RZ, 0, s);
+    cg_pupdate(h->n0, h->st, h->cz, h->cp, s);
+    launches = 3 + e.launches;
+    tail(s, cond);
+  }
+};
+
+template <typename F>
+void dispatch(mg_hierarchy* h, F&& f) {
+  if (h->e64) {
+    CgRunner<double> r{h, *h->e64};
+    f(r);
+  } else {
+    CgRunner<float> r{h, *h->e32};
+    f(r);
+  }
+}
+
+void build_graph(mg_hierarchy* h) {
+  cudaStream_t s = h->own_stream;
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle handle;
+  CK(cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault));
+  CK(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  dispatch(h, [&](auto& r) { r.head(s, (unsigned long long)handle); });
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &ndeps));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = handle;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  CK(cudaGraphAddNode(&cnode, g, deps, nullptr, ndeps, &cp));
+  cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
+  CK(cudaStreamUpdateCaptureDependencies(s, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+  CK(cudaStreamEndCapture(s, &g));
+  CK(cudaStreamBeginCaptureToGraph(s, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  dispatch(h, [&](auto& r) { r.body(s, (unsigned long long)handle); });
+  CK(cudaStreamEndCapture(s, &bodyg));
+  CK(cudaGraphInstantiate(&h->graph, g, 0));
+  CK(cudaGraphDestroy(g));
+}
+
+void count_launches(mg_hierarchy* h) {
+  // a dry pass through the schedule on a capture stream counts launches without running
+  dispatch(h, [&](auto& r) {
+    cudaStream_t s = h->own_stream;
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    r.e.launches = 0;
+    r.e.cycle(0, s);
+    h->launches_vcycle = r.e.launches;
+    r.body(s, 0);
+    h->launches_iter = r.launches;
+    CK(cudaStreamEndCapture(s, &g));
+    CK(cudaGraphDestroy(g));
+  });
+}
+
+int run_solve(mg_hierarchy* h, double rtol, int maxit, mg_solve_info_t* info, cudaStream_t s) {
+  if (!(rtol >= 0) || maxit < 1) throw Error(MG_ERR_INVALID_ARG, "rtol must be >= 0 and maxit >= 1");
+  std::memset(h->hst, 0, sizeof(CgState));
+  h->hst->rtol2 = rtol * rtol;
+  h->hst->maxit = maxit;
+  CK(cudaMemcpyAsync(h->st, h->hst, sizeof(CgState), cudaMemcpyHostToDevice, s));
+  if (h->graph) {
+    CK(cudaGraphLaunch(h->graph, s));
+  } else {
+    dispatch(h, [&](auto& r) { r.head(s, 0); });
+    check_launch("cg head");
+    for (;;) {
+      CK(cudaMemcpyAsync(h->hst, h->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (!h->hst->cont) break;
+      dispatch(h, [&](auto& r) { r.body(s, 0); });
+      check_launch("cg body");
+    }
+  }
+  // true residual r = b - A x in FP64
+  sell_resid<double>(h->A0, h->cx, h->cb, h->cq, s);
+  dot_self(h->n0, h->cq, h->part, s);
+  CK(cudaMemcpyAsync(h->hst, h->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CgState st = *h->hst;
+  cg_finish(h->nparts, h->part, h->st, FIN_NORM, 0, s);
+  CK(cudaMemcpyAsync(h->hst, h->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  double true_rr = h->hst->rr;
+  if (info) {
+    info->iterations = st.it;
+    info->converged = st.status == 1 || st.bb == 0.0;
+    info->rel_residual = st.bb > 0 ? std::sqrt(st.rr / st.bb) : 0.0;
+    info->true_rel_residual = st.bb > 0 ? std::sqrt(true_rr / st.bb) : 0.0;
+  }
+  if (st.status == 3) return MG_ERR_BREAKDOWN;
+  if (!(st.status == 1 || st.bb == 0.0)) return MG_ERR_NO_CONVERGENCE;
+  return MG_OK;
+}
+
+}  // namespace
+}  // namespace nnmg
+
+// ---- C ABI ------------------------------------------------------------------------------
+
+#define API_BEGIN try {
+#define API_END_H(h)                     \
+  }                                      \
+  catch (const nnmg::Error& e) {         \
+    if (h) (h)->err = e.what();          \
+    else nnmg::g_setup_error = e.what(); \
+    return e.code;                       \
+  }                                      \
+  catch (const std::bad_alloc&) {        \
+    if (h) (h)->err = "out of host memory"; \
+    else nnmg::g_setup_error = "out of host memory"; \
+    return MG_ERR_OOM;                   \
+  }                                      \
+  catch (const std::exception& e) {      \
+    if (h) (h)->err = e.what();          \
+    else nnmg::g_setup_error = e.what(); \
+    return MG_ERR_INVALID_ARG;           \
+  }
+
+namespace {
+
+mg_hierarchy* checked(mg_hierarchy* h, bool need_device = true) {
+  if (!h) throw Error(MG_ERR_INVALID_ARG, "null hierarchy");
+  if (need_device && !h->device) throw Error(MG_ERR_NO_DEVICE, "hierarchy was built with host_only = 1");
+  return h;
+}
+void check_level(const mg_hierarchy* h, int l, bool below_coarsest = false) {
+  if (l < 0 || l >= h->L || (below_coarsest && l >= h->L - 1))
+    throw Error(MG_ERR_INVALID_ARG, "level index out of range");
+}
+
+template <typename T>
+void load(T* dst, const double* src, int n, cudaStream_t s) {
+  if (!src) throw Error(MG_ERR_INVALID_ARG, "null vector");
+  if (std::is_same<T, double>::value) {
+    if ((const void*)dst != (const void*)src)
+      CK(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  } else {
+    convert<double, float>(n, src, (float*)dst, s);
+  }
+}
+template <typename T>
+void store(double* dst, const T* src, int n, cudaStream_t s) {
+  if (!dst) throw Error(MG_ERR_INVALID_ARG, "null vector");
+  if (std::is_same<T, double>::value) {
+    if ((const void*)dst != (const void*)src)
+      CK(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  } else {
+    convert<float, double>(n, (const float*)src, dst, s);
+  }
+}
+
+void common_setup_tail(mg_hierarchy* h) {
+  finish_setup(h);
+  if (h->device) {
+    CK(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
+    count_launches(h);
+    if (h->opt.use_graph) build_graph(h);
+    CK(cudaDeviceSynchronize());
+  }
+}
+
+}  // namespace
+
+namespace {
+template <typename F>
+int level_step(mg_hierarchy_t* h, int32_t l, const double* b, double* x, void* stream, F&& step) {
+  checked(h);
+  check_level(h, l, true);
+  cudaStream_t s = (cudaStream_t)stream;
+  h->with_engine([&](auto& e) {
+    using T = typename std::remove_pointer<decltype(e.lv[0].b)>::type;
+    auto& L = e.lv[l];
+    load<T>(L.b, b, L.n, s);
+    load<T>(L.x, x, L.n, s);
+    step(e, s);
+    store<T>(x, L.x, L.n, s);
+  });
+  check_launch("level step");
+  return MG_OK;
+}
+}  // namespace
+
+extern "C" {
+
+void mg_default_options(mg_options_t* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->cheb_degree = 2;
+  o->nu = 1;
+  o->patch_layers = 1;
+  o->smoother = MG_SMOOTHER_SANDWICH;
+  o->adjusted_lambda = 1;
+  o->precision = MG_PREC_FP64;
+  o->host_only = 0;
+  o->eig_maxit = 600;
+  o->lmin_ratio = 0.1;
+  o->lmax_safety = 1.0;
+  o->eig_tol = 1e-8;
+  o->lambda_override = nullptr;
+  o->use_graph = 1;
+  o->local_levels_mask = -1;
+  o->quality_threshold = 0.1;
+  o->sell_sigma = 1;
+}
+
+int mg_setup(const mg_mesh_t* levels, int32_t L, int32_t degree, double quality_threshold, const mg_options_t* opt,
+             mg_hierarchy_t** out) {
+  mg_hierarchy* h = nullptr;
+  API_BEGIN
+  nnmg::g_setup_error.clear();
+  if (!out) throw Error(MG_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!levels || L < 2 || L > 32) throw Error(MG_ERR_INVALID_ARG, "need 2 <= L <= 32 mesh levels");
+  if (degree != 1 && degree != 2) throw Error(MG_ERR_INVALID_ARG, "degree must be 1 or 2");
+  std::unique_ptr<mg_hierarchy> H(new mg_hierarchy());
+  if (opt) H->opt = *opt;
+  else mg_default_options(&H->opt);
+  H->opt.quality_threshold = quality_threshold;
+  validate_options(H->opt);
+  H->L = L;
+  H->degree = degree;
+  H->geometric = true;
+  std::vector<MeshH> meshes(L);
+  std::vector<DofMapH> dms(L);
+  H->host.resize(L);
+  PhaseTimer tm;
+  for (int l = 0; l < L; ++l) {
+    const mg_mesh_t& m = levels[l];
+    if ((m.dim != 2 && m.dim != 3) || m.nv < m.dim + 1 || m.nc < 1 || !m.coords || !m.cells)
+      throw Error(MG_ERR_INVALID_ARG, "invalid mesh at level " + std::to_string(l));
+    if (m.dim != levels[0].dim) throw Error(MG_ERR_INVALID_ARG, "all levels must have the same dimension");
+    MeshH& M = meshes[l];
+    M.dim = m.dim;
+    M.nv = m.nv;
+    M.nc = m.nc;
+    M.x.assign(m.coords, m.coords + m.nv * m.dim);
+    M.c.assign(m.cells, m.cells + m.nc * (m.dim + 1));
+    for (int32_t v : M.c)
+      if (v < 0 || v >= m.nv) throw Error(MG_ERR_INVALID_ARG, "cell vertex index out of range at level " + std::to_string(l));
+    if (m.dirichlet_vertex_mask) M.mask.assign(m.dirichlet_vertex_mask, m.dirichlet_vertex_mask + m.nv);
+    dms[l] = build_dofmap(M, degree);
+    LevelH& lv = H->host[l];
+    lv.dim = m.dim;
+    lv.gamma = radius_ratio(M);
+    for (int64_t c = 0; c < M.nc; ++c)
+      if (!(lv.gamma[c] > 0)) throw Error(MG_ERR_DEGENERATE_CELL, "level " + std::to_string(l) + ": cell " + std::to_string(c) + " is degenerate");
+    lv.dof_points.resize(dms[l].nfree * m.dim);
+    for (int64_t i = 0; i < dms[l].nfree; ++i)
+      for (int r = 0; r < m.dim; ++r) lv.dof_points[i * m.dim + r] = dms[l].points[dms[l].free_list[i] * m.dim + r];
+    if ((H->opt.local_levels_mask >> std::min(l, 31)) & 1)
+      local_patches(M, dms[l], lv.gamma, quality_threshold, H->opt.patch_layers, lv.patch_ptr, lv.patch_dofs);
+    else
+      lv.patch_ptr.assign(1, 0);
+    H->ncells.push_back(M.nc);
+    tm.mark("dofmap/gamma/patches L" + std::to_string(l));
+  }
+  H->host[0].A = assemble_stiffness(meshes[0], dms[0]);
+  H->fine_load_unit = load_constant(meshes[0], dms[0], 1.0);
+  tm.mark("assembly L0");
+  for (int l = 1; l < L; ++l) {
+    LevelH& f = H->host[l - 1];
+    f.P = prolongation(dms[l - 1], meshes[l], dms[l]);
+    f.R = transpose(f.P);
+    Csr AP = spgemm(f.A, f.P);
+    H->host[l].A = unit_diagonal_on_empty_rows(spgemm(f.R, AP));
+    tm.mark("transfer+galerkin L" + std::to_string(l));
+  }
+  meshes.clear();
+  dms.clear();
+  common_setup_tail(H.get());
+  *out = H.release();
+  return MG_OK;
+  API_END_H(h)
+}
+
+int mg_setup_csr(const mg_csr_t* A, const mg_csr_t* P, int32_t L, const int32_t* const* patch_ptr,
+                 const int32_t* const* patch_dofs, const int32_t* num_patches, const mg_options_t* opt,
+                 mg_hierarchy_t** out) {
+  mg_hierarchy* h = nullptr;
+  API_BEGIN
+  nnmg::g_setup_error.clear();
+  if (!out) throw Error(MG_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!A || !P || L < 2 || L > 32) throw Error(MG_ERR_INVALID_ARG, "need 2 <= L <= 32 levels and A, P arrays");
+  std::unique_ptr<mg_hierarchy> H(new mg_hierarchy());
+  if (opt) H->opt = *opt;
+  else mg_default_options(&H->opt);
+  validate_options(H->opt);
+  if (!H->opt.lambda_override) throw Error(MG_ERR_INVALID_ARG, "mg_setup_csr needs opt->lambda_override");
+  H->L = L;
+  H->host.resize(L);
+  auto copy_csr = [](const mg_csr_t& c, Csr& d) {
+    if (c.nrows < 1 || c.ncols < 1 || !c.rowptr || c.nrows >= INT32_MAX || c.ncols >= INT32_MAX)
+      throw Error(MG_ERR_INVALID_ARG, "invalid CSR matrix");
+    d.nrows = c.nrows;
+    d.ncols = c.ncols;
+    d.rp.assign(c.rowptr, c.rowptr + c.nrows + 1);
+    int64_t nnz = d.rp[c.nrows];
+    if (d.rp[0] != 0 || nnz < 0) throw Error(MG_ERR_INVALID_ARG, "invalid CSR row pointer");
+    for (int64_t i = 0; i < c.nrows; ++i)
+      if (d.rp[i + 1] < d.rp[i]) throw Error(MG_ERR_INVALID_ARG, "CSR row pointer not monotone");
+    if (nnz > 0 && (!c.colidx || !c.values)) throw Error(MG_ERR_INVALID_ARG, "null CSR arrays");
+    d.ci.assign(c.colidx, c.colidx + nnz);
+    d.v.assign(c.values, c.values + nnz);
+    for (int32_t j : d.ci)
+      if (j < 0 || j >= c.ncols) throw Error(MG_ERR_INVALID_ARG, "CSR column index out of range");
+  };
+  for (int l = 0; l < L; ++l) {
+    copy_csr(A[l], H->host[l].A);
+    if (A[l].nrows != A[l].ncols) throw Error(MG_ERR_INVALID_ARG, "A must be square");
+    LevelH& lv = H->host[l];
+    lv.patch_ptr.assign(1, 0);
+    if (patch_ptr && patch_dofs && num_patches && patch_ptr[l] && num_patches[l] > 0) {
+      int np = num_patches[l];
+      lv.patch_ptr.assign(patch_ptr[l], patch_ptr[l] + np + 1);
+      lv.patch_dofs.assign(patch_dofs[l], patch_dofs[l] + lv.patch_ptr[np]);
+      std::vector<uint8_t> seen(A[l].nrows, 0);
+      for (int32_t f : lv.patch_dofs) {
+        if (f < 0 || f >= A[l].nrows || seen[f]) throw Error(MG_ERR_INVALID_ARG, "patch DoFs out of range or not disjoint");
+        seen[f] = 1;
+      }
+    }
+  }
+  for (int l = 0; l + 1 < L; ++l) {
+    copy_csr(P[l], H->host[l].P);
+    if (P[l].nrows != A[l].nrows || P[l].ncols != A[l + 1].nrows) throw Error(MG_ERR_INVALID_ARG, "P shape mismatch");
+    H->host[l].R = transpose(H->host[l].P);
+  }
+  common_setup_tail(H.get());
+  *out = H.release();
+  return MG_OK;
+  API_END_H(h)
+}
+
+void mg_free(mg_hierarchy_t* h) { delete h; }
+
+const char* mg_last_error(const mg_hierarchy_t* h) { return h ? h->err.c_str() : nnmg::g_setup_error.c_str(); }
+
+int32_t mg_num_levels(const mg_hierarchy_t* h) { return h ? h->L : 0; }
+
+int64_t mg_num_dofs(const mg_hierarchy_t* h, int32_t l) {
+  if (!h || l < 0 || l >= h->L) return -1;
+  return h->host[l].A.nrows;
+}
+int64_t mg_level_nnz(const mg_hierarchy_t* h, int32_t l) {
+  if (!h || l < 0 || l >= h->L) return -1;
+  return h->host[l].A.nnz();
+}
+int64_t mg_transfer_nnz(const mg_hierarchy_t* h, int32_t l) {
+  if (!h || l < 0 || l >= h->L - 1) return -1;
+  return h->host[l].P.nnz();
+}
+
+int mg_num_patches(const mg_hierarchy_t* hc, int32_t l, int32_t* num, int64_t* total) {
+  mg_hierarchy* h = const_cast<mg_hierarchy*>(hc);
+  API_BEGIN
+  checked(h, false);
+  check_level(h, l);
+  if (num) *num = (int32_t)h->host[l].patch_ptr.size() - 1;
+  if (total) *total = (int64_t)h->host[l].patch_dofs.size();
+  return MG_OK;
+  API_END_H(h)
+}
+
+int mg_export_level(const mg_hierarchy_t* hc, int32_t l, int32_t* rowptr, int32_t* colidx, double* values) {
+  mg_hierarchy* h = const_cast<mg_hierarchy*>(hc);
+  API_BEGIN
+  checked(h, false);
+  check_level(h, l);
+  const Csr& A = h->host[l].A;
+  if (rowptr) std::copy(A.rp.begin(), A.rp.end(), rowptr);
+  if (colidx) std::copy(A.ci.begin(), A.ci.end(), colidx);
+  if (values) std::copy(A.v.begin(), A.v.end(), values);
+  return MG_OK;
+  API_END_H(h)
+}
+
+int mg_export_transfer(const mg_hierarchy_t* hc, int32_t l, int32_t* rowptr, int32_t* colidx, double* values) {
+  mg_hierarchy* h = const_cast<mg_hierarchy*>(hc);
+  API_BEGIN
+  checked(h, false);
+  check_level(h, l, true);
+  const Csr& P = h->host[l].P;
+  if (rowptr) std::copy(P.rp.begin(), P.rp.end(), rowptr);
+  if (colidx) std::copy(P.ci.begin(), P.ci.end(), colidx);
+  if (values) std::copy(P.v.begin(), P.v.end(), values);
+  return MG_OK;
+  API_END_H(h)
+}
+
+int mg_export_patches(const mg_hierarchy_t* hc, int32_t l, int32_t* ptr, int32_t* dofs) {
+  mg_hierarchy* h = const_cast<mg_hierarchy*>(hc);
+  API_BEGIN
+  checked(h, false);
+  check_level(h, l);
+  const LevelH& lv = h->host[l];
+  if (ptr) std::copy(lv.patch_ptr.begin(), lv.patch_ptr.end(), ptr);
+  if (dofs) std::copy(lv.patch_dofs.begin(), lv.patch_dofs.end(), dofs);
+  return MG_OK;
+  API_END_H(h)
+}
+
+int mg_eigs(const mg_hierarchy_t* hc, int32_t l, double* lmax, double* lmax_adj, double* lmax_used) {
+  mg_hierarchy* h = const_cast<mg_hierarchy*>(hc);
+  API_BEGIN
+  checked(h, false);
+  check_level(h, l, true);
+  const LevelH& lv = h->host[l];
+  if (lmax) *lmax = lv.lmax_unadj;
+  if (lmax_adj) *lmax_adj = lv.lmax_adj;
+  if (lmax_used) *lmax_used = lv.lmax;
+  return MG_OK;
+  API_END_H(h)
+}
+
+int mg_dof_coords(const mg_hierarchy_t* hc, int32_t l, double* out) {
+  mg_hierarchy* h = const_cast<mg_hierarchy*>(hc);
+  API_BEGIN
+  checked(h, false);
+  check_level(h, l);
+  if (!h->geometric) throw Error(MG_ERR_INVALID_ARG, "not a geometric hierarchy");
+  if (!out) throw Error(MG_ERR_INVALID_ARG, "null output");
+  std::copy(h->host[l].dof_points.begin(), h->host[l].dof_points.end(), out);
+  return MG_OK;
+  API_END_H(h)
+}
+
+int mg_cell_quality(const mg_hierarchy_t* hc, int32_t l, double* out) {
+  mg_hierarchy* h = const_cast<mg_hierarchy*>(hc);
+  API_BEGIN
+  checked(h, false);
+  check_level(h, l);
+  if (!h->geometric) throw Error(MG_ERR_INVALID_ARG, "not a geometric hierarchy");
+  if (!out) throw Error(MG_ERR_INVALID_ARG, "null output");
+  std::copy(h->host[l].gamma.begin(), h->host[l].gamma.end(), out);
+  return MG_OK;
+  API_END_H(h)
+}
+
+int mg_load_constant(const mg_hierarchy_t* hc, double f, double* out) {
+  mg_hierarchy* h = const_cast<mg_hierarchy*>(hc);
+  API_BEGIN
+  checked(h, false);
+  if (!h->geometric) throw Error(MG_ERR_INVALID_ARG, "not a geometric hierarchy");
+  if (!out) throw Error(MG_ERR_INVALID_ARG, "null output");
+  for (size_t i = 0; i < h->fine_load_unit.size(); ++i) out[i] = f * h->fine_load_unit[i];
+  return MG_OK;
+  API_END_H(h)
+}
+
+int mg_vcycle(mg_hierarchy_t* h, const double* b, double* x, void* stream) {
+  API_BEGIN
+  checked(h);
+  if (!b || !x) throw Error(MG_ERR_INVALID_ARG, "null vector");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = h->n0;
+  // x += V(b - A x): r into the CG residual buffer, the cycle from a zero guess
+  sell_resid<double>(h->A0, x, b, h->cr, s);
+  h->with_engine([&](auto& e) {
+    using T = typename std::remove_pointer<decltype(e.lv[0].b)>::type;
+    load<T>(e.lv[0].b, h->cr, n, s);
+    CK(cudaMemsetAsync(e.lv[0].x, 0, sizeof(T) * n, s));
+    e.cycle(0, s);
+    axpy_from<T>(n, e.lv[0].x, x, s);
+  });
+  check_launch("mg_vcycle");
+  return MG_OK;
+  API_END_H(h)
+}
+
+int mg_solve(mg_hierarchy_t* h, const double* b, double* x, double rtol, int32_t maxit, mg_solve_info_t* info,
+             void* stream) {
+  API_BEGIN
+  checked(h);
+  if (!b || !x) throw Error(MG_ERR_INVALID_ARG, "null vector");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(h->cb, b, sizeof(double) * h->n0, cudaMemcpyDeviceToDevice, s));
+  int rc = run_solve(h, rtol, maxit, info, s);
+  CK(cudaMemcpyAsync(x, h->cx, sizeof(double) * h->n0, cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  if (rc != MG_OK) h->err = rc == MG_ERR_BREAKDOWN ? "CG breakdown" : "no convergence within maxit";
+  return rc;
+  API_END_H(h)
+}
+
+int mg_solve_host(mg_hierarchy_t* h, const double* b, double* x, double rtol, int32_t maxit, mg_solve_info_t* info,
+                  void* stream) {
+  API_BEGIN
+  checked(h);
+  if (!b || !x) throw Error(MG_ERR_INVALID_ARG, "null vector");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(h->cb, b, sizeof(double) * h->n0, cudaMemcpyHostToDevice, s));
+  int rc = run_solve(h, rtol, maxit, info, s);
+  CK(cudaMemcpyAsync(x, h->cx, sizeof(double) * h->n0, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (rc != MG_OK) h->err = rc == MG_ERR_BREAKDOWN ? "CG breakdown" : "no convergence within maxit";
+  return rc;
+  API_END_H(h)
+}
+
+int mg_solve_stationary(mg_hierarchy_t* h, const double* b, double* x, double rtol, int32_t maxit,
+                        mg_solve_info_t* info, void* stream) {
+  API_BEGIN
+  checked(h);
+  if (!b || !x) throw Error(MG_ERR_INVALID_ARG, "null vector");
+  if (!(rtol >= 0) || maxit < 1) throw Error(MG_ERR_INVALID_ARG, "rtol must be >= 0 and maxit >= 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  auto norm2 = [&](const double* v) {
+    dot_self(h->n0, v, h->part, s);
+    cg_finish(h->nparts, h->part, h->st, FIN_NORM, 0, s);
+    CK(cudaMemcpyAsync(h->hst, h->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return h->hst->rr;
+  };
+  double bb = norm2(b);
+  int it = 0;
+  double rr = 0;
+  for (;;) {
+    sell_resid<double>(h->A0, x, b, h->cq, s);
+    rr = norm2(h->cq);
+    if (bb == 0.0 || rr <= rtol * rtol * bb || it >= maxit) break;
+    int rc = mg_vcycle(h, b, x, stream);
+    if (rc != MG_OK) return rc;
+    ++it;
+  }
+  bool conv = bb == 0.0 || rr <= rtol * rtol * bb;
+  if (info) {
+    info->iterations = it;
+    info->converged = conv;
+    info->rel_residual = bb > 0 ? std::sqrt(rr / bb) : 0.0;
+    info->true_rel_residual = info->rel_residual;
+  }
+  return conv ? MG_OK : MG_ERR_NO_CONVERGENCE;
+  API_END_H(h)
+}
+
+int mg_solve_batch(mg_hierarchy_t* const* hs, const double* const* b, double* const* x, int32_t n, double rtol,
+                   int32_t maxit, mg_solve_info_t* info, void* stream) {
+  mg_hierarchy* h = nullptr;
+  API_BEGIN
+  if (n < 0 || (n > 0 && (!hs || !b || !x))) throw Error(MG_ERR_INVALID_ARG, "invalid batch arrays");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t start;
+  CK(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+  CK(cudaEventRecord(start, s));
+  // enqueue every problem on its own stream (graph launches overlap on the device)
+  for (int i = 0; i < n; ++i) {
+    mg_hierarchy* hi = checked(hs[i]);
+    CK(cudaStreamWaitEvent(hi->own_stream, start, 0));
+    std::memset(hi->hst, 0, sizeof(CgState));
+    hi->hst->rtol2 = rtol * rtol;
+    hi->hst->maxit = maxit;
+    CK(cudaMemcpyAsync(hi->cb, b[i], sizeof(double) * hi->n0, cudaMemcpyDeviceToDevice, hi->own_stream));
+    CK(cudaMemcpyAsync(hi->st, hi->hst, sizeof(CgState), cudaMemcpyHostToDevice, hi->own_stream));
+    if (!hi->graph) throw Error(MG_ERR_INVALID_ARG, "mg_solve_batch needs hierarchies built with use_graph = 1");
+    CK(cudaGraphLaunch(hi->graph, hi->own_stream));
+    CK(cudaMemcpyAsync(x[i], hi->cx, sizeof(double) * hi->n0, cudaMemcpyDeviceToDevice, hi->own_stream));
+  }
+  int rc_all = MG_OK;
+  for (int i = 0; i < n; ++i) {
+    mg_hierarchy* hi = hs[i];
+    CK(cudaMemcpyAsync(hi->hst, hi->st, sizeof(CgState), cudaMemcpyDeviceToHost, hi->own_stream));
+    CK(cudaStreamSynchronize(hi->own_stream));
+    CgState st = *hi->hst;
+    if (info) {
+      info[i].iterations = st.it;
+      info[i].converged = st.status == 1 || st.bb == 0.0;
+      info[i].rel_residual = st.bb > 0 ? std::sqrt(st.rr / st.bb) : 0.0;
+      info[i].true_rel_residual = -1.0;  // not recomputed in batch mode
+    }
+    int rc = st.status == 3 ? MG_ERR_BREAKDOWN : ((st.status == 1 || st.bb == 0.0) ? MG_OK : MG_ERR_NO_CONVERGENCE);
+    if (rc_all == MG_OK) rc_all = rc;
+  }
+  cudaEventDestroy(start);
+  return rc_all;
+  API_END_H(h)
+}
+
+int mg_apply_A(mg_hierarchy_t* h, int32_t l, const double* x, double* y, void* stream) {
+  API_BEGIN
+  checked(h);
+  check_level(h, l);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!x || !y) throw Error(MG_ERR_INVALID_ARG, "null vector");
+  if (l == 0) {
+    sell_spmv<double>(h->A0, x, y, s);
+  } else {
+    h->with_engine([&](auto& e) {
+      using T = typename std::remove_pointer<decltype(e.lv[0].b)>::type;
+      auto& L = e.lv[l];
+      load<T>(L.x, x, L.n, s);
+      sell_spmv<T>(L.A, L.x, L.b, s);
+      store<T>(y, L.b, L.n, s);
+    });
+  }
+  check_launch("mg_apply_A");
+  return MG_OK;
+  API_END_H(h)
+}
+
+
+int mg_chebyshev(mg_hierarchy_t* h, int32_t l, const double* b, double* x, void* stream) {
+  API_BEGIN
+  return level_step(h, l, b, x, stream, [&](auto& e, cudaStream_t s) { e.cheb(l, s); });
+  API_END_H(h)
+}
+
+int mg_local_correction(mg_hierarchy_t* h, int32_t l, const double* b, double* x, void* stream) {
+  API_BEGIN
+  return level_step(h, l, b, x, stream, [&](auto& e, cudaStream_t s) {
+    if (e.lv[l].np > 0) e.local(l, s);
+  });
+  API_END_H(h)
+}
+
+int mg_smooth(mg_hierarchy_t* h, int32_t l, int32_t post, const double* b, double* x, void* stream) {
+  API_BEGIN
+  return level_step(h, l, b, x, stream, [&](auto& e, cudaStream_t s) { e.smooth(l, post != 0, s); });
+  API_END_H(h)
+}
+
+int mg_residual_restrict(mg_hierarchy_t* h, int32_t l, const double* b, const double* x, double* r, double* bc,
+                         void* stream) {
+  API_BEGIN
+  checked(h);
+  check_level(h, l, true);
+  if (!b || !x || !r || !bc) throw Error(MG_ERR_INVALID_ARG, "null vector");
+  cudaStream_t s = (cudaStream_t)stream;
+  h->with_engine([&](auto& e) {
+    using T = typename std::remove_pointer<decltype(e.lv[0].b)>::type;
+    auto& L = e.lv[l];
+    auto& C = e.lv[l + 1];
+    load<T>(L.b, b, L.n, s);
+    load<T>(L.x, x, L.n, s);
+    e.residual_restrict(l, s);
+    store<T>(r, L.res, L.n, s);
+    store<T>(bc, C.b, C.n, s);
+  });
+  check_launch("mg_residual_restrict");
+  return MG_OK;
+  API_END_H(h)
+}
+
+int mg_prolong_correct(mg_hierarchy_t* h, int32_t l, const double* xc, double* x, void* stream) {
+  API_BEGIN
+  checked(h);
+  check_level(h, l, true);
+  if (!xc || !x) throw Error(MG_ERR_INVALID_ARG, "null vector");
+  cudaStream_t s = (cudaStream_t)stream;
+  h->with_engine([&](auto& e) {
+    using T = typename std::remove_pointer<decltype(e.lv[0].b)>::type;
+    auto& L = e.lv[l];
+    auto& C = e.lv[l + 1];
+    load<T>(C.x, xc, C.n, s);
+    load<T>(L.x, x, L.n, s);
+    e.prolong(l, s);
+    store<T>(x, L.x, L.n, s);
+  });
+  check_launch("mg_prolong_correct");
+  return MG_OK;
+  API_END_H(h)
+}
+
+int mg_coarse_solve(mg_hierarchy_t* h, const double* b, double* x, void* stream) {
+  API_BEGIN
+  checked(h);
+  if (!b || !x) throw Error(MG_ERR_INVALID_ARG, "null vector");
+  cudaStream_t s = (cudaStream_t)stream;
+  h->with_engine([&](auto& e) {
+    using T = typename std::remove_pointer<decltype(e.lv[0].b)>::type;
+    auto& C = e.lv.back();
+    load<T>(C.b, b, C.n, s);
+    e.coarse(s);
+    store<T>(x, C.x, C.n, s);
+  });
+  check_launch("mg_coarse_solve");
+  return MG_OK;
+  API_END_H(h)
+}
+
+int mg_time_smoother_kernel(mg_hierarchy_t* h, int32_t reps, void* stream, double* ms, double* bytes) {
+  API_BEGIN
+  checked(h);
+  if (reps < 1) throw Error(MG_ERR_INVALID_ARG, "reps must be >= 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  double nbytes = 0;
+  h->with_engine([&](auto& e) {
+    using T = typename std::remove_pointer<decltype(e.lv[0].b)>::type;
+    auto& L = e.lv[0];
+    double cd = L.cd.size() > 1 ? L.cd[1] : 0.0, cr = L.cr.size() > 1 ? L.cr[1] : L.cr[0];
+    sell_cheb<T>(L.A, L.x, L.b, L.dinv, L.d, L.xt, cd, cr, false, s);  // warm-up
+    CK(cudaEventRecord(e0, s));
+    for (int i = 0; i < reps; ++i) sell_cheb<T>(L.A, L.x, L.b, L.dinv, L.d, L.xt, cd, cr, false, s);
+    CK(cudaEventRecord(e1, s));
+    const double sz = sizeof(T);
+    nbytes = (double)L.A.nnz * (sz + 4.0) + (double)L.n * 6.0 * sz + 8.0 * (L.A.nslices + 1);
+  });
+  check_launch("mg_time_smoother_kernel");
+  CK(cudaEventSynchronize(e1));
+  float t = 0;
+  CK(cudaEventElapsedTime(&t, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (ms) *ms = (double)t / reps;
+  if (bytes) *bytes = nbytes;
+  return MG_OK;
+  API_END_H(h)
+}
+
+int64_t mg_device_bytes(const mg_hierarchy_t* h) { return h ? h->mem.bytes : 0; }
+
+int mg_launch_counts(const mg_hierarchy_t* h, int32_t* per_vcycle, int32_t* per_iter) {
+  if (!h) return MG_ERR_INVALID_ARG;
+  if (per_vcycle) *per_vcycle = h->launches_vcycle;
+  if (per_iter) *per_iter = h->launches_iter;
+  return MG_OK;
+}
+
+}  // extern "C"

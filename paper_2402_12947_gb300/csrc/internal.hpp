@@ -1,0 +1,82 @@
+// Internal host-side data structures and set-up routines of the nnmg library.
+#pragma once
+
+#include <cstdint>
+#include <functional>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "nnmg.h"
+
+namespace nnmg {
+
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+// Compressed sparse rows with 32-bit indices (row pointers fit: nnz < 2^31).
+struct Csr {
+  int64_t nrows = 0, ncols = 0;
+  std::vector<int32_t> rp, ci;
+  std::vector<double> v;
+  int64_t nnz() const { return (int64_t)ci.size(); }
+};
+
+struct MeshH {
+  int dim = 0;
+  int64_t nv = 0, nc = 0;
+  std::vector<double> x;        // [nv*dim]
+  std::vector<int32_t> c;       // [nc*(dim+1)]
+  std::vector<uint8_t> mask;    // [nv] Dirichlet-allowed vertices (empty = all)
+};
+
+struct DofMapH {
+  int degree = 1, dim = 2, nloc = 3;
+  int64_t ndofs = 0, nfree = 0, nv = 0;
+  std::vector<int64_t> cell_dofs;   // [nc*nloc] all-DoF ids
+  std::vector<int64_t> edges;       // [ne*2] sorted vertex pairs (P2)
+  std::vector<double> points;       // [ndofs*dim]
+  std::vector<uint8_t> dirichlet;   // [ndofs]
+  std::vector<int64_t> free_index;  // [ndofs] free id or -1
+  std::vector<int64_t> free_list;   // [nfree] all-DoF id of each free DoF
+};
+
+// One level of the hierarchy as built on the host.
+struct LevelH {
+  Csr A;                     // free-DoF operator (assembled on level 0, Galerkin below)
+  Csr P, R;                  // P: level l+1 -> l (rows n_l); R = P^T (empty on the coarsest)
+  std::vector<double> dinv;  // 1 / diag(A)
+  std::vector<int32_t> patch_ptr, patch_dofs;
+  double lmax_unadj = 0, lmax_adj = 0, lmax = 0, lmin = 0;
+  int lanczos_iters = 0;
+  int dim = 0;
+  std::vector<double> dof_points;   // [n*dim] (geometric hierarchies)
+  std::vector<double> gamma;        // [nc]    (geometric hierarchies)
+};
+
+// ---- threading helper ----
+int num_threads();
+void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& body);
+
+// ---- setup_fem.cpp: DoF maps, assembly, quality, patches ----
+DofMapH build_dofmap(const MeshH& m, int degree);
+std::vector<double> radius_ratio(const MeshH& m);
+Csr assemble_stiffness(const MeshH& m, const DofMapH& dm);
+std::vector<double> load_constant(const MeshH& m, const DofMapH& dm, double f);
+void local_patches(const MeshH& m, const DofMapH& dm, const std::vector<double>& gamma,
+                   double threshold, int layers, std::vector<int32_t>& ptr, std::vector<int32_t>& dofs);
+
+// ---- setup_algebra.cpp: transfer, sparse products, dense factorisations, eigenvalues ----
+Csr prolongation(const DofMapH& fine, const MeshH& coarse_mesh, const DofMapH& coarse);
+Csr transpose(const Csr& A);
+// Coarse DoFs that P never reaches have empty rows in P^T A P: give them A_ii = 1.
+Csr unit_diagonal_on_empty_rows(const Csr& A);
+Csr spgemm(const Csr& A, const Csr& B);
+// lambda_max of D^{-1/2} A D^{-1/2} restricted to rows/cols with keep[i] != 0 (NULL: all).
+double lanczos_lmax(const Csr& A, const uint8_t* keep, double tol, int maxit, int* iters);
+std::vector<double> dense_submatrix(const Csr& A, const int32_t* idx, int64_t n);
+void spmv_host(const Csr& A, const double* x, double* y);
+
+}  // namespace nnmg

@@ -1,0 +1,539 @@
+// Device kernels of the nnmg hot path (sm_103a). See kernels.cuh for the data layout.
+//
+// Kernels and the steps they implement (Chen & Wells, arXiv:2402.12947):
+//   sell_cheb      Chebyshev-Jacobi step of S_g (Sec. 3.2, Sec. 5): SpMV fused with the
+//                  residual, the Jacobi scaling and the three-term update
+//   sell_resid +   residual and restriction b_{l+1} = P_l^T (b_l - A_l u_l) (Eq. 4),
+//   sell_restrict  R = P^T stored explicitly so that both are row-wise gathers
+//   sell_prolong   coarse-grid correction u_l += P_l u_{l+1} (Alg. 1)
+//   patch_*        local correction S_c (Sec. 4.1, Alg. 2): patch residual, then the dense
+//                  FP64 solve with (A^[d])^{-1} and the scatter back
+//   dense_solve    direct solve on the coarsest level (Alg. 1)
+//   cg_*           CG preconditioned by one V-cycle (Sec. 6.2), deterministic reductions
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+#include <type_traits>
+
+#include "internal.hpp"
+#include "kernels.cuh"
+
+namespace nnmg {
+
+void check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw Error(MG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+namespace {
+
+// Streaming loads for matrix data (read once per pass; keep the vectors in L2).
+__device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
+__device__ __forceinline__ int32_t ld_stream(const int32_t* p) { return __ldcs(p); }
+
+template <typename T>
+__device__ __forceinline__ T sell_row(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                                      const T* __restrict__ val, const T* __restrict__ x, int row) {
+  const int s = row >> 5, lane = row & 31;
+  const int64_t o = off[s];
+  const int w = (int)((off[s + 1] - o) >> 5);
+  const T* vp = val + o + lane;
+  const int32_t* cp = col + o + lane;
+  T acc = T(0);
+  int j = 0;
+  for (; j + 4 <= w; j += 4) {
+    const T v0 = ld_stream(vp), v1 = ld_stream(vp + 32), v2 = ld_stream(vp + 64), v3 = ld_stream(vp + 96);
+    const int32_t c0 = ld_stream(cp), c1 = ld_stream(cp + 32), c2 = ld_stream(cp + 64), c3 = ld_stream(cp + 96);
+    const T x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2), x3 = __ldg(x + c3);
+    acc = fma(v0, x0, acc);
+    acc = fma(v1, x1, acc);
+    acc = fma(v2, x2, acc);
+    acc = fma(v3, x3, acc);
+    vp += 128;
+    cp += 128;
+  }
+  for (; j < w; ++j) {
+    acc = fma(ld_stream(vp), __ldg(x + ld_stream(cp)), acc);
+    vp += 32;
+    cp += 32;
+  }
+  return acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_sell_spmv(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                                                      const T* __restrict__ val, int nrows, const T* __restrict__ x,
+                                                      T* __restrict__ y) {
+  const int row = blockIdx.x * kBlock + threadIdx.x;
+  if (row >= nrows) return;
+  y[row] = sell_row(off, col, val, x, row);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_sell_resid(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                                                       const T* __restrict__ val, int nrows, const T* __restrict__ x,
+                                                       const T* __restrict__ b, T* __restrict__ r) {
+  const int row = blockIdx.x * kBlock + threadIdx.x;
+  if (row >= nrows) return;
+  r[row] = b[row] - sell_row(off, col, val, x, row);
+}
+
+template <typename T, bool FIRST>
+__global__ void __launch_bounds__(kBlock) k_sell_cheb(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                                                      const T* __restrict__ val, int nrows, const T* __restrict__ xin,
+                                                      const T* __restrict__ b, const T* __restrict__ dinv,
+                                                      T* __restrict__ d, T* __restrict__ xout, T cd, T cr) {
+  const int row = blockIdx.x * kBlock + threadIdx.x;
+  if (row >= nrows) return;
+  const T ax = sell_row(off, col, val, xin, row);
+  const T r = b[row] - ax;
+  const T t = dinv[row] * r;
+  const T dn = FIRST ? cr * t : fma(cd, d[row], cr * t);
+  d[row] = dn;
+  xout[row] = xin[row] + dn;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_sell_prolong(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                                                         const T* __restrict__ val, int nrows, const T* __restrict__ xc,
+                                                         T* __restrict__ x) {
+  const int row = blockIdx.x * kBlock + threadIdx.x;
+  if (row >= nrows) return;
+  x[row] = x[row] + sell_row(off, col, val, xc, row);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_sell_restrict(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                                                          const T* __restrict__ val, int nrows, const T* __restrict__ r,
+                                                          T* __restrict__ bc, T* __restrict__ xc) {
+  const int row = blockIdx.x * kBlock + threadIdx.x;
+  if (row >= nrows) return;
+  bc[row] = sell_row(off, col, val, r, row);
+  xc[row] = T(0);
+}
+
+// Block-wide sum in a fixed order (warp shuffles, then the warps' sums by warp 0).
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double ws[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) ws[w] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  double t = 0.0;
+  if (w == 0) {
+    t = l < nw ? ws[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  }
+  return t;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kBlock) k_sell_ap(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                                                    const double* __restrict__ val, int nrows,
+                                                    const double* __restrict__ p, double* __restrict__ q,
+                                                    double* __restrict__ part) {
+  const int row = blockIdx.x * kBlock + threadIdx.x;
+  double v = 0.0;
+  if (row < nrows) {
+    const double ap = sell_row(off, col, val, p, row);
+    q[row] = ap;
+    v = p[row] * ap;
+  }
+  v = block_sum(v);
+  if (threadIdx.x == 0) part[blockIdx.x] = v;
+}
+
+template <typename T>
+__global__ void k_patch_residual(int nt, const int32_t* __restrict__ pdofs, const int32_t* __restrict__ prp,
+                                 const int32_t* __restrict__ pci, const double* __restrict__ pv,
+                                 const T* __restrict__ b, const T* __restrict__ x, double* __restrict__ rbuf) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  double s = 0.0;
+  for (int k = prp[t]; k < prp[t + 1]; ++k) s = fma(pv[k], (double)x[pci[k]], s);
+  rbuf[t] = (double)b[pdofs[t]] - s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_patch_solve(const PatchItem* __restrict__ items,
+                                                        const int32_t* __restrict__ pptr,
+                                                        const int32_t* __restrict__ pdofs,
+                                                        const int64_t* __restrict__ inv_off,
+                                                        const double* __restrict__ inv,
+                                                        const double* __restrict__ rbuf, T* __restrict__ x) {
+  extern __shared__ double rs[];
+  const PatchItem it = items[blockIdx.x];
+  const int p0 = pptr[it.patch], n = pptr[it.patch + 1] - p0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) rs[j] = rbuf[p0 + j];
+  __syncthreads();
+  const int i = it.row0 + threadIdx.x;
+  if (i >= n) return;
+  // X is symmetric: row i is read as column i, coalesced across the block's threads
+  const double* X = inv + inv_off[it.patch] + i;
+  double e = 0.0;
+  int j = 0;
+  for (; j + 4 <= n; j += 4) {
+    e = fma(X[(int64_t)j * n], rs[j], e);
+    e = fma(X[(int64_t)(j + 1) * n], rs[j + 1], e);
+    e = fma(X[(int64_t)(j + 2) * n], rs[j + 2], e);
+    e = fma(X[(int64_t)(j + 3) * n], rs[j + 3], e);
+  }
+  for (; j < n; ++j) e = fma(X[(int64_t)j * n], rs[j], e);
+  const int g = pdofs[p0 + i];
+  x[g] = (T)((double)x[g] + e);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_dense_partial(int n, int kchunk, const double* __restrict__ X,
+                                                          const T* __restrict__ b, double* __restrict__ part) {
+  extern __shared__ double bs[];
+  const int k0 = blockIdx.y * kchunk, k1 = min(n, k0 + kchunk);
+  for (int j = k0 + threadIdx.x; j < k1; j += blockDim.x) bs[j - k0] = (double)b[j];
+  __syncthreads();
+  const int i = blockIdx.x * kBlock + threadIdx.x;
+  if (i >= n) return;
+  const double* Xi = X + i;
+  double s = 0.0;
+  for (int j = k0; j < k1; ++j) s = fma(Xi[(int64_t)j * n], bs[j - k0], s);
+  part[(int64_t)blockIdx.y * n + i] = s;
+}
+
+template <typename T>
+__global__ void k_dense_reduce(int n, int nchunks, const double* __restrict__ part, T* __restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunks; ++c) s += part[(int64_t)c * n + i];
+  x[i] = (T)s;
+}
+
+template <typename Src, typename Dst>
+__global__ void k_convert(int n, const Src* __restrict__ a, Dst* __restrict__ b) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = (Dst)a[i];
+}
+
+template <typename T>
+__global__ void k_axpy_from(int n, const T* __restrict__ z, double* __restrict__ x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] += (double)z[i];
+}
+
+constexpr int kCgBlocks = 152 * 4;
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_cg_init(int n, const double* __restrict__ b, double* __restrict__ r,
+                                                    double* __restrict__ x, T* __restrict__ vb, T* __restrict__ vx,
+                                                    double* __restrict__ part) {
+  double s = 0.0;
+  for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
+    const double bi = b[i];
+    r[i] = bi;
+    x[i] = 0.0;
+    if constexpr (!std::is_same<T, double>::value) vb[i] = (T)bi;  // FP64: vb is r itself
+    vx[i] = T(0);
+    s = fma(bi, bi, s);
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_cg_update(int n, const CgState* __restrict__ st, const double* __restrict__ p,
+                                                      const double* __restrict__ q, double* __restrict__ x,
+                                                      double* __restrict__ r, T* __restrict__ vb, T* __restrict__ vx,
+                                                      double* __restrict__ part) {
+  const double a = st->alpha;
+  double s = 0.0;
+  for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
+    x[i] = fma(a, p[i], x[i]);
+    const double ri = fma(-a, q[i], r[i]);
+    r[i] = ri;
+    if constexpr (!std::is_same<T, double>::value) vb[i] = (T)ri;  // FP64: vb is r itself
+    vx[i] = T(0);
+    s = fma(ri, ri, s);
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+template <typename T, bool FIRST>
+__global__ void __launch_bounds__(kBlock) k_cg_dotz(int n, const double* __restrict__ r, const T* __restrict__ vx,
+                                                    double* __restrict__ z, double* __restrict__ p,
+                                                    double* __restrict__ part) {
+  double s = 0.0;
+  for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
+    const double zi = (double)vx[i];
+    if constexpr (!std::is_same<T, double>::value) z[i] = zi;  // FP64: vx is z itself
+    if (FIRST) p[i] = zi;
+    s = fma(r[i], zi, s);
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kBlock) k_cg_pupdate(int n, const CgState* __restrict__ st, const double* __restrict__ z,
+                                                       double* __restrict__ p) {
+  const double beta = st->beta;
+  for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) p[i] = fma(beta, p[i], z[i]);
+}
+
+__global__ void __launch_bounds__(kBlock) k_dot_self(int n, const double* __restrict__ r, double* __restrict__ part) {
+  double s = 0.0;
+  for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) s = fma(r[i], r[i], s);
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(1024) k_cg_finish(int nparts, const double* __restrict__ part, CgState* st, int op,
+                                                    unsigned long long handle) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += 1024) s += part[i];
+  s = block_sum(s);
+  if (threadIdx.x != 0) return;
+  switch (op) {
+    case FIN_BB:
+      st->bb = s;
+      st->it = 0;
+      st->status = 0;
+      st->cont = 1;
+      break;
+    case FIN_RZ0:
+      st->rz = s;
+      break;
+    case FIN_PQ:
+      if (st->bb == 0.0) {
+        st->alpha = 0.0;
+      } else if (!(s > 0.0) || !isfinite(s) || !isfinite(st->rz)) {
+        st->alpha = 0.0;
+        st->status = 3;
+      } else {
+        st->alpha = st->rz / s;
+      }
+      st->pq = s;
+      break;
+    case FIN_RR: {
+      st->rr = s;
+      st->it += 1;
+      int cont = 1;
+      if (st->status == 3) cont = 0;
+      else if (s <= st->rtol2 * st->bb) st->status = 1, cont = 0;
+      else if (st->it >= st->maxit) st->status = 2, cont = 0;
+      if (!isfinite(s)) st->status = 3, cont = 0;
+      st->cont = cont;
+      if (handle) cudaGraphSetConditional((cudaGraphConditionalHandle)handle, (unsigned)cont);
+      break;
+    }
+    case FIN_RZ:
+      st->beta = s / st->rz;
+      st->rz = s;
+      break;
+    case FIN_NORM:
+      st->rr = s;
+      break;
+  }
+}
+
+inline int grid_for(int n, int per) { return (n + per - 1) / per; }
+
+constexpr double kGjDrop = 1e-10;
+
+__global__ void k_gj_prep(GjBatch g, int k) {
+  const int b = blockIdx.x;
+  const int n = g.n[b];
+  if (k >= n) return;
+  const double* M = g.M + g.off[b];
+  const double p = M[(int64_t)k * n + k];
+  const double d0 = g.diag0[g.voff[b] + k];
+  const bool bad = !(d0 > 0.0) || !isfinite(p) || p < -kGjDrop * d0;
+  const bool drop = bad || p <= kGjDrop * d0;
+  double* rk = g.rowk + g.voff[b];
+  double* ck = g.colk + g.voff[b];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    rk[j] = drop ? 0.0 : M[(int64_t)k * n + j];
+    ck[j] = drop ? 0.0 : M[(int64_t)j * n + k];
+  }
+  if (threadIdx.x == 0) {
+    g.pinv[b] = drop ? 0.0 : 1.0 / p;
+    g.drop[b] = drop ? 1 : 0;
+    if (bad) g.bad[b] = 1;
+    if (drop) g.ndrop[b] += 1;
+  }
+}
+
+__global__ void k_gj_update(GjBatch g, int k) {
+  const int b = blockIdx.y;
+  const int n = g.n[b];
+  if (k >= n) return;
+  double* M = g.M + g.off[b];
+  const double* rk = g.rowk + g.voff[b];
+  const double* ck = g.colk + g.voff[b];
+  const double pinv = g.pinv[b];
+  const bool drop = g.drop[b] != 0;
+  const int64_t nn = (int64_t)n * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e - (int64_t)i * n);
+    if (drop) {
+      if (i == k || j == k) M[e] = 0.0;
+    } else if (i == k && j == k) {
+      M[e] = pinv;
+    } else if (i == k) {
+      M[e] = rk[j] * pinv;
+    } else if (j == k) {
+      M[e] = -ck[i] * pinv;
+    } else {
+      M[e] = fma(-ck[i] * pinv, rk[j], M[e]);
+    }
+  }
+}
+
+}  // namespace
+
+void batched_spsd_inverse(const GjBatch& g, cudaStream_t s) {
+  int active = g.nmat;
+  for (int k = 0; k < g.max_n; ++k) {
+    while (active > 0 && g.hn[active - 1] <= k) --active;
+    if (active == 0) break;
+    const int64_t nn = (int64_t)g.hn[0] * g.hn[0];
+    const int bx = (int)std::min<int64_t>((nn + kBlock - 1) / kBlock, 4096);
+    k_gj_prep<<<active, kBlock, 0, s>>>(g, k);
+    k_gj_update<<<dim3(bx, active), kBlock, 0, s>>>(g, k);
+  }
+}
+
+int sell_blocks(int nrows) { return grid_for(nrows, kBlock); }
+
+template <typename T>
+void sell_spmv(const SellMat<T>& A, const T* x, T* y, cudaStream_t s) {
+  if (A.nrows == 0) return;
+  k_sell_spmv<T><<<sell_blocks(A.nrows), kBlock, 0, s>>>(A.off, A.col, A.val, A.nrows, x, y);
+}
+template <typename T>
+void sell_resid(const SellMat<T>& A, const T* x, const T* b, T* r, cudaStream_t s) {
+  if (A.nrows == 0) return;
+  k_sell_resid<T><<<sell_blocks(A.nrows), kBlock, 0, s>>>(A.off, A.col, A.val, A.nrows, x, b, r);
+}
+template <typename T>
+void sell_cheb(const SellMat<T>& A, const T* xin, const T* b, const T* dinv, T* d, T* xout, double cd, double cr,
+               bool first, cudaStream_t s) {
+  if (A.nrows == 0) return;
+  if (first)
+    k_sell_cheb<T, true><<<sell_blocks(A.nrows), kBlock, 0, s>>>(A.off, A.col, A.val, A.nrows, xin, b, dinv, d, xout,
+                                                                  (T)cd, (T)cr);
+  else
+    k_sell_cheb<T, false><<<sell_blocks(A.nrows), kBlock, 0, s>>>(A.off, A.col, A.val, A.nrows, xin, b, dinv, d, xout,
+                                                                   (T)cd, (T)cr);
+}
+template <typename T>
+void sell_prolong(const SellMat<T>& P, const T* xc, T* x, cudaStream_t s) {
+  if (P.nrows == 0) return;
+  k_sell_prolong<T><<<sell_blocks(P.nrows), kBlock, 0, s>>>(P.off, P.col, P.val, P.nrows, xc, x);
+}
+template <typename T>
+void sell_restrict(const SellMat<T>& R, const T* r, T* bc, T* xc, cudaStream_t s) {
+  if (R.nrows == 0) return;
+  k_sell_restrict<T><<<sell_blocks(R.nrows), kBlock, 0, s>>>(R.off, R.col, R.val, R.nrows, r, bc, xc);
+}
+void sell_ap(const SellMat<double>& A, const double* p, double* q, double* partial, int* nparts, cudaStream_t s) {
+  int nb = sell_blocks(A.nrows);
+  *nparts = nb;
+  k_sell_ap<<<nb, kBlock, 0, s>>>(A.off, A.col, A.val, A.nrows, p, q, partial);
+}
+
+template <typename T>
+void patch_residual(int nt, const int32_t* pdofs, const int32_t* prp, const int32_t* pci, const double* pv, const T* b,
+                    const T* x, double* rbuf, cudaStream_t s) {
+  if (nt == 0) return;
+  k_patch_residual<T><<<grid_for(nt, 128), 128, 0, s>>>(nt, pdofs, prp, pci, pv, b, x, rbuf);
+}
+
+void patch_solve_setup(int max_patch) {
+  size_t smem = (size_t)max_patch * sizeof(double);
+  if (smem > 48 * 1024) {
+    cudaFuncSetAttribute(k_patch_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_patch_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+}
+
+template <typename T>
+void patch_solve(int nitems, const PatchItem* items, const int32_t* pptr, const int32_t* pdofs, const int64_t* inv_off,
+                 const double* inv, const double* rbuf, T* x, int max_patch, cudaStream_t s) {
+  if (nitems == 0) return;
+  size_t smem = (size_t)max_patch * sizeof(double);
+  k_patch_solve<T><<<nitems, kBlock, smem, s>>>(items, pptr, pdofs, inv_off, inv, rbuf, x);
+}
+
+int dense_chunks(int n, int kchunk) { return grid_for(n, kchunk); }
+
+template <typename T>
+void dense_solve(int n, const double* X, const T* b, T* x, double* part, int kchunk, cudaStream_t s) {
+  int nch = dense_chunks(n, kchunk);
+  dim3 grid(grid_for(n, kBlock), nch);
+  k_dense_partial<T><<<grid, kBlock, kchunk * sizeof(double), s>>>(n, kchunk, X, b, part);
+  k_dense_reduce<T><<<grid_for(n, kBlock), kBlock, 0, s>>>(n, nch, part, x);
+}
+
+template <typename Src, typename Dst>
+void convert(int n, const Src* a, Dst* b, cudaStream_t s) {
+  if (n == 0) return;
+  k_convert<Src, Dst><<<std::min(grid_for(n, kBlock), kCgBlocks), kBlock, 0, s>>>(n, a, b);
+}
+template <typename T>
+void axpy_from(int n, const T* z, double* x, cudaStream_t s) {
+  if (n == 0) return;
+  k_axpy_from<T><<<std::min(grid_for(n, kBlock), kCgBlocks), kBlock, 0, s>>>(n, z, x);
+}
+
+int cg_parts(int n) { return std::max(1, std::min(grid_for(n, kBlock), kCgBlocks)); }
+
+template <typename T>
+void cg_init(int n, const double* b, double* r, double* x, T* vb, T* vx, double* part, cudaStream_t s) {
+  k_cg_init<T><<<cg_parts(n), kBlock, 0, s>>>(n, b, r, x, vb, vx, part);
+}
+template <typename T>
+void cg_update(int n, const CgState* st, const double* p, const double* q, double* x, double* r, T* vb, T* vx,
+               double* part, cudaStream_t s) {
+  k_cg_update<T><<<cg_parts(n), kBlock, 0, s>>>(n, st, p, q, x, r, vb, vx, part);
+}
+template <typename T>
+void cg_dotz(int n, const double* r, const T* vx, double* z, double* p, bool first, double* part, cudaStream_t s) {
+  if (first) k_cg_dotz<T, true><<<cg_parts(n), kBlock, 0, s>>>(n, r, vx, z, p, part);
+  else k_cg_dotz<T, false><<<cg_parts(n), kBlock, 0, s>>>(n, r, vx, z, p, part);
+}
+void cg_pupdate(int n, const CgState* st, const double* z, double* p, cudaStream_t s) {
+  k_cg_pupdate<<<cg_parts(n), kBlock, 0, s>>>(n, st, z, p);
+}
+void cg_finish(int nparts, const double* part, CgState* st, int op, unsigned long long cond_handle, cudaStream_t s) {
+  k_cg_finish<<<1, 1024, 0, s>>>(nparts, part, st, op, cond_handle);
+}
+void dot_self(int n, const double* r, double* part, cudaStream_t s) {
+  k_dot_self<<<cg_parts(n), kBlock, 0, s>>>(n, r, part);
+}
+
+#define NNMG_INST(T)                                                                                             \
+  template void sell_spmv<T>(const SellMat<T>&, const T*, T*, cudaStream_t);                                     \
+  template void sell_resid<T>(const SellMat<T>&, const T*, const T*, T*, cudaStream_t);                          \
+  template void sell_cheb<T>(const SellMat<T>&, const T*, const T*, const T*, T*, T*, double, double, bool,      \
+                             cudaStream_t);                                                                      \
+  template void sell_prolong<T>(const SellMat<T>&, const T*, T*, cudaStream_t);                                  \
+  template void sell_restrict<T>(const SellMat<T>&, const T*, T*, T*, cudaStream_t);                             \
+  template void patch_residual<T>(int, const int32_t*, const int32_t*, const int32_t*, const double*, const T*,  \
+                                  const T*, double*, cudaStream_t);                                              \
+  template void patch_solve<T>(int, const PatchItem*, const int32_t*, const int32_t*, const int64_t*,            \
+                               const double*, const double*, T*, int, cudaStream_t);                             \
+  template void dense_solve<T>(int, const double*, const T*, T*, double*, int, cudaStream_t);                    \
+  template void axpy_from<T>(int, const T*, double*, cudaStream_t);                                              \
+  template void cg_init<T>(int, const double*, double*, double*, T*, T*, double*, cudaStream_t);                 \
+  template void cg_update<T>(int, const CgState*, const double*, const double*, double*, double*, T*, T*,        \
+                             double*, cudaStream_t);                                                             \
+  template void cg_dotz<T>(int, const double*, const T*, double*, double*, bool, double*, cudaStream_t);
+
+NNMG_INST(double)
+NNMG_INST(float)
+template void convert<double, float>(int, const double*, float*, cudaStream_t);
+template void convert<float, double>(int, const float*, double*, cudaStream_t);
+template void convert<double, double>(int, const double*, double*, cudaStream_t);
+
+}  // namespace nnmg

@@ -1,0 +1,112 @@
+// Device kernels of the nnmg hot path (sm_103a) and their host launchers.
+//
+// Sparse operators are stored in SELL-32: rows grouped in slices of 32 (one warp), each
+// slice padded to its longest row and stored column-major, so that thread `lane` of a
+// warp owns row 32*s + lane and every load instruction of the warp reads 32 consecutive
+// values (and 32 consecutive column indices). One thread accumulates one row in CSR
+// column order, so no cross-lane reduction (and no extra FP64 additions) is needed:
+// on GB300 the FP64 pipe (~0.6 TFMA/s) is close to the HBM rate for 12-byte nonzeros.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+namespace nnmg {
+
+template <typename T>
+struct SellMat {
+  int32_t nrows = 0, ncols = 0, nslices = 0;
+  int64_t nnz = 0, padded = 0;
+  int64_t* off = nullptr;   // [nslices+1] element offset of each slice (multiple of 32)
+  int32_t* col = nullptr;   // [padded]
+  T* val = nullptr;         // [padded]
+};
+
+// Device-side state of the preconditioned CG recurrence (all FP64).
+struct CgState {
+  double bb, rz, pq, alpha, rr, beta, rtol2;
+  int32_t it, maxit, status, cont;   // status: 0 running, 1 converged, 2 maxit, 3 breakdown
+};
+
+enum FinishOp { FIN_BB = 0, FIN_RZ0 = 1, FIN_PQ = 2, FIN_RR = 3, FIN_RZ = 4, FIN_NORM = 5 };
+
+struct PatchItem {
+  int32_t patch, row0;
+};
+
+constexpr int kBlock = 256;
+
+// ---- SELL-32 SpMV family ----
+template <typename T> void sell_spmv(const SellMat<T>& A, const T* x, T* y, cudaStream_t s);
+template <typename T> void sell_resid(const SellMat<T>& A, const T* x, const T* b, T* r, cudaStream_t s);
+// One Chebyshev step: r = b - A xin; d = cd d + cr dinv r (first: cd ignored); xout = xin + d.
+template <typename T>
+void sell_cheb(const SellMat<T>& A, const T* xin, const T* b, const T* dinv, T* d, T* xout, double cd, double cr,
+               bool first, cudaStream_t s);
+// x += P xc.
+template <typename T> void sell_prolong(const SellMat<T>& P, const T* xc, T* x, cudaStream_t s);
+// bc = R r and xc = 0 (xc has R.nrows entries).
+template <typename T> void sell_restrict(const SellMat<T>& R, const T* r, T* bc, T* xc, cudaStream_t s);
+// q = A p and per-block partial sums of p.q (FP64).
+void sell_ap(const SellMat<double>& A, const double* p, double* q, double* partial, int* nparts, cudaStream_t s);
+int sell_blocks(int nrows);
+
+// ---- local correction S_c (two phases) ----
+template <typename T>
+void patch_residual(int nt, const int32_t* pdofs, const int32_t* prp, const int32_t* pci, const double* pv,
+                    const T* b, const T* x, double* rbuf, cudaStream_t s);
+// Raise the dynamic shared-memory limit of the solve kernel for patches of up to max_patch DoFs.
+void patch_solve_setup(int max_patch);
+template <typename T>
+void patch_solve(int nitems, const PatchItem* items, const int32_t* pptr, const int32_t* pdofs,
+                 const int64_t* inv_off, const double* inv, const double* rbuf, T* x, int max_patch, cudaStream_t s);
+
+// ---- coarsest level: x = X b with X = A_L^{-1} dense symmetric (split-K, deterministic) ----
+template <typename T>
+void dense_solve(int n, const double* X, const T* b, T* x, double* part, int kchunk, cudaStream_t s);
+int dense_chunks(int n, int kchunk);
+
+// ---- batched dense inversion (set-up): in-place Gauss-Jordan on symmetric positive
+// (semi-)definite matrices. A pivot <= 1e-10 of its original diagonal excludes that DoF
+// (zero row and column: the inverse of the remaining block); a negative or non-finite
+// pivot flags the matrix as indefinite in bad[b]. Matrices sorted by size, descending.
+struct GjBatch {
+  int nmat = 0, max_n = 0;
+  std::vector<int32_t> hn;     // host copy of the sizes
+  int32_t* n = nullptr;        // [nmat]
+  int64_t* off = nullptr;      // [nmat] offset of matrix b in M (row-major n_b x n_b)
+  int64_t* voff = nullptr;     // [nmat] offset of matrix b in the per-DoF vectors
+  double* M = nullptr;         // matrices, overwritten by their inverses
+  double* diag0 = nullptr;     // original diagonals
+  double *rowk = nullptr, *colk = nullptr, *pinv = nullptr;
+  int32_t *drop = nullptr, *bad = nullptr, *ndrop = nullptr;
+};
+void batched_spsd_inverse(const GjBatch& g, cudaStream_t s);
+
+// ---- vectors ----
+template <typename Src, typename Dst> void convert(int n, const Src* a, Dst* b, cudaStream_t s);
+template <typename T> void axpy_from(int n, const T* z, double* x, cudaStream_t s);   // x += (double) z
+
+// ---- CG (FP64 recurrence; the V-cycle vectors vb/vx are FP64 or FP32) ----
+int cg_parts(int n);
+// r = b, x = 0, partial b.b; V-cycle input vb = r (converted) and vx = 0.
+template <typename T> void cg_init(int n, const double* b, double* r, double* x, T* vb, T* vx, double* part, cudaStream_t s);
+// x += alpha p, r -= alpha q, partial r.r; vb = r, vx = 0.
+template <typename T>
+void cg_update(int n, const CgState* st, const double* p, const double* q, double* x, double* r, T* vb, T* vx,
+               double* part, cudaStream_t s);
+// z = (double) vx, partial r.z; with first: p = z.
+template <typename T>
+void cg_dotz(int n, const double* r, const T* vx, double* z, double* p, bool first, double* part, cudaStream_t s);
+void cg_pupdate(int n, const CgState* st, const double* z, double* p, cudaStream_t s);
+// Sum the partials in a fixed order and apply `op` to the CG state. With a non-zero
+// conditional handle, FIN_RR also sets the while-node condition (continue iterating).
+void cg_finish(int nparts, const double* part, CgState* st, int op, unsigned long long cond_handle, cudaStream_t s);
+// partial sums of |r|^2 for r = b - A x (a true-residual check)
+void dot_self(int n, const double* r, double* part, cudaStream_t s);
+
+void check_launch(const char* what);
+
+}  // namespace nnmg

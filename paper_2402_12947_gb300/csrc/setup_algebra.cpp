@@ -1,0 +1,405 @@
+// Host set-up, part 2: non-nested transfer, sparse products, dense SPD inverses and
+// the largest eigenvalue of the Jacobi-scaled operator.
+//
+// Transfer (Sec. 2, Eq. 2): [P_l]_ij = phi_j^{(l+1)}(x_i). Each free fine DoF point is
+// located in the coarse mesh through a uniform bucket grid: the lowest-numbered coarse
+// cell whose barycentric coordinates at the point are all >= -1e-12 is taken, the coarse
+// basis is evaluated at the raw barycentric coordinates, and |values| < 1e-14 are dropped.
+// Galerkin (Eq. 3): A_{l+1} = R (A P) with R = P^T, row-wise (Gustavson) products.
+// Eigenvalue (Sec. 3.2, Sec. 5): Lanczos on D^{-1/2} A D^{-1/2}, optionally restricted to
+// the DoFs outside the patches (adjusted lambda_max).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+
+#include "internal.hpp"
+
+namespace nnmg {
+
+namespace {
+
+const int kEdges2[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+const int kEdges3[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+
+// Coarse basis values at barycentric coordinates lam[d+1].
+int basis_at(int degree, int d, const double* lam, double* out) {
+  if (degree == 1) {
+    for (int a = 0; a <= d; ++a) out[a] = lam[a];
+    return d + 1;
+  }
+  for (int a = 0; a <= d; ++a) out[a] = lam[a] * (2.0 * lam[a] - 1.0);
+  const int(*le)[2] = d == 2 ? kEdges2 : kEdges3;
+  int ne = d == 2 ? 3 : 6;
+  for (int e = 0; e < ne; ++e) out[d + 1 + e] = 4.0 * lam[le[e][0]] * lam[le[e][1]];
+  return d + 1 + ne;
+}
+
+// Barycentric coordinates of point p in cell c.
+void barycentric(const MeshH& m, int64_t c, const double* p, double* lam) {
+  const int d = m.dim;
+  const int32_t* cv = &m.c[c * (d + 1)];
+  const double* x0 = &m.x[(int64_t)cv[0] * d];
+  double J[3][3], r[3];
+  for (int i = 0; i < d; ++i) {
+    r[i] = p[i] - x0[i];
+    for (int k = 0; k < d; ++k) J[i][k] = m.x[(int64_t)cv[k + 1] * d + i] - x0[i];
+  }
+  if (d == 2) {
+    double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    lam[1] = (J[1][1] * r[0] - J[0][1] * r[1]) / det;
+    lam[2] = (-J[1][0] * r[0] + J[0][0] * r[1]) / det;
+    lam[0] = 1.0 - lam[1] - lam[2];
+  } else {
+    // Cramer's rule
+    auto det3 = [](double a[3][3]) {
+      return a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) - a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0]) +
+             a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
+    };
+    double det = det3(J);
+    for (int k = 0; k < 3; ++k) {
+      double Jk[3][3];
+      std::memcpy(Jk, J, sizeof(J));
+      for (int i = 0; i < 3; ++i) Jk[i][k] = r[i];
+      lam[k + 1] = det3(Jk) / det;
+    }
+    lam[0] = 1.0 - lam[1] - lam[2] - lam[3];
+  }
+}
+
+}  // namespace
+
+Csr prolongation(const DofMapH& fine, const MeshH& cm, const DofMapH& coarse) {
+  const int d = cm.dim, d1 = d + 1;
+  const double kLocate = -1e-12, kDrop = 1e-14;
+  // bucket grid over the coarse bounding box
+  double lo[3], hi[3];
+  for (int r = 0; r < d; ++r) lo[r] = std::numeric_limits<double>::max(), hi[r] = -lo[r];
+  for (int64_t v = 0; v < cm.nv; ++v)
+    for (int r = 0; r < d; ++r) lo[r] = std::min(lo[r], cm.x[v * d + r]), hi[r] = std::max(hi[r], cm.x[v * d + r]);
+  int64_t nb = std::max<int64_t>(1, (int64_t)std::llround(std::pow((double)cm.nc / 2.0, 1.0 / d)));
+  double w[3];
+  for (int r = 0; r < d; ++r) w[r] = (hi[r] - lo[r]) / nb + 1e-300;
+  auto bidx = [&](double x, int r) {
+    int64_t b = (int64_t)std::floor((x - lo[r]) / w[r]);
+    return std::min<int64_t>(nb - 1, std::max<int64_t>(0, b));
+  };
+  int64_t nbt = 1;
+  for (int r = 0; r < d; ++r) nbt *= nb;
+  std::vector<int64_t> bstart(nbt + 1, 0);
+  auto for_cell_buckets = [&](int64_t c, const std::function<void(int64_t)>& f) {
+    int64_t b0[3], b1[3];
+    for (int r = 0; r < d; ++r) {
+      double mn = std::numeric_limits<double>::max(), mx = -mn;
+      for (int j = 0; j < d1; ++j) {
+        double x = cm.x[(int64_t)cm.c[c * d1 + j] * d + r];
+        mn = std::min(mn, x), mx = std::max(mx, x);
+      }
+      b0[r] = bidx(mn, r), b1[r] = bidx(mx, r);
+    }
+    if (d == 2) {
+      for (int64_t j = b0[1]; j <= b1[1]; ++j)
+        for (int64_t i = b0[0]; i <= b1[0]; ++i) f(j * nb + i);
+    } else {
+      for (int64_t k = b0[2]; k <= b1[2]; ++k)
+        for (int64_t j = b0[1]; j <= b1[1]; ++j)
+          for (int64_t i = b0[0]; i <= b1[0]; ++i) f((k * nb + j) * nb + i);
+    }
+  };
+  for (int64_t c = 0; c < cm.nc; ++c) for_cell_buckets(c, [&](int64_t b) { bstart[b + 1]++; });
+  for (int64_t b = 0; b < nbt; ++b) bstart[b + 1] += bstart[b];
+  std::vector<int64_t> bcells(bstart[nbt]), fill(bstart.begin(), bstart.end() - 1);
+  for (int64_t c = 0; c < cm.nc; ++c) for_cell_buckets(c, [&](int64_t b) { bcells[fill[b]++] = c; });
+
+  const int nloc = coarse.nloc;
+  const int64_t nrows = fine.nfree;
+  std::vector<int32_t> cnt(nrows, 0), tc((size_t)nrows * nloc);
+  std::vector<double> tv((size_t)nrows * nloc);
+  std::vector<uint8_t> failed(nrows, 0);
+  parallel_for(nrows, [&](int64_t rlo, int64_t rhi) {
+    for (int64_t i = rlo; i < rhi; ++i) {
+      const double* p = &fine.points[fine.free_list[i] * d];
+      int64_t b = 0;
+      if (d == 2) b = bidx(p[1], 1) * nb + bidx(p[0], 0);
+      else b = (bidx(p[2], 2) * nb + bidx(p[1], 1)) * nb + bidx(p[0], 0);
+      int64_t found = -1;
+      double lam[4];
+      for (int64_t k = bstart[b]; k < bstart[b + 1]; ++k) {
+        int64_t c = bcells[k];
+        barycentric(cm, c, p, lam);
+        double mn = lam[0];
+        for (int j = 1; j < d1; ++j) mn = std::min(mn, lam[j]);
+        if (mn >= kLocate) {
+          found = c;
+          break;
+        }
+      }
+      if (found < 0) {
+        failed[i] = 1;
+        continue;
+      }
+      double vals[10];
+      basis_at(coarse.degree, d, lam, vals);
+      std::pair<int32_t, double> e[10];
+      int n = 0;
+      for (int a = 0; a < nloc; ++a) {
+        int64_t col = coarse.free_index[coarse.cell_dofs[found * nloc + a]];
+        if (col < 0 || std::fabs(vals[a]) < kDrop) continue;
+        e[n++] = {(int32_t)col, vals[a]};
+      }
+      std::sort(e, e + n, [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) {
+        return a.first < b.first;
+      });
+      cnt[i] = n;
+      for (int k = 0; k < n; ++k) tc[i * nloc + k] = e[k].first, tv[i * nloc + k] = e[k].second;
+    }
+  });
+  for (int64_t i = 0; i < nrows; ++i)
+    if (failed[i]) throw Error(MG_ERR_POINT_LOCATION, "fine DoF " + std::to_string(i) + " lies in no coarse cell");
+  Csr P;
+  P.nrows = nrows;
+  P.ncols = coarse.nfree;
+  P.rp.assign(nrows + 1, 0);
+  for (int64_t i = 0; i < nrows; ++i) P.rp[i + 1] = P.rp[i] + cnt[i];
+  P.ci.resize(P.rp[nrows]);
+  P.v.resize(P.rp[nrows]);
+  for (int64_t i = 0; i < nrows; ++i)
+    for (int k = 0; k < cnt[i]; ++k) P.ci[P.rp[i] + k] = tc[i * nloc + k], P.v[P.rp[i] + k] = tv[i * nloc + k];
+  return P;
+}
+
+Csr unit_diagonal_on_empty_rows(const Csr& A) {
+  // rows with no entries get A_ii = 1 (coarse DoFs that the prolongation never reaches)
+  int64_t add = 0;
+  for (int64_t i = 0; i < A.nrows; ++i) add += A.rp[i + 1] == A.rp[i];
+  if (add == 0) return A;
+  Csr B;
+  B.nrows = A.nrows;
+  B.ncols = A.ncols;
+  B.rp.assign(A.nrows + 1, 0);
+  B.ci.reserve(A.nnz() + add);
+  B.v.reserve(A.nnz() + add);
+  for (int64_t i = 0; i < A.nrows; ++i) {
+    if (A.rp[i + 1] == A.rp[i]) {
+      B.ci.push_back((int32_t)i);
+      B.v.push_back(1.0);
+    } else {
+      B.ci.insert(B.ci.end(), A.ci.begin() + A.rp[i], A.ci.begin() + A.rp[i + 1]);
+      B.v.insert(B.v.end(), A.v.begin() + A.rp[i], A.v.begin() + A.rp[i + 1]);
+    }
+    B.rp[i + 1] = (int32_t)B.ci.size();
+  }
+  return B;
+}
+
+Csr transpose(const Csr& A) {
+  Csr T;
+  T.nrows = A.ncols;
+  T.ncols = A.nrows;
+  T.rp.assign(T.nrows + 1, 0);
+  for (int32_t c : A.ci) T.rp[c + 1]++;
+  for (int64_t i = 0; i < T.nrows; ++i) T.rp[i + 1] += T.rp[i];
+  T.ci.resize(A.nnz());
+  T.v.resize(A.nnz());
+  std::vector<int32_t> fill(T.rp.begin(), T.rp.end() - 1);
+  for (int64_t i = 0; i < A.nrows; ++i)
+    for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+      int32_t pos = fill[A.ci[k]]++;
+      T.ci[pos] = (int32_t)i;
+      T.v[pos] = A.v[k];
+    }
+  return T;
+}
+
+Csr spgemm(const Csr& A, const Csr& B) {
+  Csr C;
+  C.nrows = A.nrows;
+  C.ncols = B.ncols;
+  std::vector<int32_t> len(A.nrows);
+  int nt = num_threads();
+  // pass 1: row lengths
+  parallel_for(A.nrows, [&](int64_t lo, int64_t hi) {
+    std::vector<int64_t> mark(B.ncols, -1);
+    for (int64_t i = lo; i < hi; ++i) {
+      int32_t n = 0;
+      for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+        int32_t r = A.ci[k];
+        for (int32_t q = B.rp[r]; q < B.rp[r + 1]; ++q)
+          if (mark[B.ci[q]] != i) mark[B.ci[q]] = i, ++n;
+      }
+      len[i] = n;
+    }
+  });
+  (void)nt;
+  C.rp.assign(A.nrows + 1, 0);
+  for (int64_t i = 0; i < A.nrows; ++i) {
+    if ((int64_t)C.rp[i] + len[i] > INT32_MAX) throw Error(MG_ERR_INVALID_ARG, "product nnz exceeds 2^31");
+    C.rp[i + 1] = C.rp[i] + len[i];
+  }
+  C.ci.resize(C.rp[A.nrows]);
+  C.v.resize(C.rp[A.nrows]);
+  // pass 2: values, accumulated in the order of A's row then B's row
+  parallel_for(A.nrows, [&](int64_t lo, int64_t hi) {
+    std::vector<int64_t> mark(B.ncols, -1);
+    std::vector<double> acc(B.ncols, 0.0);
+    std::vector<int32_t> cols;
+    for (int64_t i = lo; i < hi; ++i) {
+      cols.clear();
+      for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+        int32_t r = A.ci[k];
+        double a = A.v[k];
+        for (int32_t q = B.rp[r]; q < B.rp[r + 1]; ++q) {
+          int32_t j = B.ci[q];
+          if (mark[j] != i) {
+            mark[j] = i;
+            acc[j] = 0.0;
+            cols.push_back(j);
+          }
+          acc[j] += a * B.v[q];
+        }
+      }
+      std::sort(cols.begin(), cols.end());
+      int32_t pos = C.rp[i];
+      for (int32_t j : cols) C.ci[pos] = j, C.v[pos++] = acc[j];
+    }
+  });
+  return C;
+}
+
+std::vector<double> dense_submatrix(const Csr& A, const int32_t* idx, int64_t n) {
+  std::vector<double> D((size_t)n * n, 0.0);
+  for (int64_t a = 0; a < n; ++a) {
+    int32_t r = idx[a];
+    for (int32_t k = A.rp[r]; k < A.rp[r + 1]; ++k) {
+      const int32_t* p = std::lower_bound(idx, idx + n, A.ci[k]);
+      if (p != idx + n && *p == A.ci[k]) D[a * n + (p - idx)] = A.v[k];
+    }
+  }
+  return D;
+}
+
+void spmv_host(const Csr& A, const double* x, double* y) {
+  parallel_for(A.nrows, [&](int64_t lo, int64_t hi) {
+    for (int64_t i = lo; i < hi; ++i) {
+      double s = 0;
+      for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) s += A.v[k] * x[A.ci[k]];
+      y[i] = s;
+    }
+  });
+}
+
+namespace {
+
+// Number of eigenvalues of the symmetric tridiagonal (a, b) smaller than x (Sturm count).
+int sturm_count(const std::vector<double>& a, const std::vector<double>& b, int m, double x) {
+  int c = 0;
+  double q = 1.0;
+  for (int i = 0; i < m; ++i) {
+    double bb = i > 0 ? b[i] * b[i] : 0.0;
+    q = a[i] - x - (i > 0 ? bb / q : 0.0);
+    if (q == 0.0) q = -1e-300;
+    if (q < 0) ++c;
+  }
+  return c;
+}
+
+// Largest eigenvalue of T_m and |last component| of its unit eigenvector.
+void tridiag_top(const std::vector<double>& a, const std::vector<double>& b, int m, double* theta, double* slast) {
+  double lo = std::numeric_limits<double>::max(), hi = -lo;
+  for (int i = 0; i < m; ++i) {
+    double r = (i > 0 ? std::fabs(b[i]) : 0.0) + (i + 1 < m ? std::fabs(b[i + 1]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(1.0, std::fabs(hi)); ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (sturm_count(a, b, m, mid) == m) hi = mid; else lo = mid;
+  }
+  *theta = hi;
+  // inverse iteration on (T - mu I) with mu just above theta (Thomas algorithm)
+  double mu = hi + 1e-10 * std::max(1.0, std::fabs(hi));
+  std::vector<double> x(m, 1.0), cp(m), dp(m);
+  for (int rep = 0; rep < 3; ++rep) {
+    double prev_c = 0;
+    for (int i = 0; i < m; ++i) {
+      double diag = a[i] - mu - (i > 0 ? b[i] * prev_c : 0.0);
+      if (diag == 0.0) diag = 1e-300;
+      double up = (i + 1 < m) ? b[i + 1] : 0.0;
+      cp[i] = up / diag;
+      dp[i] = (x[i] - (i > 0 ? b[i] * dp[i - 1] : 0.0)) / diag;
+      prev_c = cp[i];
+    }
+    for (int i = m - 1; i >= 0; --i) x[i] = dp[i] - (i + 1 < m ? cp[i] * x[i + 1] : 0.0);
+    double nrm = 0;
+    for (double v : x) nrm += v * v;
+    nrm = std::sqrt(nrm);
+    for (double& v : x) v /= nrm;
+  }
+  *slast = std::fabs(x[m - 1]);
+}
+
+}  // namespace
+
+double lanczos_lmax(const Csr& A, const uint8_t* keep, double tol, int maxit, int* iters) {
+  const int64_t n = A.nrows;
+  std::vector<double> s(n);
+  for (int64_t i = 0; i < n; ++i) {
+    double dgn = 0;
+    for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k)
+      if (A.ci[k] == i) dgn = A.v[k];
+    s[i] = (keep && !keep[i]) ? 0.0 : 1.0 / std::sqrt(dgn);
+  }
+  int64_t nk = 0;
+  for (int64_t i = 0; i < n; ++i) nk += s[i] != 0.0;
+  if (nk == 0) {
+    if (iters) *iters = 0;
+    return 0.0;
+  }
+  // deterministic start vector (splitmix64 of the index)
+  std::vector<double> v(n), vprev(n, 0.0), w(n), t(n);
+  double nrm = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    uint64_t z = (uint64_t)i * 0x9E3779B97F4A7C15ull + 0x1234567ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    v[i] = s[i] != 0.0 ? (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0 : 0.0;
+    nrm += v[i] * v[i];
+  }
+  nrm = std::sqrt(nrm);
+  for (auto& x : v) x /= nrm;
+  std::vector<double> al, be(1, 0.0);
+  double theta = 0;
+  int k = 0;
+  for (k = 0; k < std::min<int64_t>(maxit, nk); ++k) {
+    for (int64_t i = 0; i < n; ++i) t[i] = s[i] * v[i];
+    spmv_host(A, t.data(), w.data());
+    double alpha = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      w[i] *= s[i];
+      alpha += w[i] * v[i];
+    }
+    double beta = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      w[i] -= alpha * v[i] + be[k] * vprev[i];
+      beta += w[i] * w[i];
+    }
+    beta = std::sqrt(beta);
+    al.push_back(alpha);
+    be.push_back(beta);
+    double sl;
+    tridiag_top(al, be, k + 1, &theta, &sl);
+    if (beta * sl <= tol * std::fabs(theta) || beta <= 1e-14 * std::fabs(theta)) {
+      ++k;
+      break;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+      vprev[i] = v[i];
+      v[i] = w[i] / beta;
+    }
+  }
+  if (iters) *iters = k;
+  return theta;
+}
+
+}  // namespace nnmg

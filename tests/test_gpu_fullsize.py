@@ -1,0 +1,105 @@
+"""Parity at the full 2D P2 workload (1024^2 grid, 4.19M DoFs, 6 non-nested levels, 32
+needle/flattened clusters per level), in the configuration the benchmark times.
+
+The oracle cannot run the whole hierarchy at this size, so it computes sampled outputs one
+by one: rows of A_0 from the element matrices of the cells around each sampled DoF, rows of
+P_0 by point location of the sampled fine DoF points, rows of the GPU SpMV; and properties
+that hold at any size: the FP64 and mixed solves reach rtol 1e-8 with the residual
+recomputed on the host from the exported operator.
+"""
+import numpy as np
+import pytest
+
+from _util import rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import fem, transfer  # noqa: E402
+from paper_2402_12947_gb300 import inputs  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def full():
+    from paper_2402_12947_gb300 import build
+    build.build()
+    from paper_2402_12947_gb300 import nnmg
+    meshes = inputs.config_c2()
+    H64 = nnmg.Hierarchy.from_meshes(meshes, 2, 0.1)
+    lam = [H64.eigs(l)[2] for l in range(H64.num_levels - 1)]
+    H32 = nnmg.Hierarchy.from_meshes(meshes, 2, 0.1, precision="mixed", lambda_override=lam)
+    yield meshes, H64, H32
+    H64.close()
+    H32.close()
+
+
+def test_sampled_rows_of_A_and_P(full):
+    meshes, H, _ = full
+    m0, m1 = meshes[0], meshes[1]
+    dm0 = fem.dof_map(m0.coords, m0.cells, 2)
+    dm1 = fem.dof_map(m1.coords, m1.cells, 2)
+    assert H.num_dofs(0) == dm0.nfree == 2047 ** 2
+    rp, ci, v = H.export_level(0)
+    rng = np.random.default_rng(0)
+    rows = rng.choice(dm0.nfree, 300, replace=False)
+    # near-patch rows too: the ill-conditioned cells
+    pt = H.export_patches(0)
+    rows = np.unique(np.concatenate([rows, np.concatenate(pt)[::7]]))
+    for i in rows:
+        g = dm0.free[i]
+        cells = np.flatnonzero((dm0.cell_dofs == g).any(axis=1))
+        Ke = fem.element_stiffness(m0.coords, m0.cells[cells], 2)
+        row = {}
+        for c, K in zip(cells, Ke):
+            a = int(np.flatnonzero(dm0.cell_dofs[c] == g)[0])
+            for bl, gb in enumerate(dm0.cell_dofs[c]):
+                j = dm0.free_index[gb]
+                if j >= 0:
+                    row[j] = row.get(j, 0.0) + K[a, bl]
+        cols = np.array(sorted(row))
+        vals = np.array([row[j] for j in cols])
+        assert np.array_equal(ci[rp[i]:rp[i + 1]], cols)
+        assert rel_err(v[rp[i]:rp[i + 1]], vals) < 1e-12
+    prp, pci, pv = H.export_transfer(0)
+    prow = rng.choice(dm0.nfree, 300, replace=False)
+    cell, lam = transfer.locate(m1.coords, m1.cells, dm0.points[dm0.free[prow]])
+    vals = fem.basis_values(lam, 2, 2)
+    for k, i in enumerate(prow):
+        cols = dm1.free_index[dm1.cell_dofs[cell[k]]]
+        keep = (cols >= 0) & (np.abs(vals[k]) >= transfer.DROP_TOL)
+        order = np.argsort(cols[keep])
+        assert np.array_equal(pci[prp[i]:prp[i + 1]], cols[keep][order])
+        assert np.max(np.abs(pv[prp[i]:prp[i + 1]] - vals[k][keep][order])) < 1e-13
+
+
+def test_sampled_spmv_rows(full):
+    _, H, _ = full
+    n = H.num_dofs(0)
+    rp, ci, v = H.export_level(0)
+    x = np.random.default_rng(1).uniform(-1, 1, n)
+    y = torch.zeros(n, dtype=torch.float64, device="cuda")
+    H.apply_A(0, torch.from_numpy(x).cuda(), y)
+    yh = y.cpu().numpy()
+    rows = np.random.default_rng(2).choice(n, 2000, replace=False)
+    ref = np.array([v[rp[i]:rp[i + 1]] @ x[ci[rp[i]:rp[i + 1]]] for i in rows])
+    assert rel_err(yh[rows], ref) < 1e-12
+
+
+@pytest.mark.parametrize("which", ["fp64", "mixed"])
+def test_full_solve_reaches_rtol(full, which):
+    import scipy.sparse as sp
+    _, H64, H32 = full
+    H = H64 if which == "fp64" else H32
+    n = H.num_dofs(0)
+    b = inputs.uniform_rhs(n, 2)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    info = H.solve(torch.from_numpy(b).cuda(), x, rtol=1e-8, maxit=200)
+    assert info["converged"] and info["true_rel_residual"] < 1.5e-8, info
+    rp, ci, v = H64.export_level(0)
+    A = sp.csr_matrix((v, ci, rp), shape=(n, n))
+    xh = x.cpu().numpy()
+    assert np.linalg.norm(b - A @ xh) / np.linalg.norm(b) < 1.5e-8
+    if which == "mixed":
+        x64 = torch.zeros_like(x)
+        i64 = H64.solve(torch.from_numpy(b).cuda(), x64, rtol=1e-8, maxit=200)
+        assert info["iterations"] <= i64["iterations"] + 1, (info, i64)

@@ -1,0 +1,253 @@
+"""GPU parity: every step of the hot path through the C ABI against the CPU oracle.
+
+FP64 bar: relative max-norm difference <= 1e-10 (TOL64) on the same inputs, with the
+oracle's own operators (mg_setup_csr) and through the geometric set-up with identical
+eigenvalues (mg_setup + lambda_override). Mixed precision: the final true residual meets
+the rtol and the iteration count is within +1 of the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+from _util import TOL64, case, csr_arrays, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import mg, smoother  # noqa: E402
+
+CASES = ["c1_p1", "c1_p2", "c2_p2_128", "cube_p1", "cube_p2"]
+ORDERS = ["sandwich", "global_then_local", "global"]
+
+
+@pytest.fixture(scope="module")
+def nnmg():
+    from paper_2402_12947_gb300 import build
+    build.build()
+    from paper_2402_12947_gb300 import nnmg as mod
+    assert torch.cuda.is_available()
+    return mod
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+_lib_cache = {}
+
+
+def lib_csr(nnmg, name, order="sandwich", precision="fp64"):
+    key = ("csr", name, order, precision)
+    if key not in _lib_cache:
+        _, Ho, _, _ = case(name, order)
+        As, Ps, patches, lam = csr_arrays(Ho)
+        _lib_cache[key] = nnmg.Hierarchy.from_csr(As, Ps, patches, lam, smoother=order, precision=precision)
+    return _lib_cache[key]
+
+
+def lib_geo(nnmg, name, order="sandwich", precision="fp64"):
+    key = ("geo", name, order, precision)
+    if key not in _lib_cache:
+        meshes, Ho, degree, layers = case(name, order)
+        lam = [lv.lmax for lv in Ho.levels[:-1]]
+        _lib_cache[key] = nnmg.Hierarchy.from_meshes(meshes, degree, 0.1, patch_layers=layers, smoother=order,
+                                                     precision=precision, lambda_override=lam)
+    return _lib_cache[key]
+
+
+def rng_vec(n, seed):
+    return np.random.default_rng(seed).uniform(-1, 1, n)
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_apply_A_every_level(nnmg, name):
+    _, Ho, _, _ = case(name)
+    H = lib_csr(nnmg, name)
+    for l, lo in enumerate(Ho.levels):
+        x = rng_vec(lo.n, l)
+        y = torch.zeros(lo.n, dtype=torch.float64, device="cuda")
+        H.apply_A(l, dev(x), y)
+        assert rel_err(host(y), lo.A @ x) < TOL64, l
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_chebyshev_and_local_correction(nnmg, name):
+    _, Ho, _, _ = case(name)
+    H = lib_csr(nnmg, name)
+    for l, lo in enumerate(Ho.levels[:-1]):
+        b, x0 = rng_vec(lo.n, 10 + l), rng_vec(lo.n, 20 + l)
+        x = dev(x0)
+        H.chebyshev(l, dev(b), x)
+        ref = smoother.chebyshev(lo.A, lo.dinv, b, x0, lo.lmax, lo.lmin, Ho.cheb_degree)
+        assert rel_err(host(x), ref) < TOL64, ("cheb", l)
+        x = dev(x0)
+        H.local_correction(l, dev(b), x)
+        ref = lo.local.apply(lo.A, b, x0)
+        assert rel_err(host(x), ref) < TOL64, ("local", l)
+
+
+@pytest.mark.parametrize("name", ["c1_p1", "c2_p2_128", "cube_p2"])
+@pytest.mark.parametrize("order", ORDERS)
+def test_combined_smoother(nnmg, name, order):
+    _, Ho, _, _ = case(name, order)
+    H = lib_csr(nnmg, name, order)
+    for l, lo in enumerate(Ho.levels[:-1]):
+        b, x0 = rng_vec(lo.n, 30 + l), rng_vec(lo.n, 40 + l)
+        for post in (False, True):
+            x = dev(x0)
+            H.smooth(l, dev(b), x, post=post)
+            ref = smoother.smooth(lo.A, lo.dinv, b, x0, lo.lmax, lo.lmin, Ho.cheb_degree, lo.local, order, post)
+            assert rel_err(host(x), ref) < TOL64, (l, post)
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_transfer_and_coarse_solve(nnmg, name):
+    _, Ho, _, _ = case(name)
+    H = lib_csr(nnmg, name)
+    for l, lo in enumerate(Ho.levels[:-1]):
+        nc = Ho.levels[l + 1].n
+        b, x0, xc = rng_vec(lo.n, 50 + l), rng_vec(lo.n, 60 + l), rng_vec(nc, 70 + l)
+        r = torch.zeros(lo.n, dtype=torch.float64, device="cuda")
+        bc = torch.zeros(nc, dtype=torch.float64, device="cuda")
+        H.residual_restrict(l, dev(b), dev(x0), r, bc)
+        rr = b - lo.A @ x0
+        assert rel_err(host(r), rr) < TOL64
+        assert rel_err(host(bc), lo.R @ rr) < TOL64
+        x = dev(x0)
+        H.prolong_correct(l, dev(xc), x)
+        assert rel_err(host(x), x0 + lo.P @ xc) < TOL64
+    lc = Ho.levels[-1]
+    b = rng_vec(lc.n, 80)
+    x = torch.zeros(lc.n, dtype=torch.float64, device="cuda")
+    H.coarse_solve(dev(b), x)
+    assert rel_err(host(x), Ho.coarse.solve(b)) < TOL64
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("setup", ["csr", "geo"])
+def test_vcycle(nnmg, name, setup):
+    _, Ho, _, _ = case(name)
+    H = lib_csr(nnmg, name) if setup == "csr" else lib_geo(nnmg, name)
+    n = Ho.levels[0].n
+    b, x0 = rng_vec(n, 90), rng_vec(n, 91)
+    x = dev(x0)
+    H.vcycle(dev(b), x)
+    ref = x0 + mg.vcycle(Ho, b - Ho.levels[0].A @ x0)
+    assert rel_err(host(x), ref) < TOL64
+    # Alg. 1 with the initial guess inside the cycle gives the same iterate
+    assert rel_err(host(x), mg.vcycle(Ho, b, x0)) < TOL64
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("graph", [1, 0])
+def test_pcg_solve(nnmg, name, graph):
+    meshes, Ho, degree, layers = case(name)
+    lam = [lv.lmax for lv in Ho.levels[:-1]]
+    H = nnmg.Hierarchy.from_meshes(meshes, degree, 0.1, patch_layers=layers, lambda_override=lam, use_graph=graph)
+    try:
+        n = Ho.levels[0].n
+        b = rng_vec(n, 100)
+        rtol = 1e-10
+        xr, itr, hist, tr = mg.pcg(Ho, b, rtol)
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        info = H.solve(dev(b), x, rtol=rtol, maxit=200)
+        assert info["converged"] and info["iterations"] == itr, (info, itr)
+        assert abs(info["rel_residual"] - hist[-1]) <= 1e-3 * hist[-1] + 1e-14
+        assert info["true_rel_residual"] < 2 * rtol
+        assert rel_err(host(x), xr) < 1e-9
+    finally:
+        H.close()
+
+
+@pytest.mark.parametrize("name", ["c1_p1", "c1_p2", "c2_p2_128", "cube_p1"])
+def test_mixed_precision_solve(nnmg, name):
+    meshes, Ho, degree, layers = case(name)
+    H = lib_geo(nnmg, name, precision="mixed")
+    n = Ho.levels[0].n
+    b = rng_vec(n, 110)
+    rtol = 1e-8
+    xr, itr, _, _ = mg.pcg(Ho, b, rtol)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    info = H.solve(dev(b), x, rtol=rtol, maxit=200)
+    assert info["converged"] and info["iterations"] <= itr + 1, (info, itr)
+    assert info["true_rel_residual"] < 1.5 * rtol
+    xh = host(x)
+    assert np.linalg.norm(b - Ho.levels[0].A @ xh) < 1.5 * rtol * np.linalg.norm(b)
+    # one FP32 V-cycle agrees with the FP64 oracle cycle to single precision
+    z = torch.zeros(n, dtype=torch.float64, device="cuda")
+    H.vcycle(dev(b), z)
+    assert rel_err(host(z), mg.vcycle(Ho, b)) < 2e-5
+
+
+def test_stationary_multigrid(nnmg):
+    _, Ho, _, _ = case("c1_p1")
+    H = lib_geo(nnmg, "c1_p1")
+    n = Ho.levels[0].n
+    b = rng_vec(n, 120)
+    xr, itr, hist = mg.stationary(Ho, b, 1e-10)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    info = H.solve_stationary(dev(b), x, rtol=1e-10, maxit=100)
+    assert info["converged"] and info["iterations"] == itr
+    assert rel_err(host(x), xr) < 1e-9
+
+
+def test_edge_cases(nnmg):
+    _, Ho, _, _ = case("c1_p1")
+    H = lib_geo(nnmg, "c1_p1")
+    n = Ho.levels[0].n
+    # zero right-hand side: zero solution, no iterations
+    x = torch.ones(n, dtype=torch.float64, device="cuda")
+    info = H.solve(torch.zeros(n, dtype=torch.float64, device="cuda"), x, rtol=1e-8)
+    assert info["converged"] and info["iterations"] == 0 and float(x.abs().max()) == 0.0
+    # maxit reached: status and info are reported
+    b = rng_vec(n, 130)
+    info = H.solve(dev(b), torch.zeros(n, dtype=torch.float64, device="cuda"), rtol=1e-14, maxit=2,
+                   raise_on_fail=False)
+    assert info["status"] == nnmg.ERR_NO_CONVERGENCE and info["iterations"] == 2 and not info["converged"]
+    # the same solve twice is bitwise reproducible (deterministic reductions)
+    x1 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    x2 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    H.solve(dev(b), x1, rtol=1e-10)
+    H.solve(dev(b), x2, rtol=1e-10)
+    assert torch.equal(x1, x2)
+    # wrong sizes and types are rejected before any launch
+    with pytest.raises(ValueError):
+        H.vcycle(dev(b[:-1]), x1)
+    with pytest.raises(TypeError):
+        H.vcycle(dev(b).float(), x1)
+
+
+def test_clean_mesh_smoother_reduces_to_chebyshev(nnmg):
+    from paper_2402_12947_gb300 import inputs
+    from oracle import hierarchy
+    meshes = inputs.config_c1(clusters=False)
+    Ho = hierarchy.build(meshes, 1, layers=2)
+    assert all(len(lv.patches) == 0 for lv in Ho.levels)
+    lam = [lv.lmax for lv in Ho.levels[:-1]]
+    with nnmg.Hierarchy.from_meshes(meshes, 1, 0.1, patch_layers=2, lambda_override=lam) as H:
+        lo = Ho.levels[0]
+        b, x0 = rng_vec(lo.n, 140), rng_vec(lo.n, 141)
+        xs, xc = dev(x0), dev(x0)
+        H.smooth(0, dev(b), xs)
+        H.chebyshev(0, dev(b), xc)
+        assert torch.equal(xs, xc)
+
+
+def test_batch_matches_individual_solves(nnmg):
+    names = ["c1_p1", "c1_p2", "cube_p1"]
+    hs = [lib_geo(nnmg, nm) for nm in names]
+    bs = [dev(rng_vec(h.num_dofs(0), 150 + i)) for i, h in enumerate(hs)]
+    alone = []
+    for h, b in zip(hs, bs):
+        x = torch.zeros_like(b)
+        h.solve(b, x, rtol=1e-9)
+        alone.append(x)
+    xs = [torch.zeros_like(b) for b in bs]
+    infos = nnmg.solve_batch(hs, bs, xs, rtol=1e-9)
+    for a, x, inf in zip(alone, xs, infos):
+        assert inf["converged"]
+        assert torch.equal(a, x)

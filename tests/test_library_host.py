@@ -1,0 +1,150 @@
+"""The C-ABI library on the host (no GPU): it loads, exports every declared symbol, and
+its C++ set-up (assembly, quality, patches, transfer, Galerkin, eigenvalues) matches the
+oracle; error codes for invalid input."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from _util import case, csr_arrays, rel_err, to_csr
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def nnmg():
+    from paper_2402_12947_gb300 import build
+    build.build()
+    from paper_2402_12947_gb300 import nnmg as mod
+    return mod
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "nnmg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mg_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol(nnmg):
+    names = declared_functions()
+    assert len(names) >= 25
+    lib = ctypes.CDLL(nnmg.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in nnmg.EXPORTED, f"binding misses {n}"
+
+
+@pytest.mark.parametrize("name", ["c1_p1", "c1_p2", "c2_p2_128", "cube_p1", "cube_p2"])
+def test_host_setup_matches_oracle(nnmg, name):
+    meshes, Ho, degree, layers = case(name)
+    H = nnmg.Hierarchy.from_meshes(meshes, degree, 0.1, host_only=1, patch_layers=layers)
+    try:
+        assert H.num_levels == Ho.L
+        for l, lo in enumerate(Ho.levels):
+            n = lo.n
+            assert H.num_dofs(l) == n
+            A = to_csr(*H.export_level(l), (n, n))
+            assert abs(A - lo.A).max() <= 1e-12 * abs(lo.A).max(), l
+            pt = H.export_patches(l)
+            assert len(pt) == len(lo.patches)
+            for a, b in zip(pt, lo.patches):
+                assert np.array_equal(a, b)
+            g = H.cell_quality(l, meshes[l].nc)
+            assert np.max(np.abs(g - lo.gamma)) < 1e-12
+            pts = H.dof_coords(l, meshes[l].dim)
+            assert np.array_equal(pts, lo.dm.points[lo.dm.free])
+            if l < Ho.L - 1:
+                nc = Ho.levels[l + 1].n
+                P = to_csr(*H.export_transfer(l), (n, nc))
+                assert np.array_equal(P.indptr, lo.P.indptr) and np.array_equal(P.indices, lo.P.indices)
+                assert np.max(np.abs(P.data - lo.P.data)) < 1e-13
+                lu, la, used = H.eigs(l)
+                assert abs(lu - lo.lmax_unadj) < 1e-8 * lo.lmax_unadj
+                assert abs(la - lo.lmax_adj) < 1e-8 * lo.lmax_adj
+                assert used == la
+        from oracle import fem
+        dm = Ho.levels[0].dm
+        b = fem.load_vector_full(meshes[0].coords, meshes[0].cells, dm, 2.5)[dm.free]
+        assert rel_err(H.load_constant(2.5), b) < 1e-13
+    finally:
+        H.close()
+
+
+def test_csr_setup_roundtrip(nnmg):
+    _, Ho, _, _ = case("c1_p1")
+    As, Ps, patches, lam = csr_arrays(Ho)
+    H = nnmg.Hierarchy.from_csr(As, Ps, patches, lam, host_only=1)
+    try:
+        for l in range(Ho.L):
+            n = Ho.levels[l].n
+            assert (to_csr(*H.export_level(l), (n, n)) != As[l]).nnz == 0
+            assert [np.array_equal(a, b) for a, b in zip(H.export_patches(l), patches[l])] == [True] * len(patches[l])
+        assert H.eigs(0)[2] == lam[0]
+    finally:
+        H.close()
+
+
+def test_setup_errors(nnmg):
+    from paper_2402_12947_gb300 import inputs
+    meshes = inputs.config_c1()
+    with pytest.raises(nnmg.NnmgError) as e:
+        nnmg.Hierarchy.from_meshes(meshes, 3, 0.1, host_only=1)
+    assert e.value.code == nnmg.ERR_INVALID_ARG
+    with pytest.raises(nnmg.NnmgError) as e:
+        nnmg.Hierarchy.from_meshes(meshes[:1], 1, 0.1, host_only=1)
+    assert e.value.code == nnmg.ERR_INVALID_ARG
+    # a degenerate (zero-area) cell
+    bad = inputs.Mesh(coords=meshes[1].coords.copy(), cells=meshes[1].cells.copy(), n=meshes[1].n)
+    c = bad.cells[100]
+    bad.coords[c[2]] = bad.coords[c[0]]
+    with pytest.raises(nnmg.NnmgError) as e:
+        nnmg.Hierarchy.from_meshes([meshes[0], bad], 1, 0.1, host_only=1)
+    assert e.value.code == nnmg.ERR_DEGENERATE_CELL
+    # a coarse mesh that does not cover the fine one: point location fails
+    small = inputs.Mesh(coords=meshes[1].coords * 0.5, cells=meshes[1].cells, n=meshes[1].n)
+    with pytest.raises(nnmg.NnmgError) as e:
+        nnmg.Hierarchy.from_meshes([meshes[0], small], 1, 0.1, host_only=1)
+    assert e.value.code == nnmg.ERR_POINT_LOCATION
+    # out-of-range vertex index
+    broken = inputs.Mesh(coords=meshes[1].coords, cells=meshes[1].cells.copy(), n=meshes[1].n)
+    broken.cells[0, 0] = 10 ** 7
+    with pytest.raises(nnmg.NnmgError) as e:
+        nnmg.Hierarchy.from_meshes([meshes[0], broken], 1, 0.1, host_only=1)
+    assert e.value.code == nnmg.ERR_INVALID_ARG
+    # algebraic set-up needs the eigenvalues
+    _, Ho, _, _ = case("c1_p1")
+    As, Ps, patches, lam = csr_arrays(Ho)
+    with pytest.raises(nnmg.NnmgError) as e:
+        nnmg.Hierarchy.from_csr(As, Ps[:1] + [Ps[0]], patches, lam, host_only=1)
+    assert e.value.code == nnmg.ERR_INVALID_ARG
+    # compute on a host-only hierarchy
+    H = nnmg.Hierarchy.from_meshes(meshes, 1, 0.1, host_only=1)
+    try:
+        code = nnmg.lib.mg_vcycle(H._h, None, None, None)
+        assert code in (nnmg.ERR_NO_DEVICE, nnmg.ERR_INVALID_ARG)
+    finally:
+        H.close()
+
+
+def test_options_validation(nnmg):
+    from paper_2402_12947_gb300 import inputs
+    meshes = inputs.config_c1()
+    for kw in (dict(cheb_degree=0), dict(nu=0), dict(smoother=7), dict(precision=5), dict(lmin_ratio=1.5)):
+        with pytest.raises(nnmg.NnmgError) as e:
+            nnmg.Hierarchy.from_meshes(meshes, 1, 0.1, host_only=1, **kw)
+        assert e.value.code == nnmg.ERR_INVALID_ARG
+
+
+def test_unreached_coarse_dofs_get_unit_diagonal(nnmg):
+    """On a coarse level with needles shorter than the fine mesh size, some coarse P2 DoFs
+    are seen by no fine interpolation point: their Galerkin row is the unit row, on both
+    the library and the oracle side."""
+    _, Ho, _, _ = case("c2_p2_128")
+    P = Ho.levels[0].P.tocsc()
+    unreached = np.flatnonzero(np.diff(P.indptr) == 0)
+    A1 = Ho.levels[1].A
+    for j in unreached:
+        row = A1.getrow(j)
+        assert row.nnz == 1 and row.indices[0] == j and row.data[0] == 1.0

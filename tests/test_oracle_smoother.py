@@ -157,3 +157,29 @@ def test_adjusted_lambda_recovers_high_quality_value():
     assert lam["clean"][0] == lam["clean"][1]
     assert lam["bad"][0] > 1.3 * lam["clean"][0]
     assert abs(lam["bad"][1] - lam["clean"][0]) < 0.05 * lam["clean"][0]
+
+
+def test_direct_solver_spd_is_plain_solve():
+    rng = np.random.default_rng(11)
+    M = rng.normal(size=(40, 40))
+    A = M @ M.T + 40 * np.eye(40)
+    r = rng.normal(size=40)
+    ds = smoother.DirectSolver(A)
+    assert ds.keep.all()
+    assert np.max(np.abs(ds.solve(r) - np.linalg.solve(A, r))) < 1e-12
+
+
+def test_direct_solver_semidefinite_consistent():
+    """A Gram matrix of k < n vectors has rank k: exactly n - k DoFs are dependent, and
+    every consistent right-hand side (in the range) is solved exactly."""
+    rng = np.random.default_rng(12)
+    for n, k in ((30, 22), (50, 49), (12, 3)):
+        V = rng.normal(size=(n, k))
+        A = V @ V.T
+        ds = smoother.DirectSolver(A)
+        assert int((~ds.keep).sum()) == n - k
+        r = A @ rng.normal(size=n)
+        e = ds.solve(r)
+        assert np.max(np.abs(A @ e - r)) < 1e-10 * np.max(np.abs(r))
+    with pytest.raises(np.linalg.LinAlgError):
+        smoother.DirectSolver(-np.eye(3))
