@@ -1,0 +1,325 @@
+"""Benchmark: MG-preconditioned CG solves of the 2D P2 workload on GB300.
+
+Workload (one "step" = one solve, setup excluded): unit square, 1024^2 grid of squares
+split into triangles, P2 elements (4,190,209 free DoFs), 6 non-nested independently
+jittered levels (1024^2 .. 32^2), 32 seeded clusters of 2-8 needle/flattened cells (aspect
+ratio 1e2-1e4) on the fine and on every intermediate level, right-hand side U[-1, 1],
+V-cycle with the global-local combined smoother (sandwich S_c, Chebyshev degree 2 with the
+adjusted lambda_max, S_c), CG to relative residual 1e-8.
+
+`value` is the mixed-precision form (FP32 V-cycle inside FP64 CG); the plain FP64 form is
+measured on the same GPU and reported under "fp64". Multi-GPU: independent replicas, one
+problem per rank (weak scaling, no data-path collective).
+
+--impl reference times the CPU oracle (NumPy/SciPy, the same algorithm in FP64) on a
+bounded sample of the same workload family.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DoFs/s solved to rtol 1e-8 (mixed vs FP64, same GPU); SpMV HBM GB/s; p50/p99"
+WORKLOAD = ("2D Poisson P2, unit square 1024^2 x 2 triangles (4,190,209 DoFs), 6 non-nested levels, "
+            "32 needle/flattened clusters (AR 1e2-1e4) per fine/intermediate level, "
+            "sandwich S_c-Chebyshev(2)-S_c with adjusted lambda, MG-PCG rtol 1e-8, RHS U[-1,1]")
+SAMPLE_N = 256   # CPU oracle sample: the same family at 256^2 (261,121 DoFs, 4 levels)
+RTOL = 1e-8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-fine", type=int, default=1024)
+    ap.add_argument("--levels", type=int, default=6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="both", choices=["both", "mixed"],
+                    help="'mixed' builds and times only the mixed-precision form (profiling runs)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy burst)"
+    except Exception:
+        return 6800.0, "fallback (6.8 TB/s)"
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the fine-level Chebyshev kernel from the committed ncu
+    summary (a line 'traffic_bytes_per_launch: <int> kernel_rev: <rev>')."""
+    path = os.path.join(ROOT, "profiles", "sell_cheb_f32_c2.md")
+    try:
+        for line in open(path):
+            if line.startswith("traffic_bytes_per_launch:"):
+                parts = line.split()
+                rev = parts[3] if len(parts) > 3 else ""
+                return float(parts[1]), rev
+    except OSError:
+        pass
+    return None, None
+
+
+KERNEL_REV = "sell32-v1"   # bump when the timed kernel changes (invalidates the profiled traffic)
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = max(mx, float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline_subprocess(n_fine: int, steps: int = 1) -> dict:
+    """Time the CPU oracle's MG-PCG solve (setup excluded) in a fresh single-threaded process."""
+    code = f"""
+import json, time, os, sys
+sys.path.insert(0, {ROOT!r})
+from paper_2402_12947_gb300 import inputs
+from oracle import hierarchy, mg
+levels = max(2, ({n_fine}).bit_length() - 5)
+meshes = inputs.config_c2(n_fine={n_fine}, levels=levels)
+t0 = time.perf_counter()
+H = hierarchy.build(meshes, 2)
+setup = time.perf_counter() - t0
+b = inputs.uniform_rhs(H.levels[0].n, 2)
+times, its = [], []
+for s in range({steps}):
+    t0 = time.perf_counter()
+    x, it, hist, tr = mg.pcg(H, b, {RTOL})
+    times.append(time.perf_counter() - t0)
+    its.append(it)
+print(json.dumps({{"n": H.levels[0].n, "levels": levels, "setup_s": setup, "times": times, "iterations": its}}))
+"""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    env.pop("CUDA_VISIBLE_DEVICES", None)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle baseline failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    d = cpu_baseline_subprocess(SAMPLE_N, steps=args.warmup + args.steps)
+    t = d["times"][args.warmup:]
+    mean = sum(t) / len(t)
+    value = d["n"] / mean
+    sample = (f"oracle MG-PCG solve (setup excluded) on the same workload family at {SAMPLE_N}^2 "
+              f"({d['n']} DoFs, {d['levels']} levels), {d['iterations'][-1]} iterations")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DoFs/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "DoFs/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "DoFs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2402_12947_gb300 import build, inputs, nnmg
+    build.build()
+
+    meshes = inputs.config_c2(n_fine=args.n_fine, levels=args.levels, seed=2 + 1000 * rank)
+    both = args.precision == "both"
+    t0 = time.perf_counter()
+    H64 = nnmg.Hierarchy.from_meshes(meshes, 2, 0.1) if both else None
+    setup64 = time.perf_counter() - t0
+    lam = [H64.eigs(l)[2] for l in range(H64.num_levels - 1)] if both else None
+    t0 = time.perf_counter()
+    H32 = nnmg.Hierarchy.from_meshes(meshes, 2, 0.1, precision="mixed", lambda_override=lam)
+    setup32 = time.perf_counter() - t0
+    n = H32.num_dofs(0)
+    b_host = inputs.uniform_rhs(n, 2 + rank)
+    b = torch.from_numpy(b_host).cuda()
+    x = torch.zeros_like(b)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    def timed(H, steps, warmup):
+        for _ in range(warmup):
+            info = H.solve(b, x, rtol=RTOL, maxit=500)
+        per = []
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            info = H.solve(b, x, rtol=RTOL, maxit=500)
+            s1.record(stream)
+            per.append((s0, s1))
+        e1.record(stream)
+        barrier()
+        total = e0.elapsed_time(e1) / steps
+        lat = sorted(a.elapsed_time(c) for a, c in per)
+        return total, lat, info
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms32, lat32, info32 = timed(H32, args.steps, max(3, args.warmup))
+    clk = clocks.stop()
+    ms64, lat64, info64 = timed(H64, args.steps, max(3, args.warmup)) if both else (float("nan"), [float("nan")], {})
+    ms_t = torch.tensor([ms32, ms64], device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms32, ms64 = float(ms_t[0]), float(ms_t[1])
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    pin_b = torch.from_numpy(b_host).pin_memory()
+    pin_x = torch.empty_like(pin_b).pin_memory()
+    H32.solve_host(pin_b.numpy(), rtol=RTOL, out=pin_x.numpy())
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        H32.solve_host(pin_b.numpy(), rtol=RTOL, out=pin_x.numpy())
+    barrier()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    e2e_t = torch.tensor([e2e_ms], device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
+    e2e_ms = float(e2e_t[0])
+
+    # the dominant kernel: fine-level fused Chebyshev SpMV of the FP32 V-cycle
+    kms, kbytes = H32.time_smoother_kernel(reps=50)
+    kms64, kbytes64 = H64.time_smoother_kernel(reps=50) if both else (float("nan"), float("nan"))
+    peak, peak_src = measured_peak()
+    traffic, rev = profiled_traffic()
+    if rev != KERNEL_REV:
+        traffic = None
+    per_vc, per_it = H32.launch_counts()
+    launches = per_it * info32["iterations"] + 8   # head, CG init and the true-residual check
+    if rank != 0:
+        return 0
+    cpu = None
+    if not args.no_cpu_baseline:
+        d = cpu_baseline_subprocess(SAMPLE_N, steps=1)
+        cpu = {"value": d["n"] / d["times"][0], "unit": "DoFs/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle MG-PCG solve (setup excluded) on the same family at {SAMPLE_N}^2 "
+                         f"({d['n']} DoFs, {d['levels']} levels, {d['iterations'][0]} iterations, "
+                         f"{d['times'][0]:.1f} s), single-threaded NumPy/SciPy"}
+    value = n * world / (ms32 * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "DoFs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}", "rtol": RTOL,
+                   "l2": "inputs larger than L2 (A_0 alone 0.58 GB FP64 / 0.39 GB FP32)",
+                   "dofs_per_gpu": n, "levels": H32.num_levels},
+        "iterations": {"mixed": info32["iterations"], "fp64": info64.get("iterations")},
+        "p50_ms": lat32[len(lat32) // 2], "p99_ms": lat32[min(len(lat32) - 1, int(0.99 * len(lat32)))],
+        "fp64": {"value": n * world / (ms64 * 1e-3), "ms_per_step": ms64, "iterations": info64.get("iterations"),
+                 "p50_ms": lat64[len(lat64) // 2], "p99_ms": lat64[min(len(lat64) - 1, int(0.99 * len(lat64)))],
+                 "true_rel_residual": info64.get("true_rel_residual")} if both else None,
+        "true_rel_residual": info32["true_rel_residual"],
+        "e2e": {"value": n * world / (e2e_ms * 1e-3), "unit": "DoFs/s", "h2d_bytes_per_step": 8 * n,
+                "d2h_bytes_per_step": 8 * n},
+        "gpu_launches": launches * args.steps,
+        "roofline": {"bound": "hbm", "achieved": kbytes / (kms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": kbytes / (kms * 1e-3) / 1e9 / peak, "traffic": traffic,
+                     "kernel": "fine-level fused Chebyshev SELL-32 SpMV, FP32 (k_sell_cheb<float,false>)",
+                     "bytes_per_launch": kbytes, "ms_per_launch": kms, "peak_source": peak_src,
+                     "fp64_kernel": {"achieved": kbytes64 / (kms64 * 1e-3) / 1e9, "ms_per_launch": kms64,
+                                     "bytes_per_launch": kbytes64}},
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "setup_s": {"fp64": setup64 if both else None, "mixed": setup32},
+        "device_bytes": {"fp64": H64.device_bytes() if both else None, "mixed": H32.device_bytes()},
+    }
+    print(json.dumps(line), flush=True)
+    if H64 is not None:
+        H64.close()
+    H32.close()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

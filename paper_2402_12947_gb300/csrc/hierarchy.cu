@@ -536,32 +536,32 @@ struct CgRunner {
   T* vx() { return e.lv[0].x; }
   int launches = 0;
 
-  void tail(cudaStream_t s, unsigned long long cond) {
+  void tail(cudaStream_t s, int use_cond, unsigned long long cond) {
     int na = 0;
     sell_ap(h->A0, h->cp, h->cq, h->part, &na, s);
-    cg_finish(na, h->part, h->st, FIN_PQ, 0, s);
+    cg_finish(na, h->part, h->st, FIN_PQ, 0, 0, s);
     cg_update<T>(h->n0, h->st, h->cp, h->cq, h->cx, h->cr, vb(), vx(), h->part, s);
-    cg_finish(h->nparts, h->part, h->st, FIN_RR, cond, s);
+    cg_finish(h->nparts, h->part, h->st, FIN_RR, use_cond, cond, s);
     launches += 4;
   }
-  void head(cudaStream_t s, unsigned long long cond) {
+  void head(cudaStream_t s, int use_cond, unsigned long long cond) {
     cg_init<T>(h->n0, h->cb, h->cr, h->cx, vb(), vx(), h->part, s);
-    cg_finish(h->nparts, h->part, h->st, FIN_BB, 0, s);
+    cg_finish(h->nparts, h->part, h->st, FIN_BB, 0, 0, s);
     e.launches = 0;
     e.cycle(0, s);
     cg_dotz<T>(h->n0, h->cr, vx(), h->cz, h->cp, true, h->part, s);
-    cg_finish(h->nparts, h->part, h->st, FIN_RZ0, 0, s);
+    cg_finish(h->nparts, h->part, h->st, FIN_RZ0, 0, 0, s);
     launches += 4 + e.launches;
-    tail(s, cond);
+    tail(s, use_cond, cond);
   }
-  void body(cudaStream_t s, unsigned long long cond) {
+  void body(cudaStream_t s, int use_cond, unsigned long long cond) {
     e.launches = 0;
     e.cycle(0, s);
     cg_dotz<T>(h->n0, h->cr, vx(), h->cz, h->cp, false, h->part, s);
-    cg_finish(h->nparts, h->part, h->st, FIN_RZ, 0, s);
+    cg_finish(h->nparts, h->part, h->st, FIN_RZ, 0, 0, s);
     cg_pupdate(h->n0, h->st, h->cz, h->cp, s);
     launches = 3 + e.launches;
-    tail(s, cond);
+    tail(s, use_cond, cond);
   }
 };
 
@@ -583,7 +583,7 @@ void build_graph(mg_hierarchy* h) {
   cudaGraphConditionalHandle handle;
   CK(cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault));
   CK(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  dispatch(h, [&](auto& r) { r.head(s, (unsigned long long)handle); });
+  dispatch(h, [&](auto& r) { r.head(s, 1, (unsigned long long)handle); });
   cudaStreamCaptureStatus cs;
   const cudaGraphNode_t* deps = nullptr;
   size_t ndeps = 0;
@@ -599,7 +599,7 @@ void build_graph(mg_hierarchy* h) {
   CK(cudaStreamUpdateCaptureDependencies(s, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
   CK(cudaStreamEndCapture(s, &g));
   CK(cudaStreamBeginCaptureToGraph(s, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  dispatch(h, [&](auto& r) { r.body(s, (unsigned long long)handle); });
+  dispatch(h, [&](auto& r) { r.body(s, 1, (unsigned long long)handle); });
   CK(cudaStreamEndCapture(s, &bodyg));
   CK(cudaGraphInstantiate(&h->graph, g, 0));
   CK(cudaGraphDestroy(g));
@@ -614,7 +614,7 @@ void count_launches(mg_hierarchy* h) {
     r.e.launches = 0;
     r.e.cycle(0, s);
     h->launches_vcycle = r.e.launches;
-    r.body(s, 0);
+    r.body(s, 0, 0);
     h->launches_iter = r.launches;
     CK(cudaStreamEndCapture(s, &g));
     CK(cudaGraphDestroy(g));
@@ -630,13 +630,13 @@ int run_solve(mg_hierarchy* h, double rtol, int maxit, mg_solve_info_t* info, cu
   if (h->graph) {
     CK(cudaGraphLaunch(h->graph, s));
   } else {
-    dispatch(h, [&](auto& r) { r.head(s, 0); });
+    dispatch(h, [&](auto& r) { r.head(s, 0, 0); });
     check_launch("cg head");
     for (;;) {
       CK(cudaMemcpyAsync(h->hst, h->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       if (!h->hst->cont) break;
-      dispatch(h, [&](auto& r) { r.body(s, 0); });
+      dispatch(h, [&](auto& r) { r.body(s, 0, 0); });
       check_launch("cg body");
     }
   }
@@ -646,7 +646,7 @@ int run_solve(mg_hierarchy* h, double rtol, int maxit, mg_solve_info_t* info, cu
   CK(cudaMemcpyAsync(h->hst, h->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   CgState st = *h->hst;
-  cg_finish(h->nparts, h->part, h->st, FIN_NORM, 0, s);
+  cg_finish(h->nparts, h->part, h->st, FIN_NORM, 0, 0, s);
   CK(cudaMemcpyAsync(h->hst, h->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   double true_rr = h->hst->rr;
@@ -1076,7 +1076,7 @@ int mg_solve_stationary(mg_hierarchy_t* h, const double* b, double* x, double rt
   cudaStream_t s = (cudaStream_t)stream;
   auto norm2 = [&](const double* v) {
     dot_self(h->n0, v, h->part, s);
-    cg_finish(h->nparts, h->part, h->st, FIN_NORM, 0, s);
+    cg_finish(h->nparts, h->part, h->st, FIN_NORM, 0, 0, s);
     CK(cudaMemcpyAsync(h->hst, h->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return h->hst->rr;

@@ -222,6 +222,8 @@ __global__ void k_axpy_from(int n, const T* __restrict__ z, double* __restrict__
 }
 
 constexpr int kCgBlocks = 152 * 4;
+// Absolute bound on CG iterations inside one graph launch, whatever maxit says.
+constexpr int kMaxCgIterations = 100000;
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_cg_init(int n, const double* __restrict__ b, double* __restrict__ r,
@@ -288,7 +290,7 @@ __global__ void __launch_bounds__(kBlock) k_dot_self(int n, const double* __rest
 }
 
 __global__ void __launch_bounds__(1024) k_cg_finish(int nparts, const double* __restrict__ part, CgState* st, int op,
-                                                    unsigned long long handle) {
+                                                    int use_cond, unsigned long long handle) {
   double s = 0.0;
   for (int i = threadIdx.x; i < nparts; i += 1024) s += part[i];
   s = block_sum(s);
@@ -320,10 +322,10 @@ __global__ void __launch_bounds__(1024) k_cg_finish(int nparts, const double* __
       int cont = 1;
       if (st->status == 3) cont = 0;
       else if (s <= st->rtol2 * st->bb) st->status = 1, cont = 0;
-      else if (st->it >= st->maxit) st->status = 2, cont = 0;
+      else if (st->it >= st->maxit || st->it >= kMaxCgIterations) st->status = 2, cont = 0;
       if (!isfinite(s)) st->status = 3, cont = 0;
       st->cont = cont;
-      if (handle) cudaGraphSetConditional((cudaGraphConditionalHandle)handle, (unsigned)cont);
+      if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)handle, (unsigned)cont);
       break;
     }
     case FIN_RZ:
@@ -505,8 +507,9 @@ void cg_dotz(int n, const double* r, const T* vx, double* z, double* p, bool fir
 void cg_pupdate(int n, const CgState* st, const double* z, double* p, cudaStream_t s) {
   k_cg_pupdate<<<cg_parts(n), kBlock, 0, s>>>(n, st, z, p);
 }
-void cg_finish(int nparts, const double* part, CgState* st, int op, unsigned long long cond_handle, cudaStream_t s) {
-  k_cg_finish<<<1, 1024, 0, s>>>(nparts, part, st, op, cond_handle);
+void cg_finish(int nparts, const double* part, CgState* st, int op, int use_cond, unsigned long long cond_handle,
+               cudaStream_t s) {
+  k_cg_finish<<<1, 1024, 0, s>>>(nparts, part, st, op, use_cond, cond_handle);
 }
 void dot_self(int n, const double* r, double* part, cudaStream_t s) {
   k_dot_self<<<cg_parts(n), kBlock, 0, s>>>(n, r, part);

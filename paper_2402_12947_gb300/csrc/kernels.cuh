@@ -101,9 +101,11 @@ void cg_update(int n, const CgState* st, const double* p, const double* q, doubl
 template <typename T>
 void cg_dotz(int n, const double* r, const T* vx, double* z, double* p, bool first, double* part, cudaStream_t s);
 void cg_pupdate(int n, const CgState* st, const double* z, double* p, cudaStream_t s);
-// Sum the partials in a fixed order and apply `op` to the CG state. With a non-zero
-// conditional handle, FIN_RR also sets the while-node condition (continue iterating).
-void cg_finish(int nparts, const double* part, CgState* st, int op, unsigned long long cond_handle, cudaStream_t s);
+// Sum the partials in a fixed order and apply `op` to the CG state. With use_cond set
+// (inside a captured graph), FIN_RR also sets the while-node condition through
+// `cond_handle`: 1 to iterate again, 0 once converged, at maxit, or on breakdown.
+void cg_finish(int nparts, const double* part, CgState* st, int op, int use_cond, unsigned long long cond_handle,
+               cudaStream_t s);
 // partial sums of |r|^2 for r = b - A x (a true-residual check)
 void dot_self(int n, const double* r, double* part, cudaStream_t s);
 
