@@ -44,6 +44,13 @@ def parse():
     ap.add_argument("--n-fine", type=int, default=1024)
     ap.add_argument("--levels", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch every kernel individually instead of one CUDA graph per solve (profilers "
+                         "cannot see kernel nodes of graphs with conditional nodes)")
+    ap.add_argument("--workload", default="c2", choices=["c2", "serve"],
+                    help="'serve': the mixed request stream through the continuous-batching server")
+    ap.add_argument("--requests", type=int, default=512)
+    ap.add_argument("--rates", default="4,16,64", help="Poisson arrival rates (requests/s) to sweep")
     ap.add_argument("--precision", default="both", choices=["both", "mixed"],
                     help="'mixed' builds and times only the mixed-precision form (profiling runs)")
     return ap.parse_args()
@@ -80,7 +87,7 @@ def profiled_traffic():
     return None, None
 
 
-KERNEL_REV = "sell32-v1"   # bump when the timed kernel changes (invalidates the profiled traffic)
+KERNEL_REV = "sell32-v2"   # bump when the timed kernel changes (invalidates the profiled traffic)
 
 
 class ClockSampler:
@@ -197,11 +204,12 @@ def run_ours(args):
     meshes = inputs.config_c2(n_fine=args.n_fine, levels=args.levels, seed=2 + 1000 * rank)
     both = args.precision == "both"
     t0 = time.perf_counter()
-    H64 = nnmg.Hierarchy.from_meshes(meshes, 2, 0.1) if both else None
+    graph = 0 if args.no_graph else 1
+    H64 = nnmg.Hierarchy.from_meshes(meshes, 2, 0.1, use_graph=graph) if both else None
     setup64 = time.perf_counter() - t0
     lam = [H64.eigs(l)[2] for l in range(H64.num_levels - 1)] if both else None
     t0 = time.perf_counter()
-    H32 = nnmg.Hierarchy.from_meshes(meshes, 2, 0.1, precision="mixed", lambda_override=lam)
+    H32 = nnmg.Hierarchy.from_meshes(meshes, 2, 0.1, precision="mixed", lambda_override=lam, use_graph=graph)
     setup32 = time.perf_counter() - t0
     n = H32.num_dofs(0)
     b_host = inputs.uniform_rhs(n, 2 + rank)
@@ -285,6 +293,7 @@ def run_ours(args):
         "warmup": max(3, args.warmup), "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}", "rtol": RTOL,
+                   "launch": "per-kernel launches" if args.no_graph else "one CUDA graph per solve (conditional while)",
                    "l2": "inputs larger than L2 (A_0 alone 0.58 GB FP64 / 0.39 GB FP32)",
                    "dofs_per_gpu": n, "levels": H32.num_levels},
         "iterations": {"mixed": info32["iterations"], "fp64": info64.get("iterations")},
@@ -314,10 +323,76 @@ def run_ours(args):
     return 0
 
 
+def serve_stream(n_requests: int, seed: int = 5):
+    """The seeded request stream: (meshes, degree, rhs, label) per request."""
+    import numpy as np
+    from paper_2402_12947_gb300 import inputs
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_requests):
+        meshes, degree, label = inputs.serving_request(rng, seed * 100000 + k)
+        n = meshes[0].n
+        dim = meshes[0].dim
+        nfree = (n - 1) ** dim if degree == 1 else (2 * n - 1) ** dim
+        out.append((meshes, degree, inputs.uniform_rhs(nfree, seed * 100000 + k), label))
+    return out
+
+
+def run_serve(args):
+    """Continuous-batching server on the mixed stream at several Poisson arrival rates."""
+    import numpy as np
+    import torch
+    from paper_2402_12947_gb300 import build, nnmg
+    build.build()
+    torch.cuda.set_device(0)
+    stream = serve_stream(args.requests)
+    free, total = torch.cuda.mem_get_info()
+    budget = int(0.5 * free)
+    results = {}
+    for prec in ("mixed", "fp64"):
+        for rate in [float(r) for r in args.rates.split(",")]:
+            arrivals = np.cumsum(np.random.default_rng(7).exponential(1.0 / rate, len(stream)))
+            with nnmg.Server(hbm_budget_bytes=budget, max_active=16, setup_threads=12) as srv:
+                t0 = time.perf_counter()
+                ids = []
+                for (meshes, degree, b, _), ta in zip(stream, arrivals):
+                    now = time.perf_counter() - t0
+                    if ta > now:
+                        time.sleep(ta - now)
+                    ids.append(srv.submit(meshes, degree, b=b, rtol=RTOL, precision=prec))
+                res = [srv.wait(i, timeout=3600) for i in ids]
+                wall = time.perf_counter() - t0
+                for i, r in zip(ids, res):
+                    srv.fetch(i, r["n"])
+                st = srv.stats()
+            lat = np.array([r["t_total_ms"] for r in res])
+            ok = [r for r in res if r["status"] == 0]
+            dofs = sum(r["n"] for r in ok)
+            results[f"{prec}@{rate:g}/s"] = {
+                "throughput_dofs_per_s": dofs / wall, "requests_per_s": len(ok) / wall,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "p50_device_ms": float(np.percentile([r["t_device_ms"] for r in res], 50)),
+                "failed": len(res) - len(ok), "peak_active": st["peak_active"], "peak_bytes": st["peak_bytes"],
+                "max_true_rel_residual": max(r["true_rel_residual"] for r in ok) if ok else None,
+                "mean_iterations": float(np.mean([r["iterations"] for r in ok])) if ok else None}
+    best = max(results.values(), key=lambda d: d["throughput_dofs_per_s"])
+    line = {"metric": METRIC, "value": best["throughput_dofs_per_s"], "unit": "DoFs/s", "n_gpus": 1,
+            "steps": args.requests, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"serving: {args.requests} seeded requests, Poisson arrivals, mixed 2D P1/P2 "
+                                   "32^2-512^2 and 3D P1 16^3-64^3 with 0-16 clusters, rtol 1e-8",
+                       "hbm_budget_bytes": budget, "max_active": 16},
+            "serve": results}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

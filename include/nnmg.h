@@ -106,8 +106,9 @@ typedef struct mg_options_t {
                               convergence test (conditional while node) (1) */
   int32_t local_levels_mask; /* bit l set: local correction on level l (-1 = all) */
   double quality_threshold;  /* set by mg_setup from its argument; ignored by mg_setup_csr */
-  int32_t sell_sigma;      /* rows sorted by length within windows of this many rows before
-                              SELL-32 slicing (1 = no sorting) (1) */
+  int32_t sell_sigma;      /* SELL-32 slot order: rows sorted by length within windows of this
+                              many rows (1 = natural order); 0 = autotune: time y = A x on the
+                              device for windows {1, 256, 2048} per operator, keep the fastest (0) */
   int32_t reserved[5];
 } mg_options_t;
 
@@ -237,6 +238,65 @@ int mg_coarse_solve(mg_hierarchy_t* h, const double* b_dev, double* x_dev, void*
  * per launch (matrix once, vectors once). Vectors are the hierarchy's own work buffers. */
 int mg_time_smoother_kernel(mg_hierarchy_t* h, int32_t reps, void* stream, double* ms_per_launch,
                             double* bytes_per_launch);
+
+/* ---- solve server: continuous batching of solve requests on one GPU ----------------
+ * (the benchmark spec serving pattern; the paper has no serving counterpart.)
+ * Requests (a mesh hierarchy and a right-hand side) go through host set-up on worker
+ * threads, wait for admission in submission order until their device-byte estimate fits
+ * under the HBM budget and one of max_active slots is free, then are set up on the device
+ * and solved by MG-PCG on their own stream, overlapping with the other active requests.
+ * Completion frees the request's device memory and admits the next ones. */
+typedef struct mg_server mg_server_t;
+
+typedef struct mg_request_t {
+  const mg_mesh_t* levels;     /* [L] host meshes, copied at submission */
+  int32_t L;
+  int32_t degree;              /* 1 or 2 */
+  double quality_threshold;    /* 0.1 in the paper */
+  const mg_options_t* opt;     /* NULL = defaults; use_graph is forced on */
+  const double* b;             /* [n_b] right-hand side on the level-0 free DoFs, or NULL: f = 1 */
+  int64_t n_b;
+  double rtol;
+  int32_t maxit;
+  int32_t reserved;
+} mg_request_t;
+
+typedef struct mg_request_result_t {
+  int32_t status;              /* -1 while pending; then MG_OK or an error code */
+  int32_t iterations;
+  double rel_residual;
+  double true_rel_residual;
+  int64_t n;                   /* free DoFs of level 0 */
+  int64_t device_bytes;        /* device memory the request held */
+  double t_queue_ms;           /* submission -> host set-up start */
+  double t_setup_ms;           /* host set-up */
+  double t_wait_ms;            /* host set-up done -> admitted to the device */
+  double t_device_ms;          /* admitted -> solution on the host (device set-up + solve) */
+  double t_total_ms;           /* submission -> done */
+} mg_request_result_t;
+
+typedef struct mg_server_stats_t {
+  int64_t submitted, completed, failed;
+  int64_t bytes_in_use, peak_bytes;
+  int32_t active, peak_active, queued, reserved;
+} mg_server_stats_t;
+
+/* Create a server with an HBM budget (bytes), max_active concurrent requests on the device
+ * and setup_threads host set-up workers. */
+int mg_server_create(int64_t hbm_budget_bytes, int32_t max_active, int32_t setup_threads, mg_server_t** out);
+/* Queue a request (inputs copied); *id identifies it. Never blocks on the device. */
+int mg_server_submit(mg_server_t* s, const mg_request_t* req, int64_t* id);
+/* Current state of a request (status -1 while pending). */
+int mg_server_poll(mg_server_t* s, int64_t id, mg_request_result_t* out);
+/* Block until the request is done or timeout_s passes (MG_ERR_TIMEOUT). */
+int mg_server_wait(mg_server_t* s, int64_t id, double timeout_s, mg_request_result_t* out);
+/* Copy a finished request's solution (x_host[n], n = result.n; NULL to discard) and forget it. */
+int mg_server_fetch(mg_server_t* s, int64_t id, double* x_host, int64_t n);
+int mg_server_stats(mg_server_t* s, mg_server_stats_t* out);
+/* Message of the last failed server call in this thread. */
+const char* mg_server_last_error(void);
+/* Finish the requests already admitted, fail the rest, free everything. */
+void mg_server_destroy(mg_server_t* s);
 
 /* Device bytes held by the hierarchy. */
 int64_t mg_device_bytes(const mg_hierarchy_t* h);

@@ -17,7 +17,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <type_traits>
 
@@ -51,24 +53,28 @@ struct PhaseTimer {
                   std::string(#x) + ": " + cudaGetErrorString(e_));                                      \
   } while (0)
 
-// Device allocations owned by one hierarchy (zero-filled on allocation).
+// Device allocations owned by one hierarchy, stream-ordered on `stream` (cudaMallocAsync
+// from the device's default pool, zero-filled; freed with cudaFreeAsync), so that building
+// or freeing one hierarchy never synchronises the device under other hierarchies' solves.
 struct DevMem {
+  cudaStream_t stream = nullptr;
   std::vector<void*> ptrs;
   int64_t bytes = 0;
   template <typename T>
   T* alloc(size_t n) {
     if (n == 0) return nullptr;
     void* p = nullptr;
-    CK(cudaMalloc(&p, n * sizeof(T)));
+    CK(cudaMallocAsync(&p, n * sizeof(T), stream));
     ptrs.push_back(p);
     bytes += (int64_t)(n * sizeof(T));
-    CK(cudaMemset(p, 0, n * sizeof(T)));
+    CK(cudaMemsetAsync(p, 0, n * sizeof(T), stream));
     return (T*)p;
   }
+  // The host buffer may be released as soon as this returns (pageable copies are staged).
   template <typename T>
   T* upload(const T* src, size_t n) {
     T* p = alloc<T>(n);
-    if (p) CK(cudaMemcpy(p, src, n * sizeof(T), cudaMemcpyHostToDevice));
+    if (p) CK(cudaMemcpyAsync(p, src, n * sizeof(T), cudaMemcpyHostToDevice, stream));
     return p;
   }
   template <typename T>
@@ -76,25 +82,53 @@ struct DevMem {
     return upload(v.data(), v.size());
   }
   void release() {
-    for (void* p : ptrs) cudaFree(p);
+    for (void* p : ptrs) cudaFreeAsync(p, stream);
     ptrs.clear();
     bytes = 0;
   }
 };
 
-// Host CSR -> device SELL-32 (values converted to T).
+// Slot order of a SELL-32 layout: rows sorted by length (descending, stable) inside
+// consecutive windows of `sigma` rows; identity for sigma <= 1.
+std::vector<int32_t> sell_order(const Csr& A, int sigma) {
+  std::vector<int32_t> ord(A.nrows);
+  for (int64_t i = 0; i < A.nrows; ++i) ord[i] = (int32_t)i;
+  if (sigma <= 1) return ord;
+  for (int64_t w0 = 0; w0 < A.nrows; w0 += sigma) {
+    int64_t w1 = std::min<int64_t>(A.nrows, w0 + sigma);
+    std::stable_sort(ord.begin() + w0, ord.begin() + w1, [&](int32_t a, int32_t b) {
+      return A.rp[a + 1] - A.rp[a] > A.rp[b + 1] - A.rp[b];
+    });
+  }
+  return ord;
+}
+
+// Padded entries of the SELL-32 layout for a slot order.
+int64_t sell_padded(const Csr& A, const std::vector<int32_t>& ord) {
+  int64_t tot = 0;
+  for (int64_t s0 = 0; s0 < A.nrows; s0 += 32) {
+    int32_t w = 0;
+    for (int64_t k = s0; k < std::min<int64_t>(A.nrows, s0 + 32); ++k) w = std::max(w, A.rp[ord[k] + 1] - A.rp[ord[k]]);
+    tot += 32 * (int64_t)w;
+  }
+  return tot;
+}
+
+// Host CSR -> device SELL-32 (values converted to T), slots in the order of sell_order.
 template <typename T>
-SellMat<T> make_sell(const Csr& A, DevMem& mem) {
+SellMat<T> make_sell(const Csr& A, DevMem& mem, int sigma = 1) {
   SellMat<T> S;
   S.nrows = (int32_t)A.nrows;
   S.ncols = (int32_t)A.ncols;
   S.nnz = A.nnz();
+  S.sigma = std::max(1, sigma);
   S.nslices = (int32_t)((A.nrows + 31) / 32);
+  std::vector<int32_t> ord = sell_order(A, sigma);
   std::vector<int64_t> off(S.nslices + 1, 0);
   for (int32_t s = 0; s < S.nslices; ++s) {
     int32_t w = 0;
-    for (int64_t r = (int64_t)s * 32; r < std::min<int64_t>(A.nrows, (int64_t)s * 32 + 32); ++r)
-      w = std::max(w, A.rp[r + 1] - A.rp[r]);
+    for (int64_t k = (int64_t)s * 32; k < std::min<int64_t>(A.nrows, (int64_t)s * 32 + 32); ++k)
+      w = std::max(w, A.rp[ord[k] + 1] - A.rp[ord[k]]);
     off[s + 1] = off[s] + 32 * (int64_t)w;
   }
   S.padded = off[S.nslices];
@@ -104,8 +138,9 @@ SellMat<T> make_sell(const Csr& A, DevMem& mem) {
     for (int64_t s = lo; s < hi; ++s) {
       int64_t w = (off[s + 1] - off[s]) / 32;
       for (int lane = 0; lane < 32; ++lane) {
-        int64_t r = s * 32 + lane;
-        int32_t len = r < A.nrows ? A.rp[r + 1] - A.rp[r] : 0;
+        int64_t k = s * 32 + lane;
+        int64_t r = k < A.nrows ? ord[k] : -1;
+        int32_t len = r >= 0 ? A.rp[r + 1] - A.rp[r] : 0;
         int32_t pad_col = len > 0 ? A.ci[A.rp[r + 1] - 1] : 0;
         for (int64_t j = 0; j < w; ++j) {
           int64_t o = off[s] + j * 32 + lane;
@@ -122,7 +157,91 @@ SellMat<T> make_sell(const Csr& A, DevMem& mem) {
   S.off = mem.upload(off);
   S.col = mem.upload(col);
   S.val = mem.upload(val);
+  if (sigma > 1) S.perm = mem.upload(ord);
   return S;
+}
+
+// Autotuner: for sigma = 0 (auto) time y = A x for each candidate window on the device
+// (CUDA events, after a warm-up launch) and keep the fastest layout; the candidates whose
+// padding equals an earlier candidate's are skipped. Other sigma values are used as given.
+// Host CSR -> device CSR-vector layout (G lanes per row; values converted to T).
+template <typename T>
+SellMat<T> make_csrv(const Csr& A, DevMem& mem, int lanes) {
+  SellMat<T> S;
+  S.nrows = (int32_t)A.nrows;
+  S.ncols = (int32_t)A.ncols;
+  S.nnz = A.nnz();
+  S.padded = A.nnz();
+  S.lanes = lanes;
+  std::vector<T> val(A.v.begin(), A.v.end());
+  S.rp = mem.upload(A.rp);
+  S.col = mem.upload(A.ci);
+  S.val = mem.upload(val);
+  return S;
+}
+
+struct Layout {
+  int lanes, sigma;
+};
+
+template <typename T>
+SellMat<T> make_layout(const Csr& A, DevMem& mem, Layout L) {
+  return L.lanes > 1 ? make_csrv<T>(A, mem, L.lanes) : make_sell<T>(A, mem, L.sigma);
+}
+
+// Autotuner (sigma option 0): time y = A x on the device for each candidate layout
+// (SELL-32 with windows 1, 256, 2048 when sorting removes padding; CSR vector with 4, 8,
+// 16, 32 lanes per row up to twice the longest row) and keep the fastest. Timing: one
+// warm-up launch, then the mean of 5 launches between CUDA events.
+template <typename T>
+SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log) {
+  if (sigma != 0 || A.nrows == 0) return make_sell<T>(A, mem, std::max(sigma, 1));
+  int maxlen = 0;
+  for (int64_t i = 0; i < A.nrows; ++i) maxlen = std::max(maxlen, A.rp[i + 1] - A.rp[i]);
+  std::vector<Layout> cand;
+  int64_t last_pad = -1;
+  for (int c : {1, 256, 2048}) {
+    int64_t pad = sell_padded(A, sell_order(A, c));
+    if (last_pad >= 0 && pad >= (int64_t)(0.995 * (double)last_pad)) continue;  // sorting gains nothing more
+    last_pad = pad;
+    cand.push_back({1, c});
+  }
+  for (int g : {4, 8, 16, 32})
+    if (g <= 2 * std::max(maxlen, 2)) cand.push_back({g, 1});
+  DevMem scratch;
+  scratch.stream = mem.stream;
+  const cudaStream_t st = mem.stream;
+  T* x = scratch.alloc<T>(std::max<int64_t>(A.ncols, 1));
+  T* y = scratch.alloc<T>(std::max<int64_t>(A.nrows, 1));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  Layout best = cand[0];
+  float best_ms = -1.f;
+  for (const Layout& c : cand) {
+    DevMem trial;
+    trial.stream = st;
+    SellMat<T> S = make_layout<T>(A, trial, c);
+    sell_spmv<T>(S, x, y, st);
+    CK(cudaEventRecord(e0, st));
+    for (int rep = 0; rep < 5; ++rep) sell_spmv<T>(S, x, y, st);
+    CK(cudaEventRecord(e1, st));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    trial.release();
+    if (log)
+      *log += std::string(" ") + (c.lanes > 1 ? "v" + std::to_string(c.lanes) : "s" + std::to_string(c.sigma)) + ":" +
+              std::to_string((int)(ms / 5 * 1e3)) + "us";
+    if (best_ms < 0 || ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  scratch.release();
+  return make_layout<T>(A, mem, best);
 }
 
 template <typename T>
@@ -138,6 +257,10 @@ struct DevLevel {
   int64_t* inv_off = nullptr;
   double *inv = nullptr, *rbuf = nullptr;
   PatchItem* items = nullptr;
+  // rows coupled to patch DoFs, with their entries of A (first Chebyshev step after S_c)
+  int nh = 0;
+  int32_t *hrow = nullptr, *hrp = nullptr, *hci = nullptr;
+  T* hv = nullptr;
 };
 
 }  // namespace
@@ -156,12 +279,19 @@ struct Engine {
   bool local_on(int l) const {
     return lv[l].np > 0 && order != MG_SMOOTHER_GLOBAL && ((local_mask >> std::min(l, 31)) & 1u);
   }
-  void cheb(int l, cudaStream_t s) {
+  // zero: 0 = general iterate, 1 = x is zero, 2 = x is zero outside the patch DoFs
+  void cheb(int l, cudaStream_t s, int zero = 0) {
     DevLevel<T>& L = lv[l];
     T *xa = L.x, *xb = L.xt;
     for (int j = 0; j < cheb_k; ++j) {
-      sell_cheb<T>(L.A, xa, L.b, L.dinv, L.d, xb, L.cd[j], L.cr[j], j == 0, s);
-      ++launches;
+      if (j == 0 && zero) {
+        const int nh = zero == 2 ? L.nh : 0;
+        cheb_first_from_zero<T>(L.n, L.b, L.dinv, xa, L.d, xb, L.cr[0], nh, L.hrow, L.hrp, L.hci, L.hv, s);
+        launches += nh > 0 ? 2 : 1;
+      } else {
+        sell_cheb<T>(L.A, xa, L.b, L.dinv, L.d, xb, L.cd[j], L.cr[j], j == 0, s);
+        ++launches;
+      }
       std::swap(xa, xb);
     }
     if (xa != L.x) {
@@ -169,23 +299,24 @@ struct Engine {
       ++launches;
     }
   }
-  void local(int l, cudaStream_t s) {
+  void local(int l, cudaStream_t s, bool zero = false) {
     DevLevel<T>& L = lv[l];
-    patch_residual<T>(L.nt, L.pdofs, L.prp, L.pci, L.pv, L.b, L.x, L.rbuf, s);
+    patch_residual<T>(L.nt, L.pdofs, L.prp, L.pci, L.pv, L.b, zero ? nullptr : L.x, L.rbuf, s);
     patch_solve<T>(L.nitems, L.items, L.pptr, L.pdofs, L.inv_off, L.inv, L.rbuf, L.x, L.max_patch, s);
     launches += 2;
   }
-  void smooth(int l, bool post, cudaStream_t s) {
+  // zero: the iterate is zero on entry (first pre-smoothing on every level of a cycle)
+  void smooth(int l, bool post, cudaStream_t s, bool zero = false) {
     if (!local_on(l)) {
-      cheb(l, s);
+      cheb(l, s, zero ? 1 : 0);
       return;
     }
     if (order == MG_SMOOTHER_SANDWICH) {
-      local(l, s);
-      cheb(l, s);
+      local(l, s, zero);
+      cheb(l, s, zero ? 2 : 0);
       local(l, s);
     } else if (!post) {
-      cheb(l, s);
+      cheb(l, s, zero ? 1 : 0);
       local(l, s);
     } else {
       local(l, s);
@@ -213,7 +344,7 @@ struct Engine {
       coarse(s);
       return;
     }
-    for (int k = 0; k < nu; ++k) smooth(l, false, s);
+    for (int k = 0; k < nu; ++k) smooth(l, false, s, k == 0);
     residual_restrict(l, s);
     cycle(l + 1, s);
     prolong(l, s);
@@ -255,11 +386,14 @@ struct mg_hierarchy {
     else f(*e32);
   }
   ~mg_hierarchy() {
-    if (device) cudaDeviceSynchronize();
+    if (own_stream) cudaStreamSynchronize(own_stream);
     if (graph) cudaGraphExecDestroy(graph);
-    if (own_stream) cudaStreamDestroy(own_stream);
-    if (hst) cudaFreeHost(hst);
     mem.release();
+    if (own_stream) {
+      cudaStreamSynchronize(own_stream);
+      cudaStreamDestroy(own_stream);
+    }
+    if (hst) pinned_release(reinterpret_cast<double*>(hst));
   }
 };
 
@@ -274,6 +408,7 @@ void validate_options(const mg_options_t& o) {
   if (o.precision < 0 || o.precision > 1) throw Error(MG_ERR_INVALID_ARG, "unknown precision");
   if (!(o.lmin_ratio > 0 && o.lmin_ratio < 1)) throw Error(MG_ERR_INVALID_ARG, "lmin_ratio must be in (0, 1)");
   if (!(o.lmax_safety > 0)) throw Error(MG_ERR_INVALID_ARG, "lmax_safety must be positive");
+  if (o.sell_sigma < 0 || o.sell_sigma > (1 << 20)) throw Error(MG_ERR_INVALID_ARG, "sell_sigma must be in [0, 2^20]");
 }
 
 // Chebyshev coefficients per step: d = cd d + cr D^{-1} r (Sec. 3.2 three-term recurrence).
@@ -291,7 +426,7 @@ void cheb_coefficients(double lmax, double lmin, int k, std::vector<double>& cd,
 
 // Everything after the operators are known: diagonals, patch inverses, eigenvalues,
 // coarsest inverse, then (unless host_only) the device upload and the solve graph.
-void finish_setup(mg_hierarchy* h) {
+void finish_setup_host(mg_hierarchy* h) {
   const mg_options_t& o = h->opt;
   const int L = h->L;
   PhaseTimer tm;
@@ -333,13 +468,23 @@ void finish_setup(mg_hierarchy* h) {
   }
   const int64_t ncoarse = h->host[L - 1].A.nrows;
   if (ncoarse > 20000) throw Error(MG_ERR_INVALID_ARG, "coarsest level too large for the dense direct solve (> 20000 DoFs)");
-  if (o.host_only) return;
+}
+
+// Device phase of set-up: upload, batched dense inverses, autotuned layouts. All work is
+// ordered on the hierarchy's own stream, which is synchronised before returning.
+void build_device(mg_hierarchy* h) {
+  const mg_options_t& o = h->opt;
+  const int L = h->L;
+  PhaseTimer tm;
+  const int64_t ncoarse = h->host[L - 1].A.nrows;
 
   // ---- device upload ----
   int dev_count = 0;
   if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0) throw Error(MG_ERR_NO_DEVICE, "no CUDA device");
+  if (!h->own_stream) CK(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
   h->device = true;
   DevMem& mem = h->mem;
+  mem.stream = h->own_stream;
   int max_patch = 0;
   // All dense blocks (every patch matrix A[B_d, B_d] of every level and the coarsest A)
   // are inverted together on the device by the batched Gauss-Jordan sweep.
@@ -404,12 +549,13 @@ void finish_setup(mg_hierarchy* h) {
   gj.drop = mem.alloc<int32_t>(gj.nmat);
   gj.bad = mem.alloc<int32_t>(gj.nmat);
   gj.ndrop = mem.alloc<int32_t>(gj.nmat);
-  batched_spsd_inverse(gj, 0);
+  batched_spsd_inverse(gj, mem.stream);
   check_launch("batched dense inverse");
   {
     std::vector<int32_t> bad(gj.nmat), nd(gj.nmat);
-    CK(cudaMemcpy(bad.data(), gj.bad, sizeof(int32_t) * gj.nmat, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(nd.data(), gj.ndrop, sizeof(int32_t) * gj.nmat, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(bad.data(), gj.bad, sizeof(int32_t) * gj.nmat, cudaMemcpyDeviceToHost, mem.stream));
+    CK(cudaMemcpyAsync(nd.data(), gj.ndrop, sizeof(int32_t) * gj.nmat, cudaMemcpyDeviceToHost, mem.stream));
+    CK(cudaStreamSynchronize(mem.stream));
     for (int sp = 0; sp < gj.nmat; ++sp) {
       const Blk& bk = blks[order[sp]];
       if (bad[sp])
@@ -435,10 +581,11 @@ void finish_setup(mg_hierarchy* h) {
       LevelH& H = h->host[l];
       DevLevel<T>& D = eng->lv[l];
       D.n = (int)H.A.nrows;
-      D.A = make_sell<T>(H.A, mem);
+      std::string tlog;
+      D.A = tuned_sell<T>(H.A, mem, o.sell_sigma, &tlog);
       if (l < L - 1) {
-        D.P = make_sell<T>(H.P, mem);
-        D.R = make_sell<T>(H.R, mem);
+        D.P = tuned_sell<T>(H.P, mem, o.sell_sigma, &tlog);
+        D.R = tuned_sell<T>(H.R, mem, o.sell_sigma, &tlog);
         std::vector<T> dv(H.dinv.begin(), H.dinv.end());
         D.dinv = mem.upload(dv);
         cheb_coefficients(H.lmax, H.lmin, o.cheb_degree, D.cd, D.cr);
@@ -462,7 +609,7 @@ void finish_setup(mg_hierarchy* h) {
           for (int p = 0; p < D.np; ++p) {
             int m = H.patch_ptr[p + 1] - H.patch_ptr[p];
             D.max_patch = std::max(D.max_patch, m);
-            for (int r0 = 0; r0 < m; r0 += kBlock) items.push_back({p, r0});
+            for (int r0 = 0; r0 < m; r0 += kPatchRowsPerItem) items.push_back({p, r0});
           }
           if (D.max_patch > 27000) throw Error(MG_ERR_INVALID_ARG, "patch larger than 27000 DoFs");
           max_patch = std::max(max_patch, D.max_patch);
@@ -474,8 +621,34 @@ void finish_setup(mg_hierarchy* h) {
           D.inv = gj.M;
           D.rbuf = mem.alloc<double>(D.nt);
           D.items = mem.upload(items);
+          // rows of A with an entry in a patch column (A is symmetric: patch DoFs and neighbours)
+          std::vector<uint8_t> inpatch(D.n, 0), halo(D.n, 0);
+          for (int32_t f : H.patch_dofs) inpatch[f] = 1;
+          for (int64_t i = 0; i < D.n; ++i)
+            for (int32_t k = H.A.rp[i]; k < H.A.rp[i + 1]; ++k)
+              if (inpatch[H.A.ci[k]]) {
+                halo[i] = 1;
+                break;
+              }
+          std::vector<int32_t> hrow, hrp(1, 0), hci;
+          std::vector<T> hv;
+          for (int64_t i = 0; i < D.n; ++i)
+            if (halo[i]) {
+              hrow.push_back((int32_t)i);
+              for (int32_t k = H.A.rp[i]; k < H.A.rp[i + 1]; ++k) hci.push_back(H.A.ci[k]), hv.push_back((T)H.A.v[k]);
+              hrp.push_back((int32_t)hci.size());
+            }
+          D.nh = (int)hrow.size();
+          D.hrow = mem.upload(hrow);
+          D.hrp = mem.upload(hrp);
+          D.hci = mem.upload(hci);
+          D.hv = mem.upload(hv);
         }
       }
+      auto lay = [](const SellMat<T>& M) {
+        return M.lanes > 1 ? "v" + std::to_string(M.lanes) : "s" + std::to_string(M.sigma);
+      };
+      tm.mark("upload L" + std::to_string(l) + " A/P/R " + lay(D.A) + "/" + lay(D.P) + "/" + lay(D.R) + " |" + tlog);
       bool fine_shared = (l == 0) && std::is_same<T, double>::value;
       if (!fine_shared) {
         D.b = mem.alloc<T>(D.n);
@@ -499,15 +672,16 @@ void finish_setup(mg_hierarchy* h) {
   h->cq = mem.alloc<double>(n0);
   h->cz = mem.alloc<double>(n0);
   h->nparts = cg_parts(n0);
-  h->ap_parts = sell_blocks(n0);
+  h->ap_parts = sell_blocks(n0, 32);  // partials of k_ap for any layout
   h->part = mem.alloc<double>(std::max(h->nparts, h->ap_parts));
   h->st = mem.alloc<CgState>(1);
-  CK(cudaMallocHost(&h->hst, sizeof(CgState)));
+  h->hst = reinterpret_cast<CgState*>(pinned_acquire((sizeof(CgState) + 7) / 8));
   std::memset(h->hst, 0, sizeof(CgState));
   if (h->mixed()) {
     h->e32.reset(new Engine<float>());
     upload_engine(h->e32.get(), float());
-    h->A0 = make_sell<double>(h->host[0].A, mem);
+    std::string tlog;
+    h->A0 = tuned_sell<double>(h->host[0].A, mem, o.sell_sigma, &tlog);
   } else {
     h->e64.reset(new Engine<double>());
     upload_engine(h->e64.get(), double());
@@ -516,7 +690,7 @@ void finish_setup(mg_hierarchy* h) {
     h->A0 = h->e64->lv[0].A;
   }
   if (max_patch > 0) patch_solve_setup(max_patch);
-  CK(cudaDeviceSynchronize());
+  CK(cudaStreamSynchronize(h->own_stream));
   tm.mark("device upload");
 }
 
@@ -621,12 +795,37 @@ void count_launches(mg_hierarchy* h) {
   });
 }
 
-int run_solve(mg_hierarchy* h, double rtol, int maxit, mg_solve_info_t* info, cudaStream_t s) {
+void enqueue_state(mg_hierarchy* h, double rtol, int maxit, cudaStream_t s) {
   if (!(rtol >= 0) || maxit < 1) throw Error(MG_ERR_INVALID_ARG, "rtol must be >= 0 and maxit >= 1");
   std::memset(h->hst, 0, sizeof(CgState));
   h->hst->rtol2 = rtol * rtol;
   h->hst->maxit = maxit;
   CK(cudaMemcpyAsync(h->st, h->hst, sizeof(CgState), cudaMemcpyHostToDevice, s));
+}
+
+// The FP64 residual b - A x of the final iterate, then the whole CG state to the host.
+void enqueue_exit(mg_hierarchy* h, cudaStream_t s) {
+  sell_resid<double>(h->A0, h->cx, h->cb, h->cq, s);
+  dot_self(h->n0, h->cq, h->part, s);
+  cg_finish(h->nparts, h->part, h->st, FIN_TRUE, 0, 0, s);
+  CK(cudaMemcpyAsync(h->hst, h->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+}
+
+int collect_state(const mg_hierarchy* h, mg_solve_info_t* info) {
+  const CgState st = *h->hst;
+  if (info) {
+    info->iterations = st.it;
+    info->converged = st.status == 1 || st.bb == 0.0;
+    info->rel_residual = st.bb > 0 ? std::sqrt(st.rr / st.bb) : 0.0;
+    info->true_rel_residual = st.bb > 0 ? std::sqrt(st.rr_true / st.bb) : 0.0;
+  }
+  if (st.status == 3) return MG_ERR_BREAKDOWN;
+  if (!(st.status == 1 || st.bb == 0.0)) return MG_ERR_NO_CONVERGENCE;
+  return MG_OK;
+}
+
+int run_solve(mg_hierarchy* h, double rtol, int maxit, mg_solve_info_t* info, cudaStream_t s) {
+  enqueue_state(h, rtol, maxit, s);
   if (h->graph) {
     CK(cudaGraphLaunch(h->graph, s));
   } else {
@@ -640,25 +839,9 @@ int run_solve(mg_hierarchy* h, double rtol, int maxit, mg_solve_info_t* info, cu
       check_launch("cg body");
     }
   }
-  // true residual r = b - A x in FP64
-  sell_resid<double>(h->A0, h->cx, h->cb, h->cq, s);
-  dot_self(h->n0, h->cq, h->part, s);
-  CK(cudaMemcpyAsync(h->hst, h->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+  enqueue_exit(h, s);
   CK(cudaStreamSynchronize(s));
-  CgState st = *h->hst;
-  cg_finish(h->nparts, h->part, h->st, FIN_NORM, 0, 0, s);
-  CK(cudaMemcpyAsync(h->hst, h->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  double true_rr = h->hst->rr;
-  if (info) {
-    info->iterations = st.it;
-    info->converged = st.status == 1 || st.bb == 0.0;
-    info->rel_residual = st.bb > 0 ? std::sqrt(st.rr / st.bb) : 0.0;
-    info->true_rel_residual = st.bb > 0 ? std::sqrt(true_rr / st.bb) : 0.0;
-  }
-  if (st.status == 3) return MG_ERR_BREAKDOWN;
-  if (!(st.status == 1 || st.bb == 0.0)) return MG_ERR_NO_CONVERGENCE;
-  return MG_OK;
+  return collect_state(h, info);
 }
 
 }  // namespace
@@ -718,14 +901,16 @@ void store(double* dst, const T* src, int n, cudaStream_t s) {
   }
 }
 
+void device_phase(mg_hierarchy* h) {
+  build_device(h);
+  count_launches(h);
+  if (h->opt.use_graph) build_graph(h);
+  CK(cudaStreamSynchronize(h->own_stream));
+}
+
 void common_setup_tail(mg_hierarchy* h) {
-  finish_setup(h);
-  if (h->device) {
-    CK(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
-    count_launches(h);
-    if (h->opt.use_graph) build_graph(h);
-    CK(cudaDeviceSynchronize());
-  }
+  finish_setup_host(h);
+  if (!h->opt.host_only) device_phase(h);
 }
 
 }  // namespace
@@ -769,16 +954,17 @@ void mg_default_options(mg_options_t* o) {
   o->use_graph = 1;
   o->local_levels_mask = -1;
   o->quality_threshold = 0.1;
-  o->sell_sigma = 1;
+  o->sell_sigma = 0;
 }
 
-int mg_setup(const mg_mesh_t* levels, int32_t L, int32_t degree, double quality_threshold, const mg_options_t* opt,
-             mg_hierarchy_t** out) {
-  mg_hierarchy* h = nullptr;
-  API_BEGIN
-  nnmg::g_setup_error.clear();
-  if (!out) throw Error(MG_ERR_INVALID_ARG, "out is NULL");
-  *out = nullptr;
+}  // extern "C"
+
+namespace nnmg {
+
+// Everything mg_setup does on the host: DoF maps, assembly, quality, patches, transfer,
+// Galerkin operators, diagonals and eigenvalues. The device phase is separate.
+mg_hierarchy* build_host_hierarchy(const mg_mesh_t* levels, int32_t L, int32_t degree, double quality_threshold,
+                                   const mg_options_t* opt) {
   if (!levels || L < 2 || L > 32) throw Error(MG_ERR_INVALID_ARG, "need 2 <= L <= 32 mesh levels");
   if (degree != 1 && degree != 2) throw Error(MG_ERR_INVALID_ARG, "degree must be 1 or 2");
   std::unique_ptr<mg_hierarchy> H(new mg_hierarchy());
@@ -836,7 +1022,104 @@ int mg_setup(const mg_mesh_t* levels, int32_t L, int32_t degree, double quality_
   }
   meshes.clear();
   dms.clear();
-  common_setup_tail(H.get());
+  finish_setup_host(H.get());
+  return H.release();
+}
+
+void build_device_hierarchy(mg_hierarchy* h) { device_phase(h); }
+
+int64_t estimate_device_bytes(const mg_hierarchy* h) {
+  const int vbytes = h->opt.precision == MG_PREC_MIXED ? 4 : 8;
+  int64_t tot = 0, largest = 0;
+  auto op = [&](const Csr& A) {
+    // SELL padding and the layout candidates of the autotuner: bound by 1.5 x CSR
+    int64_t b = (int64_t)(1.5 * (double)A.nnz() * (vbytes + 4)) + 8 * (A.nrows + 1);
+    largest = std::max(largest, b);
+    tot += b;
+  };
+  for (int l = 0; l < h->L; ++l) {
+    const LevelH& lv = h->host[l];
+    op(lv.A);
+    if (l + 1 < h->L) {
+      op(lv.P);
+      op(lv.R);
+    }
+    tot += 8 * vbytes * lv.A.nrows;  // level vectors
+    const int64_t np = (int64_t)lv.patch_ptr.size() - 1;
+    for (int64_t p = 0; p < np; ++p) {
+      int64_t m = lv.patch_ptr[p + 1] - lv.patch_ptr[p];
+      tot += 8 * m * m + 64 * m;
+    }
+    if (np > 0) tot += 16 * (int64_t)lv.A.nnz() / std::max<int64_t>(lv.A.nrows, 1) * (int64_t)lv.patch_dofs.size() * 4;
+  }
+  const int64_t nc = h->host[h->L - 1].A.nrows;
+  tot += 16 * nc * nc;  // coarse inverse and split-K partials
+  const int64_t n0 = h->host[0].A.nrows;
+  tot += 8 * 8 * n0;    // CG vectors
+  if (h->opt.precision == MG_PREC_MIXED) tot += 12 * h->host[0].A.nnz() * 3 / 2;
+  return tot + 2 * largest + (64 << 20);  // autotuner trial layouts + slack
+}
+
+int64_t hierarchy_device_bytes(const mg_hierarchy* h) { return h->mem.bytes; }
+int64_t hierarchy_dofs(const mg_hierarchy* h) { return h->host[0].A.nrows; }
+const std::vector<double>& hierarchy_unit_load(const mg_hierarchy* h) { return h->fine_load_unit; }
+
+void enqueue_host_solve(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit, cudaEvent_t done) {
+  if (!h->graph) throw Error(MG_ERR_INVALID_ARG, "the solve server needs hierarchies built with use_graph = 1");
+  cudaStream_t s = h->own_stream;
+  CK(cudaMemcpyAsync(h->cb, b, sizeof(double) * h->n0, cudaMemcpyHostToDevice, s));
+  enqueue_state(h, rtol, maxit, s);
+  CK(cudaGraphLaunch(h->graph, s));
+  enqueue_exit(h, s);
+  CK(cudaMemcpyAsync(x, h->cx, sizeof(double) * h->n0, cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(done, s));
+}
+
+int collect_host_solve(const mg_hierarchy* h, mg_solve_info_t* info) { return collect_state(h, info); }
+
+void destroy_hierarchy(mg_hierarchy* h) { delete h; }
+
+namespace {
+std::mutex g_pinned_mu;
+std::multimap<int64_t, double*> g_pinned_free;   // capacity -> buffer
+std::map<double*, int64_t> g_pinned_cap;
+}  // namespace
+
+double* pinned_acquire(int64_t n) {
+  std::lock_guard<std::mutex> lk(g_pinned_mu);
+  auto it = g_pinned_free.lower_bound(n);
+  if (it != g_pinned_free.end()) {
+    double* p = it->second;
+    g_pinned_free.erase(it);
+    return p;
+  }
+  int64_t cap = 1024;
+  while (cap < n) cap *= 2;
+  double* p = nullptr;
+  CK(cudaMallocHost(&p, sizeof(double) * cap));
+  g_pinned_cap[p] = cap;
+  return p;
+}
+
+void pinned_release(double* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pinned_mu);
+  g_pinned_free.emplace(g_pinned_cap[p], p);
+}
+
+}  // namespace nnmg
+
+extern "C" {
+
+int mg_setup(const mg_mesh_t* levels, int32_t L, int32_t degree, double quality_threshold, const mg_options_t* opt,
+             mg_hierarchy_t** out) {
+  mg_hierarchy* h = nullptr;
+  API_BEGIN
+  nnmg::g_setup_error.clear();
+  if (!out) throw Error(MG_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  std::unique_ptr<mg_hierarchy> H(build_host_hierarchy(levels, L, degree, quality_threshold, opt));
+  if (!H->opt.host_only) device_phase(H.get());
   *out = H.release();
   return MG_OK;
   API_END_H(h)
@@ -1123,21 +1406,14 @@ int mg_solve_batch(mg_hierarchy_t* const* hs, const double* const* b, double* co
     CK(cudaMemcpyAsync(hi->st, hi->hst, sizeof(CgState), cudaMemcpyHostToDevice, hi->own_stream));
     if (!hi->graph) throw Error(MG_ERR_INVALID_ARG, "mg_solve_batch needs hierarchies built with use_graph = 1");
     CK(cudaGraphLaunch(hi->graph, hi->own_stream));
+    enqueue_exit(hi, hi->own_stream);
     CK(cudaMemcpyAsync(x[i], hi->cx, sizeof(double) * hi->n0, cudaMemcpyDeviceToDevice, hi->own_stream));
   }
   int rc_all = MG_OK;
   for (int i = 0; i < n; ++i) {
     mg_hierarchy* hi = hs[i];
-    CK(cudaMemcpyAsync(hi->hst, hi->st, sizeof(CgState), cudaMemcpyDeviceToHost, hi->own_stream));
     CK(cudaStreamSynchronize(hi->own_stream));
-    CgState st = *hi->hst;
-    if (info) {
-      info[i].iterations = st.it;
-      info[i].converged = st.status == 1 || st.bb == 0.0;
-      info[i].rel_residual = st.bb > 0 ? std::sqrt(st.rr / st.bb) : 0.0;
-      info[i].true_rel_residual = -1.0;  // not recomputed in batch mode
-    }
-    int rc = st.status == 3 ? MG_ERR_BREAKDOWN : ((st.status == 1 || st.bb == 0.0) ? MG_OK : MG_ERR_NO_CONVERGENCE);
+    int rc = collect_state(hi, info ? &info[i] : nullptr);
     if (rc_all == MG_OK) rc_all = rc;
   }
   cudaEventDestroy(start);

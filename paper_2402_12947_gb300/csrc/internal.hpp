@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_runtime_api.h>
+
 #include "nnmg.h"
 
 namespace nnmg {
@@ -78,5 +80,28 @@ Csr spgemm(const Csr& A, const Csr& B);
 double lanczos_lmax(const Csr& A, const uint8_t* keep, double tol, int maxit, int* iters);
 std::vector<double> dense_submatrix(const Csr& A, const int32_t* idx, int64_t n);
 void spmv_host(const Csr& A, const double* x, double* y);
+
+// ---- hierarchy.cu: phases of a hierarchy's life used by the solve server ----
+// Host phase of mg_setup (throws Error).
+mg_hierarchy* build_host_hierarchy(const mg_mesh_t* levels, int32_t L, int32_t degree, double quality_threshold,
+                                   const mg_options_t* opt);
+// Device phase (upload, dense inverses, layouts, solve graph) on the hierarchy's stream.
+void build_device_hierarchy(mg_hierarchy* h);
+// Upper bound of the device bytes the device phase will allocate (host phase done).
+int64_t estimate_device_bytes(const mg_hierarchy* h);
+int64_t hierarchy_device_bytes(const mg_hierarchy* h);
+int64_t hierarchy_dofs(const mg_hierarchy* h);
+// b for f = 1 on the free DoFs of level 0 (geometric hierarchies).
+const std::vector<double>& hierarchy_unit_load(const mg_hierarchy* h);
+// Enqueue one MG-PCG solve on the hierarchy's own stream: b (page-locked host, n_0) in, the
+// solution to x (page-locked host) and the CG state out, then record `done`.
+void enqueue_host_solve(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit, cudaEvent_t done);
+// After `done` has completed: the solve's status and info.
+int collect_host_solve(const mg_hierarchy* h, mg_solve_info_t* info);
+void destroy_hierarchy(mg_hierarchy* h);
+// Page-locked host staging buffers reused across requests (allocating page-locked memory
+// would synchronise every stream of the device).
+double* pinned_acquire(int64_t n);
+void pinned_release(double* p);
 
 }  // namespace nnmg

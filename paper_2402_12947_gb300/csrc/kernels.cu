@@ -35,14 +35,29 @@ __device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p);
 __device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
 __device__ __forceinline__ int32_t ld_stream(const int32_t* p) { return __ldcs(p); }
 
+// Matrix operands of one launch, in one of two layouts:
+//  * lanes == 1, SELL-32: slot `srow` (slice srow/32, lane srow%32) holds matrix row
+//    perm[srow] (srow itself when perm is null); one thread accumulates one row;
+//  * lanes == G > 1, CSR vector: G consecutive threads share row `slot`, stride over its
+//    CSR entries (coalesced) and combine their partial sums with xor shuffles.
+// Every vector access of an epilogue goes through the matrix row.
 template <typename T>
-__device__ __forceinline__ T sell_row(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                                      const T* __restrict__ val, const T* __restrict__ x, int row) {
-  const int s = row >> 5, lane = row & 31;
-  const int64_t o = off[s];
-  const int w = (int)((off[s + 1] - o) >> 5);
-  const T* vp = val + o + lane;
-  const int32_t* cp = col + o + lane;
+struct OpView {
+  const int64_t* __restrict__ off;
+  const int32_t* __restrict__ rp;
+  const int32_t* __restrict__ col;
+  const T* __restrict__ val;
+  const int32_t* __restrict__ perm;
+  int nrows;
+};
+
+template <typename T>
+__device__ __forceinline__ T sell_row(const OpView<T>& m, const T* __restrict__ x, int srow) {
+  const int s = srow >> 5, lane = srow & 31;
+  const int64_t o = m.off[s];
+  const int w = (int)((m.off[s + 1] - o) >> 5);
+  const T* vp = m.val + o + lane;
+  const int32_t* cp = m.col + o + lane;
   T acc = T(0);
   int j = 0;
   for (; j + 4 <= w; j += 4) {
@@ -64,32 +79,73 @@ __device__ __forceinline__ T sell_row(const int64_t* __restrict__ off, const int
   return acc;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kBlock) k_sell_spmv(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                                                      const T* __restrict__ val, int nrows, const T* __restrict__ x,
-                                                      T* __restrict__ y) {
-  const int row = blockIdx.x * kBlock + threadIdx.x;
-  if (row >= nrows) return;
-  y[row] = sell_row(off, col, val, x, row);
+// Row sum of the calling thread's row. Returns false for threads past the last row; for
+// G > 1 every lane of a group receives the group's total (all lanes take part in the
+// shuffles, so no lane leaves early).
+template <typename T, int G>
+__device__ __forceinline__ bool op_row(const OpView<T>& m, const T* __restrict__ x, int& row, T& acc) {
+  const int tid = blockIdx.x * kBlock + threadIdx.x;
+  if constexpr (G == 1) {
+    if (tid >= m.nrows) return false;
+    row = m.perm ? m.perm[tid] : tid;
+    acc = sell_row(m, x, tid);
+    return true;
+  } else {
+    const int slot = tid / G, lane = tid & (G - 1);
+    const bool valid = slot < m.nrows;
+    row = valid ? slot : 0;
+    T a = T(0);
+    if (valid) {
+      const int k1 = m.rp[row + 1];
+      int k = m.rp[row] + lane;
+      for (; k + 3 * G < k1; k += 4 * G) {
+        const T v0 = ld_stream(m.val + k), v1 = ld_stream(m.val + k + G), v2 = ld_stream(m.val + k + 2 * G),
+                v3 = ld_stream(m.val + k + 3 * G);
+        const int32_t c0 = ld_stream(m.col + k), c1 = ld_stream(m.col + k + G), c2 = ld_stream(m.col + k + 2 * G),
+                      c3 = ld_stream(m.col + k + 3 * G);
+        a = fma(v0, __ldg(x + c0), a);
+        a = fma(v1, __ldg(x + c1), a);
+        a = fma(v2, __ldg(x + c2), a);
+        a = fma(v3, __ldg(x + c3), a);
+      }
+      for (; k < k1; k += G) a = fma(ld_stream(m.val + k), __ldg(x + ld_stream(m.col + k)), a);
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    acc = a;
+    return valid;
+  }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kBlock) k_sell_resid(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                                                       const T* __restrict__ val, int nrows, const T* __restrict__ x,
-                                                       const T* __restrict__ b, T* __restrict__ r) {
-  const int row = blockIdx.x * kBlock + threadIdx.x;
-  if (row >= nrows) return;
-  r[row] = b[row] - sell_row(off, col, val, x, row);
+template <int G>
+__device__ __forceinline__ bool group_leader() {
+  return G == 1 || (threadIdx.x & (G - 1)) == 0;
 }
 
-template <typename T, bool FIRST>
-__global__ void __launch_bounds__(kBlock) k_sell_cheb(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                                                      const T* __restrict__ val, int nrows, const T* __restrict__ xin,
-                                                      const T* __restrict__ b, const T* __restrict__ dinv,
-                                                      T* __restrict__ d, T* __restrict__ xout, T cd, T cr) {
-  const int row = blockIdx.x * kBlock + threadIdx.x;
-  if (row >= nrows) return;
-  const T ax = sell_row(off, col, val, xin, row);
+template <typename T, int G>
+__global__ void __launch_bounds__(kBlock) k_spmv(OpView<T> m, const T* __restrict__ x, T* __restrict__ y) {
+  int row;
+  T ax;
+  if (!op_row<T, G>(m, x, row, ax) || !group_leader<G>()) return;
+  y[row] = ax;
+}
+
+template <typename T, int G>
+__global__ void __launch_bounds__(kBlock) k_resid(OpView<T> m, const T* __restrict__ x, const T* __restrict__ b,
+                                                  T* __restrict__ r) {
+  int row;
+  T ax;
+  if (!op_row<T, G>(m, x, row, ax) || !group_leader<G>()) return;
+  r[row] = b[row] - ax;
+}
+
+template <typename T, int G, bool FIRST>
+__global__ void __launch_bounds__(kBlock) k_cheb(OpView<T> m, const T* __restrict__ xin, const T* __restrict__ b,
+                                                 const T* __restrict__ dinv, T* __restrict__ d, T* __restrict__ xout,
+                                                 T cd, T cr) {
+  int row;
+  T ax;
+  if (!op_row<T, G>(m, xin, row, ax) || !group_leader<G>()) return;
   const T r = b[row] - ax;
   const T t = dinv[row] * r;
   const T dn = FIRST ? cr * t : fma(cd, d[row], cr * t);
@@ -97,23 +153,28 @@ __global__ void __launch_bounds__(kBlock) k_sell_cheb(const int64_t* __restrict_
   xout[row] = xin[row] + dn;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kBlock) k_sell_prolong(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                                                         const T* __restrict__ val, int nrows, const T* __restrict__ xc,
-                                                         T* __restrict__ x) {
-  const int row = blockIdx.x * kBlock + threadIdx.x;
-  if (row >= nrows) return;
-  x[row] = x[row] + sell_row(off, col, val, xc, row);
+template <typename T, int G>
+__global__ void __launch_bounds__(kBlock) k_prolong(OpView<T> m, const T* __restrict__ xc, T* __restrict__ x) {
+  int row;
+  T ax;
+  if (!op_row<T, G>(m, xc, row, ax) || !group_leader<G>()) return;
+  x[row] = x[row] + ax;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kBlock) k_sell_restrict(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                                                          const T* __restrict__ val, int nrows, const T* __restrict__ r,
-                                                          T* __restrict__ bc, T* __restrict__ xc) {
-  const int row = blockIdx.x * kBlock + threadIdx.x;
-  if (row >= nrows) return;
-  bc[row] = sell_row(off, col, val, r, row);
+template <typename T, int G>
+__global__ void __launch_bounds__(kBlock) k_restrict(OpView<T> m, const T* __restrict__ r, T* __restrict__ bc,
+                                                     T* __restrict__ xc) {
+  int row;
+  T ax;
+  if (!op_row<T, G>(m, r, row, ax) || !group_leader<G>()) return;
+  bc[row] = ax;
   xc[row] = T(0);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
 // Block-wide sum in a fixed order (warp shuffles, then the warps' sums by warp 0).
@@ -132,14 +193,13 @@ __device__ __forceinline__ double block_sum(double v) {
   return t;  // valid in thread 0
 }
 
-__global__ void __launch_bounds__(kBlock) k_sell_ap(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                                                    const double* __restrict__ val, int nrows,
-                                                    const double* __restrict__ p, double* __restrict__ q,
-                                                    double* __restrict__ part) {
-  const int row = blockIdx.x * kBlock + threadIdx.x;
+template <int G>
+__global__ void __launch_bounds__(kBlock) k_ap(OpView<double> m, const double* __restrict__ p, double* __restrict__ q,
+                                               double* __restrict__ part) {
+  int row;
+  double ap;
   double v = 0.0;
-  if (row < nrows) {
-    const double ap = sell_row(off, col, val, p, row);
+  if (op_row<double, G>(m, p, row, ap) && group_leader<G>()) {
     q[row] = ap;
     v = p[row] * ap;
   }
@@ -147,17 +207,57 @@ __global__ void __launch_bounds__(kBlock) k_sell_ap(const int64_t* __restrict__ 
   if (threadIdx.x == 0) part[blockIdx.x] = v;
 }
 
+// First Chebyshev step from a zero iterate: r = b, d = cr D^{-1} b, x_out = x_in + d for
+// every row (x_in is zero there) ...
 template <typename T>
-__global__ void k_patch_residual(int nt, const int32_t* __restrict__ pdofs, const int32_t* __restrict__ prp,
-                                 const int32_t* __restrict__ pci, const double* __restrict__ pv,
-                                 const T* __restrict__ b, const T* __restrict__ x, double* __restrict__ rbuf) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nt) return;
-  double s = 0.0;
-  for (int k = prp[t]; k < prp[t + 1]; ++k) s = fma(pv[k], (double)x[pci[k]], s);
-  rbuf[t] = (double)b[pdofs[t]] - s;
+__global__ void __launch_bounds__(kBlock) k_cheb0_all(int n, const T* __restrict__ b, const T* __restrict__ dinv,
+                                                      const T* __restrict__ xin, T* __restrict__ d,
+                                                      T* __restrict__ xout, T cr) {
+  const int i = blockIdx.x * kBlock + threadIdx.x;
+  if (i >= n) return;
+  const T t = dinv[i] * b[i];
+  const T dn = cr * t;
+  d[i] = dn;
+  xout[i] = xin[i] + dn;
 }
 
+// ... then the rows coupled to patch DoFs (where x_in may be non-zero after S_c) are redone
+// with their full row: r = b - A x_in. One thread per such row, CSR order.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_cheb0_halo(int nh, const int32_t* __restrict__ hrow,
+                                                       const int32_t* __restrict__ hrp, const int32_t* __restrict__ hci,
+                                                       const T* __restrict__ hv, const T* __restrict__ b,
+                                                       const T* __restrict__ dinv, const T* __restrict__ xin,
+                                                       T* __restrict__ d, T* __restrict__ xout, T cr) {
+  const int t = blockIdx.x * kBlock + threadIdx.x;
+  if (t >= nh) return;
+  const int i = hrow[t];
+  T ax = T(0);
+  for (int k = hrp[t]; k < hrp[t + 1]; ++k) ax = fma(hv[k], xin[hci[k]], ax);
+  const T r = b[i] - ax;
+  const T tt = dinv[i] * r;
+  const T dn = cr * tt;
+  d[i] = dn;
+  xout[i] = xin[i] + dn;
+}
+
+// S_c phase 1: r_B = b_B - (A x)_B for every patch row, one warp per row (FP64).
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_patch_residual(int nt, const int32_t* __restrict__ pdofs,
+                                                           const int32_t* __restrict__ prp,
+                                                           const int32_t* __restrict__ pci,
+                                                           const double* __restrict__ pv, const T* __restrict__ b,
+                                                           const T* x, double* __restrict__ rbuf) {
+  const int t = (blockIdx.x * kBlock + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  double s = 0.0;
+  if (t < nt && x != nullptr)  // x == nullptr: the iterate is zero, r_B = b_B
+    for (int k = prp[t] + lane; k < prp[t + 1]; k += 32) s = fma(pv[k], (double)x[pci[k]], s);
+  s = warp_sum(s);
+  if (t < nt && lane == 0) rbuf[t] = (double)b[pdofs[t]] - s;
+}
+
+// S_c phase 2: e = (A^[d])^{-1} r_B and x_B += e. A work item is 32 consecutive rows of one
+// patch; each warp computes 4 of them, reading row i of the symmetric inverse contiguously.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_patch_solve(const PatchItem* __restrict__ items,
                                                         const int32_t* __restrict__ pptr,
@@ -170,21 +270,40 @@ __global__ void __launch_bounds__(kBlock) k_patch_solve(const PatchItem* __restr
   const int p0 = pptr[it.patch], n = pptr[it.patch + 1] - p0;
   for (int j = threadIdx.x; j < n; j += blockDim.x) rs[j] = rbuf[p0 + j];
   __syncthreads();
-  const int i = it.row0 + threadIdx.x;
-  if (i >= n) return;
-  // X is symmetric: row i is read as column i, coalesced across the block's threads
-  const double* X = inv + inv_off[it.patch] + i;
-  double e = 0.0;
-  int j = 0;
-  for (; j + 4 <= n; j += 4) {
-    e = fma(X[(int64_t)j * n], rs[j], e);
-    e = fma(X[(int64_t)(j + 1) * n], rs[j + 1], e);
-    e = fma(X[(int64_t)(j + 2) * n], rs[j + 2], e);
-    e = fma(X[(int64_t)(j + 3) * n], rs[j + 3], e);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int R = kPatchRowsPerItem / 8;  // rows per warp, accumulated together
+  const int i0 = it.row0 + warp * R;
+  if (i0 >= n) return;  // warp-uniform; no block barrier follows
+  const double* X = inv + inv_off[it.patch];
+  const double* Xi[R];
+  bool ok[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    ok[q] = i0 + q < n;
+    Xi[q] = X + (int64_t)(ok[q] ? i0 + q : i0) * n;
   }
-  for (; j < n; ++j) e = fma(X[(int64_t)j * n], rs[j], e);
-  const int g = pdofs[p0 + i];
-  x[g] = (T)((double)x[g] + e);
+  double e[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) e[q] = 0.0;
+  int j = lane;
+  for (; j + 32 < n; j += 64) {
+    const double r0 = rs[j], r1 = rs[j + 32];
+#pragma unroll
+    for (int q = 0; q < R; ++q) e[q] = fma(Xi[q][j + 32], r1, fma(Xi[q][j], r0, e[q]));
+  }
+  if (j < n) {
+    const double r0 = rs[j];
+#pragma unroll
+    for (int q = 0; q < R; ++q) e[q] = fma(Xi[q][j], r0, e[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const double eq = warp_sum(e[q]);
+    if (lane == 0 && ok[q]) {
+      const int g = pdofs[p0 + i0 + q];
+      x[g] = (T)((double)x[g] + eq);
+    }
+  }
 }
 
 template <typename T>
@@ -318,8 +437,14 @@ __global__ void __launch_bounds__(1024) k_cg_finish(int nparts, const double* __
       break;
     case FIN_RR: {
       st->rr = s;
-      st->it += 1;
       int cont = 1;
+      if (st->bb == 0.0) {  // b = 0: x = 0 is exact, no iteration
+        st->status = 1;
+        st->cont = 0;
+        if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)handle, 0u);
+        break;
+      }
+      st->it += 1;
       if (st->status == 3) cont = 0;
       else if (s <= st->rtol2 * st->bb) st->status = 1, cont = 0;
       else if (st->it >= st->maxit || st->it >= kMaxCgIterations) st->status = 2, cont = 0;
@@ -334,6 +459,9 @@ __global__ void __launch_bounds__(1024) k_cg_finish(int nparts, const double* __
       break;
     case FIN_NORM:
       st->rr = s;
+      break;
+    case FIN_TRUE:
+      st->rr_true = s;
       break;
   }
 }
@@ -405,50 +533,85 @@ void batched_spsd_inverse(const GjBatch& g, cudaStream_t s) {
   }
 }
 
-int sell_blocks(int nrows) { return grid_for(nrows, kBlock); }
+int sell_blocks(int nrows, int lanes) { return grid_for((int)std::min<int64_t>((int64_t)nrows * lanes, INT32_MAX), kBlock); }
+
+template <typename T>
+OpView<T> view(const SellMat<T>& A) {
+  return OpView<T>{A.off, A.rp, A.col, A.val, A.perm, A.nrows};
+}
+
+// Dispatch on the layout: F<G>(grid) is called with the kernel's lanes-per-row.
+template <typename F>
+void by_lanes(int lanes, F&& f) {
+  switch (lanes) {
+    case 1: f(std::integral_constant<int, 1>()); break;
+    case 4: f(std::integral_constant<int, 4>()); break;
+    case 8: f(std::integral_constant<int, 8>()); break;
+    case 16: f(std::integral_constant<int, 16>()); break;
+    case 32: f(std::integral_constant<int, 32>()); break;
+    default: throw Error(MG_ERR_INVALID_ARG, "unsupported lanes per row");
+  }
+}
 
 template <typename T>
 void sell_spmv(const SellMat<T>& A, const T* x, T* y, cudaStream_t s) {
   if (A.nrows == 0) return;
-  k_sell_spmv<T><<<sell_blocks(A.nrows), kBlock, 0, s>>>(A.off, A.col, A.val, A.nrows, x, y);
+  by_lanes(A.lanes, [&](auto g) {
+    k_spmv<T, decltype(g)::value><<<sell_blocks(A.nrows, A.lanes), kBlock, 0, s>>>(view(A), x, y);
+  });
 }
 template <typename T>
 void sell_resid(const SellMat<T>& A, const T* x, const T* b, T* r, cudaStream_t s) {
   if (A.nrows == 0) return;
-  k_sell_resid<T><<<sell_blocks(A.nrows), kBlock, 0, s>>>(A.off, A.col, A.val, A.nrows, x, b, r);
+  by_lanes(A.lanes, [&](auto g) {
+    k_resid<T, decltype(g)::value><<<sell_blocks(A.nrows, A.lanes), kBlock, 0, s>>>(view(A), x, b, r);
+  });
 }
 template <typename T>
 void sell_cheb(const SellMat<T>& A, const T* xin, const T* b, const T* dinv, T* d, T* xout, double cd, double cr,
                bool first, cudaStream_t s) {
   if (A.nrows == 0) return;
-  if (first)
-    k_sell_cheb<T, true><<<sell_blocks(A.nrows), kBlock, 0, s>>>(A.off, A.col, A.val, A.nrows, xin, b, dinv, d, xout,
-                                                                  (T)cd, (T)cr);
-  else
-    k_sell_cheb<T, false><<<sell_blocks(A.nrows), kBlock, 0, s>>>(A.off, A.col, A.val, A.nrows, xin, b, dinv, d, xout,
-                                                                   (T)cd, (T)cr);
+  by_lanes(A.lanes, [&](auto g) {
+    constexpr int G = decltype(g)::value;
+    if (first)
+      k_cheb<T, G, true><<<sell_blocks(A.nrows, G), kBlock, 0, s>>>(view(A), xin, b, dinv, d, xout, (T)cd, (T)cr);
+    else
+      k_cheb<T, G, false><<<sell_blocks(A.nrows, G), kBlock, 0, s>>>(view(A), xin, b, dinv, d, xout, (T)cd, (T)cr);
+  });
 }
 template <typename T>
 void sell_prolong(const SellMat<T>& P, const T* xc, T* x, cudaStream_t s) {
   if (P.nrows == 0) return;
-  k_sell_prolong<T><<<sell_blocks(P.nrows), kBlock, 0, s>>>(P.off, P.col, P.val, P.nrows, xc, x);
+  by_lanes(P.lanes, [&](auto g) {
+    k_prolong<T, decltype(g)::value><<<sell_blocks(P.nrows, P.lanes), kBlock, 0, s>>>(view(P), xc, x);
+  });
 }
 template <typename T>
 void sell_restrict(const SellMat<T>& R, const T* r, T* bc, T* xc, cudaStream_t s) {
   if (R.nrows == 0) return;
-  k_sell_restrict<T><<<sell_blocks(R.nrows), kBlock, 0, s>>>(R.off, R.col, R.val, R.nrows, r, bc, xc);
+  by_lanes(R.lanes, [&](auto g) {
+    k_restrict<T, decltype(g)::value><<<sell_blocks(R.nrows, R.lanes), kBlock, 0, s>>>(view(R), r, bc, xc);
+  });
 }
 void sell_ap(const SellMat<double>& A, const double* p, double* q, double* partial, int* nparts, cudaStream_t s) {
-  int nb = sell_blocks(A.nrows);
+  int nb = sell_blocks(A.nrows, A.lanes);
   *nparts = nb;
-  k_sell_ap<<<nb, kBlock, 0, s>>>(A.off, A.col, A.val, A.nrows, p, q, partial);
+  by_lanes(A.lanes, [&](auto g) { k_ap<decltype(g)::value><<<nb, kBlock, 0, s>>>(view(A), p, q, partial); });
+}
+
+template <typename T>
+void cheb_first_from_zero(int n, const T* b, const T* dinv, const T* xin, T* d, T* xout, double cr, int nh,
+                          const int32_t* hrow, const int32_t* hrp, const int32_t* hci, const T* hv, cudaStream_t s) {
+  if (n == 0) return;
+  k_cheb0_all<T><<<grid_for(n, kBlock), kBlock, 0, s>>>(n, b, dinv, xin, d, xout, (T)cr);
+  if (nh > 0) k_cheb0_halo<T><<<grid_for(nh, kBlock), kBlock, 0, s>>>(nh, hrow, hrp, hci, hv, b, dinv, xin, d, xout, (T)cr);
 }
 
 template <typename T>
 void patch_residual(int nt, const int32_t* pdofs, const int32_t* prp, const int32_t* pci, const double* pv, const T* b,
                     const T* x, double* rbuf, cudaStream_t s) {
   if (nt == 0) return;
-  k_patch_residual<T><<<grid_for(nt, 128), 128, 0, s>>>(nt, pdofs, prp, pci, pv, b, x, rbuf);
+  k_patch_residual<T><<<grid_for(nt, kBlock / 32), kBlock, 0, s>>>(nt, pdofs, prp, pci, pv, b, x, rbuf);
 }
 
 void patch_solve_setup(int max_patch) {
@@ -522,6 +685,8 @@ void dot_self(int n, const double* r, double* part, cudaStream_t s) {
                              cudaStream_t);                                                                      \
   template void sell_prolong<T>(const SellMat<T>&, const T*, T*, cudaStream_t);                                  \
   template void sell_restrict<T>(const SellMat<T>&, const T*, T*, T*, cudaStream_t);                             \
+  template void cheb_first_from_zero<T>(int, const T*, const T*, const T*, T*, T*, double, int, const int32_t*, \
+                                        const int32_t*, const int32_t*, const T*, cudaStream_t);                 \
   template void patch_residual<T>(int, const int32_t*, const int32_t*, const int32_t*, const double*, const T*,  \
                                   const T*, double*, cudaStream_t);                                              \
   template void patch_solve<T>(int, const PatchItem*, const int32_t*, const int32_t*, const int64_t*,            \

@@ -22,21 +22,27 @@ struct SellMat {
   int64_t* off = nullptr;   // [nslices+1] element offset of each slice (multiple of 32)
   int32_t* col = nullptr;   // [padded]
   T* val = nullptr;         // [padded]
+  int32_t* perm = nullptr;  // [nrows] matrix row held by each slot, or null (identity)
+  int32_t sigma = 1;        // window within which rows were sorted by length
+  int32_t lanes = 1;        // 1: SELL-32 (off/col/val/perm); G > 1: CSR vector (rp/col/val)
+  int32_t* rp = nullptr;    // [nrows+1] CSR row pointer (lanes > 1)
 };
 
 // Device-side state of the preconditioned CG recurrence (all FP64).
 struct CgState {
-  double bb, rz, pq, alpha, rr, beta, rtol2;
+  double bb, rz, pq, alpha, rr, beta, rtol2, rr_true;
   int32_t it, maxit, status, cont;   // status: 0 running, 1 converged, 2 maxit, 3 breakdown
 };
 
-enum FinishOp { FIN_BB = 0, FIN_RZ0 = 1, FIN_PQ = 2, FIN_RR = 3, FIN_RZ = 4, FIN_NORM = 5 };
+// FIN_NORM: rr = the sum; FIN_TRUE: rr_true = the sum (|b - A x|^2 recomputed at exit)
+enum FinishOp { FIN_BB = 0, FIN_RZ0 = 1, FIN_PQ = 2, FIN_RR = 3, FIN_RZ = 4, FIN_NORM = 5, FIN_TRUE = 6 };
 
 struct PatchItem {
   int32_t patch, row0;
 };
 
 constexpr int kBlock = 256;
+constexpr int kPatchRowsPerItem = 32;   // rows of one patch per S_c work item (8 warps x 4)
 
 // ---- SELL-32 SpMV family ----
 template <typename T> void sell_spmv(const SellMat<T>& A, const T* x, T* y, cudaStream_t s);
@@ -45,15 +51,21 @@ template <typename T> void sell_resid(const SellMat<T>& A, const T* x, const T* 
 template <typename T>
 void sell_cheb(const SellMat<T>& A, const T* xin, const T* b, const T* dinv, T* d, T* xout, double cd, double cr,
                bool first, cudaStream_t s);
+// The first Chebyshev step when x_in is zero except possibly on the rows listed in hrow
+// (the rows coupled to patch DoFs, with their entries of A in hrp/hci/hv): r = b on all
+// other rows, so their step needs no SpMV. nh = 0 when x_in is zero everywhere.
+template <typename T>
+void cheb_first_from_zero(int n, const T* b, const T* dinv, const T* xin, T* d, T* xout, double cr, int nh,
+                          const int32_t* hrow, const int32_t* hrp, const int32_t* hci, const T* hv, cudaStream_t s);
 // x += P xc.
 template <typename T> void sell_prolong(const SellMat<T>& P, const T* xc, T* x, cudaStream_t s);
 // bc = R r and xc = 0 (xc has R.nrows entries).
 template <typename T> void sell_restrict(const SellMat<T>& R, const T* r, T* bc, T* xc, cudaStream_t s);
 // q = A p and per-block partial sums of p.q (FP64).
 void sell_ap(const SellMat<double>& A, const double* p, double* q, double* partial, int* nparts, cudaStream_t s);
-int sell_blocks(int nrows);
+int sell_blocks(int nrows, int lanes);
 
-// ---- local correction S_c (two phases) ----
+// ---- local correction S_c (two phases); x == nullptr means the iterate is zero ----
 template <typename T>
 void patch_residual(int nt, const int32_t* pdofs, const int32_t* prp, const int32_t* pci, const double* pv,
                     const T* b, const T* x, double* rbuf, cudaStream_t s);

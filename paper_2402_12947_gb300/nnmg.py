@@ -55,6 +55,31 @@ class MgCsr(C.Structure):
                 ("values", C.c_void_p)]
 
 
+class MgRequest(C.Structure):
+    _fields_ = [("levels", C.c_void_p), ("L", C.c_int32), ("degree", C.c_int32), ("quality_threshold", C.c_double),
+                ("opt", C.c_void_p), ("b", C.c_void_p), ("n_b", C.c_int64), ("rtol", C.c_double),
+                ("maxit", C.c_int32), ("reserved", C.c_int32)]
+
+
+class MgRequestResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("rel_residual", C.c_double),
+                ("true_rel_residual", C.c_double), ("n", C.c_int64), ("device_bytes", C.c_int64),
+                ("t_queue_ms", C.c_double), ("t_setup_ms", C.c_double), ("t_wait_ms", C.c_double),
+                ("t_device_ms", C.c_double), ("t_total_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class MgServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("bytes_in_use", C.c_int64), ("peak_bytes", C.c_int64), ("active", C.c_int32),
+                ("peak_active", C.c_int32), ("queued", C.c_int32), ("reserved", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 _P = C.c_void_p
 _SIGS = {
     "mg_default_options": (None, [C.POINTER(MgOptions)]),
@@ -89,6 +114,14 @@ _SIGS = {
     "mg_coarse_solve": (C.c_int, [_P, _P, _P, _P]),
     "mg_time_smoother_kernel": (C.c_int, [_P, C.c_int32, _P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mg_device_bytes": (C.c_int64, [_P]),
+    "mg_server_create": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.POINTER(_P)]),
+    "mg_server_submit": (C.c_int, [_P, C.POINTER(MgRequest), C.POINTER(C.c_int64)]),
+    "mg_server_poll": (C.c_int, [_P, C.c_int64, C.POINTER(MgRequestResult)]),
+    "mg_server_wait": (C.c_int, [_P, C.c_int64, C.c_double, C.POINTER(MgRequestResult)]),
+    "mg_server_fetch": (C.c_int, [_P, C.c_int64, _P, C.c_int64]),
+    "mg_server_stats": (C.c_int, [_P, C.POINTER(MgServerStats)]),
+    "mg_server_last_error": (C.c_char_p, []),
+    "mg_server_destroy": (None, [_P]),
     "mg_launch_counts": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
 }
 
@@ -386,3 +419,73 @@ def solve_batch(hs, bs, xs, rtol=1e-8, maxit=500, stream=None):
     if code not in (OK, ERR_NO_CONVERGENCE):
         raise NnmgError(code, _err(None))
     return [infos[i].as_dict() for i in range(n)]
+
+
+class Server:
+    """Continuous-batching solve server (see mg_server_* in include/nnmg.h)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 8, setup_threads: int = 4):
+        self._s = C.c_void_p()
+        code = lib.mg_server_create(int(hbm_budget_bytes), max_active, setup_threads, C.byref(self._s))
+        if code != OK:
+            raise NnmgError(code, lib.mg_server_last_error().decode())
+
+    def submit(self, meshes, degree, b=None, rtol=1e-8, maxit=500, quality_threshold=0.1, **opts) -> int:
+        arr = (MgMesh * len(meshes))()
+        keep = []
+        for i, m in enumerate(meshes):
+            coords = _np(m.coords, np.float64)
+            cells = _np(m.cells, np.int32)
+            keep += [coords, cells]
+            arr[i].dim, arr[i].nv, arr[i].nc = coords.shape[1], coords.shape[0], cells.shape[0]
+            arr[i].coords, arr[i].cells = coords.ctypes.data, cells.ctypes.data
+        o = default_options(**opts)
+        q = MgRequest()
+        q.levels = C.cast(arr, C.c_void_p)
+        q.L, q.degree, q.quality_threshold = len(meshes), degree, quality_threshold
+        q.opt = C.cast(C.pointer(o), C.c_void_p)
+        if b is not None:
+            bb = _np(b, np.float64)
+            keep.append(bb)
+            q.b, q.n_b = bb.ctypes.data, bb.size
+        q.rtol, q.maxit = rtol, maxit
+        rid = C.c_int64()
+        code = lib.mg_server_submit(self._s, C.byref(q), C.byref(rid))
+        if code != OK:
+            raise NnmgError(code, lib.mg_server_last_error().decode())
+        return rid.value
+
+    def poll(self, rid: int) -> dict:
+        r = MgRequestResult()
+        _check(lib.mg_server_poll(self._s, rid, C.byref(r)))
+        return r.as_dict()
+
+    def wait(self, rid: int, timeout: float = 600.0) -> dict:
+        r = MgRequestResult()
+        code = lib.mg_server_wait(self._s, rid, timeout, C.byref(r))
+        if code not in (OK, ERR_TIMEOUT):
+            raise NnmgError(code, "wait failed")
+        d = r.as_dict()
+        d["timed_out"] = code == ERR_TIMEOUT
+        return d
+
+    def fetch(self, rid: int, n: int) -> np.ndarray:
+        x = np.zeros(n)
+        _check(lib.mg_server_fetch(self._s, rid, x.ctypes.data, n))
+        return x
+
+    def stats(self) -> dict:
+        st = MgServerStats()
+        _check(lib.mg_server_stats(self._s, C.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if self._s:
+            lib.mg_server_destroy(self._s)
+            self._s = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
