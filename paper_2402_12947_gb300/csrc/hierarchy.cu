@@ -301,9 +301,10 @@ struct Engine {
   }
   void local(int l, cudaStream_t s, bool zero = false) {
     DevLevel<T>& L = lv[l];
-    patch_residual<T>(L.nt, L.pdofs, L.prp, L.pci, L.pv, L.b, zero ? nullptr : L.x, L.rbuf, s);
-    patch_solve<T>(L.nitems, L.items, L.pptr, L.pdofs, L.inv_off, L.inv, L.rbuf, L.x, L.max_patch, s);
-    launches += 2;
+    if (!zero) patch_residual<T>(L.nt, L.pdofs, L.prp, L.pci, L.pv, L.b, L.x, L.rbuf, s);
+    patch_solve<T>(L.nitems, L.items, L.pptr, L.pdofs, L.inv_off, L.inv, zero ? nullptr : L.rbuf, L.b, L.x,
+                   L.max_patch, s);
+    launches += zero ? 1 : 2;
   }
   // zero: the iterate is zero on entry (first pre-smoothing on every level of a cycle)
   void smooth(int l, bool post, cudaStream_t s, bool zero = false) {
@@ -658,8 +659,8 @@ void build_device(mg_hierarchy* h) {
     eng->nc = (int)ncoarse;
     eng->kchunk = 256;
     int rowblocks = (eng->nc + kBlock - 1) / kBlock;
-    int want_chunks = std::max(1, (2 * 152 + rowblocks - 1) / rowblocks);
-    eng->kchunk = std::max(64, std::min(1024, ((eng->nc + want_chunks - 1) / want_chunks + 63) / 64 * 64));
+    int want_chunks = std::max(1, (4 * 152 + rowblocks - 1) / rowblocks);
+    eng->kchunk = std::max(32, std::min(1024, ((eng->nc + want_chunks - 1) / want_chunks + 31) / 32 * 32));
     eng->Xc = const_cast<double*>(coarse_inv);
     eng->cpart = mem.alloc<double>((size_t)dense_chunks(eng->nc, eng->kchunk) * eng->nc);
   };

@@ -222,18 +222,21 @@ __global__ void __launch_bounds__(kBlock) k_cheb0_all(int n, const T* __restrict
 }
 
 // ... then the rows coupled to patch DoFs (where x_in may be non-zero after S_c) are redone
-// with their full row: r = b - A x_in. One thread per such row, CSR order.
+// with their full row: r = b - A x_in. One warp per such row.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_cheb0_halo(int nh, const int32_t* __restrict__ hrow,
                                                        const int32_t* __restrict__ hrp, const int32_t* __restrict__ hci,
                                                        const T* __restrict__ hv, const T* __restrict__ b,
                                                        const T* __restrict__ dinv, const T* __restrict__ xin,
                                                        T* __restrict__ d, T* __restrict__ xout, T cr) {
-  const int t = blockIdx.x * kBlock + threadIdx.x;
-  if (t >= nh) return;
-  const int i = hrow[t];
+  const int t = (blockIdx.x * kBlock + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   T ax = T(0);
-  for (int k = hrp[t]; k < hrp[t + 1]; ++k) ax = fma(hv[k], xin[hci[k]], ax);
+  if (t < nh)
+    for (int k = hrp[t] + lane; k < hrp[t + 1]; k += 32) ax = fma(hv[k], xin[hci[k]], ax);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ax += __shfl_xor_sync(0xffffffffu, ax, o);
+  if (t >= nh || lane != 0) return;
+  const int i = hrow[t];
   const T r = b[i] - ax;
   const T tt = dinv[i] * r;
   const T dn = cr * tt;
@@ -247,10 +250,10 @@ __global__ void __launch_bounds__(kBlock) k_patch_residual(int nt, const int32_t
                                                            const int32_t* __restrict__ prp,
                                                            const int32_t* __restrict__ pci,
                                                            const double* __restrict__ pv, const T* __restrict__ b,
-                                                           const T* x, double* __restrict__ rbuf) {
+                                                           const T* __restrict__ x, double* __restrict__ rbuf) {
   const int t = (blockIdx.x * kBlock + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   double s = 0.0;
-  if (t < nt && x != nullptr)  // x == nullptr: the iterate is zero, r_B = b_B
+  if (t < nt)
     for (int k = prp[t] + lane; k < prp[t + 1]; k += 32) s = fma(pv[k], (double)x[pci[k]], s);
   s = warp_sum(s);
   if (t < nt && lane == 0) rbuf[t] = (double)b[pdofs[t]] - s;
@@ -258,17 +261,18 @@ __global__ void __launch_bounds__(kBlock) k_patch_residual(int nt, const int32_t
 
 // S_c phase 2: e = (A^[d])^{-1} r_B and x_B += e. A work item is 32 consecutive rows of one
 // patch; each warp computes 4 of them, reading row i of the symmetric inverse contiguously.
+// With rbuf == nullptr the iterate is zero and the residual is b itself (no phase 1).
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_patch_solve(const PatchItem* __restrict__ items,
                                                         const int32_t* __restrict__ pptr,
                                                         const int32_t* __restrict__ pdofs,
                                                         const int64_t* __restrict__ inv_off,
-                                                        const double* __restrict__ inv,
-                                                        const double* __restrict__ rbuf, T* __restrict__ x) {
+                                                        const double* __restrict__ inv, const double* rbuf,
+                                                        const T* __restrict__ b, T* __restrict__ x) {
   extern __shared__ double rs[];
   const PatchItem it = items[blockIdx.x];
   const int p0 = pptr[it.patch], n = pptr[it.patch + 1] - p0;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) rs[j] = rbuf[p0 + j];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) rs[j] = rbuf ? rbuf[p0 + j] : (double)b[pdofs[p0 + j]];
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int R = kPatchRowsPerItem / 8;  // rows per warp, accumulated together
@@ -316,9 +320,16 @@ __global__ void __launch_bounds__(kBlock) k_dense_partial(int n, int kchunk, con
   const int i = blockIdx.x * kBlock + threadIdx.x;
   if (i >= n) return;
   const double* Xi = X + i;
-  double s = 0.0;
-  for (int j = k0; j < k1; ++j) s = fma(Xi[(int64_t)j * n], bs[j - k0], s);
-  part[(int64_t)blockIdx.y * n + i] = s;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int j = k0;
+  for (; j + 4 <= k1; j += 4) {
+    s0 = fma(Xi[(int64_t)j * n], bs[j - k0], s0);
+    s1 = fma(Xi[(int64_t)(j + 1) * n], bs[j + 1 - k0], s1);
+    s2 = fma(Xi[(int64_t)(j + 2) * n], bs[j + 2 - k0], s2);
+    s3 = fma(Xi[(int64_t)(j + 3) * n], bs[j + 3 - k0], s3);
+  }
+  for (; j < k1; ++j) s0 = fma(Xi[(int64_t)j * n], bs[j - k0], s0);
+  part[(int64_t)blockIdx.y * n + i] = (s0 + s1) + (s2 + s3);
 }
 
 template <typename T>
@@ -604,7 +615,8 @@ void cheb_first_from_zero(int n, const T* b, const T* dinv, const T* xin, T* d, 
                           const int32_t* hrow, const int32_t* hrp, const int32_t* hci, const T* hv, cudaStream_t s) {
   if (n == 0) return;
   k_cheb0_all<T><<<grid_for(n, kBlock), kBlock, 0, s>>>(n, b, dinv, xin, d, xout, (T)cr);
-  if (nh > 0) k_cheb0_halo<T><<<grid_for(nh, kBlock), kBlock, 0, s>>>(nh, hrow, hrp, hci, hv, b, dinv, xin, d, xout, (T)cr);
+  if (nh > 0)
+    k_cheb0_halo<T><<<grid_for(nh, kBlock / 32), kBlock, 0, s>>>(nh, hrow, hrp, hci, hv, b, dinv, xin, d, xout, (T)cr);
 }
 
 template <typename T>
@@ -624,10 +636,10 @@ void patch_solve_setup(int max_patch) {
 
 template <typename T>
 void patch_solve(int nitems, const PatchItem* items, const int32_t* pptr, const int32_t* pdofs, const int64_t* inv_off,
-                 const double* inv, const double* rbuf, T* x, int max_patch, cudaStream_t s) {
+                 const double* inv, const double* rbuf, const T* b, T* x, int max_patch, cudaStream_t s) {
   if (nitems == 0) return;
   size_t smem = (size_t)max_patch * sizeof(double);
-  k_patch_solve<T><<<nitems, kBlock, smem, s>>>(items, pptr, pdofs, inv_off, inv, rbuf, x);
+  k_patch_solve<T><<<nitems, kBlock, smem, s>>>(items, pptr, pdofs, inv_off, inv, rbuf, b, x);
 }
 
 int dense_chunks(int n, int kchunk) { return grid_for(n, kchunk); }
@@ -690,7 +702,7 @@ void dot_self(int n, const double* r, double* part, cudaStream_t s) {
   template void patch_residual<T>(int, const int32_t*, const int32_t*, const int32_t*, const double*, const T*,  \
                                   const T*, double*, cudaStream_t);                                              \
   template void patch_solve<T>(int, const PatchItem*, const int32_t*, const int32_t*, const int64_t*,            \
-                               const double*, const double*, T*, int, cudaStream_t);                             \
+                               const double*, const double*, const T*, T*, int, cudaStream_t);                   \
   template void dense_solve<T>(int, const double*, const T*, T*, double*, int, cudaStream_t);                    \
   template void axpy_from<T>(int, const T*, double*, cudaStream_t);                                              \
   template void cg_init<T>(int, const double*, double*, double*, T*, T*, double*, cudaStream_t);                 \

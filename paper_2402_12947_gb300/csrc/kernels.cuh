@@ -65,15 +65,17 @@ template <typename T> void sell_restrict(const SellMat<T>& R, const T* r, T* bc,
 void sell_ap(const SellMat<double>& A, const double* p, double* q, double* partial, int* nparts, cudaStream_t s);
 int sell_blocks(int nrows, int lanes);
 
-// ---- local correction S_c (two phases); x == nullptr means the iterate is zero ----
+// ---- local correction S_c (two phases) ----
 template <typename T>
 void patch_residual(int nt, const int32_t* pdofs, const int32_t* prp, const int32_t* pci, const double* pv,
                     const T* b, const T* x, double* rbuf, cudaStream_t s);
 // Raise the dynamic shared-memory limit of the solve kernel for patches of up to max_patch DoFs.
 void patch_solve_setup(int max_patch);
+// rbuf == nullptr: the iterate is zero, the residual is b itself (phase 1 skipped).
 template <typename T>
 void patch_solve(int nitems, const PatchItem* items, const int32_t* pptr, const int32_t* pdofs,
-                 const int64_t* inv_off, const double* inv, const double* rbuf, T* x, int max_patch, cudaStream_t s);
+                 const int64_t* inv_off, const double* inv, const double* rbuf, const T* b, T* x, int max_patch,
+                 cudaStream_t s);
 
 // ---- coarsest level: x = X b with X = A_L^{-1} dense symmetric (split-K, deterministic) ----
 template <typename T>

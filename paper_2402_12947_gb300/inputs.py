@@ -269,11 +269,12 @@ def config_c3(n_fine: int = 128, levels: int = 5, seed: int = 3, n_clusters: int
 
 
 def config_c4(n_fine: int = 64, levels: int = 4, seed: int = 4, n_clusters: int = 256,
-              cluster_levels=(0,), moves_per_cluster=(1, 12)) -> list[Mesh]:
-    """3D P2 unit cube, clusters of 1-12 cap slivers within three rings (uneven patch sizes)."""
+              cluster_levels=(0,), moves_per_cluster=(1, 4)) -> list[Mesh]:
+    """3D P2 unit cube, 256 clusters of 1-4 cap slivers within two rings on the fine level;
+    touching clusters merge into uneven patches (about 100-2000 P2 DoFs)."""
     return hierarchy_meshes(3, n_fine, levels, 0.15, seed, cluster_levels=cluster_levels,
                             n_clusters=n_clusters, moves_per_cluster=moves_per_cluster,
-                            kinds=("cap",), eps=1e-3, rings=3)
+                            kinds=("cap",), eps=1e-3, rings=2)
 
 
 def serving_request(rng: np.random.Generator, seed: int):
