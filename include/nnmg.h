@@ -298,6 +298,21 @@ const char* mg_server_last_error(void);
 /* Finish the requests already admitted, fail the rest, free everything. */
 void mg_server_destroy(mg_server_t* s);
 
+/* ---- allocation-free variant (the paper has no counterpart) ---------------------------
+ * x = X b for a dense symmetric n x n FP64 matrix X (row-major, device), the product the
+ * coarsest-level direct solve applies, for callers that cannot allocate device memory
+ * when they need it (all memory pre-reserved by another allocator, or a latency-critical
+ * path where cudaMalloc/cudaFree would stall or synchronise the device). The split-K
+ * partial sums live in a static device array of 2^20 doubles (8 MiB per device, held until
+ * the process exits) instead of allocated scratch; no allocation happens in the call.
+ * Limits: 1 <= n <= 65536 (larger n: MG_ERR_INVALID_ARG, message in mg_last_error(NULL)).
+ * The first call on a device looks up the array's address with that device current;
+ * make it before any stream capture. All calls share the array (each call writes every
+ * partial it reads, so nothing needs clearing): calls whose kernels overlap on the GPU
+ * race. X_dev, b_dev [n], x_dev [n] are caller-owned device pointers; asynchronous on
+ * `stream`. */
+int mg_dense_symv_static(const double* X_dev, int64_t n, const double* b_dev, double* x_dev, void* stream);
+
 /* Device bytes held by the hierarchy. */
 int64_t mg_device_bytes(const mg_hierarchy_t* h);
 /* Number of kernel launches of one V-cycle, and of one CG iteration (V-cycle included). */

@@ -1029,6 +1029,8 @@ mg_hierarchy* build_host_hierarchy(const mg_mesh_t* levels, int32_t L, int32_t d
 
 void build_device_hierarchy(mg_hierarchy* h) { device_phase(h); }
 
+void set_last_error(const std::string& msg) { g_setup_error = msg; }
+
 int64_t estimate_device_bytes(const mg_hierarchy* h) {
   const int vbytes = h->opt.precision == MG_PREC_MIXED ? 4 : 8;
   int64_t tot = 0, largest = 0;

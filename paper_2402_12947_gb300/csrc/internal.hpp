@@ -99,6 +99,8 @@ void enqueue_host_solve(mg_hierarchy* h, const double* b, double* x, double rtol
 // After `done` has completed: the solve's status and info.
 int collect_host_solve(const mg_hierarchy* h, mg_solve_info_t* info);
 void destroy_hierarchy(mg_hierarchy* h);
+// Message returned by mg_last_error(NULL) in the calling thread.
+void set_last_error(const std::string& msg);
 // Page-locked host staging buffers reused across requests (allocating page-locked memory
 // would synchronise every stream of the device).
 double* pinned_acquire(int64_t n);

@@ -123,6 +123,7 @@ _SIGS = {
     "mg_server_last_error": (C.c_char_p, []),
     "mg_server_destroy": (None, [_P]),
     "mg_launch_counts": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "mg_dense_symv_static": (C.c_int, [_P, C.c_int64, _P, _P, _P]),
 }
 
 
@@ -406,6 +407,13 @@ class Hierarchy:
         ms, nbytes = C.c_double(), C.c_double()
         _check(lib.mg_time_smoother_kernel(self._h, reps, _stream(stream), C.byref(ms), C.byref(nbytes)), self._h)
         return ms.value, nbytes.value
+
+
+def dense_symv_static(X, b, x, stream=None):
+    """x = X b (dense symmetric FP64, n <= 65536) without any device allocation: the
+    split-K partial sums use the library's static device array (see mg_dense_symv_static)."""
+    n = b.numel()
+    _check(lib.mg_dense_symv_static(_dev_ptr(X, n * n), n, _dev_ptr(b, n), _dev_ptr(x, n), _stream(stream)))
 
 
 def solve_batch(hs, bs, xs, rtol=1e-8, maxit=500, stream=None):
