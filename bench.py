@@ -307,7 +307,7 @@ def run_ours(args):
         "gpu_launches": launches * args.steps,
         "roofline": {"bound": "hbm", "achieved": kbytes / (kms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": kbytes / (kms * 1e-3) / 1e9 / peak, "traffic": traffic,
-                     "kernel": "fine-level fused Chebyshev SELL-32 SpMV, FP32 (k_sell_cheb<float,false>)",
+                     "kernel": "fine-level fused Chebyshev SELL-32 SpMV, FP32 (k_cheb<float,1,false>)",
                      "bytes_per_launch": kbytes, "ms_per_launch": kms, "peak_source": peak_src,
                      "fp64_kernel": {"achieved": kbytes64 / (kms64 * 1e-3) / 1e9, "ms_per_launch": kms64,
                                      "bytes_per_launch": kbytes64}},

@@ -427,10 +427,104 @@ void cheb_coefficients(double lmax, double lmin, int k, std::vector<double>& cd,
 
 // Everything after the operators are known: diagonals, patch inverses, eigenvalues,
 // coarsest inverse, then (unless host_only) the device upload and the solve graph.
+// lambda_max of D^{-1/2} A D^{-1/2} restricted to keep (NULL: all) by Lanczos on the device:
+// the scaled operator is uploaded once as a SELL-32 FP64 matrix, every step is an SpMV and
+// two fixed-order reductions, and the host solves the tridiagonal Ritz problem. Same start
+// vector and stopping rule as lanczos_lmax (residual |beta s_last| <= tol theta).
+double device_lanczos(const Csr& A, const uint8_t* keep, double tol, int maxit, int* iters, cudaStream_t s) {
+  const int64_t n = A.nrows;
+  std::vector<double> sc = lanczos_scaling(A, keep);
+  int64_t nk = 0;
+  for (double x : sc) nk += x != 0.0;
+  if (nk == 0) {
+    if (iters) *iters = 0;
+    return 0.0;
+  }
+  Csr S;
+  S.nrows = S.ncols = n;
+  S.rp.assign(n + 1, 0);
+  for (int64_t i = 0; i < n; ++i) {
+    if (sc[i] != 0.0)
+      for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k)
+        if (sc[A.ci[k]] != 0.0) {
+          S.ci.push_back(A.ci[k]);
+          S.v.push_back(sc[i] * A.v[k] * sc[A.ci[k]]);
+        }
+    S.rp[i + 1] = (int32_t)S.ci.size();
+  }
+  DevMem mem;
+  mem.stream = s;
+  SellMat<double> M = make_sell<double>(S, mem, 1);
+  double* v = mem.upload(lanczos_start(sc));
+  double* vprev = mem.alloc<double>(n);
+  double* w = mem.alloc<double>(n);
+  double* part = mem.alloc<double>(cg_parts((int)n));
+  double* ab = mem.alloc<double>(2);
+  double* hab = pinned_acquire(2);
+  std::vector<double> al, be(1, 0.0);
+  double theta = 0.0;
+  int k = 0;
+  for (k = 0; k < std::min<int64_t>(maxit, nk); ++k) {
+    sell_spmv<double>(M, v, w, s);
+    lanczos_dot((int)n, w, v, part, ab, s);
+    lanczos_update((int)n, w, v, vprev, ab, be[k], part, ab + 1, s);
+    CK(cudaMemcpyAsync(hab, ab, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double alpha = hab[0], beta = std::sqrt(hab[1]);
+    al.push_back(alpha);
+    be.push_back(beta);
+    double sl;
+    tridiag_top(al, be, k + 1, &theta, &sl);
+    if (beta * sl <= tol * std::fabs(theta) || beta <= 1e-14 * std::fabs(theta)) {
+      ++k;
+      break;
+    }
+    lanczos_next((int)n, w, v, vprev, 1.0 / beta, s);
+  }
+  check_launch("device Lanczos");
+  pinned_release(hab);
+  mem.release();
+  CK(cudaStreamSynchronize(s));
+  if (iters) *iters = k;
+  return theta;
+}
+
+// lambda_max (unadjusted and adjusted) of every smoothed level, on the host or the device.
+void compute_eigenvalues(mg_hierarchy* h, bool on_device) {
+  const mg_options_t& o = h->opt;
+  PhaseTimer tm;
+  for (int l = 0; l + 1 < h->L; ++l) {
+    LevelH& lv = h->host[l];
+    if (o.lambda_override) {
+      lv.lmax = o.lambda_override[l];
+      if (!(lv.lmax > 0)) throw Error(MG_ERR_INVALID_ARG, "lambda_override must be positive");
+    } else {
+      auto lanczos = [&](const uint8_t* keep, int* it) {
+        return on_device ? device_lanczos(lv.A, keep, o.eig_tol, o.eig_maxit, it, h->own_stream)
+                         : lanczos_lmax(lv.A, keep, o.eig_tol, o.eig_maxit, it);
+      };
+      int it = 0;
+      lv.lmax_unadj = lanczos(nullptr, &it);
+      lv.lanczos_iters = it;
+      if (lv.patch_ptr.size() > 1) {
+        std::vector<uint8_t> keep(lv.A.nrows, 1);
+        for (int32_t f : lv.patch_dofs) keep[f] = 0;
+        lv.lmax_adj = lanczos(keep.data(), &it);
+        lv.lanczos_iters += it;
+      } else {
+        lv.lmax_adj = lv.lmax_unadj;
+      }
+      lv.lmax = (o.adjusted_lambda ? lv.lmax_adj : lv.lmax_unadj) * o.lmax_safety;
+      tm.mark(std::string(on_device ? "device" : "host") + " lanczos L" + std::to_string(l) + " (" +
+              std::to_string(lv.lanczos_iters) + " it)");
+    }
+    lv.lmin = o.lmin_ratio * lv.lmax;
+  }
+}
+
 void finish_setup_host(mg_hierarchy* h) {
   const mg_options_t& o = h->opt;
   const int L = h->L;
-  PhaseTimer tm;
   for (int l = 0; l < L; ++l) {
     LevelH& lv = h->host[l];
     const int64_t n = lv.A.nrows;
@@ -443,32 +537,12 @@ void finish_setup_host(mg_hierarchy* h) {
       if (!(dg > 0)) throw Error(MG_ERR_NOT_SPD, "level " + std::to_string(l) + ": non-positive diagonal at " + std::to_string(i));
       lv.dinv[i] = 1.0 / dg;
     }
-    if (l == L - 1) continue;
-    const int64_t np = (int64_t)lv.patch_ptr.size() - 1;
-    // eigenvalues (Sec. 3.2 / Sec. 5)
-    if (o.lambda_override) {
-      lv.lmax = o.lambda_override[l];
-      if (!(lv.lmax > 0)) throw Error(MG_ERR_INVALID_ARG, "lambda_override must be positive");
-    } else {
-      int it = 0;
-      lv.lmax_unadj = lanczos_lmax(lv.A, nullptr, o.eig_tol, o.eig_maxit, &it);
-      lv.lanczos_iters = it;
-      if (np > 0) {
-        std::vector<uint8_t> keep(n, 1);
-        for (int32_t f : lv.patch_dofs) keep[f] = 0;
-        lv.lmax_adj = lanczos_lmax(lv.A, keep.data(), o.eig_tol, o.eig_maxit, &it);
-        lv.lanczos_iters += it;
-      } else {
-        lv.lmax_adj = lv.lmax_unadj;
-      }
-      tm.mark("lanczos L" + std::to_string(l) + " (" + std::to_string(lv.lanczos_iters) + " it)");
-      lv.lmax = o.adjusted_lambda ? lv.lmax_adj : lv.lmax_unadj;
-      lv.lmax *= o.lmax_safety;
-    }
-    lv.lmin = o.lmin_ratio * lv.lmax;
   }
   const int64_t ncoarse = h->host[L - 1].A.nrows;
   if (ncoarse > 20000) throw Error(MG_ERR_INVALID_ARG, "coarsest level too large for the dense direct solve (> 20000 DoFs)");
+  // eigenvalues (Sec. 3.2 / Sec. 5): on the host only for host-only hierarchies; otherwise
+  // the device phase computes them on the GPU before the smoother coefficients are set
+  if (o.host_only) compute_eigenvalues(h, false);
 }
 
 // Device phase of set-up: upload, batched dense inverses, autotuned layouts. All work is
@@ -486,6 +560,7 @@ void build_device(mg_hierarchy* h) {
   h->device = true;
   DevMem& mem = h->mem;
   mem.stream = h->own_stream;
+  compute_eigenvalues(h, true);
   int max_patch = 0;
   // All dense blocks (every patch matrix A[B_d, B_d] of every level and the coarsest A)
   // are inverted together on the device by the batched Gauss-Jordan sweep.

@@ -59,7 +59,10 @@ struct LevelH {
 };
 
 // ---- threading helper ----
+// Threads a parallel_for may use; set_thread_budget(k) limits the calling thread's loops
+// to k threads (0 = all hardware threads).
 int num_threads();
+void set_thread_budget(int k);
 void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& body);
 
 // ---- setup_fem.cpp: DoF maps, assembly, quality, patches ----
@@ -78,8 +81,21 @@ Csr unit_diagonal_on_empty_rows(const Csr& A);
 Csr spgemm(const Csr& A, const Csr& B);
 // lambda_max of D^{-1/2} A D^{-1/2} restricted to rows/cols with keep[i] != 0 (NULL: all).
 double lanczos_lmax(const Csr& A, const uint8_t* keep, double tol, int maxit, int* iters);
+// Pieces of the Lanczos iteration shared by the host and device versions: the scaling
+// D^{-1/2} (0 on excluded rows), the deterministic unit start vector, and the largest
+// eigenvalue of the tridiagonal T_m (a = diagonal, b[1..m-1] = off-diagonal) with the
+// modulus of the last component of its unit eigenvector.
+std::vector<double> lanczos_scaling(const Csr& A, const uint8_t* keep);
+std::vector<double> lanczos_start(const std::vector<double>& s);
+void tridiag_top(const std::vector<double>& a, const std::vector<double>& b, int m, double* theta, double* slast);
 std::vector<double> dense_submatrix(const Csr& A, const int32_t* idx, int64_t n);
 void spmv_host(const Csr& A, const double* x, double* y);
+
+// Reverse Cuthill-McKee order of A's graph (perm[new] = old), per connected component.
+std::vector<int32_t> rcm_order(const Csr& A);
+// B[i, :] = A[rowperm[i], :] with columns mapped by colmap (old -> new); empty = identity.
+Csr permute_csr(const Csr& A, const std::vector<int32_t>& rowperm, const std::vector<int32_t>& colmap);
+std::vector<int32_t> inverse_perm(const std::vector<int32_t>& p);
 
 // ---- hierarchy.cu: phases of a hierarchy's life used by the solve server ----
 // Host phase of mg_setup (throws Error).

@@ -479,6 +479,46 @@ __global__ void __launch_bounds__(1024) k_cg_finish(int nparts, const double* __
 
 inline int grid_for(int n, int per) { return (n + per - 1) / per; }
 
+// ---- Lanczos on the scaled operator S (set-up): w = S v is a plain SpMV ----
+__global__ void __launch_bounds__(kBlock) k_lz_dot(int n, const double* __restrict__ w, const double* __restrict__ v,
+                                                   double* __restrict__ part) {
+  double s = 0.0;
+  for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) s = fma(w[i], v[i], s);
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// w -= alpha v + beta vprev, partial sums of |w|^2
+__global__ void __launch_bounds__(kBlock) k_lz_update(int n, double* __restrict__ w, const double* __restrict__ v,
+                                                      const double* __restrict__ vprev, const double* __restrict__ alpha,
+                                                      double beta, double* __restrict__ part) {
+  const double a = *alpha;
+  double s = 0.0;
+  for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
+    const double wi = w[i] - (a * v[i] + beta * vprev[i]);
+    w[i] = wi;
+    s = fma(wi, wi, s);
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kBlock) k_lz_next(int n, const double* __restrict__ w, double* __restrict__ v,
+                                                    double* __restrict__ vprev, double inv_beta) {
+  for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
+    vprev[i] = v[i];
+    v[i] = w[i] * inv_beta;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_reduce_sum(int nparts, const double* __restrict__ part,
+                                                     double* __restrict__ out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += 1024) s += part[i];
+  s = block_sum(s);
+  if (threadIdx.x == 0) *out = s;
+}
+
 constexpr double kGjDrop = 1e-10;
 
 __global__ void k_gj_prep(GjBatch g, int k) {
@@ -531,6 +571,19 @@ __global__ void k_gj_update(GjBatch g, int k) {
 }
 
 }  // namespace
+
+void lanczos_dot(int n, const double* w, const double* v, double* part, double* out, cudaStream_t s) {
+  k_lz_dot<<<cg_parts(n), kBlock, 0, s>>>(n, w, v, part);
+  k_reduce_sum<<<1, 1024, 0, s>>>(cg_parts(n), part, out);
+}
+void lanczos_update(int n, double* w, const double* v, const double* vprev, const double* alpha, double beta,
+                    double* part, double* out, cudaStream_t s) {
+  k_lz_update<<<cg_parts(n), kBlock, 0, s>>>(n, w, v, vprev, alpha, beta, part);
+  k_reduce_sum<<<1, 1024, 0, s>>>(cg_parts(n), part, out);
+}
+void lanczos_next(int n, const double* w, double* v, double* vprev, double inv_beta, cudaStream_t s) {
+  k_lz_next<<<cg_parts(n), kBlock, 0, s>>>(n, w, v, vprev, inv_beta);
+}
 
 void batched_spsd_inverse(const GjBatch& g, cudaStream_t s) {
   int active = g.nmat;

@@ -99,6 +99,13 @@ struct GjBatch {
 };
 void batched_spsd_inverse(const GjBatch& g, cudaStream_t s);
 
+// ---- Lanczos (set-up): out = w.v; w -= alpha v + beta vprev with out = |w|^2; v, vprev
+// advanced with v = w / beta. Reductions in a fixed order. ----
+void lanczos_dot(int n, const double* w, const double* v, double* part, double* out, cudaStream_t s);
+void lanczos_update(int n, double* w, const double* v, const double* vprev, const double* alpha, double beta,
+                    double* part, double* out, cudaStream_t s);
+void lanczos_next(int n, const double* w, double* v, double* vprev, double inv_beta, cudaStream_t s);
+
 // ---- vectors ----
 template <typename Src, typename Dst> void convert(int n, const Src* a, Dst* b, cudaStream_t s);
 template <typename T> void axpy_from(int n, const T* z, double* x, cudaStream_t s);   // x += (double) z

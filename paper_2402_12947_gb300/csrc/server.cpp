@@ -12,6 +12,7 @@
 // each). A request's arithmetic does not depend on what else is running: its kernels see
 // only its own buffers (with fixed layouts, sell_sigma >= 1, the result is bitwise the same
 // alone and in the mix).
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -79,6 +80,7 @@ struct mg_server {
   int n_active = 0, peak_active = 0;
   bool stop = false;
   std::vector<std::thread> workers;
+  size_t workers_n = 1;
   std::thread poller;
 
   void finish_locked(Request* r, int status, const std::string& err) {
@@ -91,6 +93,8 @@ struct mg_server {
   }
 
   void worker() {
+    // the set-up workers share the host cores instead of each using all of them
+    nnmg::set_thread_budget(std::max(1, (int)std::thread::hardware_concurrency() / (int)workers_n));
     for (;;) {
       Request* r = nullptr;
       {
@@ -252,6 +256,7 @@ int mg_server_create(int64_t hbm_budget_bytes, int32_t max_active, int32_t setup
   mg_server* s = new mg_server();
   s->budget = hbm_budget_bytes;
   s->max_active = max_active;
+  s->workers_n = (size_t)setup_threads;
   for (int i = 0; i < setup_threads; ++i) s->workers.emplace_back(&mg_server::worker, s);
   s->poller = std::thread(&mg_server::poll, s);
   *out = s;

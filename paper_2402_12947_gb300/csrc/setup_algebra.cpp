@@ -288,10 +288,8 @@ void spmv_host(const Csr& A, const double* x, double* y) {
   });
 }
 
-namespace {
-
 // Number of eigenvalues of the symmetric tridiagonal (a, b) smaller than x (Sturm count).
-int sturm_count(const std::vector<double>& a, const std::vector<double>& b, int m, double x) {
+static int sturm_count(const std::vector<double>& a, const std::vector<double>& b, int m, double x) {
   int c = 0;
   double q = 1.0;
   for (int i = 0; i < m; ++i) {
@@ -338,25 +336,21 @@ void tridiag_top(const std::vector<double>& a, const std::vector<double>& b, int
   *slast = std::fabs(x[m - 1]);
 }
 
-}  // namespace
 
-double lanczos_lmax(const Csr& A, const uint8_t* keep, double tol, int maxit, int* iters) {
-  const int64_t n = A.nrows;
-  std::vector<double> s(n);
-  for (int64_t i = 0; i < n; ++i) {
+std::vector<double> lanczos_scaling(const Csr& A, const uint8_t* keep) {
+  std::vector<double> s(A.nrows);
+  for (int64_t i = 0; i < A.nrows; ++i) {
     double dgn = 0;
     for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k)
       if (A.ci[k] == i) dgn = A.v[k];
     s[i] = (keep && !keep[i]) ? 0.0 : 1.0 / std::sqrt(dgn);
   }
-  int64_t nk = 0;
-  for (int64_t i = 0; i < n; ++i) nk += s[i] != 0.0;
-  if (nk == 0) {
-    if (iters) *iters = 0;
-    return 0.0;
-  }
-  // deterministic start vector (splitmix64 of the index)
-  std::vector<double> v(n), vprev(n, 0.0), w(n), t(n);
+  return s;
+}
+
+std::vector<double> lanczos_start(const std::vector<double>& s) {
+  const int64_t n = (int64_t)s.size();
+  std::vector<double> v(n);
   double nrm = 0;
   for (int64_t i = 0; i < n; ++i) {
     uint64_t z = (uint64_t)i * 0x9E3779B97F4A7C15ull + 0x1234567ull;
@@ -367,7 +361,22 @@ double lanczos_lmax(const Csr& A, const uint8_t* keep, double tol, int maxit, in
     nrm += v[i] * v[i];
   }
   nrm = std::sqrt(nrm);
-  for (auto& x : v) x /= nrm;
+  if (nrm > 0)
+    for (auto& x : v) x /= nrm;
+  return v;
+}
+
+double lanczos_lmax(const Csr& A, const uint8_t* keep, double tol, int maxit, int* iters) {
+  const int64_t n = A.nrows;
+  std::vector<double> s = lanczos_scaling(A, keep);
+  int64_t nk = 0;
+  for (int64_t i = 0; i < n; ++i) nk += s[i] != 0.0;
+  if (nk == 0) {
+    if (iters) *iters = 0;
+    return 0.0;
+  }
+  // deterministic start vector (splitmix64 of the index)
+  std::vector<double> v = lanczos_start(s), vprev(n, 0.0), w(n), t(n);
   std::vector<double> al, be(1, 0.0);
   double theta = 0;
   int k = 0;
@@ -400,6 +409,100 @@ double lanczos_lmax(const Csr& A, const uint8_t* keep, double tol, int maxit, in
   }
   if (iters) *iters = k;
   return theta;
+}
+
+}  // namespace nnmg
+
+namespace nnmg {
+
+// Reverse Cuthill-McKee order of the graph of A (symmetric pattern): breadth-first search
+// from a pseudo-peripheral vertex of each connected component, neighbours visited by
+// increasing degree, then reversed. Returns perm with perm[new] = old.
+std::vector<int32_t> rcm_order(const Csr& A) {
+  const int64_t n = A.nrows;
+  std::vector<int32_t> deg(n), order;
+  order.reserve(n);
+  for (int64_t i = 0; i < n; ++i) deg[i] = A.rp[i + 1] - A.rp[i];
+  std::vector<uint8_t> seen(n, 0);
+  std::vector<int32_t> level(n, -1), nb;
+  // breadth-first levels from s inside the unvisited part; returns the last vertex reached
+  auto bfs_far = [&](int32_t s, std::vector<int32_t>& visited) {
+    visited.clear();
+    visited.push_back(s);
+    level[s] = 0;
+    int32_t far = s;
+    for (size_t h = 0; h < visited.size(); ++h) {
+      int32_t u = visited[h];
+      for (int32_t k = A.rp[u]; k < A.rp[u + 1]; ++k) {
+        int32_t w = A.ci[k];
+        if (w == u || seen[w] || level[w] >= 0) continue;
+        level[w] = level[u] + 1;
+        visited.push_back(w);
+        if (level[w] > level[far] || (level[w] == level[far] && deg[w] < deg[far])) far = w;
+      }
+    }
+    for (int32_t u : visited) level[u] = -1;
+    return far;
+  };
+  std::vector<int32_t> comp;
+  for (int64_t s0 = 0; s0 < n; ++s0) {
+    if (seen[s0]) continue;
+    int32_t start = (int32_t)s0;
+    for (int pass = 0; pass < 2; ++pass) start = bfs_far(start, comp);
+    // Cuthill-McKee from `start`
+    size_t head = order.size();
+    order.push_back(start);
+    seen[start] = 1;
+    for (size_t h = head; h < order.size(); ++h) {
+      int32_t u = order[h];
+      nb.clear();
+      for (int32_t k = A.rp[u]; k < A.rp[u + 1]; ++k) {
+        int32_t w = A.ci[k];
+        if (!seen[w]) {
+          seen[w] = 1;
+          nb.push_back(w);
+        }
+      }
+      std::stable_sort(nb.begin(), nb.end(), [&](int32_t a, int32_t b) { return deg[a] < deg[b]; });
+      order.insert(order.end(), nb.begin(), nb.end());
+    }
+  }
+  std::reverse(order.begin(), order.end());
+  return order;
+}
+
+// B[i, :] = A[rowperm[i], :] with columns renumbered by colmap (old -> new), sorted.
+Csr permute_csr(const Csr& A, const std::vector<int32_t>& rowperm, const std::vector<int32_t>& colmap) {
+  Csr B;
+  B.nrows = A.nrows;
+  B.ncols = A.ncols;
+  B.rp.assign(A.nrows + 1, 0);
+  for (int64_t i = 0; i < A.nrows; ++i) {
+    int32_t r = rowperm.empty() ? (int32_t)i : rowperm[i];
+    B.rp[i + 1] = B.rp[i] + (A.rp[r + 1] - A.rp[r]);
+  }
+  B.ci.resize(A.nnz());
+  B.v.resize(A.nnz());
+  parallel_for(A.nrows, [&](int64_t lo, int64_t hi) {
+    std::vector<std::pair<int32_t, double>> row;
+    for (int64_t i = lo; i < hi; ++i) {
+      int32_t r = rowperm.empty() ? (int32_t)i : rowperm[i];
+      row.clear();
+      for (int32_t k = A.rp[r]; k < A.rp[r + 1]; ++k)
+        row.emplace_back(colmap.empty() ? A.ci[k] : colmap[A.ci[k]], A.v[k]);
+      std::sort(row.begin(), row.end(), [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) {
+        return a.first < b.first;
+      });
+      for (size_t k = 0; k < row.size(); ++k) B.ci[B.rp[i] + k] = row[k].first, B.v[B.rp[i] + k] = row[k].second;
+    }
+  });
+  return B;
+}
+
+std::vector<int32_t> inverse_perm(const std::vector<int32_t>& p) {
+  std::vector<int32_t> q(p.size());
+  for (size_t i = 0; i < p.size(); ++i) q[p[i]] = (int32_t)i;
+  return q;
 }
 
 }  // namespace nnmg

@@ -15,9 +15,16 @@
 
 namespace nnmg {
 
+namespace {
+thread_local int tl_thread_budget = 0;
+}
+
+void set_thread_budget(int k) { tl_thread_budget = k; }
+
 int num_threads() {
   unsigned n = std::thread::hardware_concurrency();
-  return (int)std::max(1u, std::min(n, 32u));
+  int all = (int)std::max(1u, std::min(n, 32u));
+  return tl_thread_budget > 0 ? std::min(all, tl_thread_budget) : all;
 }
 
 void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& body) {

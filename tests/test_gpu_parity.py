@@ -252,3 +252,16 @@ def test_batch_matches_individual_solves(nnmg):
     for a, x, inf in zip(alone, xs, infos):
         assert inf["converged"]
         assert torch.equal(a, x)
+
+
+@pytest.mark.parametrize("name", ["c1_p1", "c1_p2", "c2_p2_128", "cube_p1"])
+def test_device_lanczos_eigenvalues(nnmg, name):
+    """lambda_max of D^-1 A (Sec. 3.2) and the adjusted value (Sec. 5), estimated by the
+    device Lanczos, agree with the oracle's dense/ARPACK values to 1e-8."""
+    meshes, Ho, degree, layers = case(name)
+    with nnmg.Hierarchy.from_meshes(meshes, degree, 0.1, patch_layers=layers) as H:
+        for l, lo in enumerate(Ho.levels[:-1]):
+            lu, la, used = H.eigs(l)
+            assert abs(lu - lo.lmax_unadj) < 1e-8 * lo.lmax_unadj, (l, lu, lo.lmax_unadj)
+            assert abs(la - lo.lmax_adj) < 1e-8 * lo.lmax_adj, (l, la, lo.lmax_adj)
+            assert used == la
