@@ -31,6 +31,13 @@ METRIC = "DoFs/s solved to rtol 1e-8 (mixed vs FP64, same GPU); SpMV HBM GB/s; p
 WORKLOAD = ("2D Poisson P2, unit square 1024^2 x 2 triangles (4,190,209 DoFs), 6 non-nested levels, "
             "32 needle/flattened clusters (AR 1e2-1e4) per fine/intermediate level, "
             "sandwich S_c-Chebyshev(2)-S_c with adjusted lambda, MG-PCG rtol 1e-8, RHS U[-1,1]")
+WORKLOADS = {
+    "c2": (WORKLOAD, 2),
+    "c3": ("3D Poisson P1, unit cube 128^3 x 6 tets (2,048,383 DoFs), 5 non-nested levels, 64 cap slivers "
+           "(1e-3 h) on the fine and 2nd-coarsest level, sandwich smoother, MG-PCG rtol 1e-8, RHS U[-1,1]", 1),
+    "c4": ("3D Poisson P2, unit cube 64^3 x 6 tets (2,048,383 DoFs), 4 non-nested levels, 256 sliver clusters "
+           "merged into 212 patches of 118-2053 DoFs, sandwich smoother, MG-PCG rtol 1e-8, RHS U[-1,1]", 2),
+}
 SAMPLE_N = 256   # CPU oracle sample: the same family at 256^2 (261,121 DoFs, 4 levels)
 RTOL = 1e-8
 
@@ -47,8 +54,13 @@ def parse():
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every kernel individually instead of one CUDA graph per solve (profilers "
                          "cannot see kernel nodes of graphs with conditional nodes)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "serve"],
-                    help="'serve': the mixed request stream through the continuous-batching server")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "serve", "paper"],
+                    help="'serve': the mixed request stream through the continuous-batching server; "
+                         "'paper': the Case A/B comparison and the residual history of the paper's examples")
+    ap.add_argument("--reorder", default=None, choices=["none", "rcm", "spatial"],
+                    help="device-internal DoF order (default: the library's default)")
+    ap.add_argument("--global-smoother", default="chebyshev", choices=["chebyshev", "sgs"],
+                    help="S_g of the combined smoother (c2/c3/c4)")
     ap.add_argument("--requests", type=int, default=512)
     ap.add_argument("--rates", default="4,16,64", help="Poisson arrival rates (requests/s) to sweep")
     ap.add_argument("--precision", default="both", choices=["both", "mixed"],
@@ -87,7 +99,7 @@ def profiled_traffic():
     return None, None
 
 
-KERNEL_REV = "sell32-v2"   # bump when the timed kernel changes (invalidates the profiled traffic)
+KERNEL_REV = "sell32-morton16-v4"   # bump when the timed kernel changes (invalidates the profiled traffic)
 
 
 class ClockSampler:
@@ -190,6 +202,7 @@ def run_reference(args):
 
 
 def run_ours(args):
+    """C2 (the headline), C3 or C4: mixed and FP64 MG-PCG solves to rtol 1e-8."""
     import numpy as np
     import torch
 
@@ -201,15 +214,27 @@ def run_ours(args):
     from paper_2402_12947_gb300 import build, inputs, nnmg
     build.build()
 
-    meshes = inputs.config_c2(n_fine=args.n_fine, levels=args.levels, seed=2 + 1000 * rank)
+    workload, degree = WORKLOADS[args.workload]
+    if args.global_smoother == "sgs":
+        workload = workload.replace("Chebyshev(2)", "multicolour SGS")
+    if args.workload == "c2":
+        meshes = inputs.config_c2(n_fine=args.n_fine, levels=args.levels, seed=2 + 1000 * rank)
+    elif args.workload == "c3":
+        meshes = inputs.config_c3(seed=3 + 1000 * rank)
+    else:
+        meshes = inputs.config_c4(seed=4 + 1000 * rank)
     both = args.precision == "both"
     t0 = time.perf_counter()
     graph = 0 if args.no_graph else 1
-    H64 = nnmg.Hierarchy.from_meshes(meshes, 2, 0.1, use_graph=graph) if both else None
+    opts = dict(use_graph=graph, global_smoother=args.global_smoother)
+    if args.reorder is not None:
+        opts["reorder"] = {"none": 0, "rcm": 1, "spatial": 2}[args.reorder]
+    sgs = args.global_smoother == "sgs"
+    H64 = nnmg.Hierarchy.from_meshes(meshes, degree, 0.1, **opts) if both else None
     setup64 = time.perf_counter() - t0
-    lam = [H64.eigs(l)[2] for l in range(H64.num_levels - 1)] if both else None
+    lam = [H64.eigs(l)[2] for l in range(H64.num_levels - 1)] if both and not sgs else None
     t0 = time.perf_counter()
-    H32 = nnmg.Hierarchy.from_meshes(meshes, 2, 0.1, precision="mixed", lambda_override=lam, use_graph=graph)
+    H32 = nnmg.Hierarchy.from_meshes(meshes, degree, 0.1, precision="mixed", lambda_override=lam, **opts)
     setup32 = time.perf_counter() - t0
     n = H32.num_dofs(0)
     b_host = inputs.uniform_rhs(n, 2 + rank)
@@ -274,28 +299,36 @@ def run_ours(args):
     kms64, kbytes64 = H64.time_smoother_kernel(reps=50) if both else (float("nan"), float("nan"))
     peak, peak_src = measured_peak()
     traffic, rev = profiled_traffic()
-    if rev != KERNEL_REV:
+    if rev != KERNEL_REV or sgs:
         traffic = None
     per_vc, per_it = H32.launch_counts()
+    nnz0 = int(nnmg.lib.mg_level_nnz(H32._h, 0))
     launches = per_it * info32["iterations"] + 8   # head, CG init and the true-residual check
     if rank != 0:
         return 0
     cpu = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and args.workload == "c2":
         d = cpu_baseline_subprocess(SAMPLE_N, steps=1)
         cpu = {"value": d["n"] / d["times"][0], "unit": "DoFs/s", "cores": 1, "kind": "oracle",
                "sample": f"oracle MG-PCG solve (setup excluded) on the same family at {SAMPLE_N}^2 "
                          f"({d['n']} DoFs, {d['levels']} levels, {d['iterations'][0]} iterations, "
                          f"{d['times'][0]:.1f} s), single-threaded NumPy/SciPy"}
     value = n * world / (ms32 * 1e-3)
+    order = args.reorder or "spatial"
+    kernel_name = (f"fine-level multicolour SGS application, FP32 (k_gs, one launch per colour and sweep, "
+                   f"autotuned layouts, {order} order)" if sgs else
+                   f"fine-level fused Chebyshev SpMV, FP32 (k_cheb, autotuned layout, {order} order, 16-bit "
+                   f"column offsets where a slice spans < 2^16 columns)")
     line = {
         "metric": METRIC, "value": value, "unit": "DoFs/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}", "rtol": RTOL,
+        "config": {"workload": workload, "parallelism": f"replicas x{world}", "rtol": RTOL,
                    "launch": "per-kernel launches" if args.no_graph else "one CUDA graph per solve (conditional while)",
-                   "l2": "inputs larger than L2 (A_0 alone 0.58 GB FP64 / 0.39 GB FP32)",
-                   "dofs_per_gpu": n, "levels": H32.num_levels},
+                   "l2": f"inputs larger than L2 (A_0 alone {12e-9 * nnz0:.2f} GB FP64 / {8e-9 * nnz0:.2f} GB FP32 "
+                         "with 32-bit indices)",
+                   "dofs_per_gpu": n, "levels": H32.num_levels, "global_smoother": args.global_smoother,
+                   "internal_order": order},
         "iterations": {"mixed": info32["iterations"], "fp64": info64.get("iterations")},
         "p50_ms": lat32[len(lat32) // 2], "p99_ms": lat32[min(len(lat32) - 1, int(0.99 * len(lat32)))],
         "fp64": {"value": n * world / (ms64 * 1e-3), "ms_per_step": ms64, "iterations": info64.get("iterations"),
@@ -307,7 +340,7 @@ def run_ours(args):
         "gpu_launches": launches * args.steps,
         "roofline": {"bound": "hbm", "achieved": kbytes / (kms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": kbytes / (kms * 1e-3) / 1e9 / peak, "traffic": traffic,
-                     "kernel": "fine-level fused Chebyshev SELL-32 SpMV, FP32 (k_cheb<float,1,false>)",
+                     "kernel": kernel_name,
                      "bytes_per_launch": kbytes, "ms_per_launch": kms, "peak_source": peak_src,
                      "fp64_kernel": {"achieved": kbytes64 / (kms64 * 1e-3) / 1e9, "ms_per_launch": kms64,
                                      "bytes_per_launch": kbytes64}},
@@ -387,8 +420,74 @@ def run_serve(args):
     return 0
 
 
+def run_paper(args):
+    """Sec. 6 comparisons on synthetic hierarchies (the paper's meshes are not available):
+    CG iterations (one V-cycle per iteration) and stationary V-cycles to 1e-10 for the clean
+    reference, Case A (clusters on every level) and Case B (every level but the finest),
+    without correction, with correction and the unadjusted lambda_max, and with correction
+    and the adjusted lambda_max (the layout of Table number_struct); and the residual
+    history of a two-level cycle on f = 0 from u0 = sin(10 pi x) sin(10 pi y) (Sec. 6.1.1)."""
+    import numpy as np
+    import torch
+    from paper_2402_12947_gb300 import build, inputs, nnmg
+    build.build()
+    torch.cuda.set_device(0)
+    problems = [("2D P1 256^2", 2, 1, 256, 4), ("2D P2 256^2", 2, 2, 256, 4),
+                ("3D P1 32^3", 3, 1, 32, 3), ("3D P2 16^3", 3, 2, 16, 3)]
+    table = {}
+    for label, dim, degree, n, levels in problems:
+        amp = 0.2 if dim == 2 else 0.15
+        kw = dict(n_clusters=8 if dim == 2 else 6, moves_per_cluster=(2, 4), kinds=("cap",), eps=1e-3)
+        meshes = {"reference": inputs.hierarchy_meshes(dim, n, levels, amp, 11),
+                  "A": inputs.hierarchy_meshes(dim, n, levels, amp, 11, cluster_levels=tuple(range(levels)), **kw),
+                  "B": inputs.hierarchy_meshes(dim, n, levels, amp, 11, cluster_levels=tuple(range(1, levels)), **kw)}
+        nfree = (n - 1) ** dim if degree == 1 else (2 * n - 1) ** dim
+        b = torch.from_numpy(inputs.uniform_rhs(nfree, 3)).cuda()
+        variants = {"reference": ("reference", dict())}
+        for case in ("A", "B"):
+            variants[f"{case} without correction"] = (case, dict(smoother="global", adjusted_lambda=0))
+            variants[f"{case} correction, unadjusted lambda"] = (case, dict(adjusted_lambda=0))
+            variants[f"{case} correction, adjusted lambda"] = (case, dict(adjusted_lambda=1))
+        row = {}
+        for name, (case, opt) in variants.items():
+            with nnmg.Hierarchy.from_meshes(meshes[case], degree, 0.1, **opt) as H:
+                x = torch.zeros_like(b)
+                cg = H.solve(b, x, rtol=1e-10, maxit=300, raise_on_fail=False)
+                x.zero_()
+                st = H.solve_stationary(b, x, rtol=1e-10, maxit=300)
+                row[name] = {"cg": cg["iterations"] if cg["converged"] else f">{cg['iterations']}",
+                             "stationary": st["iterations"] if st["converged"] else f">{st['iterations']}",
+                             "lambda_used_L0": H.eigs(0)[2]}
+        table[label] = row
+    # residual history, two levels (Sec. 6.1.1 shape): 64^2 fine with one cluster, 32^2 coarse
+    hist = {}
+    base = inputs.hierarchy_meshes(2, 64, 2, 0.2, 21)
+    bad = inputs.hierarchy_meshes(2, 64, 2, 0.2, 21, cluster_levels=(0,), n_clusters=1, moves_per_cluster=(3, 3),
+                                  kinds=("cap",), eps=1e-3)
+    for name, ms, opt in (("high quality", base, dict()), ("low quality, no correction", bad,
+                          dict(smoother="global", adjusted_lambda=0)), ("low quality, correction", bad, dict())):
+        with nnmg.Hierarchy.from_meshes(ms, 1, 0.1, **opt) as H:
+            pts = H.dof_coords(0, 2)
+            x = torch.from_numpy(np.sin(10 * np.pi * pts[:, 0]) * np.sin(10 * np.pi * pts[:, 1])).cuda()
+            zero = torch.zeros_like(x)
+            ax = torch.zeros_like(x)
+            H.apply_A(0, x, ax)
+            r0 = float(ax.norm())
+            h = []
+            for _ in range(12):
+                H.vcycle(zero, x)
+                H.apply_A(0, x, ax)
+                h.append(float(ax.norm()) / r0)
+            hist[name] = h
+    print(json.dumps({"workload": "paper", "iterations_to_1e-10": table, "residual_history_two_level": hist}),
+          flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "paper":
+        return run_paper(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "serve":

@@ -64,6 +64,28 @@ enum mg_smoother {
   MG_SMOOTHER_GLOBAL = 2             /* S_g only (no local correction) */
 };
 
+/* Global smoother S_g (option `global_smoother`). */
+enum mg_global_smoother {
+  MG_GLOBAL_CHEBYSHEV = 0, /* Chebyshev on D^-1 A, cheb_degree steps (Sec. 3.2) */
+  MG_GLOBAL_SGS = 1        /* symmetric Gauss-Seidel (Sec. 3.1 and Sec. 6 experiments), in
+                              the multicolour form: rows greedily coloured in library index
+                              order, ignoring couplings |a_ij| <= 1e-12 sqrt(a_ii a_jj); one
+                              application sweeps the colours 0..C-1 then C-1..0, each colour's
+                              rows at once (x_i = (b_i - sum_{j != i} a_ij x_j) / a_ii). No
+                              lambda_max is computed. */
+};
+
+/* Device-internal DoF order of the smoothed levels (option `reorder`). Column indices are
+ * stored as 16-bit offsets from a per-slice (per-row) base wherever the slice spans fewer
+ * than 2^16 columns, so orders that keep neighbours close in index shrink the matrix. */
+enum mg_reorder {
+  MG_REORDER_NONE = 0,    /* the library numbering */
+  MG_REORDER_RCM = 1,     /* reverse Cuthill-McKee of the matrix graph */
+  MG_REORDER_SPATIAL = 2  /* Z-order (Morton) of the DoF points, vertex and edge DoFs
+                             interleaved; the library numbering where a level has no points
+                             (mg_setup_csr) */
+};
+
 /* Arithmetic of the V-cycle (option `precision`). */
 enum mg_precision {
   MG_PREC_FP64 = 0,   /* everything in FP64 */
@@ -109,7 +131,11 @@ typedef struct mg_options_t {
   int32_t sell_sigma;      /* SELL-32 slot order: rows sorted by length within windows of this
                               many rows (1 = natural order); 0 = autotune: time y = A x on the
                               device for windows {1, 256, 2048} per operator, keep the fastest (0) */
-  int32_t reserved[5];
+  int32_t reorder;         /* enum mg_reorder: the order in which the device stores each
+                              level but the coarsest (vectors at the ABI stay in the library's
+                              numbering) (SPATIAL) */
+  int32_t global_smoother; /* enum mg_global_smoother (CHEBYSHEV) */
+  int32_t reserved[3];
 } mg_options_t;
 
 /* Result of a solve. */
@@ -176,6 +202,10 @@ int mg_export_level(const mg_hierarchy_t* h, int32_t level, int32_t* rowptr, int
 int mg_export_transfer(const mg_hierarchy_t* h, int32_t level, int32_t* rowptr, int32_t* colidx, double* values);
 /* Patches of a level: ptr[num+1], dofs[total] (free DoF ids). */
 int mg_export_patches(const mg_hierarchy_t* h, int32_t level, int32_t* ptr, int32_t* dofs);
+/* The multicolour SGS colouring of level l (library numbering): *ncolours, and colour[n]
+ * (nullable) with each DoF's colour. INVALID_ARG unless global_smoother = MG_GLOBAL_SGS
+ * and l is below the coarsest level. Works for host-only hierarchies. */
+int mg_export_colouring(const mg_hierarchy_t* h, int32_t level, int32_t* ncolours, int32_t* colour);
 /* lambda_max of D^-1 A_l, unadjusted and adjusted (Sec. 5), as estimated at setup (0 when
  * an override was given), and the value the smoother uses. */
 int mg_eigs(const mg_hierarchy_t* h, int32_t level, double* lmax, double* lmax_adj, double* lmax_used);
@@ -221,6 +251,10 @@ int mg_solve_batch(mg_hierarchy_t* const* hs, const double* const* b_dev, double
 int mg_apply_A(mg_hierarchy_t* h, int32_t level, const double* x_dev, double* y_dev, void* stream);
 /* One Chebyshev smoother application S_g of cheb_degree steps on level l, in place. */
 int mg_chebyshev(mg_hierarchy_t* h, int32_t level, const double* b_dev, double* x_dev, void* stream);
+/* One multicolour symmetric Gauss-Seidel application on level l (forward then backward
+ * colour sweep, see MG_GLOBAL_SGS), in place. INVALID_ARG unless the hierarchy was built
+ * with global_smoother = MG_GLOBAL_SGS. */
+int mg_sgs(mg_hierarchy_t* h, int32_t level, const double* b_dev, double* x_dev, void* stream);
 /* One local correction S_c on level l (Alg. 2), in place. */
 int mg_local_correction(mg_hierarchy_t* h, int32_t level, const double* b_dev, double* x_dev, void* stream);
 /* One combined smoother application on level l (post = 0: pre-smoothing order), in place. */

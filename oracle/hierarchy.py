@@ -19,6 +19,7 @@ import scipy.sparse as sp
 
 from . import eig as _eig
 from . import fem, patches as _patches, quality, transfer
+from . import smoother
 from .smoother import DirectSolver, LocalSolver
 
 
@@ -38,6 +39,7 @@ class Level:
     lmax_adj: float = 0.0
     lmax: float = 0.0
     lmin: float = 0.0
+    colour: np.ndarray | None = None    # greedy colouring (multicolour SGS)
 
     @property
     def n(self) -> int:
@@ -52,6 +54,7 @@ class Hierarchy:
     nu: int = 1
     order: str = "sandwich"
     coarse: DirectSolver | None = None
+    smoother_kind: str = "chebyshev"     # global smoother: "chebyshev" or "sgs"
 
     @property
     def L(self) -> int:
@@ -61,7 +64,7 @@ class Hierarchy:
 def build(meshes, degree: int, threshold: float = 0.1, layers: int = 1, adjusted: bool = True,
           lmin_ratio: float = 0.1, cheb_degree: int = 2, nu: int = 1, order: str = "sandwich",
           lambda_override=None, dirichlet_masks=None, local_levels=None,
-          compute_eigs: bool = True) -> Hierarchy:
+          compute_eigs: bool = True, smoother_kind: str = "chebyshev") -> Hierarchy:
     L = len(meshes)
     levels = []
     for l, m in enumerate(meshes):
@@ -85,6 +88,9 @@ def build(meshes, degree: int, threshold: float = 0.1, layers: int = 1, adjusted
         lev.local = LocalSolver(lev.A, lev.patches)
         if l == L - 1:
             continue
+        if smoother_kind == "sgs":
+            lev.colour = smoother.greedy_colouring(lev.A)
+            continue
         if lambda_override is not None:
             lev.lmax = float(lambda_override[l])
         elif compute_eigs:
@@ -94,7 +100,7 @@ def build(meshes, degree: int, threshold: float = 0.1, layers: int = 1, adjusted
         lev.lmin = lmin_ratio * lev.lmax
     coarse = DirectSolver(levels[-1].A.toarray())
     return Hierarchy(levels=levels, degree=degree, cheb_degree=cheb_degree, nu=nu, order=order,
-                     coarse=coarse)
+                     coarse=coarse, smoother_kind=smoother_kind)
 
 
 def from_matrices(As, Ps, patches, lmax, cheb_degree=2, nu=1, order="sandwich", lmin_ratio=0.1):

@@ -30,13 +30,15 @@ def vcycle(H: Hierarchy, b: np.ndarray, x: np.ndarray | None = None, l: int = 0)
         return H.coarse.solve(b)
     x = np.zeros_like(b) if x is None else x.copy()
     for _ in range(H.nu):
-        x = smooth(lev.A, lev.dinv, b, x, lev.lmax, lev.lmin, H.cheb_degree, lev.local, H.order, post=False)
+        x = smooth(lev.A, lev.dinv, b, x, lev.lmax, lev.lmin, H.cheb_degree, lev.local, H.order, post=False,
+                   kind=H.smoother_kind, colour=lev.colour)
     r = b - lev.A @ x
     bc = lev.R @ r
     xc = vcycle(H, bc, None, l + 1)
     x = x + lev.P @ xc
     for _ in range(H.nu):
-        x = smooth(lev.A, lev.dinv, b, x, lev.lmax, lev.lmin, H.cheb_degree, lev.local, H.order, post=True)
+        x = smooth(lev.A, lev.dinv, b, x, lev.lmax, lev.lmin, H.cheb_degree, lev.local, H.order, post=True,
+                   kind=H.smoother_kind, colour=lev.colour)
     return x
 
 

@@ -24,6 +24,15 @@ Reading for the smoother order option: "sandwich" (default, the paper's form);
 "global_then_local" applies S_g then S_c before the coarse correction and S_c then S_g
 after it (still symmetric); "global" is S_g alone (no local correction).
 
+S_g alternative (the paper's other global smoother, Sec. 3.1 and Sec. 6: symmetric
+Gauss-Seidel): a multicolour symmetric Gauss-Seidel sweep. Rows are coloured greedily in
+index order (the smallest colour not used by an already coloured neighbour; couplings
+below 1e-12 sqrt(a_ii a_jj), rounding residue of the Galerkin products, are ignored);
+a forward
+sweep updates the colours 0..C-1 in turn, each colour's rows at once
+(x_i += (b - A x)_i / a_ii), and a backward sweep the colours C-1..0. This is exactly
+sequential symmetric Gauss-Seidel in the colour-sorted row order.
+
 Pinned by tests/test_oracle_smoother.py: Chebyshev error polynomial against the
 closed form via a dense eigendecomposition; S_c exact when one patch covers all DoFs;
 S_gc applied to unit vectors equals the explicit formula and is symmetric; no patches
@@ -112,19 +121,60 @@ class LocalSolver:
         return x
 
 
-def smooth(A, dinv, b, x, lmax, lmin, k, local: LocalSolver | None, order: str, post: bool):
+COLOUR_TOL = 1e-12
+
+
+def greedy_colouring(A: sp.csr_matrix) -> np.ndarray:
+    """colour[i] = the smallest colour not taken by a neighbour j < i (index order)."""
+    n = A.shape[0]
+    d = np.sqrt(np.abs(A.diagonal()))
+    colour = -np.ones(n, dtype=np.int64)
+    for i in range(n):
+        cols = A.indices[A.indptr[i]:A.indptr[i + 1]]
+        vals = A.data[A.indptr[i]:A.indptr[i + 1]]
+        cols = cols[np.abs(vals) > COLOUR_TOL * d[i] * d[cols]]
+        used = set(colour[cols].tolist())
+        c = 0
+        while c in used:
+            c += 1
+        colour[i] = c
+    return colour
+
+
+def multicolour_sgs(A: sp.csr_matrix, dinv: np.ndarray, b: np.ndarray, x: np.ndarray,
+                    colour: np.ndarray) -> np.ndarray:
+    """One symmetric sweep: colours 0..C-1, then C-1..0."""
+    x = x.copy()
+    C = int(colour.max()) + 1
+    for c in list(range(C)) + list(range(C - 1, -1, -1)):
+        rows = np.flatnonzero(colour == c)
+        x[rows] += dinv[rows] * (b[rows] - A[rows] @ x)
+    return x
+
+
+def global_smoother(A, dinv, b, x, lmax, lmin, k, kind: str = "chebyshev", colour=None):
+    if kind == "chebyshev":
+        return chebyshev(A, dinv, b, x, lmax, lmin, k)
+    if kind == "sgs":
+        return multicolour_sgs(A, dinv, b, x, colour)
+    raise ValueError(kind)
+
+
+def smooth(A, dinv, b, x, lmax, lmin, k, local: LocalSolver | None, order: str, post: bool,
+           kind: str = "chebyshev", colour=None):
     """One application of the combined smoother (pre-smoothing unless ``post``)."""
+    g = lambda x: global_smoother(A, dinv, b, x, lmax, lmin, k, kind, colour)
     use_local = local is not None and len(local.patches) > 0 and order != "global"
     if not use_local:
-        return chebyshev(A, dinv, b, x, lmax, lmin, k)
+        return g(x)
     if order == "sandwich":
         x = local.apply(A, b, x)
-        x = chebyshev(A, dinv, b, x, lmax, lmin, k)
+        x = g(x)
         return local.apply(A, b, x)
     if order == "global_then_local":
         if not post:
-            x = chebyshev(A, dinv, b, x, lmax, lmin, k)
+            x = g(x)
             return local.apply(A, b, x)
         x = local.apply(A, b, x)
-        return chebyshev(A, dinv, b, x, lmax, lmin, k)
+        return g(x)
     raise ValueError(order)

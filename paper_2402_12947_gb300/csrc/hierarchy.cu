@@ -114,6 +114,35 @@ int64_t sell_padded(const Csr& A, const std::vector<int32_t>& ord) {
   return tot;
 }
 
+// Column indices of a layout (SELL slices or CSR-vector rows, "groups"): col = the 32-bit
+// indices, base[g] = the smallest column of group g when it spans < 2^16 columns, else -1.
+// Mostly narrow (at least half the nonzeros in narrow groups): 16-bit offsets, plus the
+// 32-bit array when some group is wide; mostly wide: 32-bit indices only.
+template <typename T, typename Each>
+void set_indices(SellMat<T>& S, DevMem& mem, const std::vector<int32_t>& col, std::vector<int32_t>& base,
+                 int64_t narrow_nnz, Each&& each) {
+  const int64_t nnz = S.nnz;
+  if (2 * narrow_nnz < nnz) {
+    S.col = mem.upload(col);
+    S.idx_bytes = 4.0 * (double)nnz;
+    return;
+  }
+  std::vector<uint16_t> c16(col.size(), 0);
+  bool any_wide = false;
+  for (size_t g = 0; g < base.size(); ++g) {
+    if (base[g] < 0) {
+      any_wide = true;
+      continue;
+    }
+    const int32_t b = base[g];
+    each((int64_t)g, [&](int64_t k) { c16[k] = (uint16_t)(col[k] - b); });
+  }
+  S.col16 = mem.upload(c16);
+  S.cbase = mem.upload(base);
+  if (any_wide) S.col = mem.upload(col);
+  S.idx_bytes = 2.0 * (double)narrow_nnz + 4.0 * (double)(nnz - narrow_nnz);
+}
+
 // Host CSR -> device SELL-32 (values converted to T), slots in the order of sell_order.
 template <typename T>
 SellMat<T> make_sell(const Csr& A, DevMem& mem, int sigma = 1) {
@@ -155,15 +184,28 @@ SellMat<T> make_sell(const Csr& A, DevMem& mem, int sigma = 1) {
     }
   });
   S.off = mem.upload(off);
-  S.col = mem.upload(col);
   S.val = mem.upload(val);
+  // 16-bit column offsets from the slice's smallest column for every slice that spans
+  // < 2^16 columns; the others keep 32-bit indices (cbase = -1)
+  std::vector<int32_t> base(S.nslices, 0);
+  std::vector<int64_t> snnz(S.nslices, 0);
+  int64_t narrow_nnz = 0;
+  for (int32_t sl = 0; sl < S.nslices; ++sl) {
+    for (int64_t k = (int64_t)sl * 32; k < std::min<int64_t>(A.nrows, (int64_t)sl * 32 + 32); ++k)
+      snnz[sl] += A.rp[ord[k] + 1] - A.rp[ord[k]];
+    if (off[sl + 1] == off[sl]) continue;
+    int32_t mn = INT32_MAX, mx = INT32_MIN;
+    for (int64_t k = off[sl]; k < off[sl + 1]; ++k) mn = std::min(mn, col[k]), mx = std::max(mx, col[k]);
+    base[sl] = (int64_t)mx - mn <= 65535 ? mn : -1;
+    if (base[sl] >= 0) narrow_nnz += snnz[sl];
+  }
+  set_indices(S, mem, col, base, narrow_nnz, [&](int32_t sl, auto&& f) {
+    for (int64_t k = off[sl]; k < off[sl + 1]; ++k) f(k);
+  });
   if (sigma > 1) S.perm = mem.upload(ord);
   return S;
 }
 
-// Autotuner: for sigma = 0 (auto) time y = A x for each candidate window on the device
-// (CUDA events, after a warm-up launch) and keep the fastest layout; the candidates whose
-// padding equals an earlier candidate's are skipped. Other sigma values are used as given.
 // Host CSR -> device CSR-vector layout (G lanes per row; values converted to T).
 template <typename T>
 SellMat<T> make_csrv(const Csr& A, DevMem& mem, int lanes) {
@@ -175,8 +217,19 @@ SellMat<T> make_csrv(const Csr& A, DevMem& mem, int lanes) {
   S.lanes = lanes;
   std::vector<T> val(A.v.begin(), A.v.end());
   S.rp = mem.upload(A.rp);
-  S.col = mem.upload(A.ci);
   S.val = mem.upload(val);
+  // 16-bit column offsets from each row's first (smallest) column for rows spanning
+  // < 2^16 columns; the others keep 32-bit indices (cbase = -1)
+  std::vector<int32_t> base(A.nrows, 0);
+  int64_t narrow_nnz = 0;
+  for (int64_t i = 0; i < A.nrows; ++i)
+    if (A.rp[i + 1] > A.rp[i]) {
+      base[i] = (int64_t)A.ci[A.rp[i + 1] - 1] - A.ci[A.rp[i]] <= 65535 ? A.ci[A.rp[i]] : -1;
+      if (base[i] >= 0) narrow_nnz += A.rp[i + 1] - A.rp[i];
+    }
+  set_indices(S, mem, A.ci, base, narrow_nnz, [&](int64_t i, auto&& f) {
+    for (int64_t k = A.rp[i]; k < A.rp[i + 1]; ++k) f(k);
+  });
   return S;
 }
 
@@ -247,6 +300,7 @@ SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log) {
 template <typename T>
 struct DevLevel {
   int n = 0;
+  int32_t* perm = nullptr;  // internal index -> library index (null: same numbering)
   SellMat<T> A, P, R;
   T *dinv = nullptr, *b = nullptr, *x = nullptr, *xt = nullptr, *d = nullptr, *res = nullptr;
   std::vector<double> cd, cr;
@@ -261,6 +315,10 @@ struct DevLevel {
   int nh = 0;
   int32_t *hrow = nullptr, *hrp = nullptr, *hci = nullptr;
   T* hv = nullptr;
+  // multicolour SGS: per colour, its rows of A without the diagonal and without couplings
+  // inside the colour, and the level rows they update
+  std::vector<SellMat<T>> gs;
+  std::vector<int32_t*> gs_rows;
 };
 
 }  // namespace
@@ -270,6 +328,7 @@ template <typename T>
 struct Engine {
   std::vector<DevLevel<T>> lv;
   int cheb_k = 2, nu = 1, order = MG_SMOOTHER_SANDWICH;
+  bool sgs = false;   // global smoother: multicolour SGS instead of Chebyshev
   uint32_t local_mask = 0xffffffffu;
   // coarsest level
   int nc = 0, kchunk = 256;
@@ -299,6 +358,21 @@ struct Engine {
       ++launches;
     }
   }
+  // One symmetric sweep: colours 0..C-1, then C-1..0.
+  void sgs_sweep(int l, cudaStream_t s) {
+    DevLevel<T>& L = lv[l];
+    const int C = (int)L.gs.size();
+    for (int j = 0; j < 2 * C; ++j) {
+      const int c = j < C ? j : 2 * C - 1 - j;
+      sell_gs<T>(L.gs[c], L.gs_rows[c], L.b, L.dinv, L.x, s);
+    }
+    launches += 2 * C;
+  }
+  // S_g; zero as in cheb (the SGS sweep has no zero-iterate shortcut)
+  void global(int l, cudaStream_t s, int zero = 0) {
+    if (sgs) sgs_sweep(l, s);
+    else cheb(l, s, zero);
+  }
   void local(int l, cudaStream_t s, bool zero = false) {
     DevLevel<T>& L = lv[l];
     if (!zero) patch_residual<T>(L.nt, L.pdofs, L.prp, L.pci, L.pv, L.b, L.x, L.rbuf, s);
@@ -309,19 +383,19 @@ struct Engine {
   // zero: the iterate is zero on entry (first pre-smoothing on every level of a cycle)
   void smooth(int l, bool post, cudaStream_t s, bool zero = false) {
     if (!local_on(l)) {
-      cheb(l, s, zero ? 1 : 0);
+      global(l, s, zero ? 1 : 0);
       return;
     }
     if (order == MG_SMOOTHER_SANDWICH) {
       local(l, s, zero);
-      cheb(l, s, zero ? 2 : 0);
+      global(l, s, zero ? 2 : 0);
       local(l, s);
     } else if (!post) {
-      cheb(l, s, zero ? 1 : 0);
+      global(l, s, zero ? 1 : 0);
       local(l, s);
     } else {
       local(l, s);
-      cheb(l, s);
+      global(l, s);
     }
   }
   void coarse(cudaStream_t s) {
@@ -372,6 +446,7 @@ struct mg_hierarchy {
   SellMat<double> A0;  // fine operator in FP64 for the CG recurrence
   int n0 = 0;
   double *cb = nullptr, *cx = nullptr, *cr = nullptr, *cp = nullptr, *cq = nullptr, *cz = nullptr, *part = nullptr;
+  int32_t* perm0 = nullptr;  // level-0 internal order (see build_device), null = library order
   CgState* st = nullptr;
   CgState* hst = nullptr;  // pinned
   int nparts = 1, ap_parts = 1;
@@ -410,6 +485,8 @@ void validate_options(const mg_options_t& o) {
   if (!(o.lmin_ratio > 0 && o.lmin_ratio < 1)) throw Error(MG_ERR_INVALID_ARG, "lmin_ratio must be in (0, 1)");
   if (!(o.lmax_safety > 0)) throw Error(MG_ERR_INVALID_ARG, "lmax_safety must be positive");
   if (o.sell_sigma < 0 || o.sell_sigma > (1 << 20)) throw Error(MG_ERR_INVALID_ARG, "sell_sigma must be in [0, 2^20]");
+  if (o.global_smoother < 0 || o.global_smoother > 1) throw Error(MG_ERR_INVALID_ARG, "unknown global smoother");
+  if (o.reorder < 0 || o.reorder > 2) throw Error(MG_ERR_INVALID_ARG, "unknown reorder mode");
 }
 
 // Chebyshev coefficients per step: d = cd d + cr D^{-1} r (Sec. 3.2 three-term recurrence).
@@ -422,6 +499,39 @@ void cheb_coefficients(double lmax, double lmin, int k, std::vector<double>& cd,
     cd.push_back(rn * rho);
     cr.push_back(2.0 * rn / delta);
     rho = rn;
+  }
+}
+
+// Multicolour SGS operators of one level. The colouring (Hl.colour, library numbering) is
+// carried to the internal order (perm: internal -> library). Per colour: its rows of the
+// internal-order operator Hd.A without the diagonal and without couplings to rows of the
+// same colour (all below 1e-12 sqrt(a_ii a_jj) by the colouring's construction), so that
+// one launch can update the whole colour in place.
+template <typename T>
+void build_sgs_ops(const LevelH& Hl, const LevelH& Hd, const std::vector<int32_t>& perm, DevLevel<T>& D, DevMem& mem,
+                   int sigma) {
+  const int64_t n = Hd.A.nrows;
+  std::vector<int32_t> col(n);
+  for (int64_t i = 0; i < n; ++i) col[i] = Hl.colour[perm.empty() ? i : perm[i]];
+  std::vector<std::vector<int32_t>> rows(Hl.ncolours);
+  for (int64_t i = 0; i < n; ++i) rows[col[i]].push_back((int32_t)i);
+  for (int c = 0; c < Hl.ncolours; ++c) {
+    Csr M;
+    M.nrows = (int64_t)rows[c].size();
+    M.ncols = n;
+    M.rp.assign(M.nrows + 1, 0);
+    for (int64_t r = 0; r < M.nrows; ++r) {
+      const int32_t i = rows[c][r];
+      for (int32_t k = Hd.A.rp[i]; k < Hd.A.rp[i + 1]; ++k) {
+        const int32_t j = Hd.A.ci[k];
+        if (j == i || col[j] == c) continue;
+        M.ci.push_back(j);
+        M.v.push_back(Hd.A.v[k]);
+      }
+      M.rp[r + 1] = (int32_t)M.ci.size();
+    }
+    D.gs.push_back(tuned_sell<T>(M, mem, sigma, nullptr));
+    D.gs_rows.push_back(mem.upload(rows[c]));
   }
 }
 
@@ -495,6 +605,7 @@ void compute_eigenvalues(mg_hierarchy* h, bool on_device) {
   PhaseTimer tm;
   for (int l = 0; l + 1 < h->L; ++l) {
     LevelH& lv = h->host[l];
+    if (o.global_smoother == MG_GLOBAL_SGS) continue;   // SGS needs no spectral bounds
     if (o.lambda_override) {
       lv.lmax = o.lambda_override[l];
       if (!(lv.lmax > 0)) throw Error(MG_ERR_INVALID_ARG, "lambda_override must be positive");
@@ -538,6 +649,11 @@ void finish_setup_host(mg_hierarchy* h) {
       lv.dinv[i] = 1.0 / dg;
     }
   }
+  if (o.global_smoother == MG_GLOBAL_SGS) {
+    PhaseTimer tm;
+    for (int l = 0; l + 1 < L; ++l) h->host[l].ncolours = greedy_colouring(h->host[l].A, h->host[l].colour);
+    tm.mark("colouring");
+  }
   const int64_t ncoarse = h->host[L - 1].A.nrows;
   if (ncoarse > 20000) throw Error(MG_ERR_INVALID_ARG, "coarsest level too large for the dense direct solve (> 20000 DoFs)");
   // eigenvalues (Sec. 3.2 / Sec. 5): on the host only for host-only hierarchies; otherwise
@@ -561,6 +677,37 @@ void build_device(mg_hierarchy* h) {
   DevMem& mem = h->mem;
   mem.stream = h->own_stream;
   compute_eigenvalues(h, true);
+  // Internal DoF order of each level (option reorder; the coarsest level keeps the library
+  // numbering). The device holds the symmetrically permuted operators; vectors are
+  // gathered/scattered at every boundary. Where a SELL slice (CSR row) spans < 2^16
+  // columns its indices are stored as 16-bit offsets from a base.
+  std::vector<std::vector<int32_t>> perm(L), iperm(L);
+  std::vector<LevelH> dl(L);
+  for (int l = 0; l < L; ++l) {
+    if (l + 1 == L) continue;
+    const LevelH& H = h->host[l];
+    if (o.reorder == MG_REORDER_RCM) perm[l] = rcm_order(H.A);
+    else if (o.reorder == MG_REORDER_SPATIAL && !H.dof_points.empty()) perm[l] = morton_order(H.dof_points, H.dim);
+    if (!perm[l].empty()) iperm[l] = inverse_perm(perm[l]);
+  }
+  for (int l = 0; l < L; ++l) {
+    const LevelH& H = h->host[l];
+    LevelH& D = dl[l];
+    D.A = perm[l].empty() ? H.A : permute_csr(H.A, perm[l], iperm[l]);
+    if (l + 1 < L) {
+      D.P = (perm[l].empty() && iperm[l + 1].empty()) ? H.P : permute_csr(H.P, perm[l], iperm[l + 1]);
+      D.R = transpose(D.P);
+    }
+    D.dinv.resize(H.dinv.size());
+    for (size_t i = 0; i < H.dinv.size(); ++i) D.dinv[i] = H.dinv[perm[l].empty() ? i : perm[l][i]];
+    D.patch_ptr = H.patch_ptr;
+    D.patch_dofs = H.patch_dofs;
+    if (!iperm[l].empty())
+      for (int32_t& f : D.patch_dofs) f = iperm[l][f];
+    D.lmax = H.lmax;
+    D.lmin = H.lmin;
+  }
+  tm.mark("reorder");
   int max_patch = 0;
   // All dense blocks (every patch matrix A[B_d, B_d] of every level and the coarsest A)
   // are inverted together on the device by the batched Gauss-Jordan sweep.
@@ -652,10 +799,12 @@ void build_device(mg_hierarchy* h) {
     eng->nu = o.nu;
     eng->order = o.smoother;
     eng->local_mask = (uint32_t)o.local_levels_mask;
+    eng->sgs = o.global_smoother == MG_GLOBAL_SGS;
     eng->lv.resize(L);
     for (int l = 0; l < L; ++l) {
-      LevelH& H = h->host[l];
+      LevelH& H = dl[l];
       DevLevel<T>& D = eng->lv[l];
+      if (!perm[l].empty()) D.perm = mem.upload(perm[l]);
       D.n = (int)H.A.nrows;
       std::string tlog;
       D.A = tuned_sell<T>(H.A, mem, o.sell_sigma, &tlog);
@@ -664,7 +813,8 @@ void build_device(mg_hierarchy* h) {
         D.R = tuned_sell<T>(H.R, mem, o.sell_sigma, &tlog);
         std::vector<T> dv(H.dinv.begin(), H.dinv.end());
         D.dinv = mem.upload(dv);
-        cheb_coefficients(H.lmax, H.lmin, o.cheb_degree, D.cd, D.cr);
+        if (!eng->sgs) cheb_coefficients(H.lmax, H.lmin, o.cheb_degree, D.cd, D.cr);
+        else build_sgs_ops(h->host[l], H, perm[l], D, mem, o.sell_sigma);
         D.xt = mem.alloc<T>(D.n);
         D.d = mem.alloc<T>(D.n);
         D.res = mem.alloc<T>(D.n);
@@ -722,7 +872,8 @@ void build_device(mg_hierarchy* h) {
         }
       }
       auto lay = [](const SellMat<T>& M) {
-        return M.lanes > 1 ? "v" + std::to_string(M.lanes) : "s" + std::to_string(M.sigma);
+        return (M.lanes > 1 ? "v" + std::to_string(M.lanes) : "s" + std::to_string(M.sigma)) +
+               (M.col16 ? (M.col ? "/16+32" : "/16") : "/32");
       };
       tm.mark("upload L" + std::to_string(l) + " A/P/R " + lay(D.A) + "/" + lay(D.P) + "/" + lay(D.R) + " |" + tlog);
       bool fine_shared = (l == 0) && std::is_same<T, double>::value;
@@ -757,13 +908,16 @@ void build_device(mg_hierarchy* h) {
     h->e32.reset(new Engine<float>());
     upload_engine(h->e32.get(), float());
     std::string tlog;
-    h->A0 = tuned_sell<double>(h->host[0].A, mem, o.sell_sigma, &tlog);
+    h->A0 = tuned_sell<double>(dl[0].A, mem, o.sell_sigma, &tlog);
   } else {
     h->e64.reset(new Engine<double>());
     upload_engine(h->e64.get(), double());
     h->e64->lv[0].b = h->cr;  // the V-cycle of CG reads r and writes z in place
     h->e64->lv[0].x = h->cz;
     h->A0 = h->e64->lv[0].A;
+  }
+  {
+    h->perm0 = h->e64 ? h->e64->lv[0].perm : h->e32->lv[0].perm;
   }
   if (max_patch > 0) patch_solve_setup(max_patch);
   CK(cudaStreamSynchronize(h->own_stream));
@@ -956,24 +1110,26 @@ void check_level(const mg_hierarchy* h, int l, bool below_coarsest = false) {
     throw Error(MG_ERR_INVALID_ARG, "level index out of range");
 }
 
+// A library-numbered FP64 vector into a level's internal order and type (perm: internal
+// index -> library index; null = same order), and back.
 template <typename T>
-void load(T* dst, const double* src, int n, cudaStream_t s) {
+void load(T* dst, const double* src, int n, const int32_t* perm, cudaStream_t s) {
   if (!src) throw Error(MG_ERR_INVALID_ARG, "null vector");
-  if (std::is_same<T, double>::value) {
+  if (std::is_same<T, double>::value && !perm) {
     if ((const void*)dst != (const void*)src)
       CK(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   } else {
-    convert<double, float>(n, src, (float*)dst, s);
+    gather<double, T>(n, perm, src, dst, s);
   }
 }
 template <typename T>
-void store(double* dst, const T* src, int n, cudaStream_t s) {
+void store(double* dst, const T* src, int n, const int32_t* perm, cudaStream_t s) {
   if (!dst) throw Error(MG_ERR_INVALID_ARG, "null vector");
-  if (std::is_same<T, double>::value) {
+  if (std::is_same<T, double>::value && !perm) {
     if ((const void*)dst != (const void*)src)
       CK(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   } else {
-    convert<float, double>(n, (const float*)src, dst, s);
+    scatter<T, double>(n, perm, src, dst, s);
   }
 }
 
@@ -1000,10 +1156,10 @@ int level_step(mg_hierarchy_t* h, int32_t l, const double* b, double* x, void* s
   h->with_engine([&](auto& e) {
     using T = typename std::remove_pointer<decltype(e.lv[0].b)>::type;
     auto& L = e.lv[l];
-    load<T>(L.b, b, L.n, s);
-    load<T>(L.x, x, L.n, s);
+    load<T>(L.b, b, L.n, L.perm, s);
+    load<T>(L.x, x, L.n, L.perm, s);
     step(e, s);
-    store<T>(x, L.x, L.n, s);
+    store<T>(x, L.x, L.n, L.perm, s);
   });
   check_launch("level step");
   return MG_OK;
@@ -1031,6 +1187,7 @@ void mg_default_options(mg_options_t* o) {
   o->local_levels_mask = -1;
   o->quality_threshold = 0.1;
   o->sell_sigma = 0;
+  o->reorder = MG_REORDER_SPATIAL;
 }
 
 }  // extern "C"
@@ -1122,6 +1279,7 @@ int64_t estimate_device_bytes(const mg_hierarchy* h) {
       op(lv.P);
       op(lv.R);
     }
+    if (h->opt.global_smoother == MG_GLOBAL_SGS && l + 1 < h->L) op(lv.A);  // per-colour operators
     tot += 8 * vbytes * lv.A.nrows;  // level vectors
     const int64_t np = (int64_t)lv.patch_ptr.size() - 1;
     for (int64_t p = 0; p < np; ++p) {
@@ -1145,11 +1303,13 @@ const std::vector<double>& hierarchy_unit_load(const mg_hierarchy* h) { return h
 void enqueue_host_solve(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit, cudaEvent_t done) {
   if (!h->graph) throw Error(MG_ERR_INVALID_ARG, "the solve server needs hierarchies built with use_graph = 1");
   cudaStream_t s = h->own_stream;
-  CK(cudaMemcpyAsync(h->cb, b, sizeof(double) * h->n0, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->cq, b, sizeof(double) * h->n0, cudaMemcpyHostToDevice, s));
+  gather<double, double>(h->n0, h->perm0, h->cq, h->cb, s);
   enqueue_state(h, rtol, maxit, s);
   CK(cudaGraphLaunch(h->graph, s));
   enqueue_exit(h, s);
-  CK(cudaMemcpyAsync(x, h->cx, sizeof(double) * h->n0, cudaMemcpyDeviceToHost, s));
+  scatter<double, double>(h->n0, h->perm0, h->cx, h->cq, s);
+  CK(cudaMemcpyAsync(x, h->cq, sizeof(double) * h->n0, cudaMemcpyDeviceToHost, s));
   CK(cudaEventRecord(done, s));
 }
 
@@ -1330,6 +1490,20 @@ int mg_export_patches(const mg_hierarchy_t* hc, int32_t l, int32_t* ptr, int32_t
   API_END_H(h)
 }
 
+int mg_export_colouring(const mg_hierarchy_t* hc, int32_t l, int32_t* ncolours, int32_t* colour) {
+  mg_hierarchy* h = const_cast<mg_hierarchy*>(hc);
+  API_BEGIN
+  checked(h, false);
+  check_level(h, l, true);
+  if (h->opt.global_smoother != MG_GLOBAL_SGS)
+    throw Error(MG_ERR_INVALID_ARG, "the hierarchy's global smoother is not SGS");
+  const LevelH& lv = h->host[l];
+  if (ncolours) *ncolours = lv.ncolours;
+  if (colour) std::copy(lv.colour.begin(), lv.colour.end(), colour);
+  return MG_OK;
+  API_END_H(h)
+}
+
 int mg_eigs(const mg_hierarchy_t* hc, int32_t l, double* lmax, double* lmax_adj, double* lmax_used) {
   mg_hierarchy* h = const_cast<mg_hierarchy*>(hc);
   API_BEGIN
@@ -1384,15 +1558,19 @@ int mg_vcycle(mg_hierarchy_t* h, const double* b, double* x, void* stream) {
   if (!b || !x) throw Error(MG_ERR_INVALID_ARG, "null vector");
   cudaStream_t s = (cudaStream_t)stream;
   const int n = h->n0;
-  // x += V(b - A x): r into the CG residual buffer, the cycle from a zero guess
-  sell_resid<double>(h->A0, x, b, h->cr, s);
+  // x += V(b - A x) in the internal order: x and b gathered into p and q, r into the CG
+  // residual buffer, the cycle from a zero guess, then x scattered back
+  gather<double, double>(n, h->perm0, x, h->cp, s);
+  gather<double, double>(n, h->perm0, b, h->cq, s);
+  sell_resid<double>(h->A0, h->cp, h->cq, h->cr, s);
   h->with_engine([&](auto& e) {
     using T = typename std::remove_pointer<decltype(e.lv[0].b)>::type;
-    load<T>(e.lv[0].b, h->cr, n, s);
+    load<T>(e.lv[0].b, h->cr, n, nullptr, s);
     CK(cudaMemsetAsync(e.lv[0].x, 0, sizeof(T) * n, s));
     e.cycle(0, s);
-    axpy_from<T>(n, e.lv[0].x, x, s);
+    axpy_from<T>(n, e.lv[0].x, h->cp, s);
   });
+  scatter<double, double>(n, h->perm0, h->cp, x, s);
   check_launch("mg_vcycle");
   return MG_OK;
   API_END_H(h)
@@ -1404,9 +1582,9 @@ int mg_solve(mg_hierarchy_t* h, const double* b, double* x, double rtol, int32_t
   checked(h);
   if (!b || !x) throw Error(MG_ERR_INVALID_ARG, "null vector");
   cudaStream_t s = (cudaStream_t)stream;
-  CK(cudaMemcpyAsync(h->cb, b, sizeof(double) * h->n0, cudaMemcpyDeviceToDevice, s));
+  gather<double, double>(h->n0, h->perm0, b, h->cb, s);
   int rc = run_solve(h, rtol, maxit, info, s);
-  CK(cudaMemcpyAsync(x, h->cx, sizeof(double) * h->n0, cudaMemcpyDeviceToDevice, s));
+  scatter<double, double>(h->n0, h->perm0, h->cx, x, s);
   CK(cudaStreamSynchronize(s));
   if (rc != MG_OK) h->err = rc == MG_ERR_BREAKDOWN ? "CG breakdown" : "no convergence within maxit";
   return rc;
@@ -1419,9 +1597,11 @@ int mg_solve_host(mg_hierarchy_t* h, const double* b, double* x, double rtol, in
   checked(h);
   if (!b || !x) throw Error(MG_ERR_INVALID_ARG, "null vector");
   cudaStream_t s = (cudaStream_t)stream;
-  CK(cudaMemcpyAsync(h->cb, b, sizeof(double) * h->n0, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->cp, b, sizeof(double) * h->n0, cudaMemcpyHostToDevice, s));
+  gather<double, double>(h->n0, h->perm0, h->cp, h->cb, s);
   int rc = run_solve(h, rtol, maxit, info, s);
-  CK(cudaMemcpyAsync(x, h->cx, sizeof(double) * h->n0, cudaMemcpyDeviceToHost, s));
+  scatter<double, double>(h->n0, h->perm0, h->cx, h->cp, s);
+  CK(cudaMemcpyAsync(x, h->cp, sizeof(double) * h->n0, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (rc != MG_OK) h->err = rc == MG_ERR_BREAKDOWN ? "CG breakdown" : "no convergence within maxit";
   return rc;
@@ -1446,7 +1626,9 @@ int mg_solve_stationary(mg_hierarchy_t* h, const double* b, double* x, double rt
   int it = 0;
   double rr = 0;
   for (;;) {
-    sell_resid<double>(h->A0, x, b, h->cq, s);
+    gather<double, double>(h->n0, h->perm0, x, h->cp, s);
+    gather<double, double>(h->n0, h->perm0, b, h->cz, s);
+    sell_resid<double>(h->A0, h->cp, h->cz, h->cq, s);
     rr = norm2(h->cq);
     if (bb == 0.0 || rr <= rtol * rtol * bb || it >= maxit) break;
     int rc = mg_vcycle(h, b, x, stream);
@@ -1480,12 +1662,12 @@ int mg_solve_batch(mg_hierarchy_t* const* hs, const double* const* b, double* co
     std::memset(hi->hst, 0, sizeof(CgState));
     hi->hst->rtol2 = rtol * rtol;
     hi->hst->maxit = maxit;
-    CK(cudaMemcpyAsync(hi->cb, b[i], sizeof(double) * hi->n0, cudaMemcpyDeviceToDevice, hi->own_stream));
+    gather<double, double>(hi->n0, hi->perm0, b[i], hi->cb, hi->own_stream);
     CK(cudaMemcpyAsync(hi->st, hi->hst, sizeof(CgState), cudaMemcpyHostToDevice, hi->own_stream));
     if (!hi->graph) throw Error(MG_ERR_INVALID_ARG, "mg_solve_batch needs hierarchies built with use_graph = 1");
     CK(cudaGraphLaunch(hi->graph, hi->own_stream));
     enqueue_exit(hi, hi->own_stream);
-    CK(cudaMemcpyAsync(x[i], hi->cx, sizeof(double) * hi->n0, cudaMemcpyDeviceToDevice, hi->own_stream));
+    scatter<double, double>(hi->n0, hi->perm0, hi->cx, x[i], hi->own_stream);
   }
   int rc_all = MG_OK;
   for (int i = 0; i < n; ++i) {
@@ -1506,14 +1688,16 @@ int mg_apply_A(mg_hierarchy_t* h, int32_t l, const double* x, double* y, void* s
   cudaStream_t s = (cudaStream_t)stream;
   if (!x || !y) throw Error(MG_ERR_INVALID_ARG, "null vector");
   if (l == 0) {
-    sell_spmv<double>(h->A0, x, y, s);
+    gather<double, double>(h->n0, h->perm0, x, h->cp, s);
+    sell_spmv<double>(h->A0, h->cp, h->cq, s);
+    scatter<double, double>(h->n0, h->perm0, h->cq, y, s);
   } else {
     h->with_engine([&](auto& e) {
       using T = typename std::remove_pointer<decltype(e.lv[0].b)>::type;
       auto& L = e.lv[l];
-      load<T>(L.x, x, L.n, s);
+      load<T>(L.x, x, L.n, L.perm, s);
       sell_spmv<T>(L.A, L.x, L.b, s);
-      store<T>(y, L.b, L.n, s);
+      store<T>(y, L.b, L.n, L.perm, s);
     });
   }
   check_launch("mg_apply_A");
@@ -1524,7 +1708,17 @@ int mg_apply_A(mg_hierarchy_t* h, int32_t l, const double* x, double* y, void* s
 
 int mg_chebyshev(mg_hierarchy_t* h, int32_t l, const double* b, double* x, void* stream) {
   API_BEGIN
+  if (h && h->opt.global_smoother != MG_GLOBAL_CHEBYSHEV)
+    throw Error(MG_ERR_INVALID_ARG, "the hierarchy's global smoother is not Chebyshev");
   return level_step(h, l, b, x, stream, [&](auto& e, cudaStream_t s) { e.cheb(l, s); });
+  API_END_H(h)
+}
+
+int mg_sgs(mg_hierarchy_t* h, int32_t l, const double* b, double* x, void* stream) {
+  API_BEGIN
+  if (h && h->opt.global_smoother != MG_GLOBAL_SGS)
+    throw Error(MG_ERR_INVALID_ARG, "the hierarchy's global smoother is not SGS");
+  return level_step(h, l, b, x, stream, [&](auto& e, cudaStream_t s) { e.sgs_sweep(l, s); });
   API_END_H(h)
 }
 
@@ -1553,11 +1747,11 @@ int mg_residual_restrict(mg_hierarchy_t* h, int32_t l, const double* b, const do
     using T = typename std::remove_pointer<decltype(e.lv[0].b)>::type;
     auto& L = e.lv[l];
     auto& C = e.lv[l + 1];
-    load<T>(L.b, b, L.n, s);
-    load<T>(L.x, x, L.n, s);
+    load<T>(L.b, b, L.n, L.perm, s);
+    load<T>(L.x, x, L.n, L.perm, s);
     e.residual_restrict(l, s);
-    store<T>(r, L.res, L.n, s);
-    store<T>(bc, C.b, C.n, s);
+    store<T>(r, L.res, L.n, L.perm, s);
+    store<T>(bc, C.b, C.n, C.perm, s);
   });
   check_launch("mg_residual_restrict");
   return MG_OK;
@@ -1574,10 +1768,10 @@ int mg_prolong_correct(mg_hierarchy_t* h, int32_t l, const double* xc, double* x
     using T = typename std::remove_pointer<decltype(e.lv[0].b)>::type;
     auto& L = e.lv[l];
     auto& C = e.lv[l + 1];
-    load<T>(C.x, xc, C.n, s);
-    load<T>(L.x, x, L.n, s);
+    load<T>(C.x, xc, C.n, C.perm, s);
+    load<T>(L.x, x, L.n, L.perm, s);
     e.prolong(l, s);
-    store<T>(x, L.x, L.n, s);
+    store<T>(x, L.x, L.n, L.perm, s);
   });
   check_launch("mg_prolong_correct");
   return MG_OK;
@@ -1592,9 +1786,9 @@ int mg_coarse_solve(mg_hierarchy_t* h, const double* b, double* x, void* stream)
   h->with_engine([&](auto& e) {
     using T = typename std::remove_pointer<decltype(e.lv[0].b)>::type;
     auto& C = e.lv.back();
-    load<T>(C.b, b, C.n, s);
+    load<T>(C.b, b, C.n, C.perm, s);
     e.coarse(s);
-    store<T>(x, C.x, C.n, s);
+    store<T>(x, C.x, C.n, C.perm, s);
   });
   check_launch("mg_coarse_solve");
   return MG_OK;
@@ -1613,13 +1807,29 @@ int mg_time_smoother_kernel(mg_hierarchy_t* h, int32_t reps, void* stream, doubl
   h->with_engine([&](auto& e) {
     using T = typename std::remove_pointer<decltype(e.lv[0].b)>::type;
     auto& L = e.lv[0];
+    const double sz = sizeof(T);
+    auto meta_bytes = [&](const SellMat<T>& M) {
+      return M.lanes > 1 ? 4.0 * (M.nrows + 1) + (M.col16 ? 4.0 * M.nrows : 0.0)
+                         : 8.0 * (M.nslices + 1) + (M.col16 ? 4.0 * M.nslices : 0.0) + (M.perm ? 4.0 * M.nrows : 0.0);
+    };
+    if (e.sgs) {
+      // one multicolour SGS application on the fine level (2C launches); per colour and
+      // sweep: its nonzeros once, rows[], b, dinv read and x written for its rows
+      e.sgs_sweep(0, s);  // warm-up
+      CK(cudaEventRecord(e0, s));
+      for (int i = 0; i < reps; ++i) e.sgs_sweep(0, s);
+      CK(cudaEventRecord(e1, s));
+      for (const SellMat<T>& M : L.gs)
+        nbytes += 2.0 * ((double)M.nnz * sz + M.idx_bytes + (double)M.nrows * (4.0 + 3.0 * sz) + meta_bytes(M));
+      return;
+    }
     double cd = L.cd.size() > 1 ? L.cd[1] : 0.0, cr = L.cr.size() > 1 ? L.cr[1] : L.cr[0];
     sell_cheb<T>(L.A, L.x, L.b, L.dinv, L.d, L.xt, cd, cr, false, s);  // warm-up
     CK(cudaEventRecord(e0, s));
     for (int i = 0; i < reps; ++i) sell_cheb<T>(L.A, L.x, L.b, L.dinv, L.d, L.xt, cd, cr, false, s);
     CK(cudaEventRecord(e1, s));
-    const double sz = sizeof(T);
-    nbytes = (double)L.A.nnz * (sz + 4.0) + (double)L.n * 6.0 * sz + 8.0 * (L.A.nslices + 1);
+    // algorithmic bytes: each nonzero's value and index once, six vectors, slice/row metadata
+    nbytes = (double)L.A.nnz * sz + L.A.idx_bytes + (double)L.n * 6.0 * sz + meta_bytes(L.A);
   });
   check_launch("mg_time_smoother_kernel");
   CK(cudaEventSynchronize(e1));

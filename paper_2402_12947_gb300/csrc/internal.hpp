@@ -56,6 +56,8 @@ struct LevelH {
   int dim = 0;
   std::vector<double> dof_points;   // [n*dim] (geometric hierarchies)
   std::vector<double> gamma;        // [nc]    (geometric hierarchies)
+  std::vector<int32_t> colour;      // [n] multicolour SGS colouring (global_smoother = SGS)
+  int32_t ncolours = 0;
 };
 
 // ---- threading helper ----
@@ -81,6 +83,9 @@ Csr unit_diagonal_on_empty_rows(const Csr& A);
 Csr spgemm(const Csr& A, const Csr& B);
 // lambda_max of D^{-1/2} A D^{-1/2} restricted to rows/cols with keep[i] != 0 (NULL: all).
 double lanczos_lmax(const Csr& A, const uint8_t* keep, double tol, int maxit, int* iters);
+// Greedy colouring in index order: colour[i] = the smallest colour not held by a neighbour
+// j < i with |a_ij| > 1e-12 sqrt(|a_ii a_jj|). Returns the number of colours.
+int32_t greedy_colouring(const Csr& A, std::vector<int32_t>& colour);
 // Pieces of the Lanczos iteration shared by the host and device versions: the scaling
 // D^{-1/2} (0 on excluded rows), the deterministic unit start vector, and the largest
 // eigenvalue of the tridiagonal T_m (a = diagonal, b[1..m-1] = off-diagonal) with the
@@ -93,6 +98,9 @@ void spmv_host(const Csr& A, const double* x, double* y);
 
 // Reverse Cuthill-McKee order of A's graph (perm[new] = old), per connected component.
 std::vector<int32_t> rcm_order(const Csr& A);
+// Z-order (Morton) of points [n*dim]: coordinates scaled to integers over the bounding box
+// (31 bits in 2D, 21 in 3D), bits interleaved; equal codes keep index order.
+std::vector<int32_t> morton_order(const std::vector<double>& pts, int dim);
 // B[i, :] = A[rowperm[i], :] with columns mapped by colmap (old -> new); empty = identity.
 Csr permute_csr(const Csr& A, const std::vector<int32_t>& rowperm, const std::vector<int32_t>& colmap);
 std::vector<int32_t> inverse_perm(const std::vector<int32_t>& p);

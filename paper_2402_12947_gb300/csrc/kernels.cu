@@ -48,47 +48,88 @@ struct OpView {
   const int32_t* __restrict__ col;
   const T* __restrict__ val;
   const int32_t* __restrict__ perm;
+  const uint16_t* __restrict__ col16;   // 16-bit layouts: column = cbase + col16
+  const int32_t* __restrict__ cbase;
   int nrows;
 };
 
-template <typename T>
-__device__ __forceinline__ T sell_row(const OpView<T>& m, const T* __restrict__ x, int srow) {
-  const int s = srow >> 5, lane = srow & 31;
-  const int64_t o = m.off[s];
-  const int w = (int)((m.off[s + 1] - o) >> 5);
-  const T* vp = m.val + o + lane;
-  const int32_t* cp = m.col + o + lane;
+__device__ __forceinline__ uint16_t ld_stream(const uint16_t* p) { return __ldcs(p); }
+
+// Column index k: a 16-bit offset from the slice's/row's base column (narrow slices and
+// rows), or the 32-bit index (cbase < 0 marks a slice or row too wide for 16 bits).
+struct Col16 {
+  const uint16_t* __restrict__ c;
+  int base;
+  __device__ __forceinline__ int operator()(int64_t k) const { return base + (int)ld_stream(c + k); }
+};
+struct Col32 {
+  const int32_t* __restrict__ c;
+  __device__ __forceinline__ int operator()(int64_t k) const { return ld_stream(c + k); }
+};
+
+// Sum over the w padded entries of one SELL-32 lane starting at element k (stride 32).
+template <typename T, typename C>
+__device__ __forceinline__ T sell_lane(const T* __restrict__ vp, int64_t k, int w, C col, const T* __restrict__ x) {
   T acc = T(0);
   int j = 0;
   for (; j + 4 <= w; j += 4) {
     const T v0 = ld_stream(vp), v1 = ld_stream(vp + 32), v2 = ld_stream(vp + 64), v3 = ld_stream(vp + 96);
-    const int32_t c0 = ld_stream(cp), c1 = ld_stream(cp + 32), c2 = ld_stream(cp + 64), c3 = ld_stream(cp + 96);
+    const int c0 = col(k), c1 = col(k + 32), c2 = col(k + 64), c3 = col(k + 96);
     const T x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2), x3 = __ldg(x + c3);
     acc = fma(v0, x0, acc);
     acc = fma(v1, x1, acc);
     acc = fma(v2, x2, acc);
     acc = fma(v3, x3, acc);
     vp += 128;
-    cp += 128;
+    k += 128;
   }
   for (; j < w; ++j) {
-    acc = fma(ld_stream(vp), __ldg(x + ld_stream(cp)), acc);
+    acc = fma(ld_stream(vp), __ldg(x + col(k)), acc);
     vp += 32;
-    cp += 32;
+    k += 32;
   }
   return acc;
+}
+
+template <typename T, bool C16>
+__device__ __forceinline__ T sell_row(const OpView<T>& m, const T* __restrict__ x, int srow) {
+  const int s = srow >> 5, lane = srow & 31;
+  const int64_t o = m.off[s];
+  const int w = (int)((m.off[s + 1] - o) >> 5);
+  if constexpr (C16) {
+    const int base = m.cbase[s];   // uniform across the warp (one slice per warp)
+    if (base >= 0) return sell_lane(m.val + o + lane, o + lane, w, Col16{m.col16, base}, x);
+  }
+  return sell_lane(m.val + o + lane, o + lane, w, Col32{m.col}, x);
+}
+
+// CSR-vector partial sum of one lane of a G-lane group over row entries [k, k1).
+template <typename T, int G, typename C>
+__device__ __forceinline__ T csrv_lane(const T* __restrict__ val, int k, int k1, C col, const T* __restrict__ x) {
+  T a = T(0);
+  for (; k + 3 * G < k1; k += 4 * G) {
+    const T v0 = ld_stream(val + k), v1 = ld_stream(val + k + G), v2 = ld_stream(val + k + 2 * G),
+            v3 = ld_stream(val + k + 3 * G);
+    const int c0 = col(k), c1 = col(k + G), c2 = col(k + 2 * G), c3 = col(k + 3 * G);
+    a = fma(v0, __ldg(x + c0), a);
+    a = fma(v1, __ldg(x + c1), a);
+    a = fma(v2, __ldg(x + c2), a);
+    a = fma(v3, __ldg(x + c3), a);
+  }
+  for (; k < k1; k += G) a = fma(ld_stream(val + k), __ldg(x + col(k)), a);
+  return a;
 }
 
 // Row sum of the calling thread's row. Returns false for threads past the last row; for
 // G > 1 every lane of a group receives the group's total (all lanes take part in the
 // shuffles, so no lane leaves early).
-template <typename T, int G>
+template <typename T, int G, bool C16>
 __device__ __forceinline__ bool op_row(const OpView<T>& m, const T* __restrict__ x, int& row, T& acc) {
   const int tid = blockIdx.x * kBlock + threadIdx.x;
   if constexpr (G == 1) {
     if (tid >= m.nrows) return false;
     row = m.perm ? m.perm[tid] : tid;
-    acc = sell_row(m, x, tid);
+    acc = sell_row<T, C16>(m, x, tid);
     return true;
   } else {
     const int slot = tid / G, lane = tid & (G - 1);
@@ -96,19 +137,10 @@ __device__ __forceinline__ bool op_row(const OpView<T>& m, const T* __restrict__
     row = valid ? slot : 0;
     T a = T(0);
     if (valid) {
-      const int k1 = m.rp[row + 1];
-      int k = m.rp[row] + lane;
-      for (; k + 3 * G < k1; k += 4 * G) {
-        const T v0 = ld_stream(m.val + k), v1 = ld_stream(m.val + k + G), v2 = ld_stream(m.val + k + 2 * G),
-                v3 = ld_stream(m.val + k + 3 * G);
-        const int32_t c0 = ld_stream(m.col + k), c1 = ld_stream(m.col + k + G), c2 = ld_stream(m.col + k + 2 * G),
-                      c3 = ld_stream(m.col + k + 3 * G);
-        a = fma(v0, __ldg(x + c0), a);
-        a = fma(v1, __ldg(x + c1), a);
-        a = fma(v2, __ldg(x + c2), a);
-        a = fma(v3, __ldg(x + c3), a);
-      }
-      for (; k < k1; k += G) a = fma(ld_stream(m.val + k), __ldg(x + ld_stream(m.col + k)), a);
+      const int k0 = m.rp[row] + lane, k1 = m.rp[row + 1];
+      const int base = C16 ? m.cbase[row] : -1;
+      if (C16 && base >= 0) a = csrv_lane<T, G>(m.val, k0, k1, Col16{m.col16, base}, x);
+      else a = csrv_lane<T, G>(m.val, k0, k1, Col32{m.col}, x);
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -122,30 +154,30 @@ __device__ __forceinline__ bool group_leader() {
   return G == 1 || (threadIdx.x & (G - 1)) == 0;
 }
 
-template <typename T, int G>
+template <typename T, int G, bool C16>
 __global__ void __launch_bounds__(kBlock) k_spmv(OpView<T> m, const T* __restrict__ x, T* __restrict__ y) {
   int row;
   T ax;
-  if (!op_row<T, G>(m, x, row, ax) || !group_leader<G>()) return;
+  if (!op_row<T, G, C16>(m, x, row, ax) || !group_leader<G>()) return;
   y[row] = ax;
 }
 
-template <typename T, int G>
+template <typename T, int G, bool C16>
 __global__ void __launch_bounds__(kBlock) k_resid(OpView<T> m, const T* __restrict__ x, const T* __restrict__ b,
                                                   T* __restrict__ r) {
   int row;
   T ax;
-  if (!op_row<T, G>(m, x, row, ax) || !group_leader<G>()) return;
+  if (!op_row<T, G, C16>(m, x, row, ax) || !group_leader<G>()) return;
   r[row] = b[row] - ax;
 }
 
-template <typename T, int G, bool FIRST>
+template <typename T, int G, bool C16, bool FIRST>
 __global__ void __launch_bounds__(kBlock) k_cheb(OpView<T> m, const T* __restrict__ xin, const T* __restrict__ b,
                                                  const T* __restrict__ dinv, T* __restrict__ d, T* __restrict__ xout,
                                                  T cd, T cr) {
   int row;
   T ax;
-  if (!op_row<T, G>(m, xin, row, ax) || !group_leader<G>()) return;
+  if (!op_row<T, G, C16>(m, xin, row, ax) || !group_leader<G>()) return;
   const T r = b[row] - ax;
   const T t = dinv[row] * r;
   const T dn = FIRST ? cr * t : fma(cd, d[row], cr * t);
@@ -153,22 +185,37 @@ __global__ void __launch_bounds__(kBlock) k_cheb(OpView<T> m, const T* __restric
   xout[row] = xin[row] + dn;
 }
 
-template <typename T, int G>
+template <typename T, int G, bool C16>
 __global__ void __launch_bounds__(kBlock) k_prolong(OpView<T> m, const T* __restrict__ xc, T* __restrict__ x) {
   int row;
   T ax;
-  if (!op_row<T, G>(m, xc, row, ax) || !group_leader<G>()) return;
+  if (!op_row<T, G, C16>(m, xc, row, ax) || !group_leader<G>()) return;
   x[row] = x[row] + ax;
 }
 
-template <typename T, int G>
+template <typename T, int G, bool C16>
 __global__ void __launch_bounds__(kBlock) k_restrict(OpView<T> m, const T* __restrict__ r, T* __restrict__ bc,
                                                      T* __restrict__ xc) {
   int row;
   T ax;
-  if (!op_row<T, G>(m, r, row, ax) || !group_leader<G>()) return;
+  if (!op_row<T, G, C16>(m, r, row, ax) || !group_leader<G>()) return;
   bc[row] = ax;
   xc[row] = T(0);
+}
+
+// One colour of a multicolour Gauss-Seidel sweep. m holds the colour's rows without their
+// diagonal and without couplings between rows of the colour; rows[] maps its rows to the
+// level's. x_i = dinv_i (b_i - sum_j a_ij x_j). The kernel reads x (through xr) only at
+// entries of other colours and writes only its own colour's entries.
+template <typename T, int G, bool C16>
+__global__ void __launch_bounds__(kBlock) k_gs(OpView<T> m, const int32_t* __restrict__ rows,
+                                               const T* __restrict__ xr, const T* __restrict__ b,
+                                               const T* __restrict__ dinv, T* x) {
+  int r;
+  T s;
+  if (!op_row<T, G, C16>(m, xr, r, s) || !group_leader<G>()) return;
+  const int i = rows[r];
+  x[i] = dinv[i] * (b[i] - s);
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -193,13 +240,13 @@ __device__ __forceinline__ double block_sum(double v) {
   return t;  // valid in thread 0
 }
 
-template <int G>
+template <int G, bool C16>
 __global__ void __launch_bounds__(kBlock) k_ap(OpView<double> m, const double* __restrict__ p, double* __restrict__ q,
                                                double* __restrict__ part) {
   int row;
   double ap;
   double v = 0.0;
-  if (op_row<double, G>(m, p, row, ap) && group_leader<G>()) {
+  if (op_row<double, G, C16>(m, p, row, ap) && group_leader<G>()) {
     q[row] = ap;
     v = p[row] * ap;
   }
@@ -344,6 +391,16 @@ __global__ void k_dense_reduce(int n, int nchunks, const double* __restrict__ pa
 template <typename Src, typename Dst>
 __global__ void k_convert(int n, const Src* __restrict__ a, Dst* __restrict__ b) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = (Dst)a[i];
+}
+
+template <typename Src, typename Dst>
+__global__ void k_gather(int n, const int32_t* __restrict__ perm, const Src* __restrict__ a, Dst* __restrict__ b) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = (Dst)a[perm[i]];
+}
+
+template <typename Src, typename Dst>
+__global__ void k_scatter(int n, const int32_t* __restrict__ perm, const Src* __restrict__ a, Dst* __restrict__ b) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[perm[i]] = (Dst)a[i];
 }
 
 template <typename T>
@@ -601,66 +658,95 @@ int sell_blocks(int nrows, int lanes) { return grid_for((int)std::min<int64_t>((
 
 template <typename T>
 OpView<T> view(const SellMat<T>& A) {
-  return OpView<T>{A.off, A.rp, A.col, A.val, A.perm, A.nrows};
+  return OpView<T>{A.off, A.rp, A.col, A.val, A.perm, A.col16, A.cbase, A.nrows};
 }
 
-// Dispatch on the layout: F<G>(grid) is called with the kernel's lanes-per-row.
+template <int G, bool C>
+struct Lay {
+  static constexpr int lanes = G;
+  static constexpr bool c16 = C;
+};
+
+// Dispatch on the layout: f(Lay<G, C16>) with the kernel's lanes per row and index width.
 template <typename F>
-void by_lanes(int lanes, F&& f) {
-  switch (lanes) {
-    case 1: f(std::integral_constant<int, 1>()); break;
-    case 4: f(std::integral_constant<int, 4>()); break;
-    case 8: f(std::integral_constant<int, 8>()); break;
-    case 16: f(std::integral_constant<int, 16>()); break;
-    case 32: f(std::integral_constant<int, 32>()); break;
-    default: throw Error(MG_ERR_INVALID_ARG, "unsupported lanes per row");
-  }
+void by_layout(int lanes, bool c16, F&& f) {
+  auto go = [&](auto c) {
+    constexpr bool C = decltype(c)::value;
+    switch (lanes) {
+      case 1: f(Lay<1, C>()); break;
+      case 4: f(Lay<4, C>()); break;
+      case 8: f(Lay<8, C>()); break;
+      case 16: f(Lay<16, C>()); break;
+      case 32: f(Lay<32, C>()); break;
+      default: throw Error(MG_ERR_INVALID_ARG, "unsupported lanes per row");
+    }
+  };
+  if (c16) go(std::true_type());
+  else go(std::false_type());
 }
 
 template <typename T>
 void sell_spmv(const SellMat<T>& A, const T* x, T* y, cudaStream_t s) {
   if (A.nrows == 0) return;
-  by_lanes(A.lanes, [&](auto g) {
-    k_spmv<T, decltype(g)::value><<<sell_blocks(A.nrows, A.lanes), kBlock, 0, s>>>(view(A), x, y);
+  by_layout(A.lanes, A.col16 != nullptr, [&](auto g) {
+    using L = decltype(g);
+    k_spmv<T, L::lanes, L::c16><<<sell_blocks(A.nrows, A.lanes), kBlock, 0, s>>>(view(A), x, y);
   });
 }
 template <typename T>
 void sell_resid(const SellMat<T>& A, const T* x, const T* b, T* r, cudaStream_t s) {
   if (A.nrows == 0) return;
-  by_lanes(A.lanes, [&](auto g) {
-    k_resid<T, decltype(g)::value><<<sell_blocks(A.nrows, A.lanes), kBlock, 0, s>>>(view(A), x, b, r);
+  by_layout(A.lanes, A.col16 != nullptr, [&](auto g) {
+    using L = decltype(g);
+    k_resid<T, L::lanes, L::c16><<<sell_blocks(A.nrows, A.lanes), kBlock, 0, s>>>(view(A), x, b, r);
   });
 }
 template <typename T>
 void sell_cheb(const SellMat<T>& A, const T* xin, const T* b, const T* dinv, T* d, T* xout, double cd, double cr,
                bool first, cudaStream_t s) {
   if (A.nrows == 0) return;
-  by_lanes(A.lanes, [&](auto g) {
-    constexpr int G = decltype(g)::value;
+  by_layout(A.lanes, A.col16 != nullptr, [&](auto g) {
+    using L = decltype(g);
+    constexpr int G = L::lanes;
     if (first)
-      k_cheb<T, G, true><<<sell_blocks(A.nrows, G), kBlock, 0, s>>>(view(A), xin, b, dinv, d, xout, (T)cd, (T)cr);
+      k_cheb<T, G, L::c16, true><<<sell_blocks(A.nrows, G), kBlock, 0, s>>>(view(A), xin, b, dinv, d, xout, (T)cd,
+                                                                            (T)cr);
     else
-      k_cheb<T, G, false><<<sell_blocks(A.nrows, G), kBlock, 0, s>>>(view(A), xin, b, dinv, d, xout, (T)cd, (T)cr);
+      k_cheb<T, G, L::c16, false><<<sell_blocks(A.nrows, G), kBlock, 0, s>>>(view(A), xin, b, dinv, d, xout, (T)cd,
+                                                                             (T)cr);
   });
 }
 template <typename T>
 void sell_prolong(const SellMat<T>& P, const T* xc, T* x, cudaStream_t s) {
   if (P.nrows == 0) return;
-  by_lanes(P.lanes, [&](auto g) {
-    k_prolong<T, decltype(g)::value><<<sell_blocks(P.nrows, P.lanes), kBlock, 0, s>>>(view(P), xc, x);
+  by_layout(P.lanes, P.col16 != nullptr, [&](auto g) {
+    using L = decltype(g);
+    k_prolong<T, L::lanes, L::c16><<<sell_blocks(P.nrows, P.lanes), kBlock, 0, s>>>(view(P), xc, x);
   });
 }
 template <typename T>
 void sell_restrict(const SellMat<T>& R, const T* r, T* bc, T* xc, cudaStream_t s) {
   if (R.nrows == 0) return;
-  by_lanes(R.lanes, [&](auto g) {
-    k_restrict<T, decltype(g)::value><<<sell_blocks(R.nrows, R.lanes), kBlock, 0, s>>>(view(R), r, bc, xc);
+  by_layout(R.lanes, R.col16 != nullptr, [&](auto g) {
+    using L = decltype(g);
+    k_restrict<T, L::lanes, L::c16><<<sell_blocks(R.nrows, R.lanes), kBlock, 0, s>>>(view(R), r, bc, xc);
+  });
+}
+template <typename T>
+void sell_gs(const SellMat<T>& M, const int32_t* rows, const T* b, const T* dinv, T* x, cudaStream_t s) {
+  if (M.nrows == 0) return;
+  by_layout(M.lanes, M.col16 != nullptr, [&](auto g) {
+    using L = decltype(g);
+    k_gs<T, L::lanes, L::c16><<<sell_blocks(M.nrows, M.lanes), kBlock, 0, s>>>(view(M), rows, x, b, dinv, x);
   });
 }
 void sell_ap(const SellMat<double>& A, const double* p, double* q, double* partial, int* nparts, cudaStream_t s) {
   int nb = sell_blocks(A.nrows, A.lanes);
   *nparts = nb;
-  by_lanes(A.lanes, [&](auto g) { k_ap<decltype(g)::value><<<nb, kBlock, 0, s>>>(view(A), p, q, partial); });
+  by_layout(A.lanes, A.col16 != nullptr, [&](auto g) {
+    using L = decltype(g);
+    k_ap<L::lanes, L::c16><<<nb, kBlock, 0, s>>>(view(A), p, q, partial);
+  });
 }
 
 template <typename T>
@@ -710,6 +796,19 @@ void convert(int n, const Src* a, Dst* b, cudaStream_t s) {
   if (n == 0) return;
   k_convert<Src, Dst><<<std::min(grid_for(n, kBlock), kCgBlocks), kBlock, 0, s>>>(n, a, b);
 }
+template <typename Src, typename Dst>
+void gather(int n, const int32_t* perm, const Src* a, Dst* b, cudaStream_t s) {
+  if (n == 0) return;
+  if (!perm) return convert<Src, Dst>(n, a, b, s);
+  k_gather<Src, Dst><<<std::min(grid_for(n, kBlock), kCgBlocks), kBlock, 0, s>>>(n, perm, a, b);
+}
+template <typename Src, typename Dst>
+void scatter(int n, const int32_t* perm, const Src* a, Dst* b, cudaStream_t s) {
+  if (n == 0) return;
+  if (!perm) return convert<Src, Dst>(n, a, b, s);
+  k_scatter<Src, Dst><<<std::min(grid_for(n, kBlock), kCgBlocks), kBlock, 0, s>>>(n, perm, a, b);
+}
+
 template <typename T>
 void axpy_from(int n, const T* z, double* x, cudaStream_t s) {
   if (n == 0) return;
@@ -750,6 +849,7 @@ void dot_self(int n, const double* r, double* part, cudaStream_t s) {
                              cudaStream_t);                                                                      \
   template void sell_prolong<T>(const SellMat<T>&, const T*, T*, cudaStream_t);                                  \
   template void sell_restrict<T>(const SellMat<T>&, const T*, T*, T*, cudaStream_t);                             \
+  template void sell_gs<T>(const SellMat<T>&, const int32_t*, const T*, const T*, T*, cudaStream_t);             \
   template void cheb_first_from_zero<T>(int, const T*, const T*, const T*, T*, T*, double, int, const int32_t*, \
                                         const int32_t*, const int32_t*, const T*, cudaStream_t);                 \
   template void patch_residual<T>(int, const int32_t*, const int32_t*, const int32_t*, const double*, const T*,  \
@@ -768,5 +868,10 @@ NNMG_INST(float)
 template void convert<double, float>(int, const double*, float*, cudaStream_t);
 template void convert<float, double>(int, const float*, double*, cudaStream_t);
 template void convert<double, double>(int, const double*, double*, cudaStream_t);
+template void convert<float, float>(int, const float*, float*, cudaStream_t);
+template void gather<double, float>(int, const int32_t*, const double*, float*, cudaStream_t);
+template void gather<double, double>(int, const int32_t*, const double*, double*, cudaStream_t);
+template void scatter<float, double>(int, const int32_t*, const float*, double*, cudaStream_t);
+template void scatter<double, double>(int, const int32_t*, const double*, double*, cudaStream_t);
 
 }  // namespace nnmg

@@ -26,6 +26,12 @@ struct SellMat {
   int32_t sigma = 1;        // window within which rows were sorted by length
   int32_t lanes = 1;        // 1: SELL-32 (off/col/val/perm); G > 1: CSR vector (rp/col/val)
   int32_t* rp = nullptr;    // [nrows+1] CSR row pointer (lanes > 1)
+  // 16-bit column offsets: column = cbase[slice or row] + col16[k] where cbase >= 0; a
+  // slice or row spanning more than 2^16 columns has cbase = -1 and reads col (which is
+  // then null when every slice or row is narrow)
+  uint16_t* col16 = nullptr;
+  int32_t* cbase = nullptr; // [nslices] (SELL) or [nrows] (CSR vector)
+  double idx_bytes = 0;     // index bytes of the nonzeros (2 or 4 each), for the roofline
 };
 
 // Device-side state of the preconditioned CG recurrence (all FP64).
@@ -61,6 +67,11 @@ void cheb_first_from_zero(int n, const T* b, const T* dinv, const T* xin, T* d, 
 template <typename T> void sell_prolong(const SellMat<T>& P, const T* xc, T* x, cudaStream_t s);
 // bc = R r and xc = 0 (xc has R.nrows entries).
 template <typename T> void sell_restrict(const SellMat<T>& R, const T* r, T* bc, T* xc, cudaStream_t s);
+// One colour of a multicolour Gauss-Seidel sweep: for each row r of M (the colour's rows,
+// without the diagonal and without couplings inside the colour), i = rows[r] and
+// x_i = dinv_i (b_i - (M x)_r).
+template <typename T>
+void sell_gs(const SellMat<T>& M, const int32_t* rows, const T* b, const T* dinv, T* x, cudaStream_t s);
 // q = A p and per-block partial sums of p.q (FP64).
 void sell_ap(const SellMat<double>& A, const double* p, double* q, double* partial, int* nparts, cudaStream_t s);
 int sell_blocks(int nrows, int lanes);
@@ -108,6 +119,9 @@ void lanczos_next(int n, const double* w, double* v, double* vprev, double inv_b
 
 // ---- vectors ----
 template <typename Src, typename Dst> void convert(int n, const Src* a, Dst* b, cudaStream_t s);
+// b[i] = (Dst) a[perm[i]] (gather) and b[perm[i]] = (Dst) a[i] (scatter); perm == nullptr: convert.
+template <typename Src, typename Dst> void gather(int n, const int32_t* perm, const Src* a, Dst* b, cudaStream_t s);
+template <typename Src, typename Dst> void scatter(int n, const int32_t* perm, const Src* a, Dst* b, cudaStream_t s);
 template <typename T> void axpy_from(int n, const T* z, double* x, cudaStream_t s);   // x += (double) z
 
 // ---- CG (FP64 recurrence; the V-cycle vectors vb/vx are FP64 or FP32) ----

@@ -505,4 +505,54 @@ std::vector<int32_t> inverse_perm(const std::vector<int32_t>& p) {
   return q;
 }
 
+int32_t greedy_colouring(const Csr& A, std::vector<int32_t>& colour) {
+  const int64_t n = A.nrows;
+  std::vector<double> d(n, 0.0);
+  for (int64_t i = 0; i < n; ++i)
+    for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k)
+      if (A.ci[k] == i) d[i] = std::sqrt(std::fabs(A.v[k]));
+  colour.assign(n, -1);
+  std::vector<int64_t> seen;   // seen[c] == i: colour c is held by a neighbour of row i
+  int32_t ncol = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+      const int32_t j = A.ci[k];
+      if (j == i || colour[j] < 0 || !(std::fabs(A.v[k]) > 1e-12 * d[i] * d[j])) continue;
+      if ((size_t)colour[j] >= seen.size()) seen.resize(colour[j] + 1, -1);
+      seen[colour[j]] = i;
+    }
+    int32_t c = 0;
+    while ((size_t)c < seen.size() && seen[c] == i) ++c;
+    colour[i] = c;
+    ncol = std::max(ncol, c + 1);
+  }
+  return ncol;
+}
+
+std::vector<int32_t> morton_order(const std::vector<double>& pts, int dim) {
+  const int64_t n = dim > 0 ? (int64_t)pts.size() / dim : 0;
+  const int bits = dim == 3 ? 21 : 31;
+  double lo[3] = {0, 0, 0}, ext = 0;
+  for (int d = 0; d < dim; ++d) {
+    double mn = INFINITY, mx = -INFINITY;
+    for (int64_t i = 0; i < n; ++i) mn = std::min(mn, pts[i * dim + d]), mx = std::max(mx, pts[i * dim + d]);
+    lo[d] = mn;
+    ext = std::max(ext, mx - mn);
+  }
+  const double scale = ext > 0 ? (double)((1u << bits) - 1) / ext : 0.0;
+  std::vector<uint64_t> code(n, 0);
+  for (int64_t i = 0; i < n; ++i) {
+    uint64_t c = 0;
+    for (int d = 0; d < dim; ++d) {
+      const uint64_t q = (uint64_t)((pts[i * dim + d] - lo[d]) * scale);
+      for (int b = 0; b < bits; ++b) c |= ((q >> b) & 1u) << (b * dim + d);
+    }
+    code[i] = c;
+  }
+  std::vector<int32_t> ord(n);
+  for (int64_t i = 0; i < n; ++i) ord[i] = (int32_t)i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return code[a] < code[b]; });
+  return ord;
+}
+
 }  // namespace nnmg

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_PKG, "lib", "libnnmg.so")
 OK, ERR_INVALID_ARG, ERR_DEGENERATE_CELL, ERR_POINT_LOCATION, ERR_NOT_SPD = 0, 1, 2, 3, 4
 ERR_NO_CONVERGENCE, ERR_BREAKDOWN, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NO_DEVICE = 5, 6, 7, 8, 9, 10
 SMOOTHER = {"sandwich": 0, "global_then_local": 1, "global": 2}
+GLOBAL_SMOOTHER = {"chebyshev": 0, "sgs": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 
 
@@ -38,7 +39,8 @@ class MgOptions(C.Structure):
                 ("host_only", C.c_int32), ("eig_maxit", C.c_int32), ("lmin_ratio", C.c_double),
                 ("lmax_safety", C.c_double), ("eig_tol", C.c_double), ("lambda_override", C.c_void_p),
                 ("use_graph", C.c_int32), ("local_levels_mask", C.c_int32), ("quality_threshold", C.c_double),
-                ("sell_sigma", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("sell_sigma", C.c_int32), ("reorder", C.c_int32), ("global_smoother", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 class MgSolveInfo(C.Structure):
@@ -96,6 +98,7 @@ _SIGS = {
     "mg_export_level": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "mg_export_transfer": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "mg_export_patches": (C.c_int, [_P, C.c_int32, _P, _P]),
+    "mg_export_colouring": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int32), _P]),
     "mg_eigs": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mg_dof_coords": (C.c_int, [_P, C.c_int32, _P]),
     "mg_cell_quality": (C.c_int, [_P, C.c_int32, _P]),
@@ -107,6 +110,7 @@ _SIGS = {
     "mg_solve_batch": (C.c_int, [_P, _P, _P, C.c_int32, C.c_double, C.c_int32, C.POINTER(MgSolveInfo), _P]),
     "mg_apply_A": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "mg_chebyshev": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
+    "mg_sgs": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "mg_local_correction": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "mg_smooth": (C.c_int, [_P, C.c_int32, C.c_int32, _P, _P, _P]),
     "mg_residual_restrict": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P]),
@@ -161,6 +165,8 @@ def default_options(**kw) -> MgOptions:
             v = SMOOTHER[v]
         if k == "precision" and isinstance(v, str):
             v = PRECISION[v]
+        if k == "global_smoother" and isinstance(v, str):
+            v = GLOBAL_SMOOTHER[v]
         if k == "lambda_override":
             continue
         setattr(o, k, v)
@@ -311,6 +317,13 @@ class Hierarchy:
         _check(lib.mg_export_patches(self._h, l, ptr.ctypes.data, dofs.ctypes.data), self._h)
         return [dofs[ptr[i]:ptr[i + 1]].copy() for i in range(num.value)]
 
+    def export_colouring(self, l: int):
+        num = C.c_int32()
+        _check(lib.mg_export_colouring(self._h, l, C.byref(num), None), self._h)
+        colour = np.zeros(self.num_dofs(l), np.int32)
+        _check(lib.mg_export_colouring(self._h, l, C.byref(num), colour.ctypes.data), self._h)
+        return colour
+
     def eigs(self, l: int):
         a, b, c = C.c_double(), C.c_double(), C.c_double()
         _check(lib.mg_eigs(self._h, l, C.byref(a), C.byref(b), C.byref(c)), self._h)
@@ -381,6 +394,10 @@ class Hierarchy:
     def chebyshev(self, l, b, x, stream=None):
         n = self.num_dofs(l)
         _check(lib.mg_chebyshev(self._h, l, _dev_ptr(b, n), _dev_ptr(x, n), _stream(stream)), self._h)
+
+    def sgs(self, l, b, x, stream=None):
+        n = self.num_dofs(l)
+        _check(lib.mg_sgs(self._h, l, _dev_ptr(b, n), _dev_ptr(x, n), _stream(stream)), self._h)
 
     def local_correction(self, l, b, x, stream=None):
         n = self.num_dofs(l)

@@ -265,3 +265,24 @@ def test_device_lanczos_eigenvalues(nnmg, name):
             assert abs(lu - lo.lmax_unadj) < 1e-8 * lo.lmax_unadj, (l, lu, lo.lmax_unadj)
             assert abs(la - lo.lmax_adj) < 1e-8 * lo.lmax_adj, (l, la, lo.lmax_adj)
             assert used == la
+
+
+@pytest.mark.parametrize("name", ["c1_p2", "c2_p2_128"])
+def test_library_numbering_without_reordering(nnmg, name):
+    """The same V-cycle and solve with the internal reordering switched off (operators in the
+    library's numbering, 32-bit indices) and with it on."""
+    meshes, Ho, degree, layers = case(name)
+    lam = [lv.lmax for lv in Ho.levels[:-1]]
+    n = Ho.levels[0].n
+    b, x0 = rng_vec(n, 160), rng_vec(n, 161)
+    ref = x0 + mg.vcycle(Ho, b - Ho.levels[0].A @ x0)
+    xr, itr, _, _ = mg.pcg(Ho, b, 1e-10)
+    for reorder in (0, 1, 2):
+        with nnmg.Hierarchy.from_meshes(meshes, degree, 0.1, patch_layers=layers, lambda_override=lam,
+                                        reorder=reorder) as H:
+            x = dev(x0)
+            H.vcycle(dev(b), x)
+            assert rel_err(host(x), ref) < TOL64, reorder
+            xs = torch.zeros(n, dtype=torch.float64, device="cuda")
+            info = H.solve(dev(b), xs, rtol=1e-10)
+            assert info["iterations"] == itr and rel_err(host(xs), xr) < 1e-9, reorder

@@ -148,3 +148,20 @@ def test_unreached_coarse_dofs_get_unit_diagonal(nnmg):
     for j in unreached:
         row = A1.getrow(j)
         assert row.nnz == 1 and row.indices[0] == j and row.data[0] == 1.0
+
+
+@pytest.mark.parametrize("name", ["c1_p1", "c1_p2", "c2_p2_128", "cube_p1", "cube_p2"])
+def test_host_colouring_matches_oracle(nnmg, name):
+    """The multicolour SGS colouring of every smoothed level, bit for bit (index work)."""
+    from oracle import smoother
+    meshes, Ho, degree, layers = case(name)
+    with nnmg.Hierarchy.from_meshes(meshes, degree, 0.1, host_only=1, patch_layers=layers,
+                                    global_smoother="sgs") as H:
+        for l, lo in enumerate(Ho.levels[:-1]):
+            c = H.export_colouring(l)
+            assert np.array_equal(c, smoother.greedy_colouring(lo.A)), l
+        with pytest.raises(nnmg.NnmgError):
+            H.export_colouring(Ho.L - 1)
+    with nnmg.Hierarchy.from_meshes(meshes, degree, 0.1, host_only=1, patch_layers=layers) as H:
+        with pytest.raises(nnmg.NnmgError):
+            H.export_colouring(0)

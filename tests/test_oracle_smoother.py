@@ -183,3 +183,43 @@ def test_direct_solver_semidefinite_consistent():
         assert np.max(np.abs(A @ e - r)) < 1e-10 * np.max(np.abs(r))
     with pytest.raises(np.linalg.LinAlgError):
         smoother.DirectSolver(-np.eye(3))
+
+
+def test_multicolour_sgs_is_sequential_sgs_in_colour_order():
+    """The multicolour sweep equals plain sequential symmetric Gauss-Seidel over the rows
+    sorted by colour (brute-force row-by-row loop), the colouring is valid, and the SGS
+    error operator is self-adjoint in the A inner product."""
+    _, _, A, _, _ = _level(n=8, degree=2)
+    n = A.shape[0]
+    colour = smoother.greedy_colouring(A)
+    Ac = A.tocoo()
+    dg = np.sqrt(A.diagonal())
+    strong = (Ac.row != Ac.col) & (np.abs(Ac.data) > smoother.COLOUR_TOL * dg[Ac.row] * dg[Ac.col])
+    assert np.all(colour[Ac.row[strong]] != colour[Ac.col[strong]])
+    Ad = A.toarray()
+    d = np.diag(Ad)
+    rng = np.random.default_rng(9)
+    b, x0 = rng.normal(size=n), rng.normal(size=n)
+    order = np.argsort(colour, kind="stable")
+    x = x0.copy()
+    for i in list(order) + list(order[::-1]):
+        x[i] += (b[i] - Ad[i] @ x) / d[i]
+    y = smoother.multicolour_sgs(A, 1 / d, b, x0, colour)
+    assert np.max(np.abs(x - y)) < 1e-12 * np.max(np.abs(x))
+    E = np.stack([smoother.multicolour_sgs(A, 1 / d, np.zeros(n), np.eye(n)[i], colour) for i in range(n)], axis=1)
+    AE = Ad @ E
+    assert np.max(np.abs(AE - AE.T)) < 1e-10 * np.max(np.abs(AE))
+
+
+def test_sgs_vcycle_symmetric_and_correction_claim(c1_meshes):
+    from oracle import mg
+    H = hierarchy.build(c1_meshes, 1, layers=2, smoother_kind="sgs")
+    Hn = hierarchy.build(c1_meshes, 1, layers=2, smoother_kind="sgs", order="global")
+    n = H.levels[0].n
+    rng = np.random.default_rng(4)
+    x, y = rng.normal(size=n), rng.normal(size=n)
+    assert abs(x @ mg.vcycle(H, y) - y @ mg.vcycle(H, x)) < 1e-12 * abs(x @ mg.vcycle(H, x))
+    b = inputs.uniform_rhs(n, 6)
+    sc = mg.stationary(H, b, 1e-10)[1]
+    sn = mg.stationary(Hn, b, 1e-10, maxit=400)[1]
+    assert sn > sc, (sc, sn)
