@@ -75,6 +75,17 @@ enum mg_global_smoother {
                               lambda_max is computed. */
 };
 
+/* Operator assembled on level 0 by mg_setup (option `pde`). */
+enum mg_pde {
+  MG_PDE_POISSON = 0,     /* -lap u = f, P1/P2 (Sec. 6.1-6.2) */
+  MG_PDE_ELASTICITY = 1   /* -div sigma(u) = f, sigma = 2 mu eps(u) + lambda tr(eps(u)) I with
+                             mu = E / (2 (1 + nu)), lambda = E nu / ((1 + nu)(1 - 2 nu))
+                             (Sec. 6.3); vector P1/P2, DoF dim*k + c = component c of scalar
+                             DoF k (components interleaved); P acts componentwise (P (x) I);
+                             patches hold every component of their nodes; a Dirichlet node
+                             is clamped in every component */
+};
+
 /* Device-internal DoF order of the smoothed levels (option `reorder`). Column indices are
  * stored as 16-bit offsets from a per-slice (per-row) base wherever the slice spans fewer
  * than 2^16 columns, so orders that keep neighbours close in index shrink the matrix. */
@@ -135,7 +146,10 @@ typedef struct mg_options_t {
                               level but the coarsest (vectors at the ABI stay in the library's
                               numbering) (SPATIAL) */
   int32_t global_smoother; /* enum mg_global_smoother (CHEBYSHEV) */
-  int32_t reserved[3];
+  int32_t pde;             /* enum mg_pde (POISSON); mg_setup only */
+  double young;            /* Young's modulus E for MG_PDE_ELASTICITY (6.9e10, Sec. 6.3) */
+  double poisson_ratio;    /* Poisson's ratio nu for MG_PDE_ELASTICITY (0.33, Sec. 6.3) */
+  int32_t reserved[4];
 } mg_options_t;
 
 /* Result of a solve. */
@@ -213,7 +227,8 @@ int mg_eigs(const mg_hierarchy_t* h, int32_t level, double* lmax, double* lmax_a
 int mg_dof_coords(const mg_hierarchy_t* h, int32_t level, double* out);
 /* gamma per cell of a level's mesh: out[nc] (geometric hierarchies only). */
 int mg_cell_quality(const mg_hierarchy_t* h, int32_t level, double* out);
-/* b_i = int f phi_i for a constant f on the free DoFs of level 0: out[n_0] host. */
+/* b_i = int f phi_i for a constant f on the free DoFs of level 0: out[n_0] host
+ * (MG_PDE_POISSON hierarchies built by mg_setup). */
 int mg_load_constant(const mg_hierarchy_t* h, double f, double* out_host);
 
 /* ---- the hot path (device vectors, FP64 at the boundary) ---------------------------- */
@@ -243,6 +258,12 @@ int mg_solve_stationary(mg_hierarchy_t* h, const double* b_dev, double* x_dev, d
  * back to `stream`). Blocks; info[n] may be NULL. Returns the first non-OK status. */
 int mg_solve_batch(mg_hierarchy_t* const* hs, const double* const* b_dev, double* const* x_dev,
                    int32_t n, double rtol, int32_t maxit, mg_solve_info_t* info, void* stream);
+
+/* b = int_{Gamma_2} t . v over the boundary facets of level 0 lying in the plane
+ * x_axis = value (every vertex within 1e-12 of it), for MG_PDE_ELASTICITY hierarchies
+ * built by mg_setup (Sec. 6.3: traction (1e3, 0, 0) on the face x = 6 of the lattice).
+ * t: host [dim]; b_host: host [mg_num_dofs(h, 0)]. INVALID_ARG for other hierarchies. */
+int mg_load_traction(const mg_hierarchy_t* h, int32_t axis, double value, const double* t, double* b_host);
 
 /* ---- single steps of the hot path (device vectors in the hierarchy's V-cycle type:
  *      FP64 in FP64 mode; FP32 in MIXED mode is not exposed) -------------------------- */

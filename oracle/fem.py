@@ -30,7 +30,8 @@ import scipy.sparse as sp
 
 from .quadrature import barycentric_of_reference, simplex_rule
 
-LOCAL_EDGES = {2: [(0, 1), (0, 2), (1, 2)],
+LOCAL_EDGES = {1: [(0, 1)],
+               2: [(0, 1), (0, 2), (1, 2)],
                3: [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]}
 
 

@@ -18,6 +18,7 @@ import numpy as np
 import scipy.sparse as sp
 
 from . import eig as _eig
+from . import elasticity as _elasticity
 from . import fem, patches as _patches, quality, transfer
 from . import smoother
 from .smoother import DirectSolver, LocalSolver
@@ -64,18 +65,30 @@ class Hierarchy:
 def build(meshes, degree: int, threshold: float = 0.1, layers: int = 1, adjusted: bool = True,
           lmin_ratio: float = 0.1, cheb_degree: int = 2, nu: int = 1, order: str = "sandwich",
           lambda_override=None, dirichlet_masks=None, local_levels=None,
-          compute_eigs: bool = True, smoother_kind: str = "chebyshev") -> Hierarchy:
+          compute_eigs: bool = True, smoother_kind: str = "chebyshev", pde: str = "poisson",
+          young: float = 6.9e10, poisson_ratio: float = 0.33) -> Hierarchy:
+    """``pde``: "poisson" (Sec. 6.1-6.2) or "elasticity" (Sec. 6.3, vector DoFs numbered as
+    in ``elasticity``; P acts componentwise and patches hold every component of their nodes)."""
     L = len(meshes)
     levels = []
+    vec = pde == "elasticity"
+    if pde not in ("poisson", "elasticity"):
+        raise ValueError(pde)
     for l, m in enumerate(meshes):
         mask = None if dirichlet_masks is None else dirichlet_masks[l]
         dm = fem.dof_map(m.coords, m.cells, degree, mask)
         gamma = quality.radius_ratio(m.coords, m.cells)
         if l == 0:
-            A = fem.restrict_free(fem.assemble_stiffness_full(m.coords, m.cells, dm), dm)
+            if vec:
+                mu, lam = _elasticity.lame(young, poisson_ratio)
+                A = _elasticity.restrict_free(_elasticity.assemble_full(m.coords, m.cells, dm, mu, lam), dm)
+            else:
+                A = fem.restrict_free(fem.assemble_stiffness_full(m.coords, m.cells, dm), dm)
         else:
             prev = levels[-1]
             prev.P = transfer.prolongation(prev.dm, m.coords, m.cells, dm)
+            if vec:
+                prev.P = _elasticity.vector_prolongation(prev.P, m.coords.shape[1])
             prev.R = prev.P.T.tocsr()
             prev.R.sort_indices()
             A = transfer.galerkin(prev.A, prev.P)
@@ -83,6 +96,8 @@ def build(meshes, degree: int, threshold: float = 0.1, layers: int = 1, adjusted
         if local_levels is None or l in local_levels:
             lev.patches = _patches.local_patches(m.cells, gamma, threshold, layers, m.nv,
                                                  dm.cell_dofs, dm.free_index)
+            if vec:
+                lev.patches = _elasticity.expand_patches(lev.patches, m.coords.shape[1])
         levels.append(lev)
     for l, lev in enumerate(levels):
         lev.local = LocalSolver(lev.A, lev.patches)

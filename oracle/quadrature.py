@@ -24,6 +24,8 @@ def simplex_rule(dim: int, degree: int):
     g, w = np.polynomial.legendre.leggauss(m)
     g = 0.5 * (g + 1.0)
     w = 0.5 * w
+    if dim == 1:
+        return g[:, None].copy(), w.copy()
     if dim == 2:
         u, v = np.meshgrid(g, g, indexing="ij")
         wu, wv = np.meshgrid(w, w, indexing="ij")
@@ -41,7 +43,7 @@ def simplex_rule(dim: int, degree: int):
         wt = wu * wv * ws * (1.0 - u) ** 2 * (1.0 - v)
         pts = np.stack([x1.ravel(), x2.ravel(), x3.ravel()], axis=1)
         return pts, wt.ravel()
-    raise ValueError("dim must be 2 or 3")
+    raise ValueError("dim must be 1, 2 or 3")
 
 
 def barycentric_of_reference(pts: np.ndarray) -> np.ndarray:

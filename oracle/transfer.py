@@ -7,9 +7,11 @@ Point location (the paper delegates it to FEniCS): for each free fine DoF point 
 the containing coarse cell is the lowest-numbered cell whose barycentric coordinates at
 x_i are all >= -1e-12 (points on shared edges/vertices give the same row from any
 containing cell, up to rounding). Candidates are all cells whose centroid lies within
-the largest cell diameter of x_i, which contains every cell that can hold x_i. Basis
-values are taken at the raw barycentric coordinates; entries with |value| < 1e-14 are
-dropped; columns are the coarse free DoFs (Dirichlet columns vanish with g = 0).
+the largest cell diameter of x_i, which contains every cell that can hold x_i. Barycentric
+coordinates within 1e-12 of zero are set to zero (a point on a face, edge or vertex of
+its cell then gives exact zeros instead of rounding residue of either sign), the basis is
+evaluated there, entries with |value| < 1e-14 are dropped; columns are the coarse free
+DoFs (Dirichlet columns vanish with g = 0).
 
 Reading for degenerate coarse cells: a coarse basis function can vanish at every fine
 interpolation point (e.g. the P2 edge DoF of a needle edge much shorter than the fine
@@ -86,6 +88,7 @@ def prolongation(fine: DofMap, coarse_coords: np.ndarray, coarse_cells: np.ndarr
     rows_g = fine.free if free_only else np.arange(fine.ndofs)
     pts = fine.points[rows_g]
     cell, lam = locate(coarse_coords, coarse_cells, pts)
+    lam = np.where(np.abs(lam) <= LOCATE_TOL, 0.0, lam)
     vals = basis_values(lam, coarse.degree, coarse.dim)         # [npts, nloc]
     cols = coarse.cell_dofs[cell]                               # [npts, nloc]
     if free_only:

@@ -234,18 +234,21 @@ SellMat<T> make_csrv(const Csr& A, DevMem& mem, int lanes) {
 }
 
 struct Layout {
-  int lanes, sigma;
+  int lanes, sigma, unroll;
 };
 
 template <typename T>
 SellMat<T> make_layout(const Csr& A, DevMem& mem, Layout L) {
-  return L.lanes > 1 ? make_csrv<T>(A, mem, L.lanes) : make_sell<T>(A, mem, L.sigma);
+  SellMat<T> S = L.lanes > 1 ? make_csrv<T>(A, mem, L.lanes) : make_sell<T>(A, mem, L.sigma);
+  S.unroll = L.unroll;
+  return S;
 }
 
 // Autotuner (sigma option 0): time y = A x on the device for each candidate layout
-// (SELL-32 with windows 1, 256, 2048 when sorting removes padding; CSR vector with 4, 8,
-// 16, 32 lanes per row up to twice the longest row) and keep the fastest. Timing: one
-// warm-up launch, then the mean of 5 launches between CUDA events.
+// (SELL-32 with windows 1, 256, 2048 when sorting removes padding, each in groups of 4 and
+// of 8 entries; CSR vector with 4, 8, 16, 32 lanes per row up to twice the longest row) and
+// keep the fastest. Timing: one warm-up launch, then the mean of 5 launches between CUDA
+// events.
 template <typename T>
 SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log) {
   if (sigma != 0 || A.nrows == 0) return make_sell<T>(A, mem, std::max(sigma, 1));
@@ -257,10 +260,10 @@ SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log) {
     int64_t pad = sell_padded(A, sell_order(A, c));
     if (last_pad >= 0 && pad >= (int64_t)(0.995 * (double)last_pad)) continue;  // sorting gains nothing more
     last_pad = pad;
-    cand.push_back({1, c});
+    cand.push_back({1, c, 4});
   }
   for (int g : {4, 8, 16, 32})
-    if (g <= 2 * std::max(maxlen, 2)) cand.push_back({g, 1});
+    if (g <= 2 * std::max(maxlen, 2)) cand.push_back({g, 1, 4});
   DevMem scratch;
   scratch.stream = mem.stream;
   const cudaStream_t st = mem.stream;
@@ -275,21 +278,26 @@ SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log) {
     DevMem trial;
     trial.stream = st;
     SellMat<T> S = make_layout<T>(A, trial, c);
-    sell_spmv<T>(S, x, y, st);
-    CK(cudaEventRecord(e0, st));
-    for (int rep = 0; rep < 5; ++rep) sell_spmv<T>(S, x, y, st);
-    CK(cudaEventRecord(e1, st));
-    CK(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, e0, e1));
-    trial.release();
-    if (log)
-      *log += std::string(" ") + (c.lanes > 1 ? "v" + std::to_string(c.lanes) : "s" + std::to_string(c.sigma)) + ":" +
-              std::to_string((int)(ms / 5 * 1e3)) + "us";
-    if (best_ms < 0 || ms < best_ms) {
-      best_ms = ms;
-      best = c;
+    for (int unroll : {4, 8}) {
+      if (c.lanes > 1 && unroll != 4) continue;
+      S.unroll = unroll;
+      sell_spmv<T>(S, x, y, st);
+      CK(cudaEventRecord(e0, st));
+      for (int rep = 0; rep < 5; ++rep) sell_spmv<T>(S, x, y, st);
+      CK(cudaEventRecord(e1, st));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (log)
+        *log += std::string(" ") +
+                (c.lanes > 1 ? "v" + std::to_string(c.lanes) : "s" + std::to_string(c.sigma) + "u" + std::to_string(unroll)) +
+                ":" + std::to_string((int)(ms / 5 * 1e3)) + "us";
+      if (best_ms < 0 || ms < best_ms) {
+        best_ms = ms;
+        best = {c.lanes, c.sigma, unroll};
+      }
     }
+    trial.release();
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -305,10 +313,9 @@ struct DevLevel {
   T *dinv = nullptr, *b = nullptr, *x = nullptr, *xt = nullptr, *d = nullptr, *res = nullptr;
   std::vector<double> cd, cr;
   // local correction
-  int np = 0, nt = 0, nitems = 0, max_patch = 0;
-  int32_t *pdofs = nullptr, *pptr = nullptr, *prp = nullptr, *pci = nullptr;
+  int np = 0, nt = 0, nitems = 0, max_patch = 0, pw = 0;
+  int32_t *pdofs = nullptr, *pci = nullptr;   // patch rows of A, ELL with pw entries per row
   double* pv = nullptr;
-  int64_t* inv_off = nullptr;
   double *inv = nullptr, *rbuf = nullptr;
   PatchItem* items = nullptr;
   // rows coupled to patch DoFs, with their entries of A (first Chebyshev step after S_c)
@@ -375,9 +382,8 @@ struct Engine {
   }
   void local(int l, cudaStream_t s, bool zero = false) {
     DevLevel<T>& L = lv[l];
-    if (!zero) patch_residual<T>(L.nt, L.pdofs, L.prp, L.pci, L.pv, L.b, L.x, L.rbuf, s);
-    patch_solve<T>(L.nitems, L.items, L.pptr, L.pdofs, L.inv_off, L.inv, zero ? nullptr : L.rbuf, L.b, L.x,
-                   L.max_patch, s);
+    if (!zero) patch_residual<T>(L.nt, L.pw, L.pdofs, L.pci, L.pv, L.b, L.x, L.rbuf, s);
+    patch_solve<T>(L.nitems, L.items, L.pdofs, L.inv, zero ? nullptr : L.rbuf, L.b, L.x, L.max_patch, s);
     launches += zero ? 1 : 2;
   }
   // zero: the iterate is zero on entry (first pre-smoothing on every level of a cycle)
@@ -436,7 +442,8 @@ struct mg_hierarchy {
   int L = 0, degree = 0;
   bool geometric = false, device = false;
   std::vector<LevelH> host;
-  std::vector<double> fine_load_unit;  // b for f = 1 (geometric only)
+  std::vector<double> fine_load_unit;  // b for f = 1 (geometric Poisson only)
+  BoundaryFaces fine_faces;            // level-0 boundary facets (geometric elasticity only)
   std::vector<int64_t> ncells;
   std::string err;
   // device
@@ -487,6 +494,9 @@ void validate_options(const mg_options_t& o) {
   if (o.sell_sigma < 0 || o.sell_sigma > (1 << 20)) throw Error(MG_ERR_INVALID_ARG, "sell_sigma must be in [0, 2^20]");
   if (o.global_smoother < 0 || o.global_smoother > 1) throw Error(MG_ERR_INVALID_ARG, "unknown global smoother");
   if (o.reorder < 0 || o.reorder > 2) throw Error(MG_ERR_INVALID_ARG, "unknown reorder mode");
+  if (o.pde < 0 || o.pde > 1) throw Error(MG_ERR_INVALID_ARG, "unknown pde");
+  if (o.pde == MG_PDE_ELASTICITY && !(o.young > 0 && o.poisson_ratio > -1.0 && o.poisson_ratio < 0.5))
+    throw Error(MG_ERR_INVALID_ARG, "elasticity needs E > 0 and -1 < nu < 1/2");
 }
 
 // Chebyshev coefficients per step: d = cd d + cr D^{-1} r (Sec. 3.2 three-term recurrence).
@@ -823,27 +833,33 @@ void build_device(mg_hierarchy* h) {
         if (D.np > 0) {
           D.nt = (int)H.patch_dofs.size();
           D.pdofs = mem.upload(H.patch_dofs);
-          D.pptr = mem.upload(H.patch_ptr);
-          std::vector<int32_t> prp(D.nt + 1, 0), pci;
-          std::vector<double> pv;
-          std::vector<PatchItem> items;
+          // patch rows of A, ELL: pw entries per row, padded with value 0 at the row's own DoF
+          int pw = 1;
           for (int t = 0; t < D.nt; ++t) {
-            int32_t r = H.patch_dofs[t];
-            for (int32_t k = H.A.rp[r]; k < H.A.rp[r + 1]; ++k) pci.push_back(H.A.ci[k]), pv.push_back(H.A.v[k]);
-            prp[t + 1] = (int32_t)pci.size();
+            const int32_t r = H.patch_dofs[t];
+            pw = std::max(pw, H.A.rp[r + 1] - H.A.rp[r]);
           }
+          D.pw = pw;
+          std::vector<int32_t> pci((size_t)D.nt * pw);
+          std::vector<double> pv((size_t)D.nt * pw, 0.0);
+          for (int t = 0; t < D.nt; ++t) {
+            const int32_t r = H.patch_dofs[t];
+            const int64_t o = (int64_t)t * pw;
+            int j = 0;
+            for (int32_t k = H.A.rp[r]; k < H.A.rp[r + 1]; ++k, ++j) pci[o + j] = H.A.ci[k], pv[o + j] = H.A.v[k];
+            for (; j < pw; ++j) pci[o + j] = r;
+          }
+          std::vector<PatchItem> items;
           for (int p = 0; p < D.np; ++p) {
-            int m = H.patch_ptr[p + 1] - H.patch_ptr[p];
+            const int32_t p0 = H.patch_ptr[p], m = H.patch_ptr[p + 1] - p0;
             D.max_patch = std::max(D.max_patch, m);
-            for (int r0 = 0; r0 < m; r0 += kPatchRowsPerItem) items.push_back({p, r0});
+            for (int r0 = 0; r0 < m; r0 += kPatchRowsPerItem) items.push_back({p0, m, r0, 0, level_inv_off[l][p]});
           }
           if (D.max_patch > 27000) throw Error(MG_ERR_INVALID_ARG, "patch larger than 27000 DoFs");
           max_patch = std::max(max_patch, D.max_patch);
           D.nitems = (int)items.size();
-          D.prp = mem.upload(prp);
           D.pci = mem.upload(pci);
           D.pv = mem.upload(pv);
-          D.inv_off = mem.upload(level_inv_off[l]);
           D.inv = gj.M;
           D.rbuf = mem.alloc<double>(D.nt);
           D.items = mem.upload(items);
@@ -872,7 +888,8 @@ void build_device(mg_hierarchy* h) {
         }
       }
       auto lay = [](const SellMat<T>& M) {
-        return (M.lanes > 1 ? "v" + std::to_string(M.lanes) : "s" + std::to_string(M.sigma)) +
+        return (M.lanes > 1 ? "v" + std::to_string(M.lanes)
+                            : "s" + std::to_string(M.sigma) + "u" + std::to_string(M.unroll)) +
                (M.col16 ? (M.col ? "/16+32" : "/16") : "/32");
       };
       tm.mark("upload L" + std::to_string(l) + " A/P/R " + lay(D.A) + "/" + lay(D.P) + "/" + lay(D.R) + " |" + tlog);
@@ -1188,6 +1205,9 @@ void mg_default_options(mg_options_t* o) {
   o->quality_threshold = 0.1;
   o->sell_sigma = 0;
   o->reorder = MG_REORDER_SPATIAL;
+  o->pde = MG_PDE_POISSON;
+  o->young = 6.9e10;
+  o->poisson_ratio = 0.33;
 }
 
 }  // extern "C"
@@ -1208,6 +1228,7 @@ mg_hierarchy* build_host_hierarchy(const mg_mesh_t* levels, int32_t L, int32_t d
   H->L = L;
   H->degree = degree;
   H->geometric = true;
+  const bool elastic = H->opt.pde == MG_PDE_ELASTICITY;
   std::vector<MeshH> meshes(L);
   std::vector<DofMapH> dms(L);
   H->host.resize(L);
@@ -1232,22 +1253,41 @@ mg_hierarchy* build_host_hierarchy(const mg_mesh_t* levels, int32_t L, int32_t d
     lv.gamma = radius_ratio(M);
     for (int64_t c = 0; c < M.nc; ++c)
       if (!(lv.gamma[c] > 0)) throw Error(MG_ERR_DEGENERATE_CELL, "level " + std::to_string(l) + ": cell " + std::to_string(c) + " is degenerate");
-    lv.dof_points.resize(dms[l].nfree * m.dim);
+    // vector problems: every free node carries ncomp consecutive DoFs (same point)
+    const int ncomp = elastic ? m.dim : 1;
+    lv.dof_points.resize(dms[l].nfree * ncomp * m.dim);
     for (int64_t i = 0; i < dms[l].nfree; ++i)
-      for (int r = 0; r < m.dim; ++r) lv.dof_points[i * m.dim + r] = dms[l].points[dms[l].free_list[i] * m.dim + r];
+      for (int c = 0; c < ncomp; ++c)
+        for (int r = 0; r < m.dim; ++r)
+          lv.dof_points[(i * ncomp + c) * m.dim + r] = dms[l].points[dms[l].free_list[i] * m.dim + r];
     if ((H->opt.local_levels_mask >> std::min(l, 31)) & 1)
       local_patches(M, dms[l], lv.gamma, quality_threshold, H->opt.patch_layers, lv.patch_ptr, lv.patch_dofs);
     else
       lv.patch_ptr.assign(1, 0);
+    if (ncomp > 1) {
+      std::vector<int32_t> vdofs;
+      vdofs.reserve(lv.patch_dofs.size() * ncomp);
+      for (int32_t f : lv.patch_dofs)
+        for (int c = 0; c < ncomp; ++c) vdofs.push_back(f * ncomp + c);
+      lv.patch_dofs.swap(vdofs);
+      for (int32_t& p : lv.patch_ptr) p *= ncomp;
+    }
     H->ncells.push_back(M.nc);
     tm.mark("dofmap/gamma/patches L" + std::to_string(l));
   }
-  H->host[0].A = assemble_stiffness(meshes[0], dms[0]);
-  H->fine_load_unit = load_constant(meshes[0], dms[0], 1.0);
+  if (elastic) {
+    const double E = H->opt.young, nu = H->opt.poisson_ratio;
+    H->host[0].A = assemble_elasticity(meshes[0], dms[0], E / (2.0 * (1.0 + nu)), E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)));
+    H->fine_faces = boundary_faces(meshes[0], dms[0]);
+  } else {
+    H->host[0].A = assemble_stiffness(meshes[0], dms[0]);
+    H->fine_load_unit = load_constant(meshes[0], dms[0], 1.0);
+  }
   tm.mark("assembly L0");
   for (int l = 1; l < L; ++l) {
     LevelH& f = H->host[l - 1];
     f.P = prolongation(dms[l - 1], meshes[l], dms[l]);
+    if (elastic) f.P = kron_identity(f.P, meshes[0].dim);
     f.R = transpose(f.P);
     Csr AP = spgemm(f.A, f.P);
     H->host[l].A = unit_diagonal_on_empty_rows(spgemm(f.R, AP));
@@ -1545,9 +1585,26 @@ int mg_load_constant(const mg_hierarchy_t* hc, double f, double* out) {
   mg_hierarchy* h = const_cast<mg_hierarchy*>(hc);
   API_BEGIN
   checked(h, false);
-  if (!h->geometric) throw Error(MG_ERR_INVALID_ARG, "not a geometric hierarchy");
+  if (!h->geometric || h->opt.pde != MG_PDE_POISSON)
+    throw Error(MG_ERR_INVALID_ARG, "not a geometric Poisson hierarchy");
   if (!out) throw Error(MG_ERR_INVALID_ARG, "null output");
   for (size_t i = 0; i < h->fine_load_unit.size(); ++i) out[i] = f * h->fine_load_unit[i];
+  return MG_OK;
+  API_END_H(h)
+}
+
+int mg_load_traction(const mg_hierarchy_t* hc, int32_t axis, double value, const double* t, double* out) {
+  mg_hierarchy* h = const_cast<mg_hierarchy*>(hc);
+  API_BEGIN
+  checked(h, false);
+  if (!h->geometric || h->opt.pde != MG_PDE_ELASTICITY)
+    throw Error(MG_ERR_INVALID_ARG, "not a geometric elasticity hierarchy");
+  if (!t || !out) throw Error(MG_ERR_INVALID_ARG, "null pointer");
+  const int d = h->fine_faces.dim;
+  if (axis < 0 || axis >= d) throw Error(MG_ERR_INVALID_ARG, "axis out of range");
+  const int64_t n = h->host[0].A.nrows;
+  std::vector<double> b = traction_load(h->fine_faces, axis, value, 1e-12, t, n / d);
+  std::copy(b.begin(), b.end(), out);
   return MG_OK;
   API_END_H(h)
 }

@@ -43,6 +43,16 @@ struct DofMapH {
   std::vector<uint8_t> dirichlet;   // [ndofs]
   std::vector<int64_t> free_index;  // [ndofs] free id or -1
   std::vector<int64_t> free_list;   // [nfree] all-DoF id of each free DoF
+  std::vector<int64_t> bfaces;      // boundary facets as c*(dim+1) + (local vertex opposite)
+};
+
+// Boundary facets of a mesh with their free scalar DoFs (-1: Dirichlet), for surface loads:
+// x [nf*dim*dim] the facet's vertex coordinates, dofs [nf*nfloc] its vertex DoFs then (P2)
+// its edge DoFs.
+struct BoundaryFaces {
+  int dim = 0, degree = 1, nfloc = 0;
+  std::vector<double> x;
+  std::vector<int64_t> dofs;
 };
 
 // One level of the hierarchy as built on the host.
@@ -72,6 +82,15 @@ DofMapH build_dofmap(const MeshH& m, int degree);
 std::vector<double> radius_ratio(const MeshH& m);
 Csr assemble_stiffness(const MeshH& m, const DofMapH& dm);
 std::vector<double> load_constant(const MeshH& m, const DofMapH& dm, double f);
+// Linear elasticity (Sec. 6.3): the operator on free vector DoFs, vector DoF dim*k + c =
+// component c of free scalar DoF k; cell term mu (grad phi_a . grad phi_b) delta_ij +
+// mu d_j phi_a d_i phi_b + lambda d_i phi_a d_j phi_b (trial phi_b e_j, test phi_a e_i).
+Csr assemble_elasticity(const MeshH& m, const DofMapH& dm, double mu, double lam);
+BoundaryFaces boundary_faces(const MeshH& m, const DofMapH& dm);
+// b = int_{Gamma} t . v over the boundary facets in the plane x_axis = value (all vertices
+// within tol), over the nfree*dim vector DoFs.
+std::vector<double> traction_load(const BoundaryFaces& bf, int axis, double value, double tol, const double* t,
+                                  int64_t nfree);
 void local_patches(const MeshH& m, const DofMapH& dm, const std::vector<double>& gamma,
                    double threshold, int layers, std::vector<int32_t>& ptr, std::vector<int32_t>& dofs);
 
@@ -81,6 +100,8 @@ Csr transpose(const Csr& A);
 // Coarse DoFs that P never reaches have empty rows in P^T A P: give them A_ii = 1.
 Csr unit_diagonal_on_empty_rows(const Csr& A);
 Csr spgemm(const Csr& A, const Csr& B);
+// P (x) I_d: entry (i, j, v) becomes (d*i + c, d*j + c, v) for c < d.
+Csr kron_identity(const Csr& P, int d);
 // lambda_max of D^{-1/2} A D^{-1/2} restricted to rows/cols with keep[i] != 0 (NULL: all).
 double lanczos_lmax(const Csr& A, const uint8_t* keep, double tol, int maxit, int* iters);
 // Greedy colouring in index order: colour[i] = the smallest colour not held by a neighbour

@@ -67,69 +67,81 @@ struct Col32 {
   __device__ __forceinline__ int operator()(int64_t k) const { return ld_stream(c + k); }
 };
 
-// Sum over the w padded entries of one SELL-32 lane starting at element k (stride 32).
-template <typename T, typename C>
+// Sum over the w padded entries of one SELL-32 lane starting at element k (stride 32), in
+// groups of U entries: a group's value and index loads are issued together, then its x
+// gathers, then its FMAs (in entry order), so a row costs about two dependent memory
+// round trips per group; the last group is predicated rather than run entry by entry.
+template <typename T, int U, typename C>
 __device__ __forceinline__ T sell_lane(const T* __restrict__ vp, int64_t k, int w, C col, const T* __restrict__ x) {
   T acc = T(0);
-  int j = 0;
-  for (; j + 4 <= w; j += 4) {
-    const T v0 = ld_stream(vp), v1 = ld_stream(vp + 32), v2 = ld_stream(vp + 64), v3 = ld_stream(vp + 96);
-    const int c0 = col(k), c1 = col(k + 32), c2 = col(k + 64), c3 = col(k + 96);
-    const T x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2), x3 = __ldg(x + c3);
-    acc = fma(v0, x0, acc);
-    acc = fma(v1, x1, acc);
-    acc = fma(v2, x2, acc);
-    acc = fma(v3, x3, acc);
-    vp += 128;
-    k += 128;
-  }
-  for (; j < w; ++j) {
-    acc = fma(ld_stream(vp), __ldg(x + col(k)), acc);
-    vp += 32;
-    k += 32;
+  for (int j = 0; j < w; j += U) {
+    T v[U], xv[U];
+    int c[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = j + u < w ? ld_stream(vp + 32 * u) : T(0);
+#pragma unroll
+    for (int u = 0; u < U; ++u) c[u] = j + u < w ? col(k + 32 * u) : 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) xv[u] = j + u < w ? __ldg(x + c[u]) : T(0);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (j + u < w) acc = fma(v[u], xv[u], acc);
+    vp += 32 * U;
+    k += 32 * U;
   }
   return acc;
 }
 
-template <typename T, bool C16>
+template <typename T, bool C16, int U>
 __device__ __forceinline__ T sell_row(const OpView<T>& m, const T* __restrict__ x, int srow) {
   const int s = srow >> 5, lane = srow & 31;
   const int64_t o = m.off[s];
   const int w = (int)((m.off[s + 1] - o) >> 5);
   if constexpr (C16) {
     const int base = m.cbase[s];   // uniform across the warp (one slice per warp)
-    if (base >= 0) return sell_lane(m.val + o + lane, o + lane, w, Col16{m.col16, base}, x);
+    if (base >= 0) return sell_lane<T, U>(m.val + o + lane, o + lane, w, Col16{m.col16, base}, x);
   }
-  return sell_lane(m.val + o + lane, o + lane, w, Col32{m.col}, x);
+  return sell_lane<T, U>(m.val + o + lane, o + lane, w, Col32{m.col}, x);
 }
 
-// CSR-vector partial sum of one lane of a G-lane group over row entries [k, k1).
+// CSR-vector partial sum of one lane of a G-lane group over row entries [k, k1), four
+// strided entries per group, the last group predicated.
 template <typename T, int G, typename C>
 __device__ __forceinline__ T csrv_lane(const T* __restrict__ val, int k, int k1, C col, const T* __restrict__ x) {
   T a = T(0);
-  for (; k + 3 * G < k1; k += 4 * G) {
-    const T v0 = ld_stream(val + k), v1 = ld_stream(val + k + G), v2 = ld_stream(val + k + 2 * G),
-            v3 = ld_stream(val + k + 3 * G);
-    const int c0 = col(k), c1 = col(k + G), c2 = col(k + 2 * G), c3 = col(k + 3 * G);
-    a = fma(v0, __ldg(x + c0), a);
-    a = fma(v1, __ldg(x + c1), a);
-    a = fma(v2, __ldg(x + c2), a);
-    a = fma(v3, __ldg(x + c3), a);
+  for (; k < k1; k += 4 * G) {
+    T v[4], xv[4];
+    int c[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = k + u * G < k1 ? ld_stream(val + k + u * G) : T(0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) c[u] = k + u * G < k1 ? col(k + u * G) : 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) xv[u] = k + u * G < k1 ? __ldg(x + c[u]) : T(0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (k + u * G < k1) a = fma(v[u], xv[u], a);
   }
-  for (; k < k1; k += G) a = fma(ld_stream(val + k), __ldg(x + col(k)), a);
   return a;
 }
 
+// Kernel layout parameter G: 1 = SELL-32 in groups of 4 entries, 2 = SELL-32 in groups of
+// 8, G >= 4 = CSR vector with G lanes per row.
+template <int G>
+__host__ __device__ constexpr bool is_sell() {
+  return G <= 2;
+}
+
 // Row sum of the calling thread's row. Returns false for threads past the last row; for
-// G > 1 every lane of a group receives the group's total (all lanes take part in the
+// CSR vector every lane of a group receives the group's total (all lanes take part in the
 // shuffles, so no lane leaves early).
 template <typename T, int G, bool C16>
 __device__ __forceinline__ bool op_row(const OpView<T>& m, const T* __restrict__ x, int& row, T& acc) {
   const int tid = blockIdx.x * kBlock + threadIdx.x;
-  if constexpr (G == 1) {
+  if constexpr (is_sell<G>()) {
     if (tid >= m.nrows) return false;
     row = m.perm ? m.perm[tid] : tid;
-    acc = sell_row<T, C16>(m, x, tid);
+    acc = sell_row<T, C16, G == 2 ? 8 : 4>(m, x, tid);
     return true;
   } else {
     const int slot = tid / G, lane = tid & (G - 1);
@@ -151,7 +163,7 @@ __device__ __forceinline__ bool op_row(const OpView<T>& m, const T* __restrict__
 
 template <int G>
 __device__ __forceinline__ bool group_leader() {
-  return G == 1 || (threadIdx.x & (G - 1)) == 0;
+  return is_sell<G>() || (threadIdx.x & (G - 1)) == 0;
 }
 
 template <typename T, int G, bool C16>
@@ -293,46 +305,49 @@ __global__ void __launch_bounds__(kBlock) k_cheb0_halo(int nh, const int32_t* __
 
 // S_c phase 1: r_B = b_B - (A x)_B for every patch row, one warp per row (FP64).
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_patch_residual(int nt, const int32_t* __restrict__ pdofs,
-                                                           const int32_t* __restrict__ prp,
+__global__ void __launch_bounds__(kBlock) k_patch_residual(int nt, int w, const int32_t* __restrict__ pdofs,
                                                            const int32_t* __restrict__ pci,
                                                            const double* __restrict__ pv, const T* __restrict__ b,
                                                            const T* __restrict__ x, double* __restrict__ rbuf) {
   const int t = (blockIdx.x * kBlock + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (t >= nt) return;  // warp-uniform
+  const double bt = (double)b[pdofs[t]];
+  const int64_t r0 = (int64_t)t * w;
   double s = 0.0;
-  if (t < nt)
-    for (int k = prp[t] + lane; k < prp[t + 1]; k += 32) s = fma(pv[k], (double)x[pci[k]], s);
+  for (int k = lane; k < w; k += 32) s = fma(pv[r0 + k], (double)x[pci[r0 + k]], s);
   s = warp_sum(s);
-  if (t < nt && lane == 0) rbuf[t] = (double)b[pdofs[t]] - s;
+  if (lane == 0) rbuf[t] = bt - s;
 }
 
 // S_c phase 2: e = (A^[d])^{-1} r_B and x_B += e. A work item is 32 consecutive rows of one
 // patch; each warp computes 4 of them, reading row i of the symmetric inverse contiguously.
-// With rbuf == nullptr the iterate is zero and the residual is b itself (no phase 1).
+// Every load that does not depend on r_B (the item, the output rows' DoF ids and current
+// values) is issued before the block barrier, so a launch costs about three dependent
+// memory round trips. With rbuf == nullptr the iterate is zero and the residual is b.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_patch_solve(const PatchItem* __restrict__ items,
-                                                        const int32_t* __restrict__ pptr,
                                                         const int32_t* __restrict__ pdofs,
-                                                        const int64_t* __restrict__ inv_off,
                                                         const double* __restrict__ inv, const double* rbuf,
                                                         const T* __restrict__ b, T* __restrict__ x) {
   extern __shared__ double rs[];
   const PatchItem it = items[blockIdx.x];
-  const int p0 = pptr[it.patch], n = pptr[it.patch + 1] - p0;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) rs[j] = rbuf ? rbuf[p0 + j] : (double)b[pdofs[p0 + j]];
-  __syncthreads();
+  const int p0 = it.p0, n = it.n;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int R = kPatchRowsPerItem / 8;  // rows per warp, accumulated together
   const int i0 = it.row0 + warp * R;
-  if (i0 >= n) return;  // warp-uniform; no block barrier follows
-  const double* X = inv + inv_off[it.patch];
-  const double* Xi[R];
-  bool ok[R];
+  int g[R];
+  T xg[R];
 #pragma unroll
-  for (int q = 0; q < R; ++q) {
-    ok[q] = i0 + q < n;
-    Xi[q] = X + (int64_t)(ok[q] ? i0 + q : i0) * n;
-  }
+  for (int q = 0; q < R; ++q) g[q] = i0 + q < n ? pdofs[p0 + i0 + q] : -1;
+#pragma unroll
+  for (int q = 0; q < R; ++q) xg[q] = g[q] >= 0 ? x[g[q]] : T(0);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) rs[j] = rbuf ? rbuf[p0 + j] : (double)b[pdofs[p0 + j]];
+  __syncthreads();
+  if (i0 >= n) return;  // warp-uniform; no block barrier follows
+  const double* X = inv + it.inv;
+  const double* Xi[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) Xi[q] = X + (int64_t)(g[q] >= 0 ? i0 + q : i0) * n;
   double e[R];
 #pragma unroll
   for (int q = 0; q < R; ++q) e[q] = 0.0;
@@ -350,10 +365,7 @@ __global__ void __launch_bounds__(kBlock) k_patch_solve(const PatchItem* __restr
 #pragma unroll
   for (int q = 0; q < R; ++q) {
     const double eq = warp_sum(e[q]);
-    if (lane == 0 && ok[q]) {
-      const int g = pdofs[p0 + i0 + q];
-      x[g] = (T)((double)x[g] + eq);
-    }
+    if (lane == 0 && g[q] >= 0) x[g[q]] = (T)((double)xg[q] + eq);
   }
 }
 
@@ -667,13 +679,17 @@ struct Lay {
   static constexpr bool c16 = C;
 };
 
-// Dispatch on the layout: f(Lay<G, C16>) with the kernel's lanes per row and index width.
+// Dispatch on the layout: f(Lay<G, C16>) with the kernel's layout parameter G (see is_sell)
+// and index width.
 template <typename F>
-void by_layout(int lanes, bool c16, F&& f) {
+void by_layout(int lanes, int unroll, bool c16, F&& f) {
   auto go = [&](auto c) {
     constexpr bool C = decltype(c)::value;
     switch (lanes) {
-      case 1: f(Lay<1, C>()); break;
+      case 1:
+        if (unroll == 8) f(Lay<2, C>());
+        else f(Lay<1, C>());
+        break;
       case 4: f(Lay<4, C>()); break;
       case 8: f(Lay<8, C>()); break;
       case 16: f(Lay<16, C>()); break;
@@ -688,7 +704,7 @@ void by_layout(int lanes, bool c16, F&& f) {
 template <typename T>
 void sell_spmv(const SellMat<T>& A, const T* x, T* y, cudaStream_t s) {
   if (A.nrows == 0) return;
-  by_layout(A.lanes, A.col16 != nullptr, [&](auto g) {
+  by_layout(A.lanes, A.unroll, A.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
     k_spmv<T, L::lanes, L::c16><<<sell_blocks(A.nrows, A.lanes), kBlock, 0, s>>>(view(A), x, y);
   });
@@ -696,7 +712,7 @@ void sell_spmv(const SellMat<T>& A, const T* x, T* y, cudaStream_t s) {
 template <typename T>
 void sell_resid(const SellMat<T>& A, const T* x, const T* b, T* r, cudaStream_t s) {
   if (A.nrows == 0) return;
-  by_layout(A.lanes, A.col16 != nullptr, [&](auto g) {
+  by_layout(A.lanes, A.unroll, A.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
     k_resid<T, L::lanes, L::c16><<<sell_blocks(A.nrows, A.lanes), kBlock, 0, s>>>(view(A), x, b, r);
   });
@@ -705,21 +721,21 @@ template <typename T>
 void sell_cheb(const SellMat<T>& A, const T* xin, const T* b, const T* dinv, T* d, T* xout, double cd, double cr,
                bool first, cudaStream_t s) {
   if (A.nrows == 0) return;
-  by_layout(A.lanes, A.col16 != nullptr, [&](auto g) {
+  by_layout(A.lanes, A.unroll, A.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
     constexpr int G = L::lanes;
     if (first)
-      k_cheb<T, G, L::c16, true><<<sell_blocks(A.nrows, G), kBlock, 0, s>>>(view(A), xin, b, dinv, d, xout, (T)cd,
+      k_cheb<T, G, L::c16, true><<<sell_blocks(A.nrows, A.lanes), kBlock, 0, s>>>(view(A), xin, b, dinv, d, xout, (T)cd,
                                                                             (T)cr);
     else
-      k_cheb<T, G, L::c16, false><<<sell_blocks(A.nrows, G), kBlock, 0, s>>>(view(A), xin, b, dinv, d, xout, (T)cd,
+      k_cheb<T, G, L::c16, false><<<sell_blocks(A.nrows, A.lanes), kBlock, 0, s>>>(view(A), xin, b, dinv, d, xout, (T)cd,
                                                                              (T)cr);
   });
 }
 template <typename T>
 void sell_prolong(const SellMat<T>& P, const T* xc, T* x, cudaStream_t s) {
   if (P.nrows == 0) return;
-  by_layout(P.lanes, P.col16 != nullptr, [&](auto g) {
+  by_layout(P.lanes, P.unroll, P.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
     k_prolong<T, L::lanes, L::c16><<<sell_blocks(P.nrows, P.lanes), kBlock, 0, s>>>(view(P), xc, x);
   });
@@ -727,7 +743,7 @@ void sell_prolong(const SellMat<T>& P, const T* xc, T* x, cudaStream_t s) {
 template <typename T>
 void sell_restrict(const SellMat<T>& R, const T* r, T* bc, T* xc, cudaStream_t s) {
   if (R.nrows == 0) return;
-  by_layout(R.lanes, R.col16 != nullptr, [&](auto g) {
+  by_layout(R.lanes, R.unroll, R.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
     k_restrict<T, L::lanes, L::c16><<<sell_blocks(R.nrows, R.lanes), kBlock, 0, s>>>(view(R), r, bc, xc);
   });
@@ -735,7 +751,7 @@ void sell_restrict(const SellMat<T>& R, const T* r, T* bc, T* xc, cudaStream_t s
 template <typename T>
 void sell_gs(const SellMat<T>& M, const int32_t* rows, const T* b, const T* dinv, T* x, cudaStream_t s) {
   if (M.nrows == 0) return;
-  by_layout(M.lanes, M.col16 != nullptr, [&](auto g) {
+  by_layout(M.lanes, M.unroll, M.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
     k_gs<T, L::lanes, L::c16><<<sell_blocks(M.nrows, M.lanes), kBlock, 0, s>>>(view(M), rows, x, b, dinv, x);
   });
@@ -743,7 +759,7 @@ void sell_gs(const SellMat<T>& M, const int32_t* rows, const T* b, const T* dinv
 void sell_ap(const SellMat<double>& A, const double* p, double* q, double* partial, int* nparts, cudaStream_t s) {
   int nb = sell_blocks(A.nrows, A.lanes);
   *nparts = nb;
-  by_layout(A.lanes, A.col16 != nullptr, [&](auto g) {
+  by_layout(A.lanes, A.unroll, A.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
     k_ap<L::lanes, L::c16><<<nb, kBlock, 0, s>>>(view(A), p, q, partial);
   });
@@ -759,10 +775,10 @@ void cheb_first_from_zero(int n, const T* b, const T* dinv, const T* xin, T* d, 
 }
 
 template <typename T>
-void patch_residual(int nt, const int32_t* pdofs, const int32_t* prp, const int32_t* pci, const double* pv, const T* b,
-                    const T* x, double* rbuf, cudaStream_t s) {
+void patch_residual(int nt, int w, const int32_t* pdofs, const int32_t* pci, const double* pv, const T* b, const T* x,
+                    double* rbuf, cudaStream_t s) {
   if (nt == 0) return;
-  k_patch_residual<T><<<grid_for(nt, kBlock / 32), kBlock, 0, s>>>(nt, pdofs, prp, pci, pv, b, x, rbuf);
+  k_patch_residual<T><<<grid_for(nt, kBlock / 32), kBlock, 0, s>>>(nt, w, pdofs, pci, pv, b, x, rbuf);
 }
 
 void patch_solve_setup(int max_patch) {
@@ -774,11 +790,11 @@ void patch_solve_setup(int max_patch) {
 }
 
 template <typename T>
-void patch_solve(int nitems, const PatchItem* items, const int32_t* pptr, const int32_t* pdofs, const int64_t* inv_off,
-                 const double* inv, const double* rbuf, const T* b, T* x, int max_patch, cudaStream_t s) {
+void patch_solve(int nitems, const PatchItem* items, const int32_t* pdofs, const double* inv, const double* rbuf,
+                 const T* b, T* x, int max_patch, cudaStream_t s) {
   if (nitems == 0) return;
   size_t smem = (size_t)max_patch * sizeof(double);
-  k_patch_solve<T><<<nitems, kBlock, smem, s>>>(items, pptr, pdofs, inv_off, inv, rbuf, b, x);
+  k_patch_solve<T><<<nitems, kBlock, smem, s>>>(items, pdofs, inv, rbuf, b, x);
 }
 
 int dense_chunks(int n, int kchunk) { return grid_for(n, kchunk); }
@@ -852,10 +868,10 @@ void dot_self(int n, const double* r, double* part, cudaStream_t s) {
   template void sell_gs<T>(const SellMat<T>&, const int32_t*, const T*, const T*, T*, cudaStream_t);             \
   template void cheb_first_from_zero<T>(int, const T*, const T*, const T*, T*, T*, double, int, const int32_t*, \
                                         const int32_t*, const int32_t*, const T*, cudaStream_t);                 \
-  template void patch_residual<T>(int, const int32_t*, const int32_t*, const int32_t*, const double*, const T*,  \
-                                  const T*, double*, cudaStream_t);                                              \
-  template void patch_solve<T>(int, const PatchItem*, const int32_t*, const int32_t*, const int64_t*,            \
-                               const double*, const double*, const T*, T*, int, cudaStream_t);                   \
+  template void patch_residual<T>(int, int, const int32_t*, const int32_t*, const double*, const T*, const T*,   \
+                                   double*, cudaStream_t);                                                \
+  template void patch_solve<T>(int, const PatchItem*, const int32_t*, const double*, const double*, const T*, T*, \
+                                int, cudaStream_t);                                                      \
   template void dense_solve<T>(int, const double*, const T*, T*, double*, int, cudaStream_t);                    \
   template void axpy_from<T>(int, const T*, double*, cudaStream_t);                                              \
   template void cg_init<T>(int, const double*, double*, double*, T*, T*, double*, cudaStream_t);                 \

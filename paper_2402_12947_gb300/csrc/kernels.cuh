@@ -25,6 +25,7 @@ struct SellMat {
   int32_t* perm = nullptr;  // [nrows] matrix row held by each slot, or null (identity)
   int32_t sigma = 1;        // window within which rows were sorted by length
   int32_t lanes = 1;        // 1: SELL-32 (off/col/val/perm); G > 1: CSR vector (rp/col/val)
+  int32_t unroll = 4;       // SELL-32: entries per lane loaded together (4 or 8)
   int32_t* rp = nullptr;    // [nrows+1] CSR row pointer (lanes > 1)
   // 16-bit column offsets: column = cbase[slice or row] + col16[k] where cbase >= 0; a
   // slice or row spanning more than 2^16 columns has cbase = -1 and reads col (which is
@@ -43,8 +44,11 @@ struct CgState {
 // FIN_NORM: rr = the sum; FIN_TRUE: rr_true = the sum (|b - A x|^2 recomputed at exit)
 enum FinishOp { FIN_BB = 0, FIN_RZ0 = 1, FIN_PQ = 2, FIN_RR = 3, FIN_RZ = 4, FIN_NORM = 5, FIN_TRUE = 6 };
 
+// One S_c work item: rows row0 .. row0 + kPatchRowsPerItem - 1 of a patch whose DoFs are
+// pdofs[p0 .. p0 + n) and whose dense inverse starts at element inv of the arena.
 struct PatchItem {
-  int32_t patch, row0;
+  int32_t p0, n, row0, pad;
+  int64_t inv;
 };
 
 constexpr int kBlock = 256;
@@ -77,16 +81,18 @@ void sell_ap(const SellMat<double>& A, const double* p, double* q, double* parti
 int sell_blocks(int nrows, int lanes);
 
 // ---- local correction S_c (two phases) ----
+// S_c phase 1: rbuf[t] = b[pdofs[t]] - (A x)[pdofs[t]] for the nt patch rows, stored
+// ELL-style with w entries per row (pci/pv [nt*w], padding has value 0).
 template <typename T>
-void patch_residual(int nt, const int32_t* pdofs, const int32_t* prp, const int32_t* pci, const double* pv,
-                    const T* b, const T* x, double* rbuf, cudaStream_t s);
+void patch_residual(int nt, int w, const int32_t* pdofs, const int32_t* pci, const double* pv, const T* b, const T* x,
+                    double* rbuf, cudaStream_t s);
 // Raise the dynamic shared-memory limit of the solve kernel for patches of up to max_patch DoFs.
 void patch_solve_setup(int max_patch);
-// rbuf == nullptr: the iterate is zero, the residual is b itself (phase 1 skipped).
+// S_c phase 2, x_B += (A^[d])^{-1} r_B per work item; rbuf == nullptr: the iterate is zero
+// and the residual is b itself (phase 1 skipped).
 template <typename T>
-void patch_solve(int nitems, const PatchItem* items, const int32_t* pptr, const int32_t* pdofs,
-                 const int64_t* inv_off, const double* inv, const double* rbuf, const T* b, T* x, int max_patch,
-                 cudaStream_t s);
+void patch_solve(int nitems, const PatchItem* items, const int32_t* pdofs, const double* inv, const double* rbuf,
+                 const T* b, T* x, int max_patch, cudaStream_t s);
 
 // ---- coarsest level: x = X b with X = A_L^{-1} dense symmetric (split-K, deterministic) ----
 template <typename T>

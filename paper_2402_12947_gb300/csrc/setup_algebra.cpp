@@ -138,6 +138,9 @@ Csr prolongation(const DofMapH& fine, const MeshH& cm, const DofMapH& coarse) {
         failed[i] = 1;
         continue;
       }
+      // barycentric coordinates within the location tolerance of zero are exact zeros
+      for (int j = 0; j < d1; ++j)
+        if (std::fabs(lam[j]) <= -kLocate) lam[j] = 0.0;
       double vals[10];
       basis_at(coarse.degree, d, lam, vals);
       std::pair<int32_t, double> e[10];
@@ -553,6 +556,23 @@ std::vector<int32_t> morton_order(const std::vector<double>& pts, int dim) {
   for (int64_t i = 0; i < n; ++i) ord[i] = (int32_t)i;
   std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return code[a] < code[b]; });
   return ord;
+}
+
+Csr kron_identity(const Csr& P, int d) {
+  Csr K;
+  K.nrows = P.nrows * d;
+  K.ncols = P.ncols * d;
+  K.rp.assign(K.nrows + 1, 0);
+  for (int64_t i = 0; i < P.nrows; ++i)
+    for (int c = 0; c < d; ++c) K.rp[i * d + c + 1] = K.rp[i * d + c] + (P.rp[i + 1] - P.rp[i]);
+  K.ci.resize(K.rp[K.nrows]);
+  K.v.resize(K.rp[K.nrows]);
+  for (int64_t i = 0; i < P.nrows; ++i)
+    for (int c = 0; c < d; ++c) {
+      int64_t o = K.rp[i * d + c];
+      for (int32_t k = P.rp[i]; k < P.rp[i + 1]; ++k, ++o) K.ci[o] = P.ci[k] * d + c, K.v[o] = P.v[k];
+    }
+  return K;
 }
 
 }  // namespace nnmg

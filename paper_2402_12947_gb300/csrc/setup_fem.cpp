@@ -228,6 +228,7 @@ DofMapH build_dofmap(const MeshH& m, int degree) {
         if (m.mask.empty() || m.mask[v]) vdir[v] = 1;
       }
     }
+  dm.bfaces = bfacets;
   fac.clear();
   fac.shrink_to_fit();
   std::vector<int64_t> facets_kept;  // vertex tuples of boundary facets
@@ -550,6 +551,168 @@ void local_patches(const MeshH& m, const DofMapH& dm, const std::vector<double>&
     dofs.insert(dofs.end(), g.begin(), g.end());
     ptr.push_back((int32_t)dofs.size());
   }
+}
+
+
+Csr assemble_elasticity(const MeshH& m, const DofMapH& dm, double mu, double lam) {
+  const int d = m.dim, d1 = d + 1, nloc = dm.nloc;
+  std::vector<int64_t> dstart(dm.ndofs + 1, 0);
+  for (int64_t k = 0; k < m.nc * nloc; ++k) dstart[dm.cell_dofs[k] + 1]++;
+  for (int64_t i = 0; i < dm.ndofs; ++i) dstart[i + 1] += dstart[i];
+  std::vector<int64_t> dcells(dstart[dm.ndofs]), fill(dstart.begin(), dstart.end() - 1);
+  std::vector<int8_t> dlocal(dstart[dm.ndofs]);
+  for (int64_t c = 0; c < m.nc; ++c)
+    for (int a = 0; a < nloc; ++a) {
+      int64_t g = dm.cell_dofs[c * nloc + a];
+      dlocal[fill[g]] = (int8_t)a;
+      dcells[fill[g]++] = c;
+    }
+  for (int64_t c = 0; c < m.nc; ++c) {
+    double G[12], vol;
+    if (!cell_geometry(m, c, G, &vol) || !(vol > 0))
+      throw Error(MG_ERR_DEGENERATE_CELL, "cell " + std::to_string(c) + " has zero volume");
+  }
+  // scalar row patterns (free nodes sharing a cell), then d rows of d * len entries each
+  const int64_t nf = dm.nfree;
+  std::vector<std::vector<int32_t>> pat(nf);
+  parallel_for(nf, [&](int64_t lo, int64_t hi) {
+    for (int64_t i = lo; i < hi; ++i) {
+      int64_t g = dm.free_list[i];
+      std::vector<int32_t>& buf = pat[i];
+      for (int64_t k = dstart[g]; k < dstart[g + 1]; ++k) {
+        int64_t c = dcells[k];
+        for (int b = 0; b < nloc; ++b) {
+          int64_t fj = dm.free_index[dm.cell_dofs[c * nloc + b]];
+          if (fj >= 0) buf.push_back((int32_t)fj);
+        }
+      }
+      std::sort(buf.begin(), buf.end());
+      buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
+    }
+  });
+  Csr A;
+  A.nrows = A.ncols = nf * d;
+  if (A.nrows > INT32_MAX) throw Error(MG_ERR_INVALID_ARG, "too many vector DoFs");
+  A.rp.assign(A.nrows + 1, 0);
+  for (int64_t i = 0; i < nf; ++i)
+    for (int c = 0; c < d; ++c) {
+      const int64_t r = i * d + c;
+      if ((int64_t)A.rp[r] + (int64_t)pat[i].size() * d > INT32_MAX) throw Error(MG_ERR_INVALID_ARG, "nnz exceeds 2^31");
+      A.rp[r + 1] = A.rp[r] + (int32_t)pat[i].size() * d;
+    }
+  A.ci.resize(A.rp[A.nrows]);
+  A.v.assign(A.rp[A.nrows], 0.0);
+  GradTerm terms[10];
+  for (int a = 0; a < nloc; ++a) terms[a] = basis_term(dm.degree, d, a);
+  parallel_for(nf, [&](int64_t lo, int64_t hi) {
+    for (int64_t i = lo; i < hi; ++i) {
+      const std::vector<int32_t>& cols = pat[i];
+      const int64_t len = (int64_t)cols.size();
+      for (int c = 0; c < d; ++c) {
+        int32_t* rc = &A.ci[A.rp[i * d + c]];
+        for (int64_t q = 0; q < len; ++q)
+          for (int e = 0; e < d; ++e) rc[q * d + e] = cols[q] * d + e;
+      }
+      const int64_t g = dm.free_list[i];
+      for (int64_t k = dstart[g]; k < dstart[g + 1]; ++k) {
+        const int64_t cell = dcells[k];
+        const int a = dlocal[k];
+        double G[12], vol;
+        cell_geometry(m, cell, G, &vol);
+        for (int b = 0; b < nloc; ++b) {
+          const int64_t fj = dm.free_index[dm.cell_dofs[cell * nloc + b]];
+          if (fj < 0) continue;
+          // M[r][s] = int d_r phi_a d_s phi_b / |K|
+          double M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+          for (int s1 = 0; s1 < terms[a].nterms; ++s1)
+            for (int t1 = 0; t1 < terms[b].nterms; ++t1) {
+              const double w = affine_product_mean(terms[a].f[s1], terms[b].f[t1], d);
+              const double* ga = &G[terms[a].p[s1] * d];
+              const double* gb = &G[terms[b].p[t1] * d];
+              for (int r = 0; r < d; ++r)
+                for (int s2 = 0; s2 < d; ++s2) M[r][s2] += w * ga[r] * gb[s2];
+            }
+          double S = 0;
+          for (int r = 0; r < d; ++r) S += M[r][r];
+          const int64_t pos = std::lower_bound(cols.begin(), cols.end(), (int32_t)fj) - cols.begin();
+          for (int ci = 0; ci < d; ++ci) {
+            double* rv = &A.v[A.rp[i * d + ci] + pos * d];
+            for (int cj = 0; cj < d; ++cj)
+              rv[cj] += vol * ((ci == cj ? mu * S : 0.0) + mu * M[cj][ci] + lam * M[ci][cj]);
+          }
+        }
+      }
+    }
+  });
+  (void)d1;
+  return A;
+}
+
+BoundaryFaces boundary_faces(const MeshH& m, const DofMapH& dm) {
+  BoundaryFaces bf;
+  const int d = m.dim, d1 = d + 1;
+  bf.dim = d;
+  bf.degree = dm.degree;
+  const int ne = dm.degree == 2 ? (d == 2 ? 1 : 3) : 0;
+  bf.nfloc = d + ne;
+  const int64_t nf = (int64_t)dm.bfaces.size();
+  bf.x.resize(nf * d * d);
+  bf.dofs.resize(nf * bf.nfloc);
+  for (int64_t f = 0; f < nf; ++f) {
+    const int64_t c = dm.bfaces[f] / d1;
+    const int opp = (int)(dm.bfaces[f] % d1);
+    int k = 0;
+    for (int j = 0; j < d1; ++j) {
+      if (j == opp) continue;
+      const int64_t v = m.c[c * d1 + j];
+      for (int r = 0; r < d; ++r) bf.x[(f * d + k) * d + r] = m.x[v * d + r];
+      bf.dofs[f * bf.nfloc + k] = dm.free_index[dm.cell_dofs[c * dm.nloc + j]];
+      ++k;
+    }
+    if (ne) {
+      const int (*le)[2] = local_edges(d);
+      for (int e = 0; e < num_local_edges(d); ++e)
+        if (le[e][0] != opp && le[e][1] != opp)
+          bf.dofs[f * bf.nfloc + k++] = dm.free_index[dm.cell_dofs[c * dm.nloc + d1 + e]];
+    }
+  }
+  return bf;
+}
+
+std::vector<double> traction_load(const BoundaryFaces& bf, int axis, double value, double tol, const double* t,
+                                  int64_t nfree) {
+  const int d = bf.dim;
+  std::vector<double> b(nfree * d, 0.0);
+  const int64_t nf = bf.nfloc ? (int64_t)bf.dofs.size() / bf.nfloc : 0;
+  for (int64_t f = 0; f < nf; ++f) {
+    const double* X = &bf.x[f * d * d];
+    bool on = true;
+    for (int k = 0; k < d; ++k) on = on && std::fabs(X[k * d + axis] - value) <= tol;
+    if (!on) continue;
+    // facet measure: segment length (2D) or triangle area (3D)
+    double area;
+    if (d == 2) {
+      area = std::hypot(X[2] - X[0], X[3] - X[1]);
+    } else {
+      double u[3], w[3];
+      for (int r = 0; r < 3; ++r) u[r] = X[3 + r] - X[r], w[r] = X[6 + r] - X[r];
+      const double cx = u[1] * w[2] - u[2] * w[1], cy = u[2] * w[0] - u[0] * w[2], cz = u[0] * w[1] - u[1] * w[0];
+      area = 0.5 * std::sqrt(cx * cx + cy * cy + cz * cz);
+    }
+    // int_F phi: P1 |F|/d per vertex; P2 segment |F|/6 (vertex), 2|F|/3 (midpoint);
+    // P2 triangle 0 (vertex), |F|/3 (edge)
+    double wv, we = 0.0;
+    if (bf.degree == 1) wv = area / d;
+    else if (d == 2) wv = area / 6.0, we = 2.0 * area / 3.0;
+    else wv = 0.0, we = area / 3.0;
+    for (int k = 0; k < bf.nfloc; ++k) {
+      const int64_t g = bf.dofs[f * bf.nfloc + k];
+      if (g < 0) continue;
+      const double w = k < d ? wv : we;
+      for (int c = 0; c < d; ++c) b[g * d + c] += t[c] * w;
+    }
+  }
+  return b;
 }
 
 }  // namespace nnmg

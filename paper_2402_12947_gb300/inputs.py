@@ -32,7 +32,7 @@ import numpy as np
 
 __all__ = [
     "Mesh", "structured_mesh", "jitter_mesh", "degrade_mesh", "signed_volumes",
-    "hierarchy_meshes", "config_c1", "config_c2", "config_c3", "config_c4",
+    "hierarchy_meshes", "config_c1", "config_c2", "config_c3", "config_c4", "lattice_mesh", "config_lattice",
     "serving_request", "uniform_rhs", "CONFIGS",
 ]
 
@@ -42,8 +42,9 @@ class Mesh:
     """A simplicial mesh: ``coords`` [nv, dim] float64 and ``cells`` [nc, dim+1] int32."""
     coords: np.ndarray
     cells: np.ndarray
-    n: int = 0                      # grid squares/cubes per side
+    n: int = 0                      # grid squares/cubes per unit length
     moves: list = field(default_factory=list)   # (vertex, kind, dist/h) per degrading move
+    boundary: np.ndarray | None = None  # [nv] bool boundary vertices (None: unit square/cube)
 
     @property
     def dim(self) -> int:
@@ -101,7 +102,10 @@ def structured_mesh(dim: int, n: int) -> Mesh:
 
 
 def boundary_vertices(mesh: Mesh) -> np.ndarray:
-    """Vertices on the boundary of the unit square/cube (exact grid coordinates)."""
+    """Vertices on the boundary of the unit square/cube (exact grid coordinates), or the
+    mesh's own boundary mask when it has one."""
+    if mesh.boundary is not None:
+        return mesh.boundary
     n = mesh.n
     idx = np.rint(mesh.coords * n).astype(np.int64)
     return np.any((idx == 0) | (idx == n), axis=1)
@@ -126,7 +130,7 @@ def jitter_mesh(mesh: Mesh, amp: float, rng: np.random.Generator) -> Mesh:
             break
         reset = np.unique(mesh.cells[bad].ravel())
         new[reset] = mesh.coords[reset]
-    return Mesh(coords=new, cells=mesh.cells, n=mesh.n)
+    return Mesh(coords=new, cells=mesh.cells, n=mesh.n, boundary=mesh.boundary)
 
 
 def _vertex_star(cells: np.ndarray, nv: int):
@@ -161,6 +165,8 @@ def degrade_mesh(mesh: Mesh, rng: np.random.Generator, n_clusters: int,
     interior = np.flatnonzero(~bnd)
     h = mesh.h
     moves = []
+    if len(interior) == 0:
+        n_clusters = 0
     for c in range(n_clusters):
         if center is not None and c == 0:
             ctr = int(center)
@@ -216,7 +222,7 @@ def degrade_mesh(mesh: Mesh, rng: np.random.Generator, n_clusters: int,
                     made += 1
                     break
                 coords[v] = old
-    return Mesh(coords=coords, cells=cells, n=mesh.n, moves=moves)
+    return Mesh(coords=coords, cells=cells, n=mesh.n, moves=moves, boundary=mesh.boundary)
 
 
 def hierarchy_meshes(dim: int, n_fine: int, levels: int, amp: float, seed: int,
@@ -275,6 +281,50 @@ def config_c4(n_fine: int = 64, levels: int = 4, seed: int = 4, n_clusters: int 
     return hierarchy_meshes(3, n_fine, levels, 0.15, seed, cluster_levels=cluster_levels,
                             n_clusters=n_clusters, moves_per_cluster=moves_per_cluster,
                             kinds=("cap",), eps=1e-3, rings=2)
+
+
+def lattice_mesh(n: int, size: float = 6.0, bar: float = 1.0) -> Mesh:
+    """The truss-like lattice of Sec. 6.3: the cube [0, size]^3 minus three orthogonal square
+    channels [bar, size - bar]^2 through it (a cube frame of 12 bars of cross-section
+    bar x bar), meshed by 6 Kuhn tetrahedra per grid cube of side 1/n; unused vertices are
+    dropped (order kept) and the boundary mask marks the vertices of boundary facets."""
+    N = int(round(size * n))
+    m = structured_mesh(3, N)
+    coords = m.coords * size
+    cen = coords[m.cells].mean(axis=1)
+    inside = (cen > bar) & (cen < size - bar)
+    keep = inside.sum(axis=1) < 2
+    cells = m.cells[keep]
+    used = np.zeros(m.nv, dtype=bool)
+    used[cells.ravel()] = True
+    new_id = -np.ones(m.nv, dtype=np.int64)
+    new_id[used] = np.arange(int(used.sum()))
+    cells = new_id[cells].astype(np.int32)
+    coords = coords[used]
+    facets = np.sort(np.concatenate([np.delete(cells, i, axis=1) for i in range(4)], axis=0), axis=1)
+    uniq, cnt = np.unique(facets, axis=0, return_counts=True)
+    bnd = np.zeros(coords.shape[0], dtype=bool)
+    bnd[uniq[cnt == 1].ravel()] = True
+    return Mesh(coords=coords, cells=cells, n=n, boundary=bnd)
+
+
+def config_lattice(ns=(13, 6, 3, 2), seed: int = 5, n_clusters: int = 16, cluster_levels=None,
+                   eps: float = 1e-4, amp: float = 0.15):
+    """Elasticity workload of Sec. 6.3 (four levels of the lattice, generated independently):
+    interior vertices jittered U(+-amp h); ``n_clusters`` sliver clusters (1-3 cap moves at
+    eps h) on each level in ``cluster_levels`` (default all: Case A; all but the finest:
+    Case B). Returns (meshes, Dirichlet vertex masks: the clamped face x = 0)."""
+    if cluster_levels is None:
+        cluster_levels = tuple(range(len(ns)))
+    meshes, masks = [], []
+    for lvl, n in enumerate(ns):
+        rng = np.random.default_rng([seed, lvl])
+        m = jitter_mesh(lattice_mesh(n), amp, rng)
+        if lvl in cluster_levels and n_clusters > 0:
+            m = degrade_mesh(m, rng, n_clusters, moves_per_cluster=(1, 3), kinds=("cap",), eps=eps)
+        meshes.append(m)
+        masks.append(np.abs(m.coords[:, 0]) <= 1e-12)
+    return meshes, masks
 
 
 def serving_request(rng: np.random.Generator, seed: int):

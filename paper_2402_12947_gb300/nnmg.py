@@ -19,6 +19,7 @@ OK, ERR_INVALID_ARG, ERR_DEGENERATE_CELL, ERR_POINT_LOCATION, ERR_NOT_SPD = 0, 1
 ERR_NO_CONVERGENCE, ERR_BREAKDOWN, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NO_DEVICE = 5, 6, 7, 8, 9, 10
 SMOOTHER = {"sandwich": 0, "global_then_local": 1, "global": 2}
 GLOBAL_SMOOTHER = {"chebyshev": 0, "sgs": 1}
+PDE = {"poisson": 0, "elasticity": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 
 
@@ -40,7 +41,8 @@ class MgOptions(C.Structure):
                 ("lmax_safety", C.c_double), ("eig_tol", C.c_double), ("lambda_override", C.c_void_p),
                 ("use_graph", C.c_int32), ("local_levels_mask", C.c_int32), ("quality_threshold", C.c_double),
                 ("sell_sigma", C.c_int32), ("reorder", C.c_int32), ("global_smoother", C.c_int32),
-                ("reserved", C.c_int32 * 3)]
+                ("pde", C.c_int32), ("young", C.c_double), ("poisson_ratio", C.c_double),
+                ("reserved", C.c_int32 * 4)]
 
 
 class MgSolveInfo(C.Structure):
@@ -103,6 +105,7 @@ _SIGS = {
     "mg_dof_coords": (C.c_int, [_P, C.c_int32, _P]),
     "mg_cell_quality": (C.c_int, [_P, C.c_int32, _P]),
     "mg_load_constant": (C.c_int, [_P, C.c_double, _P]),
+    "mg_load_traction": (C.c_int, [_P, C.c_int32, C.c_double, _P, _P]),
     "mg_vcycle": (C.c_int, [_P, _P, _P, _P]),
     "mg_solve": (C.c_int, [_P, _P, _P, C.c_double, C.c_int32, C.POINTER(MgSolveInfo), _P]),
     "mg_solve_host": (C.c_int, [_P, _P, _P, C.c_double, C.c_int32, C.POINTER(MgSolveInfo), _P]),
@@ -167,6 +170,8 @@ def default_options(**kw) -> MgOptions:
             v = PRECISION[v]
         if k == "global_smoother" and isinstance(v, str):
             v = GLOBAL_SMOOTHER[v]
+        if k == "pde" and isinstance(v, str):
+            v = PDE[v]
         if k == "lambda_override":
             continue
         setattr(o, k, v)
@@ -342,6 +347,12 @@ class Hierarchy:
     def load_constant(self, f: float = 1.0):
         out = np.zeros(self.num_dofs(0))
         _check(lib.mg_load_constant(self._h, f, out.ctypes.data), self._h)
+        return out
+
+    def load_traction(self, axis: int, value: float, t):
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        out = np.zeros(self.num_dofs(0))
+        _check(lib.mg_load_traction(self._h, axis, value, t.ctypes.data, out.ctypes.data), self._h)
         return out
 
     def device_bytes(self) -> int:

@@ -1,0 +1,90 @@
+"""GPU parity of the linear elasticity path (Sec. 6.3): vector P1/P2 on the clamped lattice
+with sliver clusters, Chebyshev and multicolour SGS global smoothers (two applications per
+side, as in the paper's elasticity runs), against the oracle."""
+import numpy as np
+import pytest
+
+from _util import TOL64, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import elasticity, hierarchy, mg  # noqa: E402
+from paper_2402_12947_gb300 import inputs  # noqa: E402
+
+CASES = {"p1": ((4, 2, 1), 1), "p2": ((2, 1), 2)}
+_cache = {}
+
+
+@pytest.fixture(scope="module")
+def nnmg():
+    from paper_2402_12947_gb300 import build
+    build.build()
+    from paper_2402_12947_gb300 import nnmg as mod
+    assert torch.cuda.is_available()
+    return mod
+
+
+def lattice(name, kind):
+    key = (name, kind)
+    if key not in _cache:
+        ns, degree = CASES[name]
+        ms, masks = inputs.config_lattice(ns=ns, n_clusters=3)
+        Ho = hierarchy.build(ms, degree, pde="elasticity", dirichlet_masks=masks, smoother_kind=kind, nu=2)
+        _cache[key] = (ms, masks, degree, Ho)
+    return _cache[key]
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def traction(ms, Ho):
+    lo = Ho.levels[0]
+    b = elasticity.traction_load_full(ms[0].coords, ms[0].cells, lo.dm, [1e3, 0, 0], 0, 6.0)
+    return b[elasticity.free_vector_dofs(lo.dm)]
+
+
+def make(nnmg, ms, masks, degree, Ho, kind, **kw):
+    opts = dict(pde="elasticity", dirichlet_masks=masks, global_smoother=kind, nu=2, **kw)
+    if kind == "chebyshev":
+        opts["lambda_override"] = [lv.lmax for lv in Ho.levels[:-1]]
+    return nnmg.Hierarchy.from_meshes(ms, degree, 0.1, **opts)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("kind", ["chebyshev", "sgs"])
+def test_vcycle_and_pcg(nnmg, name, kind):
+    ms, masks, degree, Ho = lattice(name, kind)
+    n = Ho.levels[0].n
+    rng = np.random.default_rng(7)
+    b, x0 = rng.uniform(-1, 1, n), rng.uniform(-1, 1, n)
+    with make(nnmg, ms, masks, degree, Ho, kind) as H:
+        x = dev(x0)
+        H.vcycle(dev(b), x)
+        assert rel_err(host(x), mg.vcycle(Ho, b, x0)) < TOL64
+        bt = traction(ms, Ho)
+        assert rel_err(H.load_traction(0, 6.0, [1e3, 0, 0]), bt) < 1e-13
+        xr, itr, _, _ = mg.pcg(Ho, bt, 1e-10)
+        xs = torch.zeros(n, dtype=torch.float64, device="cuda")
+        info = H.solve(dev(bt), xs, rtol=1e-10, maxit=300)
+        assert info["converged"] and info["iterations"] == itr, (info, itr)
+        assert rel_err(host(xs), xr) < 1e-8
+
+
+@pytest.mark.parametrize("kind", ["chebyshev", "sgs"])
+def test_mixed_precision(nnmg, kind):
+    ms, masks, degree, Ho = lattice("p1", kind)
+    bt = traction(ms, Ho)
+    _, itr, _, _ = mg.pcg(Ho, bt, 1e-8)
+    with make(nnmg, ms, masks, degree, Ho, kind, precision="mixed") as H:
+        x = torch.zeros(bt.size, dtype=torch.float64, device="cuda")
+        info = H.solve(dev(bt), x, rtol=1e-8, maxit=300)
+        assert info["converged"] and info["iterations"] <= itr + 1, (info, itr)
+        xh = host(x)
+        assert np.linalg.norm(bt - Ho.levels[0].A @ xh) < 1.5e-8 * np.linalg.norm(bt)

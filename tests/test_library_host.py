@@ -165,3 +165,59 @@ def test_host_colouring_matches_oracle(nnmg, name):
     with nnmg.Hierarchy.from_meshes(meshes, degree, 0.1, host_only=1, patch_layers=layers) as H:
         with pytest.raises(nnmg.NnmgError):
             H.export_colouring(0)
+
+
+_LATTICE = {}
+
+
+def lattice_case(ns, degree, **kw):
+    key = (ns, degree, tuple(sorted(kw.items())))
+    if key not in _LATTICE:
+        from oracle import hierarchy
+        from paper_2402_12947_gb300 import inputs
+        ms, masks = inputs.config_lattice(ns=ns, n_clusters=3)
+        Ho = hierarchy.build(ms, degree, pde="elasticity", dirichlet_masks=masks, **kw)
+        _LATTICE[key] = (ms, masks, Ho)
+    return _LATTICE[key]
+
+
+@pytest.mark.parametrize("ns,degree", [((4, 2, 1), 1), ((2, 1), 2)])
+def test_host_elasticity_setup_matches_oracle(nnmg, ns, degree):
+    """Sec. 6.3: vector operator, componentwise transfer, vector patches, lambda_max and
+    the traction load of the clamped lattice, against the oracle."""
+    from oracle import elasticity
+    ms, masks, Ho = lattice_case(ns, degree)
+    with nnmg.Hierarchy.from_meshes(ms, degree, 0.1, host_only=1, pde="elasticity", dirichlet_masks=masks) as H:
+        for l, lo in enumerate(Ho.levels):
+            n = lo.n
+            assert H.num_dofs(l) == n
+            A = to_csr(*H.export_level(l), (n, n))
+            assert abs(A - lo.A).max() <= 1e-12 * abs(lo.A).max(), l
+            pt = H.export_patches(l)
+            assert len(pt) == len(lo.patches) and all(np.array_equal(a, b) for a, b in zip(pt, lo.patches))
+            if l < Ho.L - 1:
+                P = to_csr(*H.export_transfer(l), (n, Ho.levels[l + 1].n))
+                assert np.array_equal(P.indptr, lo.P.indptr) and np.array_equal(P.indices, lo.P.indices)
+                assert np.max(np.abs(P.data - lo.P.data)) < 1e-13
+                lu, la, _ = H.eigs(l)
+                assert abs(lu - lo.lmax_unadj) < 1e-8 * lo.lmax_unadj
+                assert abs(la - lo.lmax_adj) < 1e-8 * lo.lmax_adj
+        m0, dm = ms[0], Ho.levels[0].dm
+        t = [1e3, -20.0, 5.0]
+        b = H.load_traction(0, 6.0, t)
+        bo = elasticity.traction_load_full(m0.coords, m0.cells, dm, t, 0, 6.0)[elasticity.free_vector_dofs(dm)]
+        assert rel_err(b, bo) < 1e-13
+        with pytest.raises(nnmg.NnmgError):
+            H.load_constant(1.0)
+
+
+def test_elasticity_options_validated(nnmg):
+    ms, masks, _ = lattice_case((4, 2, 1), 1)
+    for bad in (dict(poisson_ratio=0.5), dict(young=-1.0), dict(pde=7)):
+        with pytest.raises(nnmg.NnmgError):
+            nnmg.Hierarchy.from_meshes(ms, 1, 0.1, host_only=1, pde=bad.pop("pde", "elasticity"),
+                                       dirichlet_masks=masks, **bad)
+    meshes, _, degree, layers = case("c1_p1")
+    with nnmg.Hierarchy.from_meshes(meshes, degree, 0.1, host_only=1) as H:
+        with pytest.raises(nnmg.NnmgError):
+            H.load_traction(0, 1.0, [1.0, 0.0])
