@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every kernel individually instead of one CUDA graph per solve (profilers "
                          "cannot see kernel nodes of graphs with conditional nodes)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "serve", "paper"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "serve", "paper", "lattice"],
                     help="'serve': the mixed request stream through the continuous-batching server; "
                          "'paper': the Case A/B comparison and the residual history of the paper's examples")
     ap.add_argument("--reorder", default=None, choices=["none", "rcm", "spatial"],
@@ -99,7 +99,7 @@ def profiled_traffic():
     return None, None
 
 
-KERNEL_REV = "sell32-morton16-v4"   # bump when the timed kernel changes (invalidates the profiled traffic)
+KERNEL_REV = "sell32-pred-v6"   # bump when the timed kernel changes (invalidates the profiled traffic)
 
 
 class ClockSampler:
@@ -314,7 +314,7 @@ def run_ours(args):
                          f"({d['n']} DoFs, {d['levels']} levels, {d['iterations'][0]} iterations, "
                          f"{d['times'][0]:.1f} s), single-threaded NumPy/SciPy"}
     value = n * world / (ms32 * 1e-3)
-    order = args.reorder or "spatial"
+    order = args.reorder or "library"
     kernel_name = (f"fine-level multicolour SGS application, FP32 (k_gs, one launch per colour and sweep, "
                    f"autotuned layouts, {order} order)" if sgs else
                    f"fine-level fused Chebyshev SpMV, FP32 (k_cheb, autotuned layout, {order} order, 16-bit "
@@ -484,10 +484,80 @@ def run_paper(args):
     return 0
 
 
+def run_lattice(args):
+    """Sec. 6.3 elasticity comparison on the synthetic clamped lattice (four non-nested
+    levels, 1/h = 13, 6, 3, 2; E = 6.9e10, nu = 0.33; traction (1e3, 0, 0) on x = 6): MG-PCG
+    iterations to rtol 1e-8 with the multicolour SGS global smoother applied twice before
+    and after the coarse correction, for the clean reference, Case A (sliver clusters on
+    every level) and Case B (every level but the finest), without and with the local
+    correction; and the solve time and DoFs/s of the corrected Case A hierarchy (FP64 and
+    mixed precision)."""
+    import torch
+    from paper_2402_12947_gb300 import build, inputs, nnmg
+    build.build()
+    torch.cuda.set_device(0)
+    ns = (13, 6, 3, 2)
+    meshes = {"reference": inputs.config_lattice(ns=ns, n_clusters=0),
+              "A": inputs.config_lattice(ns=ns, n_clusters=16),
+              "B": inputs.config_lattice(ns=ns, n_clusters=16, cluster_levels=(1, 2, 3))}
+    out = {}
+    for degree in (1, 2):
+        row = {}
+        for name, case, opt in (("reference", "reference", {}), ("A without correction", "A", dict(smoother="global")),
+                                ("A with correction", "A", {}), ("B without correction", "B", dict(smoother="global")),
+                                ("B with correction", "B", {})):
+            ms, masks = meshes[case]
+            t0 = time.perf_counter()
+            with nnmg.Hierarchy.from_meshes(ms, degree, 0.1, pde="elasticity", dirichlet_masks=masks,
+                                            global_smoother="sgs", nu=2, **opt) as H:
+                setup = time.perf_counter() - t0
+                b = torch.from_numpy(H.load_traction(0, 6.0, [1e3, 0.0, 0.0])).cuda()
+                x = torch.zeros_like(b)
+                info = H.solve(b, x, rtol=RTOL, maxit=500, raise_on_fail=False)
+                entry = {"dofs": H.num_dofs(0), "iterations": info["iterations"], "converged": info["converged"],
+                         "true_rel_residual": info["true_rel_residual"], "setup_s": round(setup, 2)}
+                if name == "A with correction":
+                    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    for _ in range(2):
+                        x.zero_()
+                        H.solve(b, x, rtol=RTOL, maxit=500)
+                    ev0.record()
+                    for _ in range(5):
+                        x.zero_()
+                        H.solve(b, x, rtol=RTOL, maxit=500)
+                    ev1.record()
+                    torch.cuda.synchronize()
+                    ms_solve = ev0.elapsed_time(ev1) / 5
+                    entry.update(ms_per_solve=ms_solve, dofs_per_s=H.num_dofs(0) / (ms_solve * 1e-3))
+                row[name] = entry
+            if name == "A with correction":
+                with nnmg.Hierarchy.from_meshes(ms, degree, 0.1, pde="elasticity", dirichlet_masks=masks,
+                                                global_smoother="sgs", nu=2, precision="mixed") as H:
+                    x = torch.zeros_like(b)
+                    info = H.solve(b, x, rtol=RTOL, maxit=500, raise_on_fail=False)
+                    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    ev0.record()
+                    for _ in range(5):
+                        x.zero_()
+                        H.solve(b, x, rtol=RTOL, maxit=500)
+                    ev1.record()
+                    torch.cuda.synchronize()
+                    ms_solve = ev0.elapsed_time(ev1) / 5
+                    row["A with correction, mixed"] = {"iterations": info["iterations"],
+                                                       "true_rel_residual": info["true_rel_residual"],
+                                                       "ms_per_solve": ms_solve,
+                                                       "dofs_per_s": H.num_dofs(0) / (ms_solve * 1e-3)}
+        out[f"P{degree}"] = row
+    print(json.dumps({"workload": "lattice elasticity (Sec. 6.3)", "rtol": RTOL, "results": out}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.workload == "paper":
         return run_paper(args)
+    if args.workload == "lattice":
+        return run_lattice(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "serve":

@@ -144,7 +144,7 @@ typedef struct mg_options_t {
                               device for windows {1, 256, 2048} per operator, keep the fastest (0) */
   int32_t reorder;         /* enum mg_reorder: the order in which the device stores each
                               level but the coarsest (vectors at the ABI stay in the library's
-                              numbering) (SPATIAL) */
+                              numbering) (NONE) */
   int32_t global_smoother; /* enum mg_global_smoother (CHEBYSHEV) */
   int32_t pde;             /* enum mg_pde (POISSON); mg_setup only */
   double young;            /* Young's modulus E for MG_PDE_ELASTICITY (6.9e10, Sec. 6.3) */

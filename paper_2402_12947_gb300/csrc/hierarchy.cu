@@ -245,8 +245,8 @@ SellMat<T> make_layout(const Csr& A, DevMem& mem, Layout L) {
 }
 
 // Autotuner (sigma option 0): time y = A x on the device for each candidate layout
-// (SELL-32 with windows 1, 256, 2048 when sorting removes padding, each in groups of 4 and
-// of 8 entries; CSR vector with 4, 8, 16, 32 lanes per row up to twice the longest row) and
+// (SELL-32 with windows 1, 256, 2048 when sorting removes padding, each with the scalar
+// and the predicated row remainder; CSR vector with 4, 8, 16, 32 lanes per row up to twice the longest row) and
 // keep the fastest. Timing: one warm-up launch, then the mean of 5 launches between CUDA
 // events.
 template <typename T>
@@ -260,10 +260,10 @@ SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log) {
     int64_t pad = sell_padded(A, sell_order(A, c));
     if (last_pad >= 0 && pad >= (int64_t)(0.995 * (double)last_pad)) continue;  // sorting gains nothing more
     last_pad = pad;
-    cand.push_back({1, c, 4});
+    cand.push_back({1, c, 1});
   }
   for (int g : {4, 8, 16, 32})
-    if (g <= 2 * std::max(maxlen, 2)) cand.push_back({g, 1, 4});
+    if (g <= 2 * std::max(maxlen, 2)) cand.push_back({g, 1, 1});
   DevMem scratch;
   scratch.stream = mem.stream;
   const cudaStream_t st = mem.stream;
@@ -278,8 +278,8 @@ SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log) {
     DevMem trial;
     trial.stream = st;
     SellMat<T> S = make_layout<T>(A, trial, c);
-    for (int unroll : {4, 8}) {
-      if (c.lanes > 1 && unroll != 4) continue;
+    for (int unroll : {1, 2}) {
+      if (c.lanes > 1 && unroll != 1) continue;
       S.unroll = unroll;
       sell_spmv<T>(S, x, y, st);
       CK(cudaEventRecord(e0, st));
@@ -290,7 +290,7 @@ SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log) {
       CK(cudaEventElapsedTime(&ms, e0, e1));
       if (log)
         *log += std::string(" ") +
-                (c.lanes > 1 ? "v" + std::to_string(c.lanes) : "s" + std::to_string(c.sigma) + "u" + std::to_string(unroll)) +
+                (c.lanes > 1 ? "v" + std::to_string(c.lanes) : "s" + std::to_string(c.sigma) + (unroll == 2 ? "p" : "")) +
                 ":" + std::to_string((int)(ms / 5 * 1e3)) + "us";
       if (best_ms < 0 || ms < best_ms) {
         best_ms = ms;
@@ -889,7 +889,7 @@ void build_device(mg_hierarchy* h) {
       }
       auto lay = [](const SellMat<T>& M) {
         return (M.lanes > 1 ? "v" + std::to_string(M.lanes)
-                            : "s" + std::to_string(M.sigma) + "u" + std::to_string(M.unroll)) +
+                            : "s" + std::to_string(M.sigma) + (M.unroll == 2 ? "p" : "")) +
                (M.col16 ? (M.col ? "/16+32" : "/16") : "/32");
       };
       tm.mark("upload L" + std::to_string(l) + " A/P/R " + lay(D.A) + "/" + lay(D.P) + "/" + lay(D.R) + " |" + tlog);
@@ -1204,7 +1204,7 @@ void mg_default_options(mg_options_t* o) {
   o->local_levels_mask = -1;
   o->quality_threshold = 0.1;
   o->sell_sigma = 0;
-  o->reorder = MG_REORDER_SPATIAL;
+  o->reorder = MG_REORDER_NONE;
   o->pde = MG_PDE_POISSON;
   o->young = 6.9e10;
   o->poisson_ratio = 0.33;

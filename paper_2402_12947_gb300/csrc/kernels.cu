@@ -67,41 +67,62 @@ struct Col32 {
   __device__ __forceinline__ int operator()(int64_t k) const { return ld_stream(c + k); }
 };
 
-// Sum over the w padded entries of one SELL-32 lane starting at element k (stride 32), in
-// groups of U entries: a group's value and index loads are issued together, then its x
-// gathers, then its FMAs (in entry order), so a row costs about two dependent memory
-// round trips per group; the last group is predicated rather than run entry by entry.
-template <typename T, int U, typename C>
+// Sum over the w padded entries of one SELL-32 lane starting at element k (stride 32).
+// PRED = false: four entries per step (their value and index loads together, then the x
+// gathers, then the FMAs), the remaining w % 4 entries one at a time. PRED = true: every
+// step takes four entries, the last one predicated. Both perform the same FMAs in the same
+// order (identical results); which is faster depends on the operator and precision.
+template <typename T, bool PRED, typename C>
 __device__ __forceinline__ T sell_lane(const T* __restrict__ vp, int64_t k, int w, C col, const T* __restrict__ x) {
   T acc = T(0);
-  for (int j = 0; j < w; j += U) {
-    T v[U], xv[U];
-    int c[U];
+  if constexpr (!PRED) {
+    int j = 0;
+    for (; j + 4 <= w; j += 4) {
+      const T v0 = ld_stream(vp), v1 = ld_stream(vp + 32), v2 = ld_stream(vp + 64), v3 = ld_stream(vp + 96);
+      const int c0 = col(k), c1 = col(k + 32), c2 = col(k + 64), c3 = col(k + 96);
+      const T x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2), x3 = __ldg(x + c3);
+      acc = fma(v0, x0, acc);
+      acc = fma(v1, x1, acc);
+      acc = fma(v2, x2, acc);
+      acc = fma(v3, x3, acc);
+      vp += 128;
+      k += 128;
+    }
+    for (; j < w; ++j) {
+      acc = fma(ld_stream(vp), __ldg(x + col(k)), acc);
+      vp += 32;
+      k += 32;
+    }
+  } else {
+    for (int j = 0; j < w; j += 4) {
+      T v[4], xv[4];
+      int c[4];
 #pragma unroll
-    for (int u = 0; u < U; ++u) v[u] = j + u < w ? ld_stream(vp + 32 * u) : T(0);
+      for (int u = 0; u < 4; ++u) v[u] = j + u < w ? ld_stream(vp + 32 * u) : T(0);
 #pragma unroll
-    for (int u = 0; u < U; ++u) c[u] = j + u < w ? col(k + 32 * u) : 0;
+      for (int u = 0; u < 4; ++u) c[u] = j + u < w ? col(k + 32 * u) : 0;
 #pragma unroll
-    for (int u = 0; u < U; ++u) xv[u] = j + u < w ? __ldg(x + c[u]) : T(0);
+      for (int u = 0; u < 4; ++u) xv[u] = j + u < w ? __ldg(x + c[u]) : T(0);
 #pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (j + u < w) acc = fma(v[u], xv[u], acc);
-    vp += 32 * U;
-    k += 32 * U;
+      for (int u = 0; u < 4; ++u)
+        if (j + u < w) acc = fma(v[u], xv[u], acc);
+      vp += 128;
+      k += 128;
+    }
   }
   return acc;
 }
 
-template <typename T, bool C16, int U>
+template <typename T, bool C16, bool PRED>
 __device__ __forceinline__ T sell_row(const OpView<T>& m, const T* __restrict__ x, int srow) {
   const int s = srow >> 5, lane = srow & 31;
   const int64_t o = m.off[s];
   const int w = (int)((m.off[s + 1] - o) >> 5);
   if constexpr (C16) {
     const int base = m.cbase[s];   // uniform across the warp (one slice per warp)
-    if (base >= 0) return sell_lane<T, U>(m.val + o + lane, o + lane, w, Col16{m.col16, base}, x);
+    if (base >= 0) return sell_lane<T, PRED>(m.val + o + lane, o + lane, w, Col16{m.col16, base}, x);
   }
-  return sell_lane<T, U>(m.val + o + lane, o + lane, w, Col32{m.col}, x);
+  return sell_lane<T, PRED>(m.val + o + lane, o + lane, w, Col32{m.col}, x);
 }
 
 // CSR-vector partial sum of one lane of a G-lane group over row entries [k, k1), four
@@ -125,8 +146,8 @@ __device__ __forceinline__ T csrv_lane(const T* __restrict__ val, int k, int k1,
   return a;
 }
 
-// Kernel layout parameter G: 1 = SELL-32 in groups of 4 entries, 2 = SELL-32 in groups of
-// 8, G >= 4 = CSR vector with G lanes per row.
+// Kernel layout parameter G: 1 = SELL-32 (steps of four, scalar remainder), 2 = SELL-32
+// (predicated steps of four), G >= 4 = CSR vector with G lanes per row.
 template <int G>
 __host__ __device__ constexpr bool is_sell() {
   return G <= 2;
@@ -141,7 +162,7 @@ __device__ __forceinline__ bool op_row(const OpView<T>& m, const T* __restrict__
   if constexpr (is_sell<G>()) {
     if (tid >= m.nrows) return false;
     row = m.perm ? m.perm[tid] : tid;
-    acc = sell_row<T, C16, G == 2 ? 8 : 4>(m, x, tid);
+    acc = sell_row<T, C16, G == 2>(m, x, tid);
     return true;
   } else {
     const int slot = tid / G, lane = tid & (G - 1);
@@ -319,10 +340,11 @@ __global__ void __launch_bounds__(kBlock) k_patch_residual(int nt, int w, const 
   if (lane == 0) rbuf[t] = bt - s;
 }
 
-// S_c phase 2: e = (A^[d])^{-1} r_B and x_B += e. A work item is 32 consecutive rows of one
-// patch; each warp computes 4 of them, reading row i of the symmetric inverse contiguously.
-// Every load that does not depend on r_B (the item, the output rows' DoF ids and current
-// values) is issued before the block barrier, so a launch costs about three dependent
+// S_c phase 2: e = (A^[d])^{-1} r_B and x_B += e. A work item is kPatchRowsPerItem (8)
+// consecutive rows of one patch, one warp per row; lane l accumulates entries l, l + 32,
+// ... of row i of the symmetric inverse (contiguous), then the warp sums. Every load that
+// does not need r_B (the row's DoF id and current value, its first 256 inverse entries) is
+// issued before the block barrier, so a patch of up to 256 DoFs costs about two dependent
 // memory round trips. With rbuf == nullptr the iterate is zero and the residual is b.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_patch_solve(const PatchItem* __restrict__ items,
@@ -330,43 +352,28 @@ __global__ void __launch_bounds__(kBlock) k_patch_solve(const PatchItem* __restr
                                                         const double* __restrict__ inv, const double* rbuf,
                                                         const T* __restrict__ b, T* __restrict__ x) {
   extern __shared__ double rs[];
+  constexpr int K = 8;  // inverse entries per lane loaded ahead of the barrier (256 per row)
   const PatchItem it = items[blockIdx.x];
   const int p0 = it.p0, n = it.n;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int R = kPatchRowsPerItem / 8;  // rows per warp, accumulated together
-  const int i0 = it.row0 + warp * R;
-  int g[R];
-  T xg[R];
+  const int i = it.row0 + warp;
+  const bool ok = i < n;
+  const double* Xi = inv + it.inv + (int64_t)(ok ? i : 0) * n;
+  const int g = ok ? pdofs[p0 + i] : 0;
+  const T xg = ok ? x[g] : T(0);
+  double xr[K];
 #pragma unroll
-  for (int q = 0; q < R; ++q) g[q] = i0 + q < n ? pdofs[p0 + i0 + q] : -1;
-#pragma unroll
-  for (int q = 0; q < R; ++q) xg[q] = g[q] >= 0 ? x[g[q]] : T(0);
+  for (int u = 0; u < K; ++u) xr[u] = ok && lane + 32 * u < n ? Xi[lane + 32 * u] : 0.0;
   for (int j = threadIdx.x; j < n; j += blockDim.x) rs[j] = rbuf ? rbuf[p0 + j] : (double)b[pdofs[p0 + j]];
   __syncthreads();
-  if (i0 >= n) return;  // warp-uniform; no block barrier follows
-  const double* X = inv + it.inv;
-  const double* Xi[R];
+  if (!ok) return;  // warp-uniform; no block barrier follows
+  double e = 0.0;
 #pragma unroll
-  for (int q = 0; q < R; ++q) Xi[q] = X + (int64_t)(g[q] >= 0 ? i0 + q : i0) * n;
-  double e[R];
-#pragma unroll
-  for (int q = 0; q < R; ++q) e[q] = 0.0;
-  int j = lane;
-  for (; j + 32 < n; j += 64) {
-    const double r0 = rs[j], r1 = rs[j + 32];
-#pragma unroll
-    for (int q = 0; q < R; ++q) e[q] = fma(Xi[q][j + 32], r1, fma(Xi[q][j], r0, e[q]));
-  }
-  if (j < n) {
-    const double r0 = rs[j];
-#pragma unroll
-    for (int q = 0; q < R; ++q) e[q] = fma(Xi[q][j], r0, e[q]);
-  }
-#pragma unroll
-  for (int q = 0; q < R; ++q) {
-    const double eq = warp_sum(e[q]);
-    if (lane == 0 && g[q] >= 0) x[g[q]] = (T)((double)xg[q] + eq);
-  }
+  for (int u = 0; u < K; ++u)
+    if (lane + 32 * u < n) e = fma(xr[u], rs[lane + 32 * u], e);
+  for (int j = lane + 32 * K; j < n; j += 32) e = fma(Xi[j], rs[j], e);
+  e = warp_sum(e);
+  if (lane == 0) x[g] = (T)((double)xg + e);
 }
 
 template <typename T>
@@ -687,7 +694,7 @@ void by_layout(int lanes, int unroll, bool c16, F&& f) {
     constexpr bool C = decltype(c)::value;
     switch (lanes) {
       case 1:
-        if (unroll == 8) f(Lay<2, C>());
+        if (unroll == 2) f(Lay<2, C>());
         else f(Lay<1, C>());
         break;
       case 4: f(Lay<4, C>()); break;

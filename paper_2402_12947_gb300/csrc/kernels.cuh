@@ -25,7 +25,7 @@ struct SellMat {
   int32_t* perm = nullptr;  // [nrows] matrix row held by each slot, or null (identity)
   int32_t sigma = 1;        // window within which rows were sorted by length
   int32_t lanes = 1;        // 1: SELL-32 (off/col/val/perm); G > 1: CSR vector (rp/col/val)
-  int32_t unroll = 4;       // SELL-32: entries per lane loaded together (4 or 8)
+  int32_t unroll = 1;       // SELL-32 row loop: 1 = steps of 4 + scalar remainder, 2 = predicated steps
   int32_t* rp = nullptr;    // [nrows+1] CSR row pointer (lanes > 1)
   // 16-bit column offsets: column = cbase[slice or row] + col16[k] where cbase >= 0; a
   // slice or row spanning more than 2^16 columns has cbase = -1 and reads col (which is
@@ -52,7 +52,7 @@ struct PatchItem {
 };
 
 constexpr int kBlock = 256;
-constexpr int kPatchRowsPerItem = 32;   // rows of one patch per S_c work item (8 warps x 4)
+constexpr int kPatchRowsPerItem = 8;    // rows of one patch per S_c work item (one warp each)
 
 // ---- SELL-32 SpMV family ----
 template <typename T> void sell_spmv(const SellMat<T>& A, const T* x, T* y, cudaStream_t s);
