@@ -69,10 +69,8 @@ def parse():
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_2402_12947_gb300 import replicas
+    return replicas.dist_env()
 
 
 def measured_peak():
@@ -211,18 +209,18 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    from paper_2402_12947_gb300 import build, inputs, nnmg
+    from paper_2402_12947_gb300 import build, inputs, nnmg, replicas
     build.build()
 
     workload, degree = WORKLOADS[args.workload]
     if args.global_smoother == "sgs":
         workload = workload.replace("Chebyshev(2)", "multicolour SGS")
     if args.workload == "c2":
-        meshes = inputs.config_c2(n_fine=args.n_fine, levels=args.levels, seed=2 + 1000 * rank)
+        meshes = inputs.config_c2(n_fine=args.n_fine, levels=args.levels, seed=replicas.mesh_seed(2, rank))
     elif args.workload == "c3":
-        meshes = inputs.config_c3(seed=3 + 1000 * rank)
+        meshes = inputs.config_c3(seed=replicas.mesh_seed(3, rank))
     else:
-        meshes = inputs.config_c4(seed=4 + 1000 * rank)
+        meshes = inputs.config_c4(seed=replicas.mesh_seed(4, rank))
     both = args.precision == "both"
     t0 = time.perf_counter()
     graph = 0 if args.no_graph else 1
@@ -237,16 +235,12 @@ def run_ours(args):
     H32 = nnmg.Hierarchy.from_meshes(meshes, degree, 0.1, precision="mixed", lambda_override=lam, **opts)
     setup32 = time.perf_counter() - t0
     n = H32.num_dofs(0)
-    b_host = inputs.uniform_rhs(n, 2 + rank)
+    b_host = inputs.uniform_rhs(n, replicas.rhs_seed(2, rank))
     b = torch.from_numpy(b_host).cuda()
     x = torch.zeros_like(b)
     stream = torch.cuda.current_stream()
 
-    def barrier():
-        torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-            torch.cuda.synchronize()
+    barrier = replicas.barrier
 
     def timed(H, steps, warmup):
         for _ in range(warmup):
@@ -274,10 +268,7 @@ def run_ours(args):
     ms32, lat32, info32 = timed(H32, args.steps, max(3, args.warmup))
     clk = clocks.stop()
     ms64, lat64, info64 = timed(H64, args.steps, max(3, args.warmup)) if both else (float("nan"), [float("nan")], {})
-    ms_t = torch.tensor([ms32, ms64], device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms32, ms64 = float(ms_t[0]), float(ms_t[1])
+    ms32, ms64 = replicas.max_over_ranks([ms32, ms64], device="cuda")
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     pin_b = torch.from_numpy(b_host).pin_memory()
@@ -289,10 +280,7 @@ def run_ours(args):
         H32.solve_host(pin_b.numpy(), rtol=RTOL, out=pin_x.numpy())
     barrier()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-    e2e_t = torch.tensor([e2e_ms], device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
-    e2e_ms = float(e2e_t[0])
+    e2e_ms = replicas.max_over_ranks([e2e_ms], device="cuda")[0]
 
     # the dominant kernel: fine-level fused Chebyshev SpMV of the FP32 V-cycle
     kms, kbytes = H32.time_smoother_kernel(reps=50)
@@ -313,7 +301,7 @@ def run_ours(args):
                "sample": f"oracle MG-PCG solve (setup excluded) on the same family at {SAMPLE_N}^2 "
                          f"({d['n']} DoFs, {d['levels']} levels, {d['iterations'][0]} iterations, "
                          f"{d['times'][0]:.1f} s), single-threaded NumPy/SciPy"}
-    value = n * world / (ms32 * 1e-3)
+    value = replicas.job_throughput(n, world, ms32)
     order = args.reorder or "library"
     kernel_name = (f"fine-level multicolour SGS application, FP32 (k_gs, one launch per colour and sweep, "
                    f"autotuned layouts, {order} order)" if sgs else
@@ -331,11 +319,11 @@ def run_ours(args):
                    "internal_order": order},
         "iterations": {"mixed": info32["iterations"], "fp64": info64.get("iterations")},
         "p50_ms": lat32[len(lat32) // 2], "p99_ms": lat32[min(len(lat32) - 1, int(0.99 * len(lat32)))],
-        "fp64": {"value": n * world / (ms64 * 1e-3), "ms_per_step": ms64, "iterations": info64.get("iterations"),
+        "fp64": {"value": replicas.job_throughput(n, world, ms64), "ms_per_step": ms64, "iterations": info64.get("iterations"),
                  "p50_ms": lat64[len(lat64) // 2], "p99_ms": lat64[min(len(lat64) - 1, int(0.99 * len(lat64)))],
                  "true_rel_residual": info64.get("true_rel_residual")} if both else None,
         "true_rel_residual": info32["true_rel_residual"],
-        "e2e": {"value": n * world / (e2e_ms * 1e-3), "unit": "DoFs/s", "h2d_bytes_per_step": 8 * n,
+        "e2e": {"value": replicas.job_throughput(n, world, e2e_ms), "unit": "DoFs/s", "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 8 * n},
         "gpu_launches": launches * args.steps,
         "roofline": {"bound": "hbm", "achieved": kbytes / (kms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
