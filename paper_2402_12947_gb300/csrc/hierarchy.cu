@@ -103,13 +103,15 @@ std::vector<int32_t> sell_order(const Csr& A, int sigma) {
   return ord;
 }
 
-// Padded entries of the SELL-32 layout for a slot order.
-int64_t sell_padded(const Csr& A, const std::vector<int32_t>& ord) {
+// Padded entries of the SELL layout with `sub` lanes per row (slices of 32/sub rows, each
+// padded to its longest row rounded up to a multiple of sub) for a slot order.
+int64_t sell_padded(const Csr& A, const std::vector<int32_t>& ord, int sub = 1) {
+  const int R = 32 / sub;
   int64_t tot = 0;
-  for (int64_t s0 = 0; s0 < A.nrows; s0 += 32) {
+  for (int64_t s0 = 0; s0 < A.nrows; s0 += R) {
     int32_t w = 0;
-    for (int64_t k = s0; k < std::min<int64_t>(A.nrows, s0 + 32); ++k) w = std::max(w, A.rp[ord[k] + 1] - A.rp[ord[k]]);
-    tot += 32 * (int64_t)w;
+    for (int64_t k = s0; k < std::min<int64_t>(A.nrows, s0 + R); ++k) w = std::max(w, A.rp[ord[k] + 1] - A.rp[ord[k]]);
+    tot += 32 * (int64_t)((w + sub - 1) / sub);
   }
   return tot;
 }
@@ -143,42 +145,46 @@ void set_indices(SellMat<T>& S, DevMem& mem, const std::vector<int32_t>& col, st
   S.idx_bytes = 2.0 * (double)narrow_nnz + 4.0 * (double)(nnz - narrow_nnz);
 }
 
-// Host CSR -> device SELL-32 (values converted to T), slots in the order of sell_order.
+// Host CSR -> device SELL (values converted to T), slots in the order of sell_order. With
+// sub lanes per row a slice holds 32/sub rows and entry j of its row r sits at step j/sub,
+// lane r*sub + j%sub; padding has value 0 and the slice's smallest column.
 template <typename T>
-SellMat<T> make_sell(const Csr& A, DevMem& mem, int sigma = 1) {
+SellMat<T> make_sell(const Csr& A, DevMem& mem, int sigma = 1, int sub = 1) {
   SellMat<T> S;
+  const int R = 32 / sub;
   S.nrows = (int32_t)A.nrows;
   S.ncols = (int32_t)A.ncols;
   S.nnz = A.nnz();
   S.sigma = std::max(1, sigma);
-  S.nslices = (int32_t)((A.nrows + 31) / 32);
+  S.sub = sub;
+  S.nslices = (int32_t)((A.nrows + R - 1) / R);
   std::vector<int32_t> ord = sell_order(A, sigma);
   std::vector<int64_t> off(S.nslices + 1, 0);
+  std::vector<int32_t> smin(S.nslices, 0);
   for (int32_t s = 0; s < S.nslices; ++s) {
-    int32_t w = 0;
-    for (int64_t k = (int64_t)s * 32; k < std::min<int64_t>(A.nrows, (int64_t)s * 32 + 32); ++k)
-      w = std::max(w, A.rp[ord[k] + 1] - A.rp[ord[k]]);
-    off[s + 1] = off[s] + 32 * (int64_t)w;
+    int32_t w = 0, mn = INT32_MAX;
+    for (int64_t k = (int64_t)s * R; k < std::min<int64_t>(A.nrows, (int64_t)s * R + R); ++k) {
+      const int32_t r = ord[k], len = A.rp[r + 1] - A.rp[r];
+      w = std::max(w, len);
+      if (len > 0) mn = std::min(mn, A.ci[A.rp[r]]);
+    }
+    smin[s] = mn == INT32_MAX ? 0 : mn;
+    off[s + 1] = off[s] + 32 * (int64_t)((w + sub - 1) / sub);
   }
   S.padded = off[S.nslices];
   std::vector<int32_t> col(S.padded, 0);
   std::vector<T> val(S.padded, T(0));
   parallel_for(S.nslices, [&](int64_t lo, int64_t hi) {
     for (int64_t s = lo; s < hi; ++s) {
-      int64_t w = (off[s + 1] - off[s]) / 32;
-      for (int lane = 0; lane < 32; ++lane) {
-        int64_t k = s * 32 + lane;
-        int64_t r = k < A.nrows ? ord[k] : -1;
-        int32_t len = r >= 0 ? A.rp[r + 1] - A.rp[r] : 0;
-        int32_t pad_col = len > 0 ? A.ci[A.rp[r + 1] - 1] : 0;
-        for (int64_t j = 0; j < w; ++j) {
-          int64_t o = off[s] + j * 32 + lane;
-          if (j < len) {
-            col[o] = A.ci[A.rp[r] + j];
-            val[o] = (T)A.v[A.rp[r] + j];
-          } else {
-            col[o] = pad_col;
-          }
+      for (int64_t o = off[s]; o < off[s + 1]; ++o) col[o] = smin[s];
+      for (int r = 0; r < R; ++r) {
+        const int64_t k = s * R + r;
+        if (k >= A.nrows) break;
+        const int32_t row = ord[k], len = A.rp[row + 1] - A.rp[row];
+        for (int32_t j = 0; j < len; ++j) {
+          const int64_t o = off[s] + (int64_t)(j / sub) * 32 + r * sub + j % sub;
+          col[o] = A.ci[A.rp[row] + j];
+          val[o] = (T)A.v[A.rp[row] + j];
         }
       }
     }
@@ -191,7 +197,7 @@ SellMat<T> make_sell(const Csr& A, DevMem& mem, int sigma = 1) {
   std::vector<int64_t> snnz(S.nslices, 0);
   int64_t narrow_nnz = 0;
   for (int32_t sl = 0; sl < S.nslices; ++sl) {
-    for (int64_t k = (int64_t)sl * 32; k < std::min<int64_t>(A.nrows, (int64_t)sl * 32 + 32); ++k)
+    for (int64_t k = (int64_t)sl * R; k < std::min<int64_t>(A.nrows, (int64_t)sl * R + R); ++k)
       snnz[sl] += A.rp[ord[k] + 1] - A.rp[ord[k]];
     if (off[sl + 1] == off[sl]) continue;
     int32_t mn = INT32_MAX, mx = INT32_MIN;
@@ -234,24 +240,83 @@ SellMat<T> make_csrv(const Csr& A, DevMem& mem, int lanes) {
 }
 
 struct Layout {
-  int lanes, sigma, unroll;
+  int lanes, sigma, unroll, sub;
 };
 
 template <typename T>
 SellMat<T> make_layout(const Csr& A, DevMem& mem, Layout L) {
-  SellMat<T> S = L.lanes > 1 ? make_csrv<T>(A, mem, L.lanes) : make_sell<T>(A, mem, L.sigma);
+  SellMat<T> S = L.lanes > 1 ? make_csrv<T>(A, mem, L.lanes) : make_sell<T>(A, mem, L.sigma, L.sub);
   S.unroll = L.unroll;
   return S;
 }
 
-// Autotuner (sigma option 0): time y = A x on the device for each candidate layout
-// (SELL-32 with windows 1, 256, 2048 when sorting removes padding, each with the scalar
-// and the predicated row remainder; CSR vector with 4, 8, 16, 32 lanes per row up to twice the longest row) and
-// keep the fastest. Timing: one warm-up launch, then the mean of 5 launches between CUDA
-// events.
+std::string layout_name(const Layout& c) {
+  if (c.lanes > 1) return "v" + std::to_string(c.lanes);
+  return "s" + std::to_string(c.sigma) + (c.sub > 1 ? "x" + std::to_string(c.sub) : "") + (c.unroll == 2 ? "p" : "");
+}
+
+// Tuning cache (environment variable NNMG_TUNE_CACHE = a file path): the autotuner's choice
+// per operator, keyed by value type, shape, nonzeros and a checksum of the pattern, so that
+// another run on the same operators (a profiler run, whose own timings are distorted) uses
+// the same layouts. Lines: key lanes sigma unroll sub.
+std::mutex g_tune_mu;
+std::map<std::string, Layout>* g_tune = nullptr;
+
+std::string tune_key(const Csr& A, int vbytes) {
+  uint64_t h = 1469598103934665603ull;
+  for (int32_t c : A.ci) h = (h ^ (uint32_t)c) * 1099511628211ull;
+  for (int32_t r : A.rp) h = (h ^ (uint32_t)r) * 1099511628211ull;
+  char buf[128];
+  std::snprintf(buf, sizeof(buf), "%d:%lld:%lld:%lld:%016llx", vbytes, (long long)A.nrows, (long long)A.ncols,
+                (long long)A.nnz(), (unsigned long long)h);
+  return buf;
+}
+
+bool tune_lookup(const std::string& key, Layout* out) {
+  const char* path = std::getenv("NNMG_TUNE_CACHE");
+  if (!path || !*path) return false;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (!g_tune) {
+    g_tune = new std::map<std::string, Layout>();
+    if (FILE* f = std::fopen(path, "r")) {
+      char k[128];
+      Layout L{};
+      while (std::fscanf(f, "%127s %d %d %d %d", k, &L.lanes, &L.sigma, &L.unroll, &L.sub) == 5) (*g_tune)[k] = L;
+      std::fclose(f);
+    }
+  }
+  auto it = g_tune->find(key);
+  if (it == g_tune->end()) return false;
+  *out = it->second;
+  return true;
+}
+
+void tune_store(const std::string& key, const Layout& L) {
+  const char* path = std::getenv("NNMG_TUNE_CACHE");
+  if (!path || !*path) return;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (g_tune) (*g_tune)[key] = L;
+  if (FILE* f = std::fopen(path, "a")) {
+    std::fprintf(f, "%s %d %d %d %d\n", key.c_str(), L.lanes, L.sigma, L.unroll, L.sub);
+    std::fclose(f);
+  }
+}
+
+// Autotuner (sigma option 0): time y = A x on the device for each candidate layout and keep
+// the fastest. Candidates: SELL with one lane per row and windows 1, 256, 2048 (when sorting
+// removes padding), each with the scalar and the predicated row remainder; SELL with 2 and
+// 4 lanes per row at the best window; CSR vector with 4, 8, 16, 32 lanes per row up to
+// twice the longest row. Timing: one warm-up launch, then the mean of 5 launches between
+// CUDA events.
 template <typename T>
 SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log) {
   if (sigma != 0 || A.nrows == 0) return make_sell<T>(A, mem, std::max(sigma, 1));
+  const std::string key = tune_key(A, (int)sizeof(T));
+  Layout cached{};
+  if (tune_lookup(key, &cached)) {
+    if (log) *log += " cached " + layout_name(cached);
+    return make_layout<T>(A, mem, cached);
+  }
   int maxlen = 0;
   for (int64_t i = 0; i < A.nrows; ++i) maxlen = std::max(maxlen, A.rp[i + 1] - A.rp[i]);
   std::vector<Layout> cand;
@@ -260,10 +325,9 @@ SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log) {
     int64_t pad = sell_padded(A, sell_order(A, c));
     if (last_pad >= 0 && pad >= (int64_t)(0.995 * (double)last_pad)) continue;  // sorting gains nothing more
     last_pad = pad;
-    cand.push_back({1, c, 1});
+    cand.push_back({1, c, 1, 1});
+    cand.push_back({1, c, 2, 1});
   }
-  for (int g : {4, 8, 16, 32})
-    if (g <= 2 * std::max(maxlen, 2)) cand.push_back({g, 1, 1});
   DevMem scratch;
   scratch.stream = mem.stream;
   const cudaStream_t st = mem.stream;
@@ -274,13 +338,18 @@ SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log) {
   CK(cudaEventCreate(&e1));
   Layout best = cand[0];
   float best_ms = -1.f;
-  for (const Layout& c : cand) {
+  auto try_layouts = [&](const std::vector<Layout>& cs) {
     DevMem trial;
     trial.stream = st;
-    SellMat<T> S = make_layout<T>(A, trial, c);
-    for (int unroll : {1, 2}) {
-      if (c.lanes > 1 && unroll != 1) continue;
-      S.unroll = unroll;
+    SellMat<T> S;
+    Layout built{0, 0, 0, 0};
+    for (const Layout& c : cs) {
+      if (c.lanes != built.lanes || c.sigma != built.sigma || c.sub != built.sub) {
+        trial.release();
+        S = make_layout<T>(A, trial, c);
+        built = c;
+      }
+      S.unroll = c.unroll;
       sell_spmv<T>(S, x, y, st);
       CK(cudaEventRecord(e0, st));
       for (int rep = 0; rep < 5; ++rep) sell_spmv<T>(S, x, y, st);
@@ -288,20 +357,24 @@ SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log) {
       CK(cudaEventSynchronize(e1));
       float ms = 0.f;
       CK(cudaEventElapsedTime(&ms, e0, e1));
-      if (log)
-        *log += std::string(" ") +
-                (c.lanes > 1 ? "v" + std::to_string(c.lanes) : "s" + std::to_string(c.sigma) + (unroll == 2 ? "p" : "")) +
-                ":" + std::to_string((int)(ms / 5 * 1e3)) + "us";
+      if (log) *log += " " + layout_name(c) + ":" + std::to_string((int)(ms / 5 * 1e3)) + "us";
       if (best_ms < 0 || ms < best_ms) {
         best_ms = ms;
-        best = {c.lanes, c.sigma, unroll};
+        best = c;
       }
     }
     trial.release();
-  }
+  };
+  try_layouts(cand);
+  std::vector<Layout> more;
+  for (int sub : {2, 4}) more.push_back({1, best.sigma, 2, sub});
+  for (int g : {4, 8, 16, 32})
+    if (g <= 2 * std::max(maxlen, 2)) more.push_back({g, 1, 1, 1});
+  try_layouts(more);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   scratch.release();
+  tune_store(key, best);
   return make_layout<T>(A, mem, best);
 }
 
@@ -888,8 +961,7 @@ void build_device(mg_hierarchy* h) {
         }
       }
       auto lay = [](const SellMat<T>& M) {
-        return (M.lanes > 1 ? "v" + std::to_string(M.lanes)
-                            : "s" + std::to_string(M.sigma) + (M.unroll == 2 ? "p" : "")) +
+        return layout_name({M.lanes, M.sigma, M.unroll, M.sub}) +
                (M.col16 ? (M.col ? "/16+32" : "/16") : "/32");
       };
       tm.mark("upload L" + std::to_string(l) + " A/P/R " + lay(D.A) + "/" + lay(D.P) + "/" + lay(D.R) + " |" + tlog);

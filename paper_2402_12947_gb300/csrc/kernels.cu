@@ -50,7 +50,7 @@ struct OpView {
   const int32_t* __restrict__ perm;
   const uint16_t* __restrict__ col16;   // 16-bit layouts: column = cbase + col16
   const int32_t* __restrict__ cbase;
-  int nrows;
+  int nrows, nslices;
 };
 
 __device__ __forceinline__ uint16_t ld_stream(const uint16_t* p) { return __ldcs(p); }
@@ -146,11 +146,17 @@ __device__ __forceinline__ T csrv_lane(const T* __restrict__ val, int k, int k1,
   return a;
 }
 
-// Kernel layout parameter G: 1 = SELL-32 (steps of four, scalar remainder), 2 = SELL-32
-// (predicated steps of four), G >= 4 = CSR vector with G lanes per row.
+// Kernel layout parameter G: 1 = SELL, one lane per row (steps of four, scalar remainder);
+// 2 = the same with predicated steps; 3 = SELL with 2 lanes per row and 5 = SELL with 4
+// lanes per row (predicated steps; a row's partial sums are combined by xor shuffles);
+// G in {4, 8, 16, 32} = CSR vector with G lanes per row.
 template <int G>
 __host__ __device__ constexpr bool is_sell() {
-  return G <= 2;
+  return G == 1 || G == 2 || G == 3 || G == 5;
+}
+template <int G>
+__host__ __device__ constexpr int sell_sub() {
+  return G == 3 ? 2 : (G == 5 ? 4 : 1);
 }
 
 // Row sum of the calling thread's row. Returns false for threads past the last row; for
@@ -159,11 +165,24 @@ __host__ __device__ constexpr bool is_sell() {
 template <typename T, int G, bool C16>
 __device__ __forceinline__ bool op_row(const OpView<T>& m, const T* __restrict__ x, int& row, T& acc) {
   const int tid = blockIdx.x * kBlock + threadIdx.x;
-  if constexpr (is_sell<G>()) {
+  if constexpr (is_sell<G>() && sell_sub<G>() == 1) {
     if (tid >= m.nrows) return false;
     row = m.perm ? m.perm[tid] : tid;
     acc = sell_row<T, C16, G == 2>(m, x, tid);
     return true;
+  } else if constexpr (is_sell<G>()) {
+    // one warp per slice (warp-uniform bounds), every lane runs the slice's steps and the
+    // shuffles; lane l serves slot 32/S * slice + l / S
+    constexpr int S = sell_sub<G>();
+    const int sl = tid >> 5;
+    T a = sl < m.nslices ? sell_row<T, C16, true>(m, x, tid) : T(0);
+#pragma unroll
+    for (int o = S / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    const int slot = sl * (32 / S) + ((tid & 31) / S);
+    const bool valid = slot < m.nrows;
+    row = valid ? (m.perm ? m.perm[slot] : slot) : 0;
+    acc = a;
+    return valid;
   } else {
     const int slot = tid / G, lane = tid & (G - 1);
     const bool valid = slot < m.nrows;
@@ -184,7 +203,8 @@ __device__ __forceinline__ bool op_row(const OpView<T>& m, const T* __restrict__
 
 template <int G>
 __device__ __forceinline__ bool group_leader() {
-  return is_sell<G>() || (threadIdx.x & (G - 1)) == 0;
+  if constexpr (is_sell<G>()) return (threadIdx.x & (sell_sub<G>() - 1)) == 0;
+  else return (threadIdx.x & (G - 1)) == 0;
 }
 
 template <typename T, int G, bool C16>
@@ -675,9 +695,15 @@ void batched_spsd_inverse(const GjBatch& g, cudaStream_t s) {
 
 int sell_blocks(int nrows, int lanes) { return grid_for((int)std::min<int64_t>((int64_t)nrows * lanes, INT32_MAX), kBlock); }
 
+// Blocks of one launch over an operator: a warp per SELL slice, or G threads per CSR row.
+template <typename T>
+int op_blocks(const SellMat<T>& A) {
+  return A.lanes > 1 ? sell_blocks(A.nrows, A.lanes) : grid_for((int)std::min<int64_t>((int64_t)A.nslices * 32, INT32_MAX), kBlock);
+}
+
 template <typename T>
 OpView<T> view(const SellMat<T>& A) {
-  return OpView<T>{A.off, A.rp, A.col, A.val, A.perm, A.col16, A.cbase, A.nrows};
+  return OpView<T>{A.off, A.rp, A.col, A.val, A.perm, A.col16, A.cbase, A.nrows, A.nslices};
 }
 
 template <int G, bool C>
@@ -689,12 +715,14 @@ struct Lay {
 // Dispatch on the layout: f(Lay<G, C16>) with the kernel's layout parameter G (see is_sell)
 // and index width.
 template <typename F>
-void by_layout(int lanes, int unroll, bool c16, F&& f) {
+void by_layout(int lanes, int unroll, int sub, bool c16, F&& f) {
   auto go = [&](auto c) {
     constexpr bool C = decltype(c)::value;
     switch (lanes) {
       case 1:
-        if (unroll == 2) f(Lay<2, C>());
+        if (sub == 2) f(Lay<3, C>());
+        else if (sub == 4) f(Lay<5, C>());
+        else if (unroll == 2) f(Lay<2, C>());
         else f(Lay<1, C>());
         break;
       case 4: f(Lay<4, C>()); break;
@@ -711,62 +739,62 @@ void by_layout(int lanes, int unroll, bool c16, F&& f) {
 template <typename T>
 void sell_spmv(const SellMat<T>& A, const T* x, T* y, cudaStream_t s) {
   if (A.nrows == 0) return;
-  by_layout(A.lanes, A.unroll, A.col16 != nullptr, [&](auto g) {
+  by_layout(A.lanes, A.unroll, A.sub, A.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
-    k_spmv<T, L::lanes, L::c16><<<sell_blocks(A.nrows, A.lanes), kBlock, 0, s>>>(view(A), x, y);
+    k_spmv<T, L::lanes, L::c16><<<op_blocks(A), kBlock, 0, s>>>(view(A), x, y);
   });
 }
 template <typename T>
 void sell_resid(const SellMat<T>& A, const T* x, const T* b, T* r, cudaStream_t s) {
   if (A.nrows == 0) return;
-  by_layout(A.lanes, A.unroll, A.col16 != nullptr, [&](auto g) {
+  by_layout(A.lanes, A.unroll, A.sub, A.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
-    k_resid<T, L::lanes, L::c16><<<sell_blocks(A.nrows, A.lanes), kBlock, 0, s>>>(view(A), x, b, r);
+    k_resid<T, L::lanes, L::c16><<<op_blocks(A), kBlock, 0, s>>>(view(A), x, b, r);
   });
 }
 template <typename T>
 void sell_cheb(const SellMat<T>& A, const T* xin, const T* b, const T* dinv, T* d, T* xout, double cd, double cr,
                bool first, cudaStream_t s) {
   if (A.nrows == 0) return;
-  by_layout(A.lanes, A.unroll, A.col16 != nullptr, [&](auto g) {
+  by_layout(A.lanes, A.unroll, A.sub, A.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
     constexpr int G = L::lanes;
     if (first)
-      k_cheb<T, G, L::c16, true><<<sell_blocks(A.nrows, A.lanes), kBlock, 0, s>>>(view(A), xin, b, dinv, d, xout, (T)cd,
+      k_cheb<T, G, L::c16, true><<<op_blocks(A), kBlock, 0, s>>>(view(A), xin, b, dinv, d, xout, (T)cd,
                                                                             (T)cr);
     else
-      k_cheb<T, G, L::c16, false><<<sell_blocks(A.nrows, A.lanes), kBlock, 0, s>>>(view(A), xin, b, dinv, d, xout, (T)cd,
+      k_cheb<T, G, L::c16, false><<<op_blocks(A), kBlock, 0, s>>>(view(A), xin, b, dinv, d, xout, (T)cd,
                                                                              (T)cr);
   });
 }
 template <typename T>
 void sell_prolong(const SellMat<T>& P, const T* xc, T* x, cudaStream_t s) {
   if (P.nrows == 0) return;
-  by_layout(P.lanes, P.unroll, P.col16 != nullptr, [&](auto g) {
+  by_layout(P.lanes, P.unroll, P.sub, P.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
-    k_prolong<T, L::lanes, L::c16><<<sell_blocks(P.nrows, P.lanes), kBlock, 0, s>>>(view(P), xc, x);
+    k_prolong<T, L::lanes, L::c16><<<op_blocks(P), kBlock, 0, s>>>(view(P), xc, x);
   });
 }
 template <typename T>
 void sell_restrict(const SellMat<T>& R, const T* r, T* bc, T* xc, cudaStream_t s) {
   if (R.nrows == 0) return;
-  by_layout(R.lanes, R.unroll, R.col16 != nullptr, [&](auto g) {
+  by_layout(R.lanes, R.unroll, R.sub, R.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
-    k_restrict<T, L::lanes, L::c16><<<sell_blocks(R.nrows, R.lanes), kBlock, 0, s>>>(view(R), r, bc, xc);
+    k_restrict<T, L::lanes, L::c16><<<op_blocks(R), kBlock, 0, s>>>(view(R), r, bc, xc);
   });
 }
 template <typename T>
 void sell_gs(const SellMat<T>& M, const int32_t* rows, const T* b, const T* dinv, T* x, cudaStream_t s) {
   if (M.nrows == 0) return;
-  by_layout(M.lanes, M.unroll, M.col16 != nullptr, [&](auto g) {
+  by_layout(M.lanes, M.unroll, M.sub, M.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
-    k_gs<T, L::lanes, L::c16><<<sell_blocks(M.nrows, M.lanes), kBlock, 0, s>>>(view(M), rows, x, b, dinv, x);
+    k_gs<T, L::lanes, L::c16><<<op_blocks(M), kBlock, 0, s>>>(view(M), rows, x, b, dinv, x);
   });
 }
 void sell_ap(const SellMat<double>& A, const double* p, double* q, double* partial, int* nparts, cudaStream_t s) {
-  int nb = sell_blocks(A.nrows, A.lanes);
+  int nb = op_blocks(A);
   *nparts = nb;
-  by_layout(A.lanes, A.unroll, A.col16 != nullptr, [&](auto g) {
+  by_layout(A.lanes, A.unroll, A.sub, A.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
     k_ap<L::lanes, L::c16><<<nb, kBlock, 0, s>>>(view(A), p, q, partial);
   });

@@ -26,6 +26,8 @@ struct SellMat {
   int32_t sigma = 1;        // window within which rows were sorted by length
   int32_t lanes = 1;        // 1: SELL-32 (off/col/val/perm); G > 1: CSR vector (rp/col/val)
   int32_t unroll = 1;       // SELL-32 row loop: 1 = steps of 4 + scalar remainder, 2 = predicated steps
+  int32_t sub = 1;          // SELL: lanes per row (1, 2, 4); a slice holds 32/sub rows whose
+                            // entries j of row r sit at lane r*sub + j%sub of step j/sub
   int32_t* rp = nullptr;    // [nrows+1] CSR row pointer (lanes > 1)
   // 16-bit column offsets: column = cbase[slice or row] + col16[k] where cbase >= 0; a
   // slice or row spanning more than 2^16 columns has cbase = -1 and reads col (which is
