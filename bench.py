@@ -85,7 +85,7 @@ def measured_peak():
 def profiled_traffic():
     """DRAM bytes per launch of the fine-level Chebyshev kernel from the committed ncu
     summary (a line 'traffic_bytes_per_launch: <int> kernel_rev: <rev>')."""
-    path = os.path.join(ROOT, "profiles", "sell_cheb_f32_c2.md")
+    path = os.path.join(ROOT, "profiles", "k_cheb_f32_c2_fine.md")
     try:
         for line in open(path):
             if line.startswith("traffic_bytes_per_launch:"):
