@@ -291,7 +291,7 @@ def run_ours(args):
         traffic = None
     per_vc, per_it = H32.launch_counts()
     nnz0 = int(nnmg.lib.mg_level_nnz(H32._h, 0))
-    launches = per_it * info32["iterations"] + 8   # head, CG init and the true-residual check
+    launches = per_it * info32["iterations"] + 4   # ABI gather/scatter and the true-residual check
     if rank != 0:
         return 0
     cpu = None

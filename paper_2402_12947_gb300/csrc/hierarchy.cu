@@ -528,6 +528,7 @@ struct mg_hierarchy {
   double *cb = nullptr, *cx = nullptr, *cr = nullptr, *cp = nullptr, *cq = nullptr, *cz = nullptr, *part = nullptr;
   int32_t* perm0 = nullptr;  // level-0 internal order (see build_device), null = library order
   CgState* st = nullptr;
+  unsigned* ticket = nullptr;  // arrival counter of the fused reductions (see Reduce)
   CgState* hst = nullptr;  // pinned
   int nparts = 1, ap_parts = 1;
   cudaGraphExec_t graph = nullptr;
@@ -990,6 +991,7 @@ void build_device(mg_hierarchy* h) {
   h->nparts = cg_parts(n0);
   h->ap_parts = sell_blocks(n0, 32);  // partials of k_ap for any layout
   h->part = mem.alloc<double>(std::max(h->nparts, h->ap_parts));
+  h->ticket = mem.alloc<unsigned>(1);
   h->st = mem.alloc<CgState>(1);
   h->hst = reinterpret_cast<CgState*>(pinned_acquire((sizeof(CgState) + 7) / 8));
   std::memset(h->hst, 0, sizeof(CgState));
@@ -1029,31 +1031,29 @@ struct CgRunner {
   T* vx() { return e.lv[0].x; }
   int launches = 0;
 
+  Reduce red(int op, int use_cond = 0, unsigned long long cond = 0) {
+    return Reduce{h->part, h->ticket, h->st, op, use_cond, cond};
+  }
   void tail(cudaStream_t s, int use_cond, unsigned long long cond) {
-    int na = 0;
-    sell_ap(h->A0, h->cp, h->cq, h->part, &na, s);
-    cg_finish(na, h->part, h->st, FIN_PQ, 0, 0, s);
-    cg_update<T>(h->n0, h->st, h->cp, h->cq, h->cx, h->cr, vb(), vx(), h->part, s);
-    cg_finish(h->nparts, h->part, h->st, FIN_RR, use_cond, cond, s);
-    launches += 4;
+    sell_ap(h->A0, h->cp, h->cq, red(FIN_PQ), s);
+    cg_update<T>(h->n0, h->st, h->cp, h->cq, h->cx, h->cr, vb(), vx(), red(FIN_RR, use_cond, cond), s);
+    launches += 2;
   }
   void head(cudaStream_t s, int use_cond, unsigned long long cond) {
-    cg_init<T>(h->n0, h->cb, h->cr, h->cx, vb(), vx(), h->part, s);
-    cg_finish(h->nparts, h->part, h->st, FIN_BB, 0, 0, s);
+    CK(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned), s));
+    cg_init<T>(h->n0, h->cb, h->cr, h->cx, vb(), vx(), red(FIN_BB), s);
     e.launches = 0;
     e.cycle(0, s);
-    cg_dotz<T>(h->n0, h->cr, vx(), h->cz, h->cp, true, h->part, s);
-    cg_finish(h->nparts, h->part, h->st, FIN_RZ0, 0, 0, s);
-    launches += 4 + e.launches;
+    cg_dotz<T>(h->n0, h->cr, vx(), h->cp, true, red(FIN_RZ0), s);
+    launches += 3 + e.launches;
     tail(s, use_cond, cond);
   }
   void body(cudaStream_t s, int use_cond, unsigned long long cond) {
     e.launches = 0;
     e.cycle(0, s);
-    cg_dotz<T>(h->n0, h->cr, vx(), h->cz, h->cp, false, h->part, s);
-    cg_finish(h->nparts, h->part, h->st, FIN_RZ, 0, 0, s);
-    cg_pupdate(h->n0, h->st, h->cz, h->cp, s);
-    launches = 3 + e.launches;
+    cg_dotz<T>(h->n0, h->cr, vx(), h->cp, false, red(FIN_RZ), s);
+    cg_pupdate<T>(h->n0, h->st, vx(), h->cp, s);
+    launches = 2 + e.launches;
     tail(s, use_cond, cond);
   }
 };
@@ -1125,8 +1125,7 @@ void enqueue_state(mg_hierarchy* h, double rtol, int maxit, cudaStream_t s) {
 // The FP64 residual b - A x of the final iterate, then the whole CG state to the host.
 void enqueue_exit(mg_hierarchy* h, cudaStream_t s) {
   sell_resid<double>(h->A0, h->cx, h->cb, h->cq, s);
-  dot_self(h->n0, h->cq, h->part, s);
-  cg_finish(h->nparts, h->part, h->st, FIN_TRUE, 0, 0, s);
+  dot_self(h->n0, h->cq, Reduce{h->part, h->ticket, h->st, FIN_TRUE, 0, 0}, s);
   CK(cudaMemcpyAsync(h->hst, h->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
 }
 
@@ -1745,8 +1744,8 @@ int mg_solve_stationary(mg_hierarchy_t* h, const double* b, double* x, double rt
   if (!(rtol >= 0) || maxit < 1) throw Error(MG_ERR_INVALID_ARG, "rtol must be >= 0 and maxit >= 1");
   cudaStream_t s = (cudaStream_t)stream;
   auto norm2 = [&](const double* v) {
-    dot_self(h->n0, v, h->part, s);
-    cg_finish(h->nparts, h->part, h->st, FIN_NORM, 0, 0, s);
+    CK(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned), s));
+    dot_self(h->n0, v, Reduce{h->part, h->ticket, h->st, FIN_NORM, 0, 0}, s);
     CK(cudaMemcpyAsync(h->hst, h->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return h->hst->rr;

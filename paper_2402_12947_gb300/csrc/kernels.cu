@@ -293,9 +293,87 @@ __device__ __forceinline__ double block_sum(double v) {
   return t;  // valid in thread 0
 }
 
+constexpr int kCgBlocks = 152 * 4;
+// Absolute bound on CG iterations inside one graph launch, whatever maxit says.
+constexpr int kMaxCgIterations = 100000;
+
+__device__ void apply_finish(CgState* st, double s, int op, int use_cond, unsigned long long handle) {
+  switch (op) {
+    case FIN_BB:
+      st->bb = s;
+      st->it = 0;
+      st->status = 0;
+      st->cont = 1;
+      break;
+    case FIN_RZ0:
+      st->rz = s;
+      break;
+    case FIN_PQ:
+      if (st->bb == 0.0) {
+        st->alpha = 0.0;
+      } else if (!(s > 0.0) || !isfinite(s) || !isfinite(st->rz)) {
+        st->alpha = 0.0;
+        st->status = 3;
+      } else {
+        st->alpha = st->rz / s;
+      }
+      st->pq = s;
+      break;
+    case FIN_RR: {
+      st->rr = s;
+      int cont = 1;
+      if (st->bb == 0.0) {  // b = 0: x = 0 is exact, no iteration
+        st->status = 1;
+        st->cont = 0;
+        if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)handle, 0u);
+        break;
+      }
+      st->it += 1;
+      if (st->status == 3) cont = 0;
+      else if (s <= st->rtol2 * st->bb) st->status = 1, cont = 0;
+      else if (st->it >= st->maxit || st->it >= kMaxCgIterations) st->status = 2, cont = 0;
+      if (!isfinite(s)) st->status = 3, cont = 0;
+      st->cont = cont;
+      if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)handle, (unsigned)cont);
+      break;
+    }
+    case FIN_RZ:
+      st->beta = s / st->rz;
+      st->rz = s;
+      break;
+    case FIN_NORM:
+      st->rr = s;
+      break;
+    case FIN_TRUE:
+      st->rr_true = s;
+      break;
+  }
+}
+
+// Every thread of the block calls this with the block's partial s (valid in thread 0, as
+// block_sum returns it). The last block to arrive sums all partials in index order.
+__device__ void reduce_finish(double s, const Reduce& rd) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    rd.part[blockIdx.x] = s;
+    __threadfence();
+    last = atomicAdd(rd.ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;  // block-uniform
+  __threadfence();
+  double t = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += __ldcg(rd.part + i);
+  t = block_sum(t);
+  if (threadIdx.x == 0) {
+    apply_finish(rd.st, t, rd.op, rd.use_cond, rd.handle);
+    *rd.ticket = 0u;
+  }
+}
+
 template <int G, bool C16>
 __global__ void __launch_bounds__(kBlock) k_ap(OpView<double> m, const double* __restrict__ p, double* __restrict__ q,
-                                               double* __restrict__ part) {
+                                               Reduce rd) {
   int row;
   double ap;
   double v = 0.0;
@@ -303,8 +381,7 @@ __global__ void __launch_bounds__(kBlock) k_ap(OpView<double> m, const double* _
     q[row] = ap;
     v = p[row] * ap;
   }
-  v = block_sum(v);
-  if (threadIdx.x == 0) part[blockIdx.x] = v;
+  reduce_finish(block_sum(v), rd);
 }
 
 // First Chebyshev step from a zero iterate: r = b, d = cr D^{-1} b, x_out = x_in + d for
@@ -447,14 +524,10 @@ __global__ void k_axpy_from(int n, const T* __restrict__ z, double* __restrict__
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] += (double)z[i];
 }
 
-constexpr int kCgBlocks = 152 * 4;
-// Absolute bound on CG iterations inside one graph launch, whatever maxit says.
-constexpr int kMaxCgIterations = 100000;
-
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_cg_init(int n, const double* __restrict__ b, double* __restrict__ r,
                                                     double* __restrict__ x, T* __restrict__ vb, T* __restrict__ vx,
-                                                    double* __restrict__ part) {
+                                                    Reduce rd) {
   double s = 0.0;
   for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
     const double bi = b[i];
@@ -464,15 +537,14 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(int n, const double* __restr
     vx[i] = T(0);
     s = fma(bi, bi, s);
   }
-  s = block_sum(s);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  reduce_finish(block_sum(s), rd);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_cg_update(int n, const CgState* __restrict__ st, const double* __restrict__ p,
                                                       const double* __restrict__ q, double* __restrict__ x,
                                                       double* __restrict__ r, T* __restrict__ vb, T* __restrict__ vx,
-                                                      double* __restrict__ part) {
+                                                      Reduce rd) {
   const double a = st->alpha;
   double s = 0.0;
   for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
@@ -483,94 +555,33 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(int n, const CgState* __re
     vx[i] = T(0);
     s = fma(ri, ri, s);
   }
-  s = block_sum(s);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  reduce_finish(block_sum(s), rd);
 }
 
 template <typename T, bool FIRST>
 __global__ void __launch_bounds__(kBlock) k_cg_dotz(int n, const double* __restrict__ r, const T* __restrict__ vx,
-                                                    double* __restrict__ z, double* __restrict__ p,
-                                                    double* __restrict__ part) {
+                                                    double* __restrict__ p, Reduce rd) {
   double s = 0.0;
   for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
     const double zi = (double)vx[i];
-    if constexpr (!std::is_same<T, double>::value) z[i] = zi;  // FP64: vx is z itself
     if (FIRST) p[i] = zi;
     s = fma(r[i], zi, s);
   }
-  s = block_sum(s);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  reduce_finish(block_sum(s), rd);
 }
 
-__global__ void __launch_bounds__(kBlock) k_cg_pupdate(int n, const CgState* __restrict__ st, const double* __restrict__ z,
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_cg_pupdate(int n, const CgState* __restrict__ st, const T* __restrict__ vx,
                                                        double* __restrict__ p) {
   const double beta = st->beta;
-  for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) p[i] = fma(beta, p[i], z[i]);
+  for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock)
+    p[i] = fma(beta, p[i], (double)vx[i]);
 }
 
-__global__ void __launch_bounds__(kBlock) k_dot_self(int n, const double* __restrict__ r, double* __restrict__ part) {
+__global__ void __launch_bounds__(kBlock) k_dot_self(int n, const double* __restrict__ r, Reduce rd) {
   double s = 0.0;
   for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) s = fma(r[i], r[i], s);
-  s = block_sum(s);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
-__global__ void __launch_bounds__(1024) k_cg_finish(int nparts, const double* __restrict__ part, CgState* st, int op,
-                                                    int use_cond, unsigned long long handle) {
-  double s = 0.0;
-  for (int i = threadIdx.x; i < nparts; i += 1024) s += part[i];
-  s = block_sum(s);
-  if (threadIdx.x != 0) return;
-  switch (op) {
-    case FIN_BB:
-      st->bb = s;
-      st->it = 0;
-      st->status = 0;
-      st->cont = 1;
-      break;
-    case FIN_RZ0:
-      st->rz = s;
-      break;
-    case FIN_PQ:
-      if (st->bb == 0.0) {
-        st->alpha = 0.0;
-      } else if (!(s > 0.0) || !isfinite(s) || !isfinite(st->rz)) {
-        st->alpha = 0.0;
-        st->status = 3;
-      } else {
-        st->alpha = st->rz / s;
-      }
-      st->pq = s;
-      break;
-    case FIN_RR: {
-      st->rr = s;
-      int cont = 1;
-      if (st->bb == 0.0) {  // b = 0: x = 0 is exact, no iteration
-        st->status = 1;
-        st->cont = 0;
-        if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)handle, 0u);
-        break;
-      }
-      st->it += 1;
-      if (st->status == 3) cont = 0;
-      else if (s <= st->rtol2 * st->bb) st->status = 1, cont = 0;
-      else if (st->it >= st->maxit || st->it >= kMaxCgIterations) st->status = 2, cont = 0;
-      if (!isfinite(s)) st->status = 3, cont = 0;
-      st->cont = cont;
-      if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)handle, (unsigned)cont);
-      break;
-    }
-    case FIN_RZ:
-      st->beta = s / st->rz;
-      st->rz = s;
-      break;
-    case FIN_NORM:
-      st->rr = s;
-      break;
-    case FIN_TRUE:
-      st->rr_true = s;
-      break;
-  }
+  reduce_finish(block_sum(s), rd);
 }
 
 inline int grid_for(int n, int per) { return (n + per - 1) / per; }
@@ -791,12 +802,11 @@ void sell_gs(const SellMat<T>& M, const int32_t* rows, const T* b, const T* dinv
     k_gs<T, L::lanes, L::c16><<<op_blocks(M), kBlock, 0, s>>>(view(M), rows, x, b, dinv, x);
   });
 }
-void sell_ap(const SellMat<double>& A, const double* p, double* q, double* partial, int* nparts, cudaStream_t s) {
+void sell_ap(const SellMat<double>& A, const double* p, double* q, const Reduce& rd, cudaStream_t s) {
   int nb = op_blocks(A);
-  *nparts = nb;
   by_layout(A.lanes, A.unroll, A.sub, A.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
-    k_ap<L::lanes, L::c16><<<nb, kBlock, 0, s>>>(view(A), p, q, partial);
+    k_ap<L::lanes, L::c16><<<nb, kBlock, 0, s>>>(view(A), p, q, rd);
   });
 }
 
@@ -869,28 +879,25 @@ void axpy_from(int n, const T* z, double* x, cudaStream_t s) {
 int cg_parts(int n) { return std::max(1, std::min(grid_for(n, kBlock), kCgBlocks)); }
 
 template <typename T>
-void cg_init(int n, const double* b, double* r, double* x, T* vb, T* vx, double* part, cudaStream_t s) {
-  k_cg_init<T><<<cg_parts(n), kBlock, 0, s>>>(n, b, r, x, vb, vx, part);
+void cg_init(int n, const double* b, double* r, double* x, T* vb, T* vx, const Reduce& rd, cudaStream_t s) {
+  k_cg_init<T><<<cg_parts(n), kBlock, 0, s>>>(n, b, r, x, vb, vx, rd);
 }
 template <typename T>
 void cg_update(int n, const CgState* st, const double* p, const double* q, double* x, double* r, T* vb, T* vx,
-               double* part, cudaStream_t s) {
-  k_cg_update<T><<<cg_parts(n), kBlock, 0, s>>>(n, st, p, q, x, r, vb, vx, part);
+               const Reduce& rd, cudaStream_t s) {
+  k_cg_update<T><<<cg_parts(n), kBlock, 0, s>>>(n, st, p, q, x, r, vb, vx, rd);
 }
 template <typename T>
-void cg_dotz(int n, const double* r, const T* vx, double* z, double* p, bool first, double* part, cudaStream_t s) {
-  if (first) k_cg_dotz<T, true><<<cg_parts(n), kBlock, 0, s>>>(n, r, vx, z, p, part);
-  else k_cg_dotz<T, false><<<cg_parts(n), kBlock, 0, s>>>(n, r, vx, z, p, part);
+void cg_dotz(int n, const double* r, const T* vx, double* p, bool first, const Reduce& rd, cudaStream_t s) {
+  if (first) k_cg_dotz<T, true><<<cg_parts(n), kBlock, 0, s>>>(n, r, vx, p, rd);
+  else k_cg_dotz<T, false><<<cg_parts(n), kBlock, 0, s>>>(n, r, vx, p, rd);
 }
-void cg_pupdate(int n, const CgState* st, const double* z, double* p, cudaStream_t s) {
-  k_cg_pupdate<<<cg_parts(n), kBlock, 0, s>>>(n, st, z, p);
+template <typename T>
+void cg_pupdate(int n, const CgState* st, const T* vx, double* p, cudaStream_t s) {
+  k_cg_pupdate<T><<<cg_parts(n), kBlock, 0, s>>>(n, st, vx, p);
 }
-void cg_finish(int nparts, const double* part, CgState* st, int op, int use_cond, unsigned long long cond_handle,
-               cudaStream_t s) {
-  k_cg_finish<<<1, 1024, 0, s>>>(nparts, part, st, op, use_cond, cond_handle);
-}
-void dot_self(int n, const double* r, double* part, cudaStream_t s) {
-  k_dot_self<<<cg_parts(n), kBlock, 0, s>>>(n, r, part);
+void dot_self(int n, const double* r, const Reduce& rd, cudaStream_t s) {
+  k_dot_self<<<cg_parts(n), kBlock, 0, s>>>(n, r, rd);
 }
 
 #define NNMG_INST(T)                                                                                             \
@@ -909,10 +916,11 @@ void dot_self(int n, const double* r, double* part, cudaStream_t s) {
                                 int, cudaStream_t);                                                      \
   template void dense_solve<T>(int, const double*, const T*, T*, double*, int, cudaStream_t);                    \
   template void axpy_from<T>(int, const T*, double*, cudaStream_t);                                              \
-  template void cg_init<T>(int, const double*, double*, double*, T*, T*, double*, cudaStream_t);                 \
+  template void cg_init<T>(int, const double*, double*, double*, T*, T*, const Reduce&, cudaStream_t);         \
   template void cg_update<T>(int, const CgState*, const double*, const double*, double*, double*, T*, T*,        \
-                             double*, cudaStream_t);                                                             \
-  template void cg_dotz<T>(int, const double*, const T*, double*, double*, bool, double*, cudaStream_t);
+                             const Reduce&, cudaStream_t);                                                       \
+  template void cg_dotz<T>(int, const double*, const T*, double*, bool, const Reduce&, cudaStream_t);            \
+  template void cg_pupdate<T>(int, const CgState*, const T*, double*, cudaStream_t);
 
 NNMG_INST(double)
 NNMG_INST(float)

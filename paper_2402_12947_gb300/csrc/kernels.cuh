@@ -46,6 +46,19 @@ struct CgState {
 // FIN_NORM: rr = the sum; FIN_TRUE: rr_true = the sum (|b - A x|^2 recomputed at exit)
 enum FinishOp { FIN_BB = 0, FIN_RZ0 = 1, FIN_PQ = 2, FIN_RR = 3, FIN_RZ = 4, FIN_NORM = 5, FIN_TRUE = 6 };
 
+// A reduction fused into the kernel that produces it: every block writes its partial sum to
+// part[block]; the last block to finish (an atomic ticket, reset by that block) sums the
+// partials in a fixed order and applies `op` to the CG state. With use_cond set (inside a
+// captured graph), FIN_RR also sets the while-node condition through `handle`: 1 to iterate
+// again, 0 once converged, at maxit, or on breakdown.
+struct Reduce {
+  double* part;
+  unsigned* ticket;
+  CgState* st;
+  int op, use_cond;
+  unsigned long long handle;
+};
+
 // One S_c work item: rows row0 .. row0 + kPatchRowsPerItem - 1 of a patch whose DoFs are
 // pdofs[p0 .. p0 + n) and whose dense inverse starts at element inv of the arena.
 struct PatchItem {
@@ -78,8 +91,8 @@ template <typename T> void sell_restrict(const SellMat<T>& R, const T* r, T* bc,
 // x_i = dinv_i (b_i - (M x)_r).
 template <typename T>
 void sell_gs(const SellMat<T>& M, const int32_t* rows, const T* b, const T* dinv, T* x, cudaStream_t s);
-// q = A p and per-block partial sums of p.q (FP64).
-void sell_ap(const SellMat<double>& A, const double* p, double* q, double* partial, int* nparts, cudaStream_t s);
+// q = A p and the reduction of p.q (FP64).
+void sell_ap(const SellMat<double>& A, const double* p, double* q, const Reduce& rd, cudaStream_t s);
 int sell_blocks(int nrows, int lanes);
 
 // ---- local correction S_c (two phases) ----
@@ -134,23 +147,19 @@ template <typename T> void axpy_from(int n, const T* z, double* x, cudaStream_t 
 
 // ---- CG (FP64 recurrence; the V-cycle vectors vb/vx are FP64 or FP32) ----
 int cg_parts(int n);
-// r = b, x = 0, partial b.b; V-cycle input vb = r (converted) and vx = 0.
-template <typename T> void cg_init(int n, const double* b, double* r, double* x, T* vb, T* vx, double* part, cudaStream_t s);
-// x += alpha p, r -= alpha q, partial r.r; vb = r, vx = 0.
+// r = b, x = 0, reduction of b.b; V-cycle input vb = r (converted) and vx = 0.
+template <typename T> void cg_init(int n, const double* b, double* r, double* x, T* vb, T* vx, const Reduce& rd, cudaStream_t s);
+// x += alpha p, r -= alpha q, reduction of r.r; vb = r, vx = 0.
 template <typename T>
 void cg_update(int n, const CgState* st, const double* p, const double* q, double* x, double* r, T* vb, T* vx,
-               double* part, cudaStream_t s);
-// z = (double) vx, partial r.z; with first: p = z.
+               const Reduce& rd, cudaStream_t s);
+// reduction of r.z with z = (double) vx; with first: p = z.
 template <typename T>
-void cg_dotz(int n, const double* r, const T* vx, double* z, double* p, bool first, double* part, cudaStream_t s);
-void cg_pupdate(int n, const CgState* st, const double* z, double* p, cudaStream_t s);
-// Sum the partials in a fixed order and apply `op` to the CG state. With use_cond set
-// (inside a captured graph), FIN_RR also sets the while-node condition through
-// `cond_handle`: 1 to iterate again, 0 once converged, at maxit, or on breakdown.
-void cg_finish(int nparts, const double* part, CgState* st, int op, int use_cond, unsigned long long cond_handle,
-               cudaStream_t s);
-// partial sums of |r|^2 for r = b - A x (a true-residual check)
-void dot_self(int n, const double* r, double* part, cudaStream_t s);
+void cg_dotz(int n, const double* r, const T* vx, double* p, bool first, const Reduce& rd, cudaStream_t s);
+// p = z + beta p with z = (double) vx.
+template <typename T> void cg_pupdate(int n, const CgState* st, const T* vx, double* p, cudaStream_t s);
+// reduction of |r|^2
+void dot_self(int n, const double* r, const Reduce& rd, cudaStream_t s);
 
 void check_launch(const char* what);
 
