@@ -288,6 +288,13 @@ int mg_prolong_correct(mg_hierarchy_t* h, int32_t level, const double* xc_dev, d
 /* x = A_{L-1}^{-1} b on the coarsest level (direct solve). */
 int mg_coarse_solve(mg_hierarchy_t* h, const double* b_dev, double* x_dev, void* stream);
 
+/* Capture the V-cycle from level `level` down (Alg. 1 entered at that level with a zero
+ * iterate on the level's current right-hand side; level 0 = the whole preconditioner) into
+ * a CUDA graph and time `reps` replays on `stream` with CUDA events; returns the mean ms per
+ * replay. The difference between consecutive levels is that level's in-graph cost. The
+ * level's work vectors are overwritten. */
+int mg_time_vcycle(mg_hierarchy_t* h, int32_t level, int32_t reps, void* stream, double* ms_per_cycle);
+
 /* Time `reps` back-to-back launches of the fine-level fused Chebyshev SpMV kernel with CUDA
  * events on `stream`; returns the mean duration in ms and the kernel's algorithmic bytes
  * per launch (matrix once, vectors once). Vectors are the hierarchy's own work buffers. */

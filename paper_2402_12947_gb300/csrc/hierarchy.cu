@@ -1923,6 +1923,40 @@ int mg_coarse_solve(mg_hierarchy_t* h, const double* b, double* x, void* stream)
   API_END_H(h)
 }
 
+int mg_time_vcycle(mg_hierarchy_t* h, int32_t level, int32_t reps, void* stream, double* ms) {
+  API_BEGIN
+  checked(h);
+  check_level(h, level);
+  if (reps < 1) throw Error(MG_ERR_INVALID_ARG, "reps must be >= 1");
+  cudaStream_t s = h->own_stream;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  h->with_engine([&](auto& e) {
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    e.cycle(level, s);
+    CK(cudaStreamEndCapture(s, &g));
+  });
+  CK(cudaGraphInstantiate(&ge, g, 0));
+  cudaStream_t us = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaGraphLaunch(ge, us));  // warm-up
+  CK(cudaEventRecord(e0, us));
+  for (int i = 0; i < reps; ++i) CK(cudaGraphLaunch(ge, us));
+  CK(cudaEventRecord(e1, us));
+  CK(cudaEventSynchronize(e1));
+  float t = 0;
+  CK(cudaEventElapsedTime(&t, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGraphExecDestroy(ge);
+  cudaGraphDestroy(g);
+  if (ms) *ms = (double)t / reps;
+  return MG_OK;
+  API_END_H(h)
+}
+
 int mg_time_smoother_kernel(mg_hierarchy_t* h, int32_t reps, void* stream, double* ms, double* bytes) {
   API_BEGIN
   checked(h);

@@ -113,6 +113,7 @@ _SIGS = {
     "mg_solve_batch": (C.c_int, [_P, _P, _P, C.c_int32, C.c_double, C.c_int32, C.POINTER(MgSolveInfo), _P]),
     "mg_apply_A": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "mg_chebyshev": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
+    "mg_time_vcycle": (C.c_int, [_P, C.c_int32, C.c_int32, _P, C.POINTER(C.c_double)]),
     "mg_sgs": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "mg_local_correction": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "mg_smooth": (C.c_int, [_P, C.c_int32, C.c_int32, _P, _P, _P]),
@@ -348,6 +349,11 @@ class Hierarchy:
         out = np.zeros(self.num_dofs(0))
         _check(lib.mg_load_constant(self._h, f, out.ctypes.data), self._h)
         return out
+
+    def time_vcycle(self, level: int = 0, reps: int = 20, stream=None) -> float:
+        ms = C.c_double()
+        _check(lib.mg_time_vcycle(self._h, level, reps, _stream(stream), C.byref(ms)), self._h)
+        return ms.value
 
     def load_traction(self, axis: int, value: float, t):
         t = np.ascontiguousarray(t, dtype=np.float64)

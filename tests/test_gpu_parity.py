@@ -286,3 +286,13 @@ def test_library_numbering_without_reordering(nnmg, name):
             xs = torch.zeros(n, dtype=torch.float64, device="cuda")
             info = H.solve(dev(b), xs, rtol=1e-10)
             assert info["iterations"] == itr and rel_err(host(xs), xr) < 1e-9, reorder
+
+
+def test_time_vcycle_per_level(nnmg):
+    """The graph-timed V-cycle from each level: positive, and entering lower adds work."""
+    H = lib_geo(nnmg, "c2_p2_128")
+    t = [H.time_vcycle(l, reps=5) for l in range(H.num_levels)]
+    assert all(x > 0 for x in t)
+    assert t[0] > t[-1]
+    with pytest.raises(nnmg.NnmgError):
+        H.time_vcycle(H.num_levels, reps=1)
