@@ -975,7 +975,7 @@ void build_device(mg_hierarchy* h) {
     eng->nc = (int)ncoarse;
     eng->kchunk = 256;
     int rowblocks = (eng->nc + kBlock - 1) / kBlock;
-    int want_chunks = std::max(1, (4 * 152 + rowblocks - 1) / rowblocks);
+    int want_chunks = std::max(1, (8 * 152 + rowblocks - 1) / rowblocks);  // about 8 blocks per SM
     eng->kchunk = std::max(32, std::min(1024, ((eng->nc + want_chunks - 1) / want_chunks + 31) / 32 * 32));
     eng->Xc = const_cast<double*>(coarse_inv);
     eng->cpart = mem.alloc<double>((size_t)dense_chunks(eng->nc, eng->kchunk) * eng->nc);

@@ -468,7 +468,14 @@ __global__ void __launch_bounds__(kBlock) k_patch_solve(const PatchItem* __restr
 #pragma unroll
   for (int u = 0; u < K; ++u)
     if (lane + 32 * u < n) e = fma(xr[u], rs[lane + 32 * u], e);
-  for (int j = lane + 32 * K; j < n; j += 32) e = fma(Xi[j], rs[j], e);
+  for (int j0 = 32 * K; j0 < n; j0 += 32 * K) {  // rows longer than 256: K loads per lane at a time
+    double v[K];
+#pragma unroll
+    for (int u = 0; u < K; ++u) v[u] = j0 + lane + 32 * u < n ? Xi[j0 + lane + 32 * u] : 0.0;
+#pragma unroll
+    for (int u = 0; u < K; ++u)
+      if (j0 + lane + 32 * u < n) e = fma(v[u], rs[j0 + lane + 32 * u], e);
+  }
   e = warp_sum(e);
   if (lane == 0) x[g] = (T)((double)xg + e);
 }
@@ -483,25 +490,29 @@ __global__ void __launch_bounds__(kBlock) k_dense_partial(int n, int kchunk, con
   const int i = blockIdx.x * kBlock + threadIdx.x;
   if (i >= n) return;
   const double* Xi = X + i;
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  int j = k0;
-  for (; j + 4 <= k1; j += 4) {
-    s0 = fma(Xi[(int64_t)j * n], bs[j - k0], s0);
-    s1 = fma(Xi[(int64_t)(j + 1) * n], bs[j + 1 - k0], s1);
-    s2 = fma(Xi[(int64_t)(j + 2) * n], bs[j + 2 - k0], s2);
-    s3 = fma(Xi[(int64_t)(j + 3) * n], bs[j + 3 - k0], s3);
+  // eight column loads issued together (coalesced across the block's rows), then their FMAs
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int j = k0; j < k1; j += 8) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = j + u < k1 ? Xi[(int64_t)(j + u) * n] : 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (j + u < k1) s[u & 3] = fma(v[u], bs[j + u - k0], s[u & 3]);
   }
-  for (; j < k1; ++j) s0 = fma(Xi[(int64_t)j * n], bs[j - k0], s0);
-  part[(int64_t)blockIdx.y * n + i] = (s0 + s1) + (s2 + s3);
+  part[(int64_t)blockIdx.y * n + i] = (s[0] + s[1]) + (s[2] + s[3]);
 }
 
+// x_i = sum over chunks of part[c][i]: one warp per row, lanes over the chunks (fixed order).
 template <typename T>
-__global__ void k_dense_reduce(int n, int nchunks, const double* __restrict__ part, T* __restrict__ x) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+__global__ void __launch_bounds__(kBlock) k_dense_reduce(int n, int nchunks, const double* __restrict__ part,
+                                                         T* __restrict__ x) {
+  const int i = (blockIdx.x * kBlock + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (i >= n) return;  // warp-uniform
   double s = 0.0;
-  for (int c = 0; c < nchunks; ++c) s += part[(int64_t)c * n + i];
-  x[i] = (T)s;
+  for (int c = lane; c < nchunks; c += 32) s += part[(int64_t)c * n + i];
+  s = warp_sum(s);
+  if (lane == 0) x[i] = (T)s;
 }
 
 template <typename Src, typename Dst>
@@ -849,7 +860,7 @@ void dense_solve(int n, const double* X, const T* b, T* x, double* part, int kch
   int nch = dense_chunks(n, kchunk);
   dim3 grid(grid_for(n, kBlock), nch);
   k_dense_partial<T><<<grid, kBlock, kchunk * sizeof(double), s>>>(n, kchunk, X, b, part);
-  k_dense_reduce<T><<<grid_for(n, kBlock), kBlock, 0, s>>>(n, nch, part, x);
+  k_dense_reduce<T><<<grid_for(n, kBlock / 32), kBlock, 0, s>>>(n, nch, part, x);
 }
 
 template <typename Src, typename Dst>
