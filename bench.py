@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every kernel individually instead of one CUDA graph per solve (profilers "
                          "cannot see kernel nodes of graphs with conditional nodes)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "serve", "paper", "lattice"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "serve", "paper", "lattice", "dumbbell"],
                     help="'serve': the mixed request stream through the continuous-batching server; "
                          "'paper': the Case A/B comparison and the residual history of the paper's examples")
     ap.add_argument("--reorder", default=None, choices=["none", "rcm", "spatial"],
@@ -540,12 +540,52 @@ def run_lattice(args):
     return 0
 
 
+def run_dumbbell(args):
+    """The paper's four-way comparison (Table number_struct: Case A / Case B x no correction /
+    correction with unadjusted lambda_max / correction with adjusted lambda_max, against the
+    clean reference) on the synthetic dumbbell-like elasticity structure: Chebyshev(2) global
+    smoother applied twice before and after the coarse correction, MG-PCG to 1e-10, body force
+    (0, 0, -1e3), traction (1e3, 0, 0) on x = 6, clamped at x = 0."""
+    import torch
+    from paper_2402_12947_gb300 import build, inputs, nnmg
+    build.build()
+    torch.cuda.set_device(0)
+    out = {}
+    for degree, ns in ((1, (24, 8, 4, 2)), (2, (16, 8, 4, 2))):
+        meshes = {"reference": inputs.config_dumbbell(ns=ns, n_clusters=0),
+                  "A": inputs.config_dumbbell(ns=ns),
+                  "B": inputs.config_dumbbell(ns=ns, cluster_levels=tuple(range(1, len(ns))))}
+        variants = [("reference", "reference", {})]
+        for case in ("A", "B"):
+            variants += [(f"{case} without correction", case, dict(smoother="global", adjusted_lambda=0)),
+                         (f"{case} correction, unadjusted lambda", case, dict(adjusted_lambda=0)),
+                         (f"{case} correction, adjusted lambda", case, dict(adjusted_lambda=1))]
+        row = {}
+        for name, case, opt in variants:
+            ms, masks = meshes[case]
+            with nnmg.Hierarchy.from_meshes(ms, degree, 0.1, pde="elasticity", dirichlet_masks=masks, nu=2,
+                                            **opt) as H:
+                b = H.load_body([0.0, 0.0, -1e3]) + H.load_traction(0, 6.0, [1e3, 0.0, 0.0])
+                bt = torch.from_numpy(b).cuda()
+                x = torch.zeros_like(bt)
+                info = H.solve(bt, x, rtol=1e-10, maxit=300, raise_on_fail=False)
+                row[name] = {"iterations": info["iterations"] if info["converged"] else f">{info['iterations']}",
+                             "dofs": H.num_dofs(0), "lambda_used_L0": H.eigs(0)[2],
+                             "true_rel_residual": info["true_rel_residual"]}
+        out[f"P{degree}"] = row
+    print(json.dumps({"workload": "dumbbell-like elasticity (Table number_struct layout)", "rtol": 1e-10,
+                      "results": out}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.workload == "paper":
         return run_paper(args)
     if args.workload == "lattice":
         return run_lattice(args)
+    if args.workload == "dumbbell":
+        return run_dumbbell(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "serve":

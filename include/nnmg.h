@@ -264,6 +264,10 @@ int mg_solve_batch(mg_hierarchy_t* const* hs, const double* const* b_dev, double
  * built by mg_setup (Sec. 6.3: traction (1e3, 0, 0) on the face x = 6 of the lattice).
  * t: host [dim]; b_host: host [mg_num_dofs(h, 0)]. INVALID_ARG for other hierarchies. */
 int mg_load_traction(const mg_hierarchy_t* h, int32_t axis, double value, const double* t, double* b_host);
+/* b = int_Omega f . v for a constant body force f (host [dim]) on the free DoFs of level 0
+ * (Sec. 6.3: f = (0, 0, -1e3) on the dumbbell-like structure), for MG_PDE_ELASTICITY
+ * hierarchies built by mg_setup; b_host: host [mg_num_dofs(h, 0)]. */
+int mg_load_body(const mg_hierarchy_t* h, const double* f, double* b_host);
 
 /* ---- single steps of the hot path (device vectors in the hierarchy's V-cycle type:
  *      FP64 in FP64 mode; FP32 in MIXED mode is not exposed) -------------------------- */

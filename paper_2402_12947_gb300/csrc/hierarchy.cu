@@ -1350,6 +1350,7 @@ mg_hierarchy* build_host_hierarchy(const mg_mesh_t* levels, int32_t L, int32_t d
     const double E = H->opt.young, nu = H->opt.poisson_ratio;
     H->host[0].A = assemble_elasticity(meshes[0], dms[0], E / (2.0 * (1.0 + nu)), E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)));
     H->fine_faces = boundary_faces(meshes[0], dms[0]);
+    H->fine_load_unit = load_constant(meshes[0], dms[0], 1.0);  // per node: int phi_k
   } else {
     H->host[0].A = assemble_stiffness(meshes[0], dms[0]);
     H->fine_load_unit = load_constant(meshes[0], dms[0], 1.0);
@@ -1660,6 +1661,20 @@ int mg_load_constant(const mg_hierarchy_t* hc, double f, double* out) {
     throw Error(MG_ERR_INVALID_ARG, "not a geometric Poisson hierarchy");
   if (!out) throw Error(MG_ERR_INVALID_ARG, "null output");
   for (size_t i = 0; i < h->fine_load_unit.size(); ++i) out[i] = f * h->fine_load_unit[i];
+  return MG_OK;
+  API_END_H(h)
+}
+
+int mg_load_body(const mg_hierarchy_t* hc, const double* f, double* out) {
+  mg_hierarchy* h = const_cast<mg_hierarchy*>(hc);
+  API_BEGIN
+  checked(h, false);
+  if (!h->geometric || h->opt.pde != MG_PDE_ELASTICITY)
+    throw Error(MG_ERR_INVALID_ARG, "not a geometric elasticity hierarchy");
+  if (!f || !out) throw Error(MG_ERR_INVALID_ARG, "null pointer");
+  const int d = h->fine_faces.dim;
+  for (size_t k = 0; k < h->fine_load_unit.size(); ++k)
+    for (int c = 0; c < d; ++c) out[k * d + c] = f[c] * h->fine_load_unit[k];
   return MG_OK;
   API_END_H(h)
 }

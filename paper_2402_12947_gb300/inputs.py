@@ -33,6 +33,7 @@ import numpy as np
 __all__ = [
     "Mesh", "structured_mesh", "jitter_mesh", "degrade_mesh", "signed_volumes",
     "hierarchy_meshes", "config_c1", "config_c2", "config_c3", "config_c4", "lattice_mesh", "config_lattice",
+    "dumbbell_mesh", "config_dumbbell",
     "serving_request", "uniform_rhs", "CONFIGS",
 ]
 
@@ -320,6 +321,65 @@ def config_lattice(ns=(13, 6, 3, 2), seed: int = 5, n_clusters: int = 16, cluste
     for lvl, n in enumerate(ns):
         rng = np.random.default_rng([seed, lvl])
         m = jitter_mesh(lattice_mesh(n), amp, rng)
+        if lvl in cluster_levels and n_clusters > 0:
+            m = degrade_mesh(m, rng, n_clusters, moves_per_cluster=(1, 3), kinds=("cap",), eps=eps)
+        meshes.append(m)
+        masks.append(np.abs(m.coords[:, 0]) <= 1e-12)
+    return meshes, masks
+
+
+def _box_union_mesh(n: int, extent, boxes) -> Mesh:
+    """Kuhn-tetrahedron mesh (grid spacing 1/n) of the union of axis-aligned boxes inside
+    [0, extent]^3: a grid cube is kept when its centre lies in some box; unused vertices are
+    dropped (order kept) and the boundary mask marks the vertices of boundary facets."""
+    N = [int(round(e * n)) for e in extent]
+    M = max(N)
+    m = structured_mesh(3, M)
+    coords = m.coords * (M / n)
+    cen = coords[m.cells].mean(axis=1)
+    keep = np.zeros(m.nc, dtype=bool)
+    for lo, hi in boxes:
+        keep |= np.all((cen > np.asarray(lo)) & (cen < np.asarray(hi)), axis=1)
+    cells = m.cells[keep]
+    used = np.zeros(m.nv, dtype=bool)
+    used[cells.ravel()] = True
+    new_id = -np.ones(m.nv, dtype=np.int64)
+    new_id[used] = np.arange(int(used.sum()))
+    cells = new_id[cells].astype(np.int32)
+    coords = coords[used]
+    facets = np.sort(np.concatenate([np.delete(cells, i, axis=1) for i in range(4)], axis=0), axis=1)
+    uniq, cnt = np.unique(facets, axis=0, return_counts=True)
+    bnd = np.zeros(coords.shape[0], dtype=bool)
+    bnd[uniq[cnt == 1].ravel()] = True
+    return Mesh(coords=coords, cells=cells, n=n, boundary=bnd)
+
+
+# two 1 x 2 x 2 end blocks joined by three 4 x 0.5 x 0.5 bars (grid spacing must divide 0.5)
+DUMBBELL_BOXES = [((0.0, 0.0, 0.0), (1.0, 2.0, 2.0)), ((5.0, 0.0, 0.0), (6.0, 2.0, 2.0)),
+                  ((1.0, 0.0, 0.0), (5.0, 0.5, 0.5)), ((1.0, 1.5, 0.0), (5.0, 2.0, 0.5)),
+                  ((1.0, 0.5, 1.5), (5.0, 1.0, 2.0))]
+
+
+def dumbbell_mesh(n: int) -> Mesh:
+    """A dumbbell-like structure in the spirit of Sec. 6.3 (the paper's has hexagonal ends):
+    two end blocks joined by three slender bars, grid spacing 1/n (n even)."""
+    if n % 2:
+        raise ValueError("n must be even")
+    return _box_union_mesh(n, (6.0, 2.0, 2.0), DUMBBELL_BOXES)
+
+
+def config_dumbbell(ns=(24, 8, 4, 2), seed: int = 6, n_clusters: int = 16, cluster_levels=None,
+                    eps: float = 1e-4, amp: float = 0.15):
+    """Elasticity workload shaped like the paper's dumbbell example: four independently
+    generated levels, interior jitter U(+-amp h), ``n_clusters`` sliver clusters (1-3 cap
+    moves at eps h) on each level in ``cluster_levels`` (default all: Case A). Returns
+    (meshes, Dirichlet vertex masks: the clamped face x = 0)."""
+    if cluster_levels is None:
+        cluster_levels = tuple(range(len(ns)))
+    meshes, masks = [], []
+    for lvl, n in enumerate(ns):
+        rng = np.random.default_rng([seed, lvl])
+        m = jitter_mesh(dumbbell_mesh(n), amp, rng)
         if lvl in cluster_levels and n_clusters > 0:
             m = degrade_mesh(m, rng, n_clusters, moves_per_cluster=(1, 3), kinds=("cap",), eps=eps)
         meshes.append(m)

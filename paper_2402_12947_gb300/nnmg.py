@@ -106,6 +106,7 @@ _SIGS = {
     "mg_cell_quality": (C.c_int, [_P, C.c_int32, _P]),
     "mg_load_constant": (C.c_int, [_P, C.c_double, _P]),
     "mg_load_traction": (C.c_int, [_P, C.c_int32, C.c_double, _P, _P]),
+    "mg_load_body": (C.c_int, [_P, _P, _P]),
     "mg_vcycle": (C.c_int, [_P, _P, _P, _P]),
     "mg_solve": (C.c_int, [_P, _P, _P, C.c_double, C.c_int32, C.POINTER(MgSolveInfo), _P]),
     "mg_solve_host": (C.c_int, [_P, _P, _P, C.c_double, C.c_int32, C.POINTER(MgSolveInfo), _P]),
@@ -354,6 +355,12 @@ class Hierarchy:
         ms = C.c_double()
         _check(lib.mg_time_vcycle(self._h, level, reps, _stream(stream), C.byref(ms)), self._h)
         return ms.value
+
+    def load_body(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        out = np.zeros(self.num_dofs(0))
+        _check(lib.mg_load_body(self._h, f.ctypes.data, out.ctypes.data), self._h)
+        return out
 
     def load_traction(self, axis: int, value: float, t):
         t = np.ascontiguousarray(t, dtype=np.float64)

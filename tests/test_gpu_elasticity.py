@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 from oracle import elasticity, hierarchy, mg  # noqa: E402
 from paper_2402_12947_gb300 import inputs  # noqa: E402
 
-CASES = {"p1": ((4, 2, 1), 1), "p2": ((2, 1), 2)}
+CASES = {"p1": ("lattice", (4, 2, 1), 1), "p2": ("lattice", (2, 1), 2), "dumbbell_p1": ("dumbbell", (4, 2), 1)}
 _cache = {}
 
 
@@ -28,8 +28,9 @@ def nnmg():
 def lattice(name, kind):
     key = (name, kind)
     if key not in _cache:
-        ns, degree = CASES[name]
-        ms, masks = inputs.config_lattice(ns=ns, n_clusters=3)
+        geo, ns, degree = CASES[name]
+        make = inputs.config_lattice if geo == "lattice" else inputs.config_dumbbell
+        ms, masks = make(ns=ns, n_clusters=3)
         Ho = hierarchy.build(ms, degree, pde="elasticity", dirichlet_masks=masks, smoother_kind=kind, nu=2)
         _cache[key] = (ms, masks, degree, Ho)
     return _cache[key]
@@ -57,8 +58,12 @@ def host(t):
 
 
 def traction(ms, Ho):
+    """Sec. 6.3 loads: traction (1e3, 0, 0) on x = 6 plus the body force (0, 0, -1e3)."""
+    from oracle import fem
     lo = Ho.levels[0]
     b = elasticity.traction_load_full(ms[0].coords, ms[0].cells, lo.dm, [1e3, 0, 0], 0, 6.0)
+    b = b + np.stack([fem.load_vector_full(ms[0].coords, ms[0].cells, lo.dm, fc) for fc in (0.0, 0.0, -1e3)],
+                     axis=1).ravel()
     return b[elasticity.free_vector_dofs(lo.dm)]
 
 
@@ -81,7 +86,7 @@ def test_vcycle_and_pcg(nnmg, name, kind):
         H.vcycle(dev(b), x)
         assert rel_err(host(x), mg.vcycle(Ho, b, x0)) < parity_tol(Ho)
         bt = traction(ms, Ho)
-        assert rel_err(H.load_traction(0, 6.0, [1e3, 0, 0]), bt) < 1e-13
+        assert rel_err(H.load_traction(0, 6.0, [1e3, 0, 0]) + H.load_body([0.0, 0.0, -1e3]), bt) < 1e-13
         xr, itr, _, _ = mg.pcg(Ho, bt, 1e-10)
         xs = torch.zeros(n, dtype=torch.float64, device="cuda")
         info = H.solve(dev(bt), xs, rtol=1e-10, maxit=300)

@@ -185,7 +185,7 @@ def lattice_case(ns, degree, **kw):
 def test_host_elasticity_setup_matches_oracle(nnmg, ns, degree):
     """Sec. 6.3: vector operator, componentwise transfer, vector patches, lambda_max and
     the traction load of the clamped lattice, against the oracle."""
-    from oracle import elasticity
+    from oracle import elasticity, fem
     ms, masks, Ho = lattice_case(ns, degree)
     with nnmg.Hierarchy.from_meshes(ms, degree, 0.1, host_only=1, pde="elasticity", dirichlet_masks=masks) as H:
         for l, lo in enumerate(Ho.levels):
@@ -209,6 +209,10 @@ def test_host_elasticity_setup_matches_oracle(nnmg, ns, degree):
         assert rel_err(b, bo) < 1e-13
         with pytest.raises(nnmg.NnmgError):
             H.load_constant(1.0)
+        f = [0.0, 2.0, -1e3]
+        bb = H.load_body(f)
+        bo = np.stack([fem.load_vector_full(m0.coords, m0.cells, dm, fc) for fc in f], axis=1).ravel()
+        assert rel_err(bb, bo[elasticity.free_vector_dofs(dm)]) < 1e-13
 
 
 def test_elasticity_options_validated(nnmg):
