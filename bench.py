@@ -267,7 +267,10 @@ def run_ours(args):
     clocks.start()
     ms32, lat32, info32 = timed(H32, args.steps, max(3, args.warmup))
     clk = clocks.stop()
+    x32 = x.clone()
     ms64, lat64, info64 = timed(H64, args.steps, max(3, args.warmup)) if both else (float("nan"), [float("nan")], {})
+    # error of the mixed-precision result against the FP64 result (both solved to rtol)
+    err_vs_fp64 = float((x32 - x).norm() / x.norm()) if both else None
     ms32, ms64 = replicas.max_over_ranks([ms32, ms64], device="cuda")
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
@@ -323,6 +326,7 @@ def run_ours(args):
                  "p50_ms": lat64[len(lat64) // 2], "p99_ms": lat64[min(len(lat64) - 1, int(0.99 * len(lat64)))],
                  "true_rel_residual": info64.get("true_rel_residual")} if both else None,
         "true_rel_residual": info32["true_rel_residual"],
+        "mixed_rel_error_vs_fp64": err_vs_fp64,
         "e2e": {"value": replicas.job_throughput(n, world, e2e_ms), "unit": "DoFs/s", "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 8 * n},
         "gpu_launches": launches * args.steps,

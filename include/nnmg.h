@@ -1,16 +1,16 @@
 /*
  * nnmg.h - C ABI of the GB300-native non-nested geometric multigrid library.
  *
- * The library solves the Poisson problem -lap u = f, u = 0 on the Dirichlet boundary,
- * discretised by continuous Lagrange P1/P2 elements on simplicial meshes (triangles,
- * tetrahedra), with the V-cycle of Chen & Wells, "Multigrid on unstructured meshes with
- * regions of low quality cells" (arXiv:2402.12947):
+ * The library solves the Poisson problem -lap u = f, u = 0 on the Dirichlet boundary, or
+ * linear elasticity (option pde, Sec. 6.3), discretised by continuous Lagrange P1/P2
+ * elements on simplicial meshes (triangles, tetrahedra), with the V-cycle of Chen & Wells,
+ * "Multigrid on unstructured meshes with regions of low quality cells" (arXiv:2402.12947):
  *   - non-nested levels Omega_1 (finest) .. Omega_L, interpolation prolongation
  *     [P_l]_ij = phi_j^(l+1)(x_i), R_l = P_l^T, Galerkin A_{l+1} = P_l^T A_l P_l (Sec. 2);
  *   - the global-local combined smoother S_gc (Sec. 4.2): local residual correction S_c on
  *     the patches around low-quality cells (Sec. 4.1, Alg. 2, patches per Sec. 4.4), a
  *     Jacobi-preconditioned Chebyshev global smoother S_g (Sec. 3.2) with the adjusted
- *     largest eigenvalue (Sec. 5), then S_c again;
+ *     largest eigenvalue (Sec. 5), or multicolour symmetric Gauss-Seidel, then S_c again;
  *   - the V-cycle of Alg. 1 and, as in Sec. 6.2, CG preconditioned by one V-cycle.
  *
  * Conventions shared by every call:
@@ -320,7 +320,8 @@ typedef struct mg_request_t {
   int32_t degree;              /* 1 or 2 */
   double quality_threshold;    /* 0.1 in the paper */
   const mg_options_t* opt;     /* NULL = defaults; use_graph is forced on */
-  const double* b;             /* [n_b] right-hand side on the level-0 free DoFs, or NULL: f = 1 */
+  const double* b;             /* [n_b] right-hand side on the level-0 free DoFs, or NULL: f = 1
+                                  (elasticity: a body force of 1 in every component) */
   int64_t n_b;
   double rtol;
   int32_t maxit;

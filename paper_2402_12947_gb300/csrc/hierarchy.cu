@@ -1410,7 +1410,14 @@ int64_t estimate_device_bytes(const mg_hierarchy* h) {
 
 int64_t hierarchy_device_bytes(const mg_hierarchy* h) { return h->mem.bytes; }
 int64_t hierarchy_dofs(const mg_hierarchy* h) { return h->host[0].A.nrows; }
-const std::vector<double>& hierarchy_unit_load(const mg_hierarchy* h) { return h->fine_load_unit; }
+std::vector<double> hierarchy_unit_load(const mg_hierarchy* h) {
+  if (h->opt.pde != MG_PDE_ELASTICITY) return h->fine_load_unit;
+  const int d = h->fine_faces.dim;
+  std::vector<double> b(h->fine_load_unit.size() * d);
+  for (size_t k = 0; k < h->fine_load_unit.size(); ++k)
+    for (int c = 0; c < d; ++c) b[k * d + c] = h->fine_load_unit[k];
+  return b;
+}
 
 void enqueue_host_solve(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit, cudaEvent_t done) {
   if (!h->graph) throw Error(MG_ERR_INVALID_ARG, "the solve server needs hierarchies built with use_graph = 1");

@@ -136,8 +136,9 @@ void build_device_hierarchy(mg_hierarchy* h);
 int64_t estimate_device_bytes(const mg_hierarchy* h);
 int64_t hierarchy_device_bytes(const mg_hierarchy* h);
 int64_t hierarchy_dofs(const mg_hierarchy* h);
-// b for f = 1 on the free DoFs of level 0 (geometric hierarchies).
-const std::vector<double>& hierarchy_unit_load(const mg_hierarchy* h);
+// b for f = 1 on the free DoFs of level 0 (geometric hierarchies; elasticity: f = 1 in
+// every component).
+std::vector<double> hierarchy_unit_load(const mg_hierarchy* h);
 // Enqueue one MG-PCG solve on the hierarchy's own stream: b (page-locked host, n_0) in, the
 // solution to x (page-locked host) and the CG state out, then record `done`.
 void enqueue_host_solve(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit, cudaEvent_t done);

@@ -555,7 +555,7 @@ void local_patches(const MeshH& m, const DofMapH& dm, const std::vector<double>&
 
 
 Csr assemble_elasticity(const MeshH& m, const DofMapH& dm, double mu, double lam) {
-  const int d = m.dim, d1 = d + 1, nloc = dm.nloc;
+  const int d = m.dim, nloc = dm.nloc;
   std::vector<int64_t> dstart(dm.ndofs + 1, 0);
   for (int64_t k = 0; k < m.nc * nloc; ++k) dstart[dm.cell_dofs[k] + 1]++;
   for (int64_t i = 0; i < dm.ndofs; ++i) dstart[i + 1] += dstart[i];
@@ -644,7 +644,6 @@ Csr assemble_elasticity(const MeshH& m, const DofMapH& dm, double mu, double lam
       }
     }
   });
-  (void)d1;
   return A;
 }
 
