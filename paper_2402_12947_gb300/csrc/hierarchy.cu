@@ -923,8 +923,14 @@ void build_device(mg_hierarchy* h) {
             for (int32_t k = H.A.rp[r]; k < H.A.rp[r + 1]; ++k, ++j) pci[o + j] = H.A.ci[k], pv[o + j] = H.A.v[k];
             for (; j < pw; ++j) pci[o + j] = r;
           }
+          // work list: the patches' row blocks, largest patches first (persistent launch)
+          std::vector<int> porder(D.np);
+          for (int p = 0; p < D.np; ++p) porder[p] = p;
+          std::stable_sort(porder.begin(), porder.end(), [&](int a, int b) {
+            return H.patch_ptr[a + 1] - H.patch_ptr[a] > H.patch_ptr[b + 1] - H.patch_ptr[b];
+          });
           std::vector<PatchItem> items;
-          for (int p = 0; p < D.np; ++p) {
+          for (int p : porder) {
             const int32_t p0 = H.patch_ptr[p], m = H.patch_ptr[p + 1] - p0;
             D.max_patch = std::max(D.max_patch, m);
             for (int r0 = 0; r0 < m; r0 += kPatchRowsPerItem) items.push_back({p0, m, r0, 0, level_inv_off[l][p]});

@@ -437,47 +437,59 @@ __global__ void __launch_bounds__(kBlock) k_patch_residual(int nt, int w, const 
   if (lane == 0) rbuf[t] = bt - s;
 }
 
-// S_c phase 2: e = (A^[d])^{-1} r_B and x_B += e. A work item is kPatchRowsPerItem (8)
-// consecutive rows of one patch, one warp per row; lane l accumulates entries l, l + 32,
-// ... of row i of the symmetric inverse (contiguous), then the warp sums. Every load that
-// does not need r_B (the row's DoF id and current value, its first 256 inverse entries) is
-// issued before the block barrier, so a patch of up to 256 DoFs costs about two dependent
-// memory round trips. With rbuf == nullptr the iterate is zero and the residual is b.
+// S_c phase 2: e = (A^[d])^{-1} r_B and x_B += e, one persistent launch over the work list.
+// A work item is kPatchRowsPerItem (8) consecutive rows of one patch, one warp per row;
+// lane l accumulates entries l, l + 32, ... of row i of the symmetric inverse (contiguous),
+// then the warp sums. The items are sorted by patch size (largest first) and each block
+// walks a contiguous range of them, staging a patch's residual in shared memory once for
+// all of its items in the range. The loads that do not need the residual (the row's DoF id
+// and current value, its first 256 inverse entries) are issued before the staging barrier.
+// With rbuf == nullptr the iterate is zero and the residual is b itself.
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_patch_solve(const PatchItem* __restrict__ items,
+__global__ void __launch_bounds__(kBlock) k_patch_solve(const PatchItem* __restrict__ items, int nitems,
                                                         const int32_t* __restrict__ pdofs,
                                                         const double* __restrict__ inv, const double* rbuf,
                                                         const T* __restrict__ b, T* __restrict__ x) {
   extern __shared__ double rs[];
   constexpr int K = 8;  // inverse entries per lane loaded ahead of the barrier (256 per row)
-  const PatchItem it = items[blockIdx.x];
-  const int p0 = it.p0, n = it.n;
+  const int per = (nitems + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int w0 = blockIdx.x * per, w1 = min(nitems, w0 + per);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = it.row0 + warp;
-  const bool ok = i < n;
-  const double* Xi = inv + it.inv + (int64_t)(ok ? i : 0) * n;
-  const int g = ok ? pdofs[p0 + i] : 0;
-  const T xg = ok ? x[g] : T(0);
-  double xr[K];
+  int staged = -1;  // p0 of the patch whose residual is in rs (block-uniform)
+  for (int w = w0; w < w1; ++w) {
+    const PatchItem it = items[w];
+    const int p0 = it.p0, n = it.n;
+    const int i = it.row0 + warp;
+    const bool ok = i < n;
+    const double* Xi = inv + it.inv + (int64_t)(ok ? i : 0) * n;
+    const int g = ok ? pdofs[p0 + i] : 0;
+    const T xg = ok ? x[g] : T(0);
+    double xr[K];
 #pragma unroll
-  for (int u = 0; u < K; ++u) xr[u] = ok && lane + 32 * u < n ? Xi[lane + 32 * u] : 0.0;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) rs[j] = rbuf ? rbuf[p0 + j] : (double)b[pdofs[p0 + j]];
-  __syncthreads();
-  if (!ok) return;  // warp-uniform; no block barrier follows
-  double e = 0.0;
+    for (int u = 0; u < K; ++u) xr[u] = ok && lane + 32 * u < n ? Xi[lane + 32 * u] : 0.0;
+    if (p0 != staged) {
+      __syncthreads();  // the previous patch's residual is no longer read
+      for (int j = threadIdx.x; j < n; j += blockDim.x) rs[j] = rbuf ? rbuf[p0 + j] : (double)b[pdofs[p0 + j]];
+      __syncthreads();
+      staged = p0;
+    }
+    if (ok) {
+      double e = 0.0;
 #pragma unroll
-  for (int u = 0; u < K; ++u)
-    if (lane + 32 * u < n) e = fma(xr[u], rs[lane + 32 * u], e);
-  for (int j0 = 32 * K; j0 < n; j0 += 32 * K) {  // rows longer than 256: K loads per lane at a time
-    double v[K];
+      for (int u = 0; u < K; ++u)
+        if (lane + 32 * u < n) e = fma(xr[u], rs[lane + 32 * u], e);
+      for (int j0 = 32 * K; j0 < n; j0 += 32 * K) {  // rows longer than 256: K loads per lane at a time
+        double v[K];
 #pragma unroll
-    for (int u = 0; u < K; ++u) v[u] = j0 + lane + 32 * u < n ? Xi[j0 + lane + 32 * u] : 0.0;
+        for (int u = 0; u < K; ++u) v[u] = j0 + lane + 32 * u < n ? Xi[j0 + lane + 32 * u] : 0.0;
 #pragma unroll
-    for (int u = 0; u < K; ++u)
-      if (j0 + lane + 32 * u < n) e = fma(v[u], rs[j0 + lane + 32 * u], e);
+        for (int u = 0; u < K; ++u)
+          if (j0 + lane + 32 * u < n) e = fma(v[u], rs[j0 + lane + 32 * u], e);
+      }
+      e = warp_sum(e);
+      if (lane == 0) x[g] = (T)((double)xg + e);
+    }
   }
-  e = warp_sum(e);
-  if (lane == 0) x[g] = (T)((double)xg + e);
 }
 
 template <typename T>
@@ -850,7 +862,8 @@ void patch_solve(int nitems, const PatchItem* items, const int32_t* pdofs, const
                  const T* b, T* x, int max_patch, cudaStream_t s) {
   if (nitems == 0) return;
   size_t smem = (size_t)max_patch * sizeof(double);
-  k_patch_solve<T><<<nitems, kBlock, smem, s>>>(items, pdofs, inv, rbuf, b, x);
+  const int grid = std::min(nitems, 152 * 8);  // persistent: at most 8 blocks per SM
+  k_patch_solve<T><<<grid, kBlock, smem, s>>>(items, nitems, pdofs, inv, rbuf, b, x);
 }
 
 int dense_chunks(int n, int kchunk) { return grid_for(n, kchunk); }
