@@ -240,19 +240,21 @@ SellMat<T> make_csrv(const Csr& A, DevMem& mem, int lanes) {
 }
 
 struct Layout {
-  int lanes, sigma, unroll, sub;
+  int lanes, sigma, unroll, sub, pf;
 };
 
 template <typename T>
 SellMat<T> make_layout(const Csr& A, DevMem& mem, Layout L) {
   SellMat<T> S = L.lanes > 1 ? make_csrv<T>(A, mem, L.lanes) : make_sell<T>(A, mem, L.sigma, L.sub);
   S.unroll = L.unroll;
+  S.pf = L.lanes > 1 ? 0 : L.pf;
   return S;
 }
 
 std::string layout_name(const Layout& c) {
   if (c.lanes > 1) return "v" + std::to_string(c.lanes);
-  return "s" + std::to_string(c.sigma) + (c.sub > 1 ? "x" + std::to_string(c.sub) : "") + (c.unroll == 2 ? "p" : "");
+  return "s" + std::to_string(c.sigma) + (c.sub > 1 ? "x" + std::to_string(c.sub) : "") + (c.unroll == 2 ? "p" : "") +
+         (c.pf > 0 ? "f" + std::to_string(c.pf) : "");
 }
 
 // Tuning cache (environment variable NNMG_TUNE_CACHE = a file path): the autotuner's choice
@@ -281,7 +283,8 @@ bool tune_lookup(const std::string& key, Layout* out) {
     if (FILE* f = std::fopen(path, "r")) {
       char k[128];
       Layout L{};
-      while (std::fscanf(f, "%127s %d %d %d %d", k, &L.lanes, &L.sigma, &L.unroll, &L.sub) == 5) (*g_tune)[k] = L;
+      while (std::fscanf(f, "%127s %d %d %d %d %d", k, &L.lanes, &L.sigma, &L.unroll, &L.sub, &L.pf) == 6)
+        (*g_tune)[k] = L;
       std::fclose(f);
     }
   }
@@ -297,7 +300,7 @@ void tune_store(const std::string& key, const Layout& L) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   if (g_tune) (*g_tune)[key] = L;
   if (FILE* f = std::fopen(path, "a")) {
-    std::fprintf(f, "%s %d %d %d %d\n", key.c_str(), L.lanes, L.sigma, L.unroll, L.sub);
+    std::fprintf(f, "%s %d %d %d %d %d\n", key.c_str(), L.lanes, L.sigma, L.unroll, L.sub, L.pf);
     std::fclose(f);
   }
 }
@@ -306,8 +309,9 @@ void tune_store(const std::string& key, const Layout& L) {
 // the fastest. Candidates: SELL with one lane per row and windows 1, 256, 2048 (when sorting
 // removes padding), each with the scalar and the predicated row remainder; SELL with 2 and
 // 4 lanes per row at the best window; CSR vector with 4, 8, 16, 32 lanes per row up to
-// twice the longest row. Timing: one warm-up launch, then the mean of 5 launches between
-// CUDA events.
+// twice the longest row; then, on large operators whose best layout is SELL, bulk L2
+// prefetch distances of half, one and two waves of slices. Timing: one warm-up launch,
+// then the mean of 5 launches between CUDA events.
 template <typename T>
 SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log) {
   if (sigma != 0 || A.nrows == 0) return make_sell<T>(A, mem, std::max(sigma, 1));
@@ -325,8 +329,8 @@ SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log) {
     int64_t pad = sell_padded(A, sell_order(A, c));
     if (last_pad >= 0 && pad >= (int64_t)(0.995 * (double)last_pad)) continue;  // sorting gains nothing more
     last_pad = pad;
-    cand.push_back({1, c, 1, 1});
-    cand.push_back({1, c, 2, 1});
+    cand.push_back({1, c, 1, 1, 0});
+    cand.push_back({1, c, 2, 1, 0});
   }
   DevMem scratch;
   scratch.stream = mem.stream;
@@ -342,7 +346,7 @@ SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log) {
     DevMem trial;
     trial.stream = st;
     SellMat<T> S;
-    Layout built{0, 0, 0, 0};
+    Layout built{0, 0, 0, 0, 0};
     for (const Layout& c : cs) {
       if (c.lanes != built.lanes || c.sigma != built.sigma || c.sub != built.sub) {
         trial.release();
@@ -350,6 +354,7 @@ SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log) {
         built = c;
       }
       S.unroll = c.unroll;
+      S.pf = c.lanes > 1 ? 0 : c.pf;
       sell_spmv<T>(S, x, y, st);
       CK(cudaEventRecord(e0, st));
       for (int rep = 0; rep < 5; ++rep) sell_spmv<T>(S, x, y, st);
@@ -367,10 +372,17 @@ SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log) {
   };
   try_layouts(cand);
   std::vector<Layout> more;
-  for (int sub : {2, 4}) more.push_back({1, best.sigma, 2, sub});
+  for (int sub : {2, 4}) more.push_back({1, best.sigma, 2, sub, 0});
   for (int g : {4, 8, 16, 32})
-    if (g <= 2 * std::max(maxlen, 2)) more.push_back({g, 1, 1, 1});
+    if (g <= 2 * std::max(maxlen, 2)) more.push_back({g, 1, 1, 1, 0});
   try_layouts(more);
+  // bulk L2 prefetch of the slices about half a wave, one wave or two waves ahead (a wave:
+  // 152 SMs x 64 resident warps, one slice per warp), on the best SELL layout
+  if (best.lanes == 1 && A.nrows >= 8 * 9728 * 32 / best.sub) {
+    std::vector<Layout> pfc;
+    for (int pf : {4864, 9728, 19456}) pfc.push_back({1, best.sigma, best.unroll, best.sub, pf});
+    try_layouts(pfc);
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   scratch.release();
@@ -391,6 +403,8 @@ struct DevLevel {
   double* pv = nullptr;
   double *inv = nullptr, *rbuf = nullptr;
   PatchItem* items = nullptr;
+  int nblocks = 0;              // blocks of the persistent patch-solve launch
+  int32_t* bstart = nullptr;    // [nblocks+1] first item of each block
   // rows coupled to patch DoFs, with their entries of A (first Chebyshev step after S_c)
   int nh = 0;
   int32_t *hrow = nullptr, *hrp = nullptr, *hci = nullptr;
@@ -456,7 +470,7 @@ struct Engine {
   void local(int l, cudaStream_t s, bool zero = false) {
     DevLevel<T>& L = lv[l];
     if (!zero) patch_residual<T>(L.nt, L.pw, L.pdofs, L.pci, L.pv, L.b, L.x, L.rbuf, s);
-    patch_solve<T>(L.nitems, L.items, L.pdofs, L.inv, zero ? nullptr : L.rbuf, L.b, L.x, L.max_patch, s);
+    patch_solve<T>(L.nblocks, L.items, L.bstart, L.pdofs, L.inv, zero ? nullptr : L.rbuf, L.b, L.x, L.max_patch, s);
     launches += zero ? 1 : 2;
   }
   // zero: the iterate is zero on entry (first pre-smoothing on every level of a cycle)
@@ -938,6 +952,23 @@ void build_device(mg_hierarchy* h) {
           if (D.max_patch > 27000) throw Error(MG_ERR_INVALID_ARG, "patch larger than 27000 DoFs");
           max_patch = std::max(max_patch, D.max_patch);
           D.nitems = (int)items.size();
+          // persistent launch: at most 8 blocks per SM, contiguous item ranges of about equal
+          // total row length (an item's work is 8 rows of its patch's size)
+          {
+            const int nb = std::min<int>(D.nitems, 152 * 8);
+            double total = 0;
+            for (const PatchItem& it : items) total += it.n;
+            std::vector<int32_t> bs(1, 0);
+            double acc = 0;
+            for (int w = 0; w < D.nitems; ++w) {
+              acc += items[w].n;
+              if ((int)bs.size() < nb && acc >= total * (double)bs.size() / nb) bs.push_back(w + 1);
+            }
+            while ((int)bs.size() < nb) bs.push_back(D.nitems);
+            bs.push_back(D.nitems);
+            D.nblocks = nb;
+            D.bstart = mem.upload(bs);
+          }
           D.pci = mem.upload(pci);
           D.pv = mem.upload(pv);
           D.inv = gj.M;
@@ -968,7 +999,7 @@ void build_device(mg_hierarchy* h) {
         }
       }
       auto lay = [](const SellMat<T>& M) {
-        return layout_name({M.lanes, M.sigma, M.unroll, M.sub}) +
+        return layout_name({M.lanes, M.sigma, M.unroll, M.sub, M.pf}) +
                (M.col16 ? (M.col ? "/16+32" : "/16") : "/32");
       };
       tm.mark("upload L" + std::to_string(l) + " A/P/R " + lay(D.A) + "/" + lay(D.P) + "/" + lay(D.R) + " |" + tlog);

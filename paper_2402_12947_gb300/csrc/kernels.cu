@@ -51,7 +51,14 @@ struct OpView {
   const uint16_t* __restrict__ col16;   // 16-bit layouts: column = cbase + col16
   const int32_t* __restrict__ cbase;
   int nrows, nslices;
+  int pf;   // SELL: bulk L2 prefetch of the slice pf slices ahead (0 = none)
 };
+
+// Asynchronous bulk prefetch of [p, p + bytes) into L2 (bytes a multiple of 16, p 16-byte
+// aligned): no registers or shared memory, the copy engine streams it ahead of its use.
+__device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 
 __device__ __forceinline__ uint16_t ld_stream(const uint16_t* p) { return __ldcs(p); }
 
@@ -116,6 +123,16 @@ __device__ __forceinline__ T sell_lane(const T* __restrict__ vp, int64_t k, int 
 template <typename T, bool C16, bool PRED>
 __device__ __forceinline__ T sell_row(const OpView<T>& m, const T* __restrict__ x, int srow) {
   const int s = srow >> 5, lane = srow & 31;
+  if (m.pf > 0 && lane == 0 && s + m.pf < m.nslices) {
+    // the slice this warp's successor about pf / (resident warps) waves later will read
+    const int t = s + m.pf;
+    const int64_t a = m.off[t], e = m.off[t + 1];
+    if (e > a) {
+      l2_prefetch(m.val + a, (uint32_t)((e - a) * (int64_t)sizeof(T)));
+      if (C16 && m.cbase[t] >= 0) l2_prefetch(m.col16 + a, (uint32_t)((e - a) * 2));
+      else l2_prefetch(m.col + a, (uint32_t)((e - a) * 4));
+    }
+  }
   const int64_t o = m.off[s];
   const int w = (int)((m.off[s + 1] - o) >> 5);
   if constexpr (C16) {
@@ -440,20 +457,20 @@ __global__ void __launch_bounds__(kBlock) k_patch_residual(int nt, int w, const 
 // S_c phase 2: e = (A^[d])^{-1} r_B and x_B += e, one persistent launch over the work list.
 // A work item is kPatchRowsPerItem (8) consecutive rows of one patch, one warp per row;
 // lane l accumulates entries l, l + 32, ... of row i of the symmetric inverse (contiguous),
-// then the warp sums. The items are sorted by patch size (largest first) and each block
-// walks a contiguous range of them, staging a patch's residual in shared memory once for
-// all of its items in the range. The loads that do not need the residual (the row's DoF id
+// then the warp sums. The items are sorted by patch size (largest first) and block b walks
+// the contiguous range [bstart[b], bstart[b+1]) of them (ranges of equal total row length),
+// staging a patch's residual in shared memory once for all of its items in the range. The loads that do not need the residual (the row's DoF id
 // and current value, its first 256 inverse entries) are issued before the staging barrier.
 // With rbuf == nullptr the iterate is zero and the residual is b itself.
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_patch_solve(const PatchItem* __restrict__ items, int nitems,
+__global__ void __launch_bounds__(kBlock) k_patch_solve(const PatchItem* __restrict__ items,
+                                                        const int32_t* __restrict__ bstart,
                                                         const int32_t* __restrict__ pdofs,
                                                         const double* __restrict__ inv, const double* rbuf,
                                                         const T* __restrict__ b, T* __restrict__ x) {
   extern __shared__ double rs[];
   constexpr int K = 8;  // inverse entries per lane loaded ahead of the barrier (256 per row)
-  const int per = (nitems + (int)gridDim.x - 1) / (int)gridDim.x;
-  const int w0 = blockIdx.x * per, w1 = min(nitems, w0 + per);
+  const int w0 = bstart[blockIdx.x], w1 = bstart[blockIdx.x + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int staged = -1;  // p0 of the patch whose residual is in rs (block-uniform)
   for (int w = w0; w < w1; ++w) {
@@ -737,7 +754,7 @@ int op_blocks(const SellMat<T>& A) {
 
 template <typename T>
 OpView<T> view(const SellMat<T>& A) {
-  return OpView<T>{A.off, A.rp, A.col, A.val, A.perm, A.col16, A.cbase, A.nrows, A.nslices};
+  return OpView<T>{A.off, A.rp, A.col, A.val, A.perm, A.col16, A.cbase, A.nrows, A.nslices, A.lanes > 1 ? 0 : A.pf};
 }
 
 template <int G, bool C>
@@ -858,12 +875,11 @@ void patch_solve_setup(int max_patch) {
 }
 
 template <typename T>
-void patch_solve(int nitems, const PatchItem* items, const int32_t* pdofs, const double* inv, const double* rbuf,
-                 const T* b, T* x, int max_patch, cudaStream_t s) {
-  if (nitems == 0) return;
+void patch_solve(int nblocks, const PatchItem* items, const int32_t* bstart, const int32_t* pdofs, const double* inv,
+                 const double* rbuf, const T* b, T* x, int max_patch, cudaStream_t s) {
+  if (nblocks == 0) return;
   size_t smem = (size_t)max_patch * sizeof(double);
-  const int grid = std::min(nitems, 152 * 8);  // persistent: at most 8 blocks per SM
-  k_patch_solve<T><<<grid, kBlock, smem, s>>>(items, nitems, pdofs, inv, rbuf, b, x);
+  k_patch_solve<T><<<nblocks, kBlock, smem, s>>>(items, bstart, pdofs, inv, rbuf, b, x);
 }
 
 int dense_chunks(int n, int kchunk) { return grid_for(n, kchunk); }
@@ -936,8 +952,8 @@ void dot_self(int n, const double* r, const Reduce& rd, cudaStream_t s) {
                                         const int32_t*, const int32_t*, const T*, cudaStream_t);                 \
   template void patch_residual<T>(int, int, const int32_t*, const int32_t*, const double*, const T*, const T*,   \
                                    double*, cudaStream_t);                                                \
-  template void patch_solve<T>(int, const PatchItem*, const int32_t*, const double*, const double*, const T*, T*, \
-                                int, cudaStream_t);                                                      \
+  template void patch_solve<T>(int, const PatchItem*, const int32_t*, const int32_t*, const double*, const double*,   \
+                                const T*, T*, int, cudaStream_t);                                              \
   template void dense_solve<T>(int, const double*, const T*, T*, double*, int, cudaStream_t);                    \
   template void axpy_from<T>(int, const T*, double*, cudaStream_t);                                              \
   template void cg_init<T>(int, const double*, double*, double*, T*, T*, const Reduce&, cudaStream_t);         \

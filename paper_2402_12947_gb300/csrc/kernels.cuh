@@ -26,6 +26,7 @@ struct SellMat {
   int32_t sigma = 1;        // window within which rows were sorted by length
   int32_t lanes = 1;        // 1: SELL-32 (off/col/val/perm); G > 1: CSR vector (rp/col/val)
   int32_t unroll = 1;       // SELL-32 row loop: 1 = steps of 4 + scalar remainder, 2 = predicated steps
+  int32_t pf = 0;           // SELL: slices ahead whose data a warp prefetches into L2 (0 = none)
   int32_t sub = 1;          // SELL: lanes per row (1, 2, 4); a slice holds 32/sub rows whose
                             // entries j of row r sit at lane r*sub + j%sub of step j/sub
   int32_t* rp = nullptr;    // [nrows+1] CSR row pointer (lanes > 1)
@@ -103,11 +104,12 @@ void patch_residual(int nt, int w, const int32_t* pdofs, const int32_t* pci, con
                     double* rbuf, cudaStream_t s);
 // Raise the dynamic shared-memory limit of the solve kernel for patches of up to max_patch DoFs.
 void patch_solve_setup(int max_patch);
-// S_c phase 2, x_B += (A^[d])^{-1} r_B per work item; rbuf == nullptr: the iterate is zero
-// and the residual is b itself (phase 1 skipped).
+// S_c phase 2, x_B += (A^[d])^{-1} r_B over the work list: block b handles the items
+// [bstart[b], bstart[b+1]) (nblocks blocks, one persistent launch); rbuf == nullptr: the
+// iterate is zero and the residual is b itself (phase 1 skipped).
 template <typename T>
-void patch_solve(int nitems, const PatchItem* items, const int32_t* pdofs, const double* inv, const double* rbuf,
-                 const T* b, T* x, int max_patch, cudaStream_t s);
+void patch_solve(int nblocks, const PatchItem* items, const int32_t* bstart, const int32_t* pdofs, const double* inv,
+                 const double* rbuf, const T* b, T* x, int max_patch, cudaStream_t s);
 
 // ---- coarsest level: x = X b with X = A_L^{-1} dense symmetric (split-K, deterministic) ----
 template <typename T>
