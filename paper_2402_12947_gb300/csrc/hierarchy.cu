@@ -403,8 +403,6 @@ struct DevLevel {
   double* pv = nullptr;
   double *inv = nullptr, *rbuf = nullptr;
   PatchItem* items = nullptr;
-  int nblocks = 0;              // blocks of the persistent patch-solve launch
-  int32_t* bstart = nullptr;    // [nblocks+1] first item of each block
   // rows coupled to patch DoFs, with their entries of A (first Chebyshev step after S_c)
   int nh = 0;
   int32_t *hrow = nullptr, *hrp = nullptr, *hci = nullptr;
@@ -470,7 +468,7 @@ struct Engine {
   void local(int l, cudaStream_t s, bool zero = false) {
     DevLevel<T>& L = lv[l];
     if (!zero) patch_residual<T>(L.nt, L.pw, L.pdofs, L.pci, L.pv, L.b, L.x, L.rbuf, s);
-    patch_solve<T>(L.nblocks, L.items, L.bstart, L.pdofs, L.inv, zero ? nullptr : L.rbuf, L.b, L.x, L.max_patch, s);
+    patch_solve<T>(L.nitems, L.items, L.pdofs, L.inv, zero ? nullptr : L.rbuf, L.b, L.x, L.max_patch, s);
     launches += zero ? 1 : 2;
   }
   // zero: the iterate is zero on entry (first pre-smoothing on every level of a cycle)
@@ -937,7 +935,7 @@ void build_device(mg_hierarchy* h) {
             for (int32_t k = H.A.rp[r]; k < H.A.rp[r + 1]; ++k, ++j) pci[o + j] = H.A.ci[k], pv[o + j] = H.A.v[k];
             for (; j < pw; ++j) pci[o + j] = r;
           }
-          // work list: the patches' row blocks, largest patches first (persistent launch)
+          // work list: the patches' row blocks, largest patches first
           std::vector<int> porder(D.np);
           for (int p = 0; p < D.np; ++p) porder[p] = p;
           std::stable_sort(porder.begin(), porder.end(), [&](int a, int b) {
@@ -952,23 +950,6 @@ void build_device(mg_hierarchy* h) {
           if (D.max_patch > 27000) throw Error(MG_ERR_INVALID_ARG, "patch larger than 27000 DoFs");
           max_patch = std::max(max_patch, D.max_patch);
           D.nitems = (int)items.size();
-          // persistent launch: at most 8 blocks per SM, contiguous item ranges of about equal
-          // total row length (an item's work is 8 rows of its patch's size)
-          {
-            const int nb = std::min<int>(D.nitems, 152 * 8);
-            double total = 0;
-            for (const PatchItem& it : items) total += it.n;
-            std::vector<int32_t> bs(1, 0);
-            double acc = 0;
-            for (int w = 0; w < D.nitems; ++w) {
-              acc += items[w].n;
-              if ((int)bs.size() < nb && acc >= total * (double)bs.size() / nb) bs.push_back(w + 1);
-            }
-            while ((int)bs.size() < nb) bs.push_back(D.nitems);
-            bs.push_back(D.nitems);
-            D.nblocks = nb;
-            D.bstart = mem.upload(bs);
-          }
           D.pci = mem.upload(pci);
           D.pv = mem.upload(pv);
           D.inv = gj.M;

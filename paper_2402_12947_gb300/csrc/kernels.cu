@@ -454,59 +454,49 @@ __global__ void __launch_bounds__(kBlock) k_patch_residual(int nt, int w, const 
   if (lane == 0) rbuf[t] = bt - s;
 }
 
-// S_c phase 2: e = (A^[d])^{-1} r_B and x_B += e, one persistent launch over the work list.
-// A work item is kPatchRowsPerItem (8) consecutive rows of one patch, one warp per row;
-// lane l accumulates entries l, l + 32, ... of row i of the symmetric inverse (contiguous),
-// then the warp sums. The items are sorted by patch size (largest first) and block b walks
-// the contiguous range [bstart[b], bstart[b+1]) of them (ranges of equal total row length),
-// staging a patch's residual in shared memory once for all of its items in the range. The loads that do not need the residual (the row's DoF id
-// and current value, its first 256 inverse entries) are issued before the staging barrier.
-// With rbuf == nullptr the iterate is zero and the residual is b itself.
+// S_c phase 2: e = (A^[d])^{-1} r_B and x_B += e, one launch over the work list. A work
+// item is kPatchRowsPerItem (8) consecutive rows of one patch, one block per item and one
+// warp per row; lane l accumulates entries l, l + 32, ... of row i of the symmetric inverse
+// (contiguous), then the warp sums. The items are sorted by patch size, largest first, so
+// the longest items start first. Every load that does not need the residual (the row's DoF
+// id and current value, its first 256 inverse entries) is issued before the block barrier
+// that stages the patch residual in shared memory. With rbuf == nullptr the iterate is zero
+// and the residual is b itself.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_patch_solve(const PatchItem* __restrict__ items,
-                                                        const int32_t* __restrict__ bstart,
                                                         const int32_t* __restrict__ pdofs,
                                                         const double* __restrict__ inv, const double* rbuf,
                                                         const T* __restrict__ b, T* __restrict__ x) {
   extern __shared__ double rs[];
   constexpr int K = 8;  // inverse entries per lane loaded ahead of the barrier (256 per row)
-  const int w0 = bstart[blockIdx.x], w1 = bstart[blockIdx.x + 1];
+  const PatchItem it = items[blockIdx.x];
+  const int p0 = it.p0, n = it.n;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int staged = -1;  // p0 of the patch whose residual is in rs (block-uniform)
-  for (int w = w0; w < w1; ++w) {
-    const PatchItem it = items[w];
-    const int p0 = it.p0, n = it.n;
-    const int i = it.row0 + warp;
-    const bool ok = i < n;
-    const double* Xi = inv + it.inv + (int64_t)(ok ? i : 0) * n;
-    const int g = ok ? pdofs[p0 + i] : 0;
-    const T xg = ok ? x[g] : T(0);
-    double xr[K];
+  const int i = it.row0 + warp;
+  const bool ok = i < n;
+  const double* Xi = inv + it.inv + (int64_t)(ok ? i : 0) * n;
+  const int g = ok ? pdofs[p0 + i] : 0;
+  const T xg = ok ? x[g] : T(0);
+  double xr[K];
 #pragma unroll
-    for (int u = 0; u < K; ++u) xr[u] = ok && lane + 32 * u < n ? Xi[lane + 32 * u] : 0.0;
-    if (p0 != staged) {
-      __syncthreads();  // the previous patch's residual is no longer read
-      for (int j = threadIdx.x; j < n; j += blockDim.x) rs[j] = rbuf ? rbuf[p0 + j] : (double)b[pdofs[p0 + j]];
-      __syncthreads();
-      staged = p0;
-    }
-    if (ok) {
-      double e = 0.0;
+  for (int u = 0; u < K; ++u) xr[u] = ok && lane + 32 * u < n ? Xi[lane + 32 * u] : 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) rs[j] = rbuf ? rbuf[p0 + j] : (double)b[pdofs[p0 + j]];
+  __syncthreads();
+  if (!ok) return;  // warp-uniform; no block barrier follows
+  double e = 0.0;
 #pragma unroll
-      for (int u = 0; u < K; ++u)
-        if (lane + 32 * u < n) e = fma(xr[u], rs[lane + 32 * u], e);
-      for (int j0 = 32 * K; j0 < n; j0 += 32 * K) {  // rows longer than 256: K loads per lane at a time
-        double v[K];
+  for (int u = 0; u < K; ++u)
+    if (lane + 32 * u < n) e = fma(xr[u], rs[lane + 32 * u], e);
+  for (int j0 = 32 * K; j0 < n; j0 += 32 * K) {  // rows longer than 256: K loads per lane at a time
+    double v[K];
 #pragma unroll
-        for (int u = 0; u < K; ++u) v[u] = j0 + lane + 32 * u < n ? Xi[j0 + lane + 32 * u] : 0.0;
+    for (int u = 0; u < K; ++u) v[u] = j0 + lane + 32 * u < n ? Xi[j0 + lane + 32 * u] : 0.0;
 #pragma unroll
-        for (int u = 0; u < K; ++u)
-          if (j0 + lane + 32 * u < n) e = fma(v[u], rs[j0 + lane + 32 * u], e);
-      }
-      e = warp_sum(e);
-      if (lane == 0) x[g] = (T)((double)xg + e);
-    }
+    for (int u = 0; u < K; ++u)
+      if (j0 + lane + 32 * u < n) e = fma(v[u], rs[j0 + lane + 32 * u], e);
   }
+  e = warp_sum(e);
+  if (lane == 0) x[g] = (T)((double)xg + e);
 }
 
 template <typename T>
@@ -875,11 +865,11 @@ void patch_solve_setup(int max_patch) {
 }
 
 template <typename T>
-void patch_solve(int nblocks, const PatchItem* items, const int32_t* bstart, const int32_t* pdofs, const double* inv,
-                 const double* rbuf, const T* b, T* x, int max_patch, cudaStream_t s) {
-  if (nblocks == 0) return;
+void patch_solve(int nitems, const PatchItem* items, const int32_t* pdofs, const double* inv, const double* rbuf,
+                 const T* b, T* x, int max_patch, cudaStream_t s) {
+  if (nitems == 0) return;
   size_t smem = (size_t)max_patch * sizeof(double);
-  k_patch_solve<T><<<nblocks, kBlock, smem, s>>>(items, bstart, pdofs, inv, rbuf, b, x);
+  k_patch_solve<T><<<nitems, kBlock, smem, s>>>(items, pdofs, inv, rbuf, b, x);
 }
 
 int dense_chunks(int n, int kchunk) { return grid_for(n, kchunk); }
@@ -952,8 +942,8 @@ void dot_self(int n, const double* r, const Reduce& rd, cudaStream_t s) {
                                         const int32_t*, const int32_t*, const T*, cudaStream_t);                 \
   template void patch_residual<T>(int, int, const int32_t*, const int32_t*, const double*, const T*, const T*,   \
                                    double*, cudaStream_t);                                                \
-  template void patch_solve<T>(int, const PatchItem*, const int32_t*, const int32_t*, const double*, const double*,   \
-                                const T*, T*, int, cudaStream_t);                                              \
+  template void patch_solve<T>(int, const PatchItem*, const int32_t*, const double*, const double*, const T*, T*, \
+                                int, cudaStream_t);                                                      \
   template void dense_solve<T>(int, const double*, const T*, T*, double*, int, cudaStream_t);                    \
   template void axpy_from<T>(int, const T*, double*, cudaStream_t);                                              \
   template void cg_init<T>(int, const double*, double*, double*, T*, T*, const Reduce&, cudaStream_t);         \

@@ -104,12 +104,11 @@ void patch_residual(int nt, int w, const int32_t* pdofs, const int32_t* pci, con
                     double* rbuf, cudaStream_t s);
 // Raise the dynamic shared-memory limit of the solve kernel for patches of up to max_patch DoFs.
 void patch_solve_setup(int max_patch);
-// S_c phase 2, x_B += (A^[d])^{-1} r_B over the work list: block b handles the items
-// [bstart[b], bstart[b+1]) (nblocks blocks, one persistent launch); rbuf == nullptr: the
+// S_c phase 2, x_B += (A^[d])^{-1} r_B, one block per work item; rbuf == nullptr: the
 // iterate is zero and the residual is b itself (phase 1 skipped).
 template <typename T>
-void patch_solve(int nblocks, const PatchItem* items, const int32_t* bstart, const int32_t* pdofs, const double* inv,
-                 const double* rbuf, const T* b, T* x, int max_patch, cudaStream_t s);
+void patch_solve(int nitems, const PatchItem* items, const int32_t* pdofs, const double* inv, const double* rbuf,
+                 const T* b, T* x, int max_patch, cudaStream_t s);
 
 // ---- coarsest level: x = X b with X = A_L^{-1} dense symmetric (split-K, deterministic) ----
 template <typename T>
