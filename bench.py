@@ -199,6 +199,35 @@ def run_reference(args):
     return 0
 
 
+def solve_bytes_per_iteration(H, nnmg, vbytes, cheb_degree=2, nu=1):
+    """Algorithmic bytes of one MG-PCG iteration (each matrix once per pass, each vector once
+    per pass, int32 indices, value size vbytes in the V-cycle, FP64 in CG), for the passes the
+    method needs: per smoothed level and side nu smoother applications of (S_c, Chebyshev,
+    S_c) where the first pre-smoothing Chebyshev step from the zero iterate needs no SpMV, one
+    residual + restriction, one prolongation, the coarsest dense solve, and the CG update.
+    S_c reads each patch's dense FP64 inverse once per application."""
+    import numpy as np
+    L = H.num_levels
+    s, tot = vbytes, 0.0
+    for l in range(L - 1):
+        n, nc = H.num_dofs(l), H.num_dofs(l + 1)
+        nnz = int(nnmg.lib.mg_level_nnz(H._h, l))
+        nnz_p = int(nnmg.lib.mg_transfer_nnz(H._h, l))
+        a_pass = nnz * (s + 4) + n * 6 * s
+        sweeps = 2 * nu * cheb_degree - 1                 # A-passes of the smoother per cycle
+        tot += sweeps * a_pass + n * 4 * s                # + the zero-iterate first step
+        tot += nnz * (s + 4) + n * 3 * s + nnz_p * (s + 4) + nc * 2 * s + n * s   # residual + restriction
+        tot += nnz_p * (s + 4) + n * 2 * s + nc * s                               # prolongation
+        sizes = np.array([len(p) for p in H.export_patches(l)], dtype=np.float64)
+        tot += 4 * nu * 8.0 * float((sizes ** 2).sum())                          # S_c applications
+    nL = H.num_dofs(L - 1)
+    tot += 8.0 * nL * nL
+    n0 = H.num_dofs(0)
+    tot += int(nnmg.lib.mg_level_nnz(H._h, 0)) * 12 + n0 * 16                 # CG: q = A p (FP64)
+    tot += n0 * (9 * 8 + 4 * s)                                               # CG vector updates
+    return tot
+
+
 def run_ours(args):
     """C2 (the headline), C3 or C4: mixed and FP64 MG-PCG solves to rtol 1e-8."""
     import numpy as np
@@ -260,6 +289,15 @@ def run_ours(args):
         e1.record(stream)
         barrier()
         total = e0.elapsed_time(e1) / steps
+        # latency percentiles over at least 30 solves (extra solves after the timed region)
+        for _ in range(max(0, 30 - steps)):
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            H.solve(b, x, rtol=RTOL, maxit=500)
+            s1.record(stream)
+            per.append((s0, s1))
+        torch.cuda.synchronize()
         lat = sorted(a.elapsed_time(c) for a, c in per)
         return total, lat, info
 
@@ -305,6 +343,16 @@ def run_ours(args):
                          f"({d['n']} DoFs, {d['levels']} levels, {d['iterations'][0]} iterations, "
                          f"{d['times'][0]:.1f} s), single-threaded NumPy/SciPy"}
     value = replicas.job_throughput(n, world, ms32)
+    bpi32 = solve_bytes_per_iteration(H32, nnmg, 4)
+    ideal32 = bpi32 * info32["iterations"] / (peak * 1e9) * 1e3
+    solve_roof = {"bytes_per_iteration": bpi32, "iterations": info32["iterations"], "ideal_ms": ideal32,
+                  "measured_ms": ms32, "frac": ideal32 / ms32, "peak_gbs": peak,
+                  "note": "every pass of a CG iteration at the measured copy peak vs the measured solve"}
+    if both:
+        bpi64 = solve_bytes_per_iteration(H64, nnmg, 8)
+        ideal64 = bpi64 * info64["iterations"] / (peak * 1e9) * 1e3
+        solve_roof["fp64"] = {"bytes_per_iteration": bpi64, "ideal_ms": ideal64, "measured_ms": ms64,
+                              "frac": ideal64 / ms64}
     order = args.reorder or "library"
     kernel_name = (f"fine-level multicolour SGS application, FP32 (k_gs, one launch per colour and sweep, "
                    f"autotuned layouts, {order} order)" if sgs else
@@ -327,6 +375,7 @@ def run_ours(args):
                  "true_rel_residual": info64.get("true_rel_residual")} if both else None,
         "true_rel_residual": info32["true_rel_residual"],
         "mixed_rel_error_vs_fp64": err_vs_fp64,
+        "solve_roofline": solve_roof,
         "e2e": {"value": replicas.job_throughput(n, world, e2e_ms), "unit": "DoFs/s", "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 8 * n},
         "gpu_launches": launches * args.steps,
