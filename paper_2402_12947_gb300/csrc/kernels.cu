@@ -379,8 +379,20 @@ __device__ void reduce_finish(double s, const Reduce& rd) {
   __syncthreads();
   if (!last) return;  // block-uniform
   __threadfence();
-  double t = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += __ldcg(rd.part + i);
+  // eight independent loads per step (up to 16k partials for the fine-level SpMV grid);
+  // the summation order is fixed by the block size and the partial count
+  const int np = (int)gridDim.x, bd = (int)blockDim.x;
+  double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int i = threadIdx.x;
+  for (; i + 7 * bd < np; i += 8 * bd) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = __ldcg(rd.part + i + u * bd);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] += v[u];
+  }
+  for (; i < np; i += bd) acc[0] += __ldcg(rd.part + i);
+  double t = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
   t = block_sum(t);
   if (threadIdx.x == 0) {
     apply_finish(rd.st, t, rd.op, rd.use_cond, rd.handle);
