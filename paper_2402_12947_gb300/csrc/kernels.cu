@@ -23,6 +23,13 @@
 
 namespace nnmg {
 
+// Programmatic dependent launch: when set (per host thread), hot-path kernels are launched
+// with programmatic stream serialization, so a kernel's blocks can be scheduled while its
+// predecessor drains; every such kernel waits for its predecessor's completion (and memory)
+// before touching memory (griddepcontrol.wait) and then lets its own successor launch.
+thread_local bool t_pdl = false;
+void set_pdl(bool on) { t_pdl = on; }
+
 void check_launch(const char* what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw Error(MG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -41,6 +48,27 @@ __device__ __forceinline__ int32_t ld_stream(const int32_t* p) { return __ldcs(p
 //  * lanes == G > 1, CSR vector: G consecutive threads share row `slot`, stride over its
 //    CSR entries (coalesced) and combine their partial sums with xor shuffles.
 // Every vector access of an epilogue goes through the matrix row.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launch on stream s, with programmatic stream serialization when enabled for this thread.
+template <typename... KArgs, typename... Args>
+void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = t_pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 template <typename T>
 struct OpView {
   const int64_t* __restrict__ off;
@@ -226,6 +254,7 @@ __device__ __forceinline__ bool group_leader() {
 
 template <typename T, int G, bool C16>
 __global__ void __launch_bounds__(kBlock) k_spmv(OpView<T> m, const T* __restrict__ x, T* __restrict__ y) {
+  pdl_enter();
   int row;
   T ax;
   if (!op_row<T, G, C16>(m, x, row, ax) || !group_leader<G>()) return;
@@ -235,6 +264,7 @@ __global__ void __launch_bounds__(kBlock) k_spmv(OpView<T> m, const T* __restric
 template <typename T, int G, bool C16>
 __global__ void __launch_bounds__(kBlock) k_resid(OpView<T> m, const T* __restrict__ x, const T* __restrict__ b,
                                                   T* __restrict__ r) {
+  pdl_enter();
   int row;
   T ax;
   if (!op_row<T, G, C16>(m, x, row, ax) || !group_leader<G>()) return;
@@ -245,6 +275,7 @@ template <typename T, int G, bool C16, bool FIRST>
 __global__ void __launch_bounds__(kBlock) k_cheb(OpView<T> m, const T* __restrict__ xin, const T* __restrict__ b,
                                                  const T* __restrict__ dinv, T* __restrict__ d, T* __restrict__ xout,
                                                  T cd, T cr) {
+  pdl_enter();
   int row;
   T ax;
   if (!op_row<T, G, C16>(m, xin, row, ax) || !group_leader<G>()) return;
@@ -257,6 +288,7 @@ __global__ void __launch_bounds__(kBlock) k_cheb(OpView<T> m, const T* __restric
 
 template <typename T, int G, bool C16>
 __global__ void __launch_bounds__(kBlock) k_prolong(OpView<T> m, const T* __restrict__ xc, T* __restrict__ x) {
+  pdl_enter();
   int row;
   T ax;
   if (!op_row<T, G, C16>(m, xc, row, ax) || !group_leader<G>()) return;
@@ -266,6 +298,7 @@ __global__ void __launch_bounds__(kBlock) k_prolong(OpView<T> m, const T* __rest
 template <typename T, int G, bool C16>
 __global__ void __launch_bounds__(kBlock) k_restrict(OpView<T> m, const T* __restrict__ r, T* __restrict__ bc,
                                                      T* __restrict__ xc) {
+  pdl_enter();
   int row;
   T ax;
   if (!op_row<T, G, C16>(m, r, row, ax) || !group_leader<G>()) return;
@@ -281,6 +314,7 @@ template <typename T, int G, bool C16>
 __global__ void __launch_bounds__(kBlock) k_gs(OpView<T> m, const int32_t* __restrict__ rows,
                                                const T* __restrict__ xr, const T* __restrict__ b,
                                                const T* __restrict__ dinv, T* x) {
+  pdl_enter();
   int r;
   T s;
   if (!op_row<T, G, C16>(m, xr, r, s) || !group_leader<G>()) return;
@@ -403,6 +437,7 @@ __device__ void reduce_finish(double s, const Reduce& rd) {
 template <int G, bool C16>
 __global__ void __launch_bounds__(kBlock) k_ap(OpView<double> m, const double* __restrict__ p, double* __restrict__ q,
                                                Reduce rd) {
+  pdl_enter();
   int row;
   double ap;
   double v = 0.0;
@@ -419,6 +454,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock) k_cheb0_all(int n, const T* __restrict__ b, const T* __restrict__ dinv,
                                                       const T* __restrict__ xin, T* __restrict__ d,
                                                       T* __restrict__ xout, T cr) {
+  pdl_enter();
   const int i = blockIdx.x * kBlock + threadIdx.x;
   if (i >= n) return;
   const T t = dinv[i] * b[i];
@@ -435,6 +471,7 @@ __global__ void __launch_bounds__(kBlock) k_cheb0_halo(int nh, const int32_t* __
                                                        const T* __restrict__ hv, const T* __restrict__ b,
                                                        const T* __restrict__ dinv, const T* __restrict__ xin,
                                                        T* __restrict__ d, T* __restrict__ xout, T cr) {
+  pdl_enter();
   const int t = (blockIdx.x * kBlock + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   T ax = T(0);
   if (t < nh)
@@ -456,6 +493,7 @@ __global__ void __launch_bounds__(kBlock) k_patch_residual(int nt, int w, const 
                                                            const int32_t* __restrict__ pci,
                                                            const double* __restrict__ pv, const T* __restrict__ b,
                                                            const T* __restrict__ x, double* __restrict__ rbuf) {
+  pdl_enter();
   const int t = (blockIdx.x * kBlock + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (t >= nt) return;  // warp-uniform
   const double bt = (double)b[pdofs[t]];
@@ -479,6 +517,7 @@ __global__ void __launch_bounds__(kBlock) k_patch_solve(const PatchItem* __restr
                                                         const int32_t* __restrict__ pdofs,
                                                         const double* __restrict__ inv, const double* rbuf,
                                                         const T* __restrict__ b, T* __restrict__ x) {
+  pdl_enter();
   extern __shared__ double rs[];
   constexpr int K = 8;  // inverse entries per lane loaded ahead of the barrier (256 per row)
   const PatchItem it = items[blockIdx.x];
@@ -514,6 +553,7 @@ __global__ void __launch_bounds__(kBlock) k_patch_solve(const PatchItem* __restr
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_dense_partial(int n, int kchunk, const double* __restrict__ X,
                                                           const T* __restrict__ b, double* __restrict__ part) {
+  pdl_enter();
   extern __shared__ double bs[];
   const int k0 = blockIdx.y * kchunk, k1 = min(n, k0 + kchunk);
   for (int j = k0 + threadIdx.x; j < k1; j += blockDim.x) bs[j - k0] = (double)b[j];
@@ -538,6 +578,7 @@ __global__ void __launch_bounds__(kBlock) k_dense_partial(int n, int kchunk, con
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_dense_reduce(int n, int nchunks, const double* __restrict__ part,
                                                          T* __restrict__ x) {
+  pdl_enter();
   const int i = (blockIdx.x * kBlock + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (i >= n) return;  // warp-uniform
   double s = 0.0;
@@ -548,21 +589,25 @@ __global__ void __launch_bounds__(kBlock) k_dense_reduce(int n, int nchunks, con
 
 template <typename Src, typename Dst>
 __global__ void k_convert(int n, const Src* __restrict__ a, Dst* __restrict__ b) {
+  pdl_enter();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = (Dst)a[i];
 }
 
 template <typename Src, typename Dst>
 __global__ void k_gather(int n, const int32_t* __restrict__ perm, const Src* __restrict__ a, Dst* __restrict__ b) {
+  pdl_enter();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = (Dst)a[perm[i]];
 }
 
 template <typename Src, typename Dst>
 __global__ void k_scatter(int n, const int32_t* __restrict__ perm, const Src* __restrict__ a, Dst* __restrict__ b) {
+  pdl_enter();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[perm[i]] = (Dst)a[i];
 }
 
 template <typename T>
 __global__ void k_axpy_from(int n, const T* __restrict__ z, double* __restrict__ x) {
+  pdl_enter();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] += (double)z[i];
 }
 
@@ -570,6 +615,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock) k_cg_init(int n, const double* __restrict__ b, double* __restrict__ r,
                                                     double* __restrict__ x, T* __restrict__ vb, T* __restrict__ vx,
                                                     Reduce rd) {
+  pdl_enter();
   double s = 0.0;
   for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
     const double bi = b[i];
@@ -587,6 +633,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(int n, const CgState* __re
                                                       const double* __restrict__ q, double* __restrict__ x,
                                                       double* __restrict__ r, T* __restrict__ vb, T* __restrict__ vx,
                                                       Reduce rd) {
+  pdl_enter();
   const double a = st->alpha;
   double s = 0.0;
   for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
@@ -603,6 +650,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(int n, const CgState* __re
 template <typename T, bool FIRST>
 __global__ void __launch_bounds__(kBlock) k_cg_dotz(int n, const double* __restrict__ r, const T* __restrict__ vx,
                                                     double* __restrict__ p, Reduce rd) {
+  pdl_enter();
   double s = 0.0;
   for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
     const double zi = (double)vx[i];
@@ -615,12 +663,14 @@ __global__ void __launch_bounds__(kBlock) k_cg_dotz(int n, const double* __restr
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_cg_pupdate(int n, const CgState* __restrict__ st, const T* __restrict__ vx,
                                                        double* __restrict__ p) {
+  pdl_enter();
   const double beta = st->beta;
   for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock)
     p[i] = fma(beta, p[i], (double)vx[i]);
 }
 
 __global__ void __launch_bounds__(kBlock) k_dot_self(int n, const double* __restrict__ r, Reduce rd) {
+  pdl_enter();
   double s = 0.0;
   for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) s = fma(r[i], r[i], s);
   reduce_finish(block_sum(s), rd);
@@ -794,7 +844,7 @@ void sell_spmv(const SellMat<T>& A, const T* x, T* y, cudaStream_t s) {
   if (A.nrows == 0) return;
   by_layout(A.lanes, A.unroll, A.sub, A.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
-    k_spmv<T, L::lanes, L::c16><<<op_blocks(A), kBlock, 0, s>>>(view(A), x, y);
+    launch(k_spmv<T, L::lanes, L::c16>, op_blocks(A), kBlock, 0, s, view(A), x, y);
   });
 }
 template <typename T>
@@ -802,7 +852,7 @@ void sell_resid(const SellMat<T>& A, const T* x, const T* b, T* r, cudaStream_t 
   if (A.nrows == 0) return;
   by_layout(A.lanes, A.unroll, A.sub, A.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
-    k_resid<T, L::lanes, L::c16><<<op_blocks(A), kBlock, 0, s>>>(view(A), x, b, r);
+    launch(k_resid<T, L::lanes, L::c16>, op_blocks(A), kBlock, 0, s, view(A), x, b, r);
   });
 }
 template <typename T>
@@ -813,10 +863,10 @@ void sell_cheb(const SellMat<T>& A, const T* xin, const T* b, const T* dinv, T* 
     using L = decltype(g);
     constexpr int G = L::lanes;
     if (first)
-      k_cheb<T, G, L::c16, true><<<op_blocks(A), kBlock, 0, s>>>(view(A), xin, b, dinv, d, xout, (T)cd,
+      launch(k_cheb<T, G, L::c16, true>, op_blocks(A), kBlock, 0, s, view(A), xin, b, dinv, d, xout, (T)cd,
                                                                             (T)cr);
     else
-      k_cheb<T, G, L::c16, false><<<op_blocks(A), kBlock, 0, s>>>(view(A), xin, b, dinv, d, xout, (T)cd,
+      launch(k_cheb<T, G, L::c16, false>, op_blocks(A), kBlock, 0, s, view(A), xin, b, dinv, d, xout, (T)cd,
                                                                              (T)cr);
   });
 }
@@ -825,7 +875,7 @@ void sell_prolong(const SellMat<T>& P, const T* xc, T* x, cudaStream_t s) {
   if (P.nrows == 0) return;
   by_layout(P.lanes, P.unroll, P.sub, P.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
-    k_prolong<T, L::lanes, L::c16><<<op_blocks(P), kBlock, 0, s>>>(view(P), xc, x);
+    launch(k_prolong<T, L::lanes, L::c16>, op_blocks(P), kBlock, 0, s, view(P), xc, x);
   });
 }
 template <typename T>
@@ -833,7 +883,7 @@ void sell_restrict(const SellMat<T>& R, const T* r, T* bc, T* xc, cudaStream_t s
   if (R.nrows == 0) return;
   by_layout(R.lanes, R.unroll, R.sub, R.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
-    k_restrict<T, L::lanes, L::c16><<<op_blocks(R), kBlock, 0, s>>>(view(R), r, bc, xc);
+    launch(k_restrict<T, L::lanes, L::c16>, op_blocks(R), kBlock, 0, s, view(R), r, bc, xc);
   });
 }
 template <typename T>
@@ -841,14 +891,14 @@ void sell_gs(const SellMat<T>& M, const int32_t* rows, const T* b, const T* dinv
   if (M.nrows == 0) return;
   by_layout(M.lanes, M.unroll, M.sub, M.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
-    k_gs<T, L::lanes, L::c16><<<op_blocks(M), kBlock, 0, s>>>(view(M), rows, x, b, dinv, x);
+    launch(k_gs<T, L::lanes, L::c16>, op_blocks(M), kBlock, 0, s, view(M), rows, x, b, dinv, x);
   });
 }
 void sell_ap(const SellMat<double>& A, const double* p, double* q, const Reduce& rd, cudaStream_t s) {
   int nb = op_blocks(A);
   by_layout(A.lanes, A.unroll, A.sub, A.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
-    k_ap<L::lanes, L::c16><<<nb, kBlock, 0, s>>>(view(A), p, q, rd);
+    launch(k_ap<L::lanes, L::c16>, nb, kBlock, 0, s, view(A), p, q, rd);
   });
 }
 
@@ -856,16 +906,16 @@ template <typename T>
 void cheb_first_from_zero(int n, const T* b, const T* dinv, const T* xin, T* d, T* xout, double cr, int nh,
                           const int32_t* hrow, const int32_t* hrp, const int32_t* hci, const T* hv, cudaStream_t s) {
   if (n == 0) return;
-  k_cheb0_all<T><<<grid_for(n, kBlock), kBlock, 0, s>>>(n, b, dinv, xin, d, xout, (T)cr);
+  launch(k_cheb0_all<T>, grid_for(n, kBlock), kBlock, 0, s, n, b, dinv, xin, d, xout, (T)cr);
   if (nh > 0)
-    k_cheb0_halo<T><<<grid_for(nh, kBlock / 32), kBlock, 0, s>>>(nh, hrow, hrp, hci, hv, b, dinv, xin, d, xout, (T)cr);
+    launch(k_cheb0_halo<T>, grid_for(nh, kBlock / 32), kBlock, 0, s, nh, hrow, hrp, hci, hv, b, dinv, xin, d, xout, (T)cr);
 }
 
 template <typename T>
 void patch_residual(int nt, int w, const int32_t* pdofs, const int32_t* pci, const double* pv, const T* b, const T* x,
                     double* rbuf, cudaStream_t s) {
   if (nt == 0) return;
-  k_patch_residual<T><<<grid_for(nt, kBlock / 32), kBlock, 0, s>>>(nt, w, pdofs, pci, pv, b, x, rbuf);
+  launch(k_patch_residual<T>, grid_for(nt, kBlock / 32), kBlock, 0, s, nt, w, pdofs, pci, pv, b, x, rbuf);
 }
 
 void patch_solve_setup(int max_patch) {
@@ -881,7 +931,7 @@ void patch_solve(int nitems, const PatchItem* items, const int32_t* pdofs, const
                  const T* b, T* x, int max_patch, cudaStream_t s) {
   if (nitems == 0) return;
   size_t smem = (size_t)max_patch * sizeof(double);
-  k_patch_solve<T><<<nitems, kBlock, smem, s>>>(items, pdofs, inv, rbuf, b, x);
+  launch(k_patch_solve<T>, nitems, kBlock, smem, s, items, pdofs, inv, rbuf, b, x);
 }
 
 int dense_chunks(int n, int kchunk) { return grid_for(n, kchunk); }
@@ -890,56 +940,56 @@ template <typename T>
 void dense_solve(int n, const double* X, const T* b, T* x, double* part, int kchunk, cudaStream_t s) {
   int nch = dense_chunks(n, kchunk);
   dim3 grid(grid_for(n, kBlock), nch);
-  k_dense_partial<T><<<grid, kBlock, kchunk * sizeof(double), s>>>(n, kchunk, X, b, part);
-  k_dense_reduce<T><<<grid_for(n, kBlock / 32), kBlock, 0, s>>>(n, nch, part, x);
+  launch(k_dense_partial<T>, grid, kBlock, kchunk * sizeof(double), s, n, kchunk, X, b, part);
+  launch(k_dense_reduce<T>, grid_for(n, kBlock / 32), kBlock, 0, s, n, nch, part, x);
 }
 
 template <typename Src, typename Dst>
 void convert(int n, const Src* a, Dst* b, cudaStream_t s) {
   if (n == 0) return;
-  k_convert<Src, Dst><<<std::min(grid_for(n, kBlock), kCgBlocks), kBlock, 0, s>>>(n, a, b);
+  launch(k_convert<Src, Dst>, std::min(grid_for(n, kBlock), kCgBlocks), kBlock, 0, s, n, a, b);
 }
 template <typename Src, typename Dst>
 void gather(int n, const int32_t* perm, const Src* a, Dst* b, cudaStream_t s) {
   if (n == 0) return;
   if (!perm) return convert<Src, Dst>(n, a, b, s);
-  k_gather<Src, Dst><<<std::min(grid_for(n, kBlock), kCgBlocks), kBlock, 0, s>>>(n, perm, a, b);
+  launch(k_gather<Src, Dst>, std::min(grid_for(n, kBlock), kCgBlocks), kBlock, 0, s, n, perm, a, b);
 }
 template <typename Src, typename Dst>
 void scatter(int n, const int32_t* perm, const Src* a, Dst* b, cudaStream_t s) {
   if (n == 0) return;
   if (!perm) return convert<Src, Dst>(n, a, b, s);
-  k_scatter<Src, Dst><<<std::min(grid_for(n, kBlock), kCgBlocks), kBlock, 0, s>>>(n, perm, a, b);
+  launch(k_scatter<Src, Dst>, std::min(grid_for(n, kBlock), kCgBlocks), kBlock, 0, s, n, perm, a, b);
 }
 
 template <typename T>
 void axpy_from(int n, const T* z, double* x, cudaStream_t s) {
   if (n == 0) return;
-  k_axpy_from<T><<<std::min(grid_for(n, kBlock), kCgBlocks), kBlock, 0, s>>>(n, z, x);
+  launch(k_axpy_from<T>, std::min(grid_for(n, kBlock), kCgBlocks), kBlock, 0, s, n, z, x);
 }
 
 int cg_parts(int n) { return std::max(1, std::min(grid_for(n, kBlock), kCgBlocks)); }
 
 template <typename T>
 void cg_init(int n, const double* b, double* r, double* x, T* vb, T* vx, const Reduce& rd, cudaStream_t s) {
-  k_cg_init<T><<<cg_parts(n), kBlock, 0, s>>>(n, b, r, x, vb, vx, rd);
+  launch(k_cg_init<T>, cg_parts(n), kBlock, 0, s, n, b, r, x, vb, vx, rd);
 }
 template <typename T>
 void cg_update(int n, const CgState* st, const double* p, const double* q, double* x, double* r, T* vb, T* vx,
                const Reduce& rd, cudaStream_t s) {
-  k_cg_update<T><<<cg_parts(n), kBlock, 0, s>>>(n, st, p, q, x, r, vb, vx, rd);
+  launch(k_cg_update<T>, cg_parts(n), kBlock, 0, s, n, st, p, q, x, r, vb, vx, rd);
 }
 template <typename T>
 void cg_dotz(int n, const double* r, const T* vx, double* p, bool first, const Reduce& rd, cudaStream_t s) {
-  if (first) k_cg_dotz<T, true><<<cg_parts(n), kBlock, 0, s>>>(n, r, vx, p, rd);
-  else k_cg_dotz<T, false><<<cg_parts(n), kBlock, 0, s>>>(n, r, vx, p, rd);
+  if (first) launch(k_cg_dotz<T, true>, cg_parts(n), kBlock, 0, s, n, r, vx, p, rd);
+  else launch(k_cg_dotz<T, false>, cg_parts(n), kBlock, 0, s, n, r, vx, p, rd);
 }
 template <typename T>
 void cg_pupdate(int n, const CgState* st, const T* vx, double* p, cudaStream_t s) {
-  k_cg_pupdate<T><<<cg_parts(n), kBlock, 0, s>>>(n, st, vx, p);
+  launch(k_cg_pupdate<T>, cg_parts(n), kBlock, 0, s, n, st, vx, p);
 }
 void dot_self(int n, const double* r, const Reduce& rd, cudaStream_t s) {
-  k_dot_self<<<cg_parts(n), kBlock, 0, s>>>(n, r, rd);
+  launch(k_dot_self, cg_parts(n), kBlock, 0, s, n, r, rd);
 }
 
 #define NNMG_INST(T)                                                                                             \
