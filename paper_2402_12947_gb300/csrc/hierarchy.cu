@@ -1055,9 +1055,9 @@ struct CgRunner {
     return Reduce{h->part, h->ticket, h->st, op, use_cond, cond};
   }
   void tail(cudaStream_t s, int use_cond, unsigned long long cond) {
-    sell_ap(h->A0, h->cp, h->cq, red(FIN_PQ), s);
+    sell_ap(h->A0, h->cp, h->cq, h->part, h->st, FIN_PQ, s);
     cg_update<T>(h->n0, h->st, h->cp, h->cq, h->cx, h->cr, vb(), vx(), red(FIN_RR, use_cond, cond), s);
-    launches += 2;
+    launches += 3;
   }
   void head(cudaStream_t s, int use_cond, unsigned long long cond) {
     CK(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned), s));

@@ -434,9 +434,12 @@ __device__ void reduce_finish(double s, const Reduce& rd) {
   }
 }
 
+// q = A p and per-block partial sums of p.q. Its grid has one block per 256 rows (16k
+// blocks on the fine level), too many for one arrival counter, so the partials are summed
+// by k_finish.
 template <int G, bool C16>
 __global__ void __launch_bounds__(kBlock) k_ap(OpView<double> m, const double* __restrict__ p, double* __restrict__ q,
-                                               Reduce rd) {
+                                               double* __restrict__ part) {
   pdl_enter();
   int row;
   double ap;
@@ -445,7 +448,27 @@ __global__ void __launch_bounds__(kBlock) k_ap(OpView<double> m, const double* _
     q[row] = ap;
     v = p[row] * ap;
   }
-  reduce_finish(block_sum(v), rd);
+  v = block_sum(v);
+  if (threadIdx.x == 0) part[blockIdx.x] = v;
+}
+
+// One block: the sum of part[0..nparts) in a fixed order (eight loads in flight per
+// thread), then op applied to the CG state.
+__global__ void __launch_bounds__(1024) k_finish(int nparts, const double* __restrict__ part, CgState* st, int op) {
+  pdl_enter();
+  double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int i = threadIdx.x;
+  for (; i + 7 * 1024 < nparts; i += 8 * 1024) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = part[i + u * 1024];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] += v[u];
+  }
+  for (; i < nparts; i += 1024) acc[0] += part[i];
+  double t = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+  t = block_sum(t);
+  if (threadIdx.x == 0) apply_finish(st, t, op, 0, 0);
 }
 
 // First Chebyshev step from a zero iterate: r = b, d = cr D^{-1} b, x_out = x_in + d for
@@ -894,12 +917,13 @@ void sell_gs(const SellMat<T>& M, const int32_t* rows, const T* b, const T* dinv
     launch(k_gs<T, L::lanes, L::c16>, op_blocks(M), kBlock, 0, s, view(M), rows, x, b, dinv, x);
   });
 }
-void sell_ap(const SellMat<double>& A, const double* p, double* q, const Reduce& rd, cudaStream_t s) {
+void sell_ap(const SellMat<double>& A, const double* p, double* q, double* part, CgState* st, int op, cudaStream_t s) {
   int nb = op_blocks(A);
   by_layout(A.lanes, A.unroll, A.sub, A.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
-    launch(k_ap<L::lanes, L::c16>, nb, kBlock, 0, s, view(A), p, q, rd);
+    launch(k_ap<L::lanes, L::c16>, nb, kBlock, 0, s, view(A), p, q, part);
   });
+  launch(k_finish, 1, 1024, 0, s, nb, (const double*)part, st, op);
 }
 
 template <typename T>

@@ -92,8 +92,8 @@ template <typename T> void sell_restrict(const SellMat<T>& R, const T* r, T* bc,
 // x_i = dinv_i (b_i - (M x)_r).
 template <typename T>
 void sell_gs(const SellMat<T>& M, const int32_t* rows, const T* b, const T* dinv, T* x, cudaStream_t s);
-// q = A p and the reduction of p.q (FP64).
-void sell_ap(const SellMat<double>& A, const double* p, double* q, const Reduce& rd, cudaStream_t s);
+// q = A p, then p.q summed by one finishing block that applies `op` to the CG state (FP64).
+void sell_ap(const SellMat<double>& A, const double* p, double* q, double* part, CgState* st, int op, cudaStream_t s);
 int sell_blocks(int nrows, int lanes);
 
 // ---- local correction S_c (two phases) ----
