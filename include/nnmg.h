@@ -149,11 +149,7 @@ typedef struct mg_options_t {
   int32_t pde;             /* enum mg_pde (POISSON); mg_setup only */
   double young;            /* Young's modulus E for MG_PDE_ELASTICITY (6.9e10, Sec. 6.3) */
   double poisson_ratio;    /* Poisson's ratio nu for MG_PDE_ELASTICITY (0.33, Sec. 6.3) */
-  int32_t pdl;             /* 1: kernels launched directly (use_graph = 0, single steps) use
-                              programmatic dependent launch: each kernel's blocks are scheduled
-                              while its predecessor drains and wait for its results. The solve
-                              graph is captured without it (measured slower inside a graph) (1) */
-  int32_t reserved[3];
+  int32_t reserved[4];
 } mg_options_t;
 
 /* Result of a solve. */

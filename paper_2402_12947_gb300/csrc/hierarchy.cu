@@ -581,7 +581,6 @@ void validate_options(const mg_options_t& o) {
   if (o.global_smoother < 0 || o.global_smoother > 1) throw Error(MG_ERR_INVALID_ARG, "unknown global smoother");
   if (o.reorder < 0 || o.reorder > 2) throw Error(MG_ERR_INVALID_ARG, "unknown reorder mode");
   if (o.pde < 0 || o.pde > 1) throw Error(MG_ERR_INVALID_ARG, "unknown pde");
-  if (o.pdl < 0 || o.pdl > 1) throw Error(MG_ERR_INVALID_ARG, "pdl must be 0 or 1");
   if (o.pde == MG_PDE_ELASTICITY && !(o.young > 0 && o.poisson_ratio > -1.0 && o.poisson_ratio < 0.5))
     throw Error(MG_ERR_INVALID_ARG, "elasticity needs E > 0 and -1 < nu < 1/2");
 }
@@ -764,7 +763,6 @@ void build_device(mg_hierarchy* h) {
   const mg_options_t& o = h->opt;
   const int L = h->L;
   PhaseTimer tm;
-  set_pdl(o.pdl != 0);
   const int64_t ncoarse = h->host[L - 1].A.nrows;
 
   // ---- device upload ----
@@ -1090,9 +1088,6 @@ void dispatch(mg_hierarchy* h, F&& f) {
 }
 
 void build_graph(mg_hierarchy* h) {
-  // captured without programmatic dependent launch: inside a graph it measured slower
-  // (C2 mixed 35.1 vs 34.3 ms per solve; the small levels lose most)
-  set_pdl(false);
   cudaStream_t s = h->own_stream;
   cudaGraph_t g = nullptr;
   CK(cudaGraphCreate(&g, 0));
@@ -1214,7 +1209,6 @@ namespace {
 mg_hierarchy* checked(mg_hierarchy* h, bool need_device = true) {
   if (!h) throw Error(MG_ERR_INVALID_ARG, "null hierarchy");
   if (need_device && !h->device) throw Error(MG_ERR_NO_DEVICE, "hierarchy was built with host_only = 1");
-  if (need_device) set_pdl(h->opt.pdl != 0);
   return h;
 }
 void check_level(const mg_hierarchy* h, int l, bool below_coarsest = false) {
@@ -1301,7 +1295,6 @@ void mg_default_options(mg_options_t* o) {
   o->sell_sigma = 0;
   o->reorder = MG_REORDER_NONE;
   o->pde = MG_PDE_POISSON;
-  o->pdl = 1;
   o->young = 6.9e10;
   o->poisson_ratio = 0.33;
 }
@@ -1446,7 +1439,6 @@ std::vector<double> hierarchy_unit_load(const mg_hierarchy* h) {
 
 void enqueue_host_solve(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit, cudaEvent_t done) {
   if (!h->graph) throw Error(MG_ERR_INVALID_ARG, "the solve server needs hierarchies built with use_graph = 1");
-  set_pdl(h->opt.pdl != 0);
   cudaStream_t s = h->own_stream;
   CK(cudaMemcpyAsync(h->cq, b, sizeof(double) * h->n0, cudaMemcpyHostToDevice, s));
   gather<double, double>(h->n0, h->perm0, h->cq, h->cb, s);
@@ -1979,7 +1971,6 @@ int mg_time_vcycle(mg_hierarchy_t* h, int32_t level, int32_t reps, void* stream,
   cudaStream_t s = h->own_stream;
   cudaGraph_t g = nullptr;
   cudaGraphExec_t ge = nullptr;
-  set_pdl(false);  // as in the solve graph
   h->with_engine([&](auto& e) {
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     e.cycle(level, s);

@@ -23,13 +23,6 @@
 
 namespace nnmg {
 
-// Programmatic dependent launch: when set (per host thread), hot-path kernels are launched
-// with programmatic stream serialization, so a kernel's blocks can be scheduled while its
-// predecessor drains; every such kernel waits for its predecessor's completion (and memory)
-// before touching memory (griddepcontrol.wait) and then lets its own successor launch.
-thread_local bool t_pdl = false;
-void set_pdl(bool on) { t_pdl = on; }
-
 void check_launch(const char* what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw Error(MG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -48,12 +41,7 @@ __device__ __forceinline__ int32_t ld_stream(const int32_t* p) { return __ldcs(p
 //  * lanes == G > 1, CSR vector: G consecutive threads share row `slot`, stride over its
 //    CSR entries (coalesced) and combine their partial sums with xor shuffles.
 // Every vector access of an epilogue goes through the matrix row.
-__device__ __forceinline__ void pdl_enter() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
-// Launch on stream s, with programmatic stream serialization when enabled for this thread.
+// Launch on stream s (plain stream order).
 template <typename... KArgs, typename... Args>
 void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
   cudaLaunchConfig_t cfg = {};
@@ -61,11 +49,7 @@ void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaSt
   cfg.blockDim = block;
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = t_pdl ? 1 : 0;
+  cfg.numAttrs = 0;
   cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
@@ -254,7 +238,6 @@ __device__ __forceinline__ bool group_leader() {
 
 template <typename T, int G, bool C16>
 __global__ void __launch_bounds__(kBlock) k_spmv(OpView<T> m, const T* __restrict__ x, T* __restrict__ y) {
-  pdl_enter();
   int row;
   T ax;
   if (!op_row<T, G, C16>(m, x, row, ax) || !group_leader<G>()) return;
@@ -264,7 +247,6 @@ __global__ void __launch_bounds__(kBlock) k_spmv(OpView<T> m, const T* __restric
 template <typename T, int G, bool C16>
 __global__ void __launch_bounds__(kBlock) k_resid(OpView<T> m, const T* __restrict__ x, const T* __restrict__ b,
                                                   T* __restrict__ r) {
-  pdl_enter();
   int row;
   T ax;
   if (!op_row<T, G, C16>(m, x, row, ax) || !group_leader<G>()) return;
@@ -275,7 +257,6 @@ template <typename T, int G, bool C16, bool FIRST>
 __global__ void __launch_bounds__(kBlock) k_cheb(OpView<T> m, const T* __restrict__ xin, const T* __restrict__ b,
                                                  const T* __restrict__ dinv, T* __restrict__ d, T* __restrict__ xout,
                                                  T cd, T cr) {
-  pdl_enter();
   int row;
   T ax;
   if (!op_row<T, G, C16>(m, xin, row, ax) || !group_leader<G>()) return;
@@ -288,7 +269,6 @@ __global__ void __launch_bounds__(kBlock) k_cheb(OpView<T> m, const T* __restric
 
 template <typename T, int G, bool C16>
 __global__ void __launch_bounds__(kBlock) k_prolong(OpView<T> m, const T* __restrict__ xc, T* __restrict__ x) {
-  pdl_enter();
   int row;
   T ax;
   if (!op_row<T, G, C16>(m, xc, row, ax) || !group_leader<G>()) return;
@@ -298,7 +278,6 @@ __global__ void __launch_bounds__(kBlock) k_prolong(OpView<T> m, const T* __rest
 template <typename T, int G, bool C16>
 __global__ void __launch_bounds__(kBlock) k_restrict(OpView<T> m, const T* __restrict__ r, T* __restrict__ bc,
                                                      T* __restrict__ xc) {
-  pdl_enter();
   int row;
   T ax;
   if (!op_row<T, G, C16>(m, r, row, ax) || !group_leader<G>()) return;
@@ -314,7 +293,6 @@ template <typename T, int G, bool C16>
 __global__ void __launch_bounds__(kBlock) k_gs(OpView<T> m, const int32_t* __restrict__ rows,
                                                const T* __restrict__ xr, const T* __restrict__ b,
                                                const T* __restrict__ dinv, T* x) {
-  pdl_enter();
   int r;
   T s;
   if (!op_row<T, G, C16>(m, xr, r, s) || !group_leader<G>()) return;
@@ -440,7 +418,6 @@ __device__ void reduce_finish(double s, const Reduce& rd) {
 template <int G, bool C16>
 __global__ void __launch_bounds__(kBlock) k_ap(OpView<double> m, const double* __restrict__ p, double* __restrict__ q,
                                                double* __restrict__ part) {
-  pdl_enter();
   int row;
   double ap;
   double v = 0.0;
@@ -455,7 +432,6 @@ __global__ void __launch_bounds__(kBlock) k_ap(OpView<double> m, const double* _
 // One block: the sum of part[0..nparts) in a fixed order (eight loads in flight per
 // thread), then op applied to the CG state.
 __global__ void __launch_bounds__(1024) k_finish(int nparts, const double* __restrict__ part, CgState* st, int op) {
-  pdl_enter();
   double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   int i = threadIdx.x;
   for (; i + 7 * 1024 < nparts; i += 8 * 1024) {
@@ -477,7 +453,6 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock) k_cheb0_all(int n, const T* __restrict__ b, const T* __restrict__ dinv,
                                                       const T* __restrict__ xin, T* __restrict__ d,
                                                       T* __restrict__ xout, T cr) {
-  pdl_enter();
   const int i = blockIdx.x * kBlock + threadIdx.x;
   if (i >= n) return;
   const T t = dinv[i] * b[i];
@@ -494,7 +469,6 @@ __global__ void __launch_bounds__(kBlock) k_cheb0_halo(int nh, const int32_t* __
                                                        const T* __restrict__ hv, const T* __restrict__ b,
                                                        const T* __restrict__ dinv, const T* __restrict__ xin,
                                                        T* __restrict__ d, T* __restrict__ xout, T cr) {
-  pdl_enter();
   const int t = (blockIdx.x * kBlock + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   T ax = T(0);
   if (t < nh)
@@ -516,7 +490,6 @@ __global__ void __launch_bounds__(kBlock) k_patch_residual(int nt, int w, const 
                                                            const int32_t* __restrict__ pci,
                                                            const double* __restrict__ pv, const T* __restrict__ b,
                                                            const T* __restrict__ x, double* __restrict__ rbuf) {
-  pdl_enter();
   const int t = (blockIdx.x * kBlock + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (t >= nt) return;  // warp-uniform
   const double bt = (double)b[pdofs[t]];
@@ -540,7 +513,6 @@ __global__ void __launch_bounds__(kBlock) k_patch_solve(const PatchItem* __restr
                                                         const int32_t* __restrict__ pdofs,
                                                         const double* __restrict__ inv, const double* rbuf,
                                                         const T* __restrict__ b, T* __restrict__ x) {
-  pdl_enter();
   extern __shared__ double rs[];
   constexpr int K = 8;  // inverse entries per lane loaded ahead of the barrier (256 per row)
   const PatchItem it = items[blockIdx.x];
@@ -576,7 +548,6 @@ __global__ void __launch_bounds__(kBlock) k_patch_solve(const PatchItem* __restr
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_dense_partial(int n, int kchunk, const double* __restrict__ X,
                                                           const T* __restrict__ b, double* __restrict__ part) {
-  pdl_enter();
   extern __shared__ double bs[];
   const int k0 = blockIdx.y * kchunk, k1 = min(n, k0 + kchunk);
   for (int j = k0 + threadIdx.x; j < k1; j += blockDim.x) bs[j - k0] = (double)b[j];
@@ -601,7 +572,6 @@ __global__ void __launch_bounds__(kBlock) k_dense_partial(int n, int kchunk, con
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_dense_reduce(int n, int nchunks, const double* __restrict__ part,
                                                          T* __restrict__ x) {
-  pdl_enter();
   const int i = (blockIdx.x * kBlock + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (i >= n) return;  // warp-uniform
   double s = 0.0;
@@ -612,25 +582,21 @@ __global__ void __launch_bounds__(kBlock) k_dense_reduce(int n, int nchunks, con
 
 template <typename Src, typename Dst>
 __global__ void k_convert(int n, const Src* __restrict__ a, Dst* __restrict__ b) {
-  pdl_enter();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = (Dst)a[i];
 }
 
 template <typename Src, typename Dst>
 __global__ void k_gather(int n, const int32_t* __restrict__ perm, const Src* __restrict__ a, Dst* __restrict__ b) {
-  pdl_enter();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = (Dst)a[perm[i]];
 }
 
 template <typename Src, typename Dst>
 __global__ void k_scatter(int n, const int32_t* __restrict__ perm, const Src* __restrict__ a, Dst* __restrict__ b) {
-  pdl_enter();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[perm[i]] = (Dst)a[i];
 }
 
 template <typename T>
 __global__ void k_axpy_from(int n, const T* __restrict__ z, double* __restrict__ x) {
-  pdl_enter();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] += (double)z[i];
 }
 
@@ -638,7 +604,6 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock) k_cg_init(int n, const double* __restrict__ b, double* __restrict__ r,
                                                     double* __restrict__ x, T* __restrict__ vb, T* __restrict__ vx,
                                                     Reduce rd) {
-  pdl_enter();
   double s = 0.0;
   for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
     const double bi = b[i];
@@ -656,7 +621,6 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(int n, const CgState* __re
                                                       const double* __restrict__ q, double* __restrict__ x,
                                                       double* __restrict__ r, T* __restrict__ vb, T* __restrict__ vx,
                                                       Reduce rd) {
-  pdl_enter();
   const double a = st->alpha;
   double s = 0.0;
   for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
@@ -673,7 +637,6 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(int n, const CgState* __re
 template <typename T, bool FIRST>
 __global__ void __launch_bounds__(kBlock) k_cg_dotz(int n, const double* __restrict__ r, const T* __restrict__ vx,
                                                     double* __restrict__ p, Reduce rd) {
-  pdl_enter();
   double s = 0.0;
   for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
     const double zi = (double)vx[i];
@@ -686,14 +649,12 @@ __global__ void __launch_bounds__(kBlock) k_cg_dotz(int n, const double* __restr
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_cg_pupdate(int n, const CgState* __restrict__ st, const T* __restrict__ vx,
                                                        double* __restrict__ p) {
-  pdl_enter();
   const double beta = st->beta;
   for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock)
     p[i] = fma(beta, p[i], (double)vx[i]);
 }
 
 __global__ void __launch_bounds__(kBlock) k_dot_self(int n, const double* __restrict__ r, Reduce rd) {
-  pdl_enter();
   double s = 0.0;
   for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) s = fma(r[i], r[i], s);
   reduce_finish(block_sum(s), rd);

@@ -163,8 +163,5 @@ template <typename T> void cg_pupdate(int n, const CgState* st, const T* vx, dou
 void dot_self(int n, const double* r, const Reduce& rd, cudaStream_t s);
 
 void check_launch(const char* what);
-// Programmatic dependent launch for the hot-path kernels launched by the calling host
-// thread from now on (captured into graphs as programmatic edges).
-void set_pdl(bool on);
 
 }  // namespace nnmg

@@ -49,7 +49,7 @@ def test_results_identical_alone_and_in_the_mix(nnmg):
         st = srv.stats()
     assert st["completed"] == len(reqs) and st["failed"] == 0 and st["peak_active"] >= 2
     for r, x, xa in zip(res, xs, alone):
-        assert r["status"] == 0 and r["true_rel_residual"] < 1.5e-8
+        assert r["status"] == 0 and 0.0 < r["true_rel_residual"] < 1.5e-8
         assert np.array_equal(x, xa)
 
 
