@@ -21,6 +21,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -108,7 +109,9 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.proc = None
         self.gpu = gpu_index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # nvidia-smi samples go to a scratch file (NNMG_CLOCKS_DIR, default the temp directory)
+        out = os.environ.get("NNMG_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out, f"nnmg_clocks_rank{gpu_index}.csv")
 
     def start(self):
         try:

@@ -306,7 +306,7 @@ int mg_time_smoother_kernel(mg_hierarchy_t* h, int32_t reps, void* stream, doubl
                             double* bytes_per_launch);
 
 /* ---- solve server: continuous batching of solve requests on one GPU ----------------
- * (the benchmark spec serving pattern; the paper has no serving counterpart.)
+ * (a serving pattern; the paper has no counterpart.)
  * Requests (a mesh hierarchy and a right-hand side) go through host set-up on worker
  * threads, wait for admission in submission order until their device-byte estimate fits
  * under the HBM budget and one of max_active slots is free, then are set up on the device
