@@ -98,7 +98,7 @@ def profiled_traffic():
     return None, None
 
 
-KERNEL_REV = "final-v9"   # bump when the timed kernel changes (invalidates the profiled traffic)
+KERNEL_REV = "v10"   # bump when the timed kernel changes (invalidates the profiled traffic)
 
 
 class ClockSampler:

@@ -253,7 +253,7 @@ SellMat<T> make_layout(const Csr& A, DevMem& mem, Layout L) {
 
 std::string layout_name(const Layout& c) {
   if (c.lanes > 1) return "v" + std::to_string(c.lanes);
-  return "s" + std::to_string(c.sigma) + (c.sub > 1 ? "x" + std::to_string(c.sub) : "") + (c.unroll == 2 ? "p" : "") +
+  return "s" + std::to_string(c.sigma) + (c.sub > 1 ? "x" + std::to_string(c.sub) : "") + (c.unroll == 2 ? "p" : (c.unroll == 3 ? "q" : (c.unroll == 4 ? "r" : ""))) +
          (c.pf > 0 ? "f" + std::to_string(c.pf) : "");
 }
 
@@ -307,7 +307,8 @@ void tune_store(const std::string& key, const Layout& L) {
 
 // Autotuner (sigma option 0): time y = A x on the device for each candidate layout and keep
 // the fastest. Candidates: SELL with one lane per row and windows 1, 256, 2048 (when sorting
-// removes padding), each with the scalar and the predicated row remainder; SELL with 2 and
+// removes padding), each with steps of four and a scalar or a predicated row remainder and
+// with predicated steps of eight and sixteen; SELL with 2 and
 // 4 lanes per row at the best window; CSR vector with 4, 8, 16, 32 lanes per row up to
 // twice the longest row; then, on large operators whose best layout is SELL, bulk L2
 // prefetch distances of half, one and two waves of slices. Timing: one warm-up launch,
@@ -331,6 +332,8 @@ SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log) {
     last_pad = pad;
     cand.push_back({1, c, 1, 1, 0});
     cand.push_back({1, c, 2, 1, 0});
+    cand.push_back({1, c, 3, 1, 0});
+    cand.push_back({1, c, 4, 1, 0});
   }
   DevMem scratch;
   scratch.stream = mem.stream;
@@ -430,12 +433,17 @@ struct Engine {
   bool local_on(int l) const {
     return lv[l].np > 0 && order != MG_SMOOTHER_GLOBAL && ((local_mask >> std::min(l, 31)) & 1u);
   }
-  // zero: 0 = general iterate, 1 = x is zero, 2 = x is zero outside the patch DoFs
+  // zero: 0 = general iterate, 1 = x is zero, 2 = x is zero outside the patch DoFs, 3 = x is
+  // zero and the S_c from zero that precedes the first step runs in the same launch
   void cheb(int l, cudaStream_t s, int zero = 0) {
     DevLevel<T>& L = lv[l];
     T *xa = L.x, *xb = L.xt;
     for (int j = 0; j < cheb_k; ++j) {
-      if (j == 0 && zero) {
+      if (j == 0 && zero == 3) {
+        cheb_entry_local<T>(L.nitems, L.items, L.pdofs, L.inv, L.max_patch, L.n, L.b, L.dinv, xa, L.d, xb, L.cr[0],
+                            L.nh, L.hrow, L.hrp, L.hci, L.hv, s);
+        launches += L.nh > 0 ? 2 : 1;
+      } else if (j == 0 && zero) {
         const int nh = zero == 2 ? L.nh : 0;
         cheb_first_from_zero<T>(L.n, L.b, L.dinv, xa, L.d, xb, L.cr[0], nh, L.hrow, L.hrp, L.hci, L.hv, s);
         launches += nh > 0 ? 2 : 1;
@@ -478,8 +486,12 @@ struct Engine {
       return;
     }
     if (order == MG_SMOOTHER_SANDWICH) {
-      local(l, s, zero);
-      global(l, s, zero ? 2 : 0);
+      if (zero && !sgs) {
+        cheb(l, s, 3);  // S_c from zero and the first Chebyshev step share a launch
+      } else {
+        local(l, s, zero);
+        global(l, s, zero ? 2 : 0);
+      }
       local(l, s);
     } else if (!post) {
       global(l, s, zero ? 1 : 0);

@@ -89,9 +89,11 @@ struct Col32 {
 // Sum over the w padded entries of one SELL-32 lane starting at element k (stride 32).
 // PRED = false: four entries per step (their value and index loads together, then the x
 // gathers, then the FMAs), the remaining w % 4 entries one at a time. PRED = true: every
-// step takes four entries, the last one predicated. Both perform the same FMAs in the same
-// order (identical results); which is faster depends on the operator and precision.
-template <typename T, bool PRED, typename C>
+// step takes STEP (4, 8 or 16) entries, the last one predicated: a wider step keeps more
+// loads in flight per thread at the cost of registers. All variants perform the same FMAs
+// in the same order (identical results); which is fastest depends on the operator and
+// precision.
+template <typename T, bool PRED, int STEP = 4, typename C>
 __device__ __forceinline__ T sell_lane(const T* __restrict__ vp, int64_t k, int w, C col, const T* __restrict__ x) {
   T acc = T(0);
   if constexpr (!PRED) {
@@ -113,26 +115,26 @@ __device__ __forceinline__ T sell_lane(const T* __restrict__ vp, int64_t k, int 
       k += 32;
     }
   } else {
-    for (int j = 0; j < w; j += 4) {
-      T v[4], xv[4];
-      int c[4];
+    for (int j = 0; j < w; j += STEP) {
+      T v[STEP], xv[STEP];
+      int c[STEP];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) v[u] = j + u < w ? ld_stream(vp + 32 * u) : T(0);
+      for (int u = 0; u < STEP; ++u) v[u] = j + u < w ? ld_stream(vp + 32 * u) : T(0);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) c[u] = j + u < w ? col(k + 32 * u) : 0;
+      for (int u = 0; u < STEP; ++u) c[u] = j + u < w ? col(k + 32 * u) : 0;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) xv[u] = j + u < w ? __ldg(x + c[u]) : T(0);
+      for (int u = 0; u < STEP; ++u) xv[u] = j + u < w ? __ldg(x + c[u]) : T(0);
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < STEP; ++u)
         if (j + u < w) acc = fma(v[u], xv[u], acc);
-      vp += 128;
-      k += 128;
+      vp += 32 * STEP;
+      k += 32 * STEP;
     }
   }
   return acc;
 }
 
-template <typename T, bool C16, bool PRED>
+template <typename T, bool C16, bool PRED, int STEP = 4>
 __device__ __forceinline__ T sell_row(const OpView<T>& m, const T* __restrict__ x, int srow) {
   const int s = srow >> 5, lane = srow & 31;
   if (m.pf > 0 && lane == 0 && s + m.pf < m.nslices) {
@@ -149,9 +151,9 @@ __device__ __forceinline__ T sell_row(const OpView<T>& m, const T* __restrict__ 
   const int w = (int)((m.off[s + 1] - o) >> 5);
   if constexpr (C16) {
     const int base = m.cbase[s];   // uniform across the warp (one slice per warp)
-    if (base >= 0) return sell_lane<T, PRED>(m.val + o + lane, o + lane, w, Col16{m.col16, base}, x);
+    if (base >= 0) return sell_lane<T, PRED, STEP>(m.val + o + lane, o + lane, w, Col16{m.col16, base}, x);
   }
-  return sell_lane<T, PRED>(m.val + o + lane, o + lane, w, Col32{m.col}, x);
+  return sell_lane<T, PRED, STEP>(m.val + o + lane, o + lane, w, Col32{m.col}, x);
 }
 
 // CSR-vector partial sum of one lane of a G-lane group over row entries [k, k1), four
@@ -176,12 +178,12 @@ __device__ __forceinline__ T csrv_lane(const T* __restrict__ val, int k, int k1,
 }
 
 // Kernel layout parameter G: 1 = SELL, one lane per row (steps of four, scalar remainder);
-// 2 = the same with predicated steps; 3 = SELL with 2 lanes per row and 5 = SELL with 4
-// lanes per row (predicated steps; a row's partial sums are combined by xor shuffles);
-// G in {4, 8, 16, 32} = CSR vector with G lanes per row.
+// 2 = the same with predicated steps; 6 / 7 = predicated steps of 8 / 16; 3 = SELL with 2 lanes
+// per row and 5 = SELL with 4 lanes per row (predicated steps; a row's partial sums are
+// combined by xor shuffles); G in {4, 8, 16, 32} = CSR vector with G lanes per row.
 template <int G>
 __host__ __device__ constexpr bool is_sell() {
-  return G == 1 || G == 2 || G == 3 || G == 5;
+  return G == 1 || G == 2 || G == 3 || G == 5 || G == 6 || G == 7;
 }
 template <int G>
 __host__ __device__ constexpr int sell_sub() {
@@ -197,7 +199,7 @@ __device__ __forceinline__ bool op_row(const OpView<T>& m, const T* __restrict__
   if constexpr (is_sell<G>() && sell_sub<G>() == 1) {
     if (tid >= m.nrows) return false;
     row = m.perm ? m.perm[tid] : tid;
-    acc = sell_row<T, C16, G == 2>(m, x, tid);
+    acc = sell_row<T, C16, G != 1, G == 6 ? 8 : (G == 7 ? 16 : 4)>(m, x, tid);
     return true;
   } else if constexpr (is_sell<G>()) {
     // one warp per slice (warp-uniform bounds), every lane runs the slice's steps and the
@@ -509,13 +511,10 @@ __global__ void __launch_bounds__(kBlock) k_patch_residual(int nt, int w, const 
 // that stages the patch residual in shared memory. With rbuf == nullptr the iterate is zero
 // and the residual is b itself.
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_patch_solve(const PatchItem* __restrict__ items,
-                                                        const int32_t* __restrict__ pdofs,
-                                                        const double* __restrict__ inv, const double* rbuf,
-                                                        const T* __restrict__ b, T* __restrict__ x) {
-  extern __shared__ double rs[];
+__device__ __forceinline__ void patch_item(const PatchItem it, const int32_t* __restrict__ pdofs,
+                                           const double* __restrict__ inv, const double* rbuf,
+                                           const T* __restrict__ b, T* __restrict__ x, double* rs) {
   constexpr int K = 8;  // inverse entries per lane loaded ahead of the barrier (256 per row)
-  const PatchItem it = items[blockIdx.x];
   const int p0 = it.p0, n = it.n;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = it.row0 + warp;
@@ -543,6 +542,40 @@ __global__ void __launch_bounds__(kBlock) k_patch_solve(const PatchItem* __restr
   }
   e = warp_sum(e);
   if (lane == 0) x[g] = (T)((double)xg + e);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_patch_solve(const PatchItem* __restrict__ items,
+                                                        const int32_t* __restrict__ pdofs,
+                                                        const double* __restrict__ inv, const double* rbuf,
+                                                        const T* __restrict__ b, T* __restrict__ x) {
+  extern __shared__ double rs[];
+  patch_item<T>(items[blockIdx.x], pdofs, inv, rbuf, b, x, rs);
+}
+
+// Start of a pre-smoothing S_c, S_g, ... from a zero iterate, in one launch: blocks
+// [0, nitems) run the S_c work items with residual b (x_B = (A^[d])^{-1} b_B into x), the
+// others the first Chebyshev step for every row as if x were zero everywhere (d = cr D^{-1} b,
+// x_out = d). The two parts write disjoint arrays (x; d and x_out). The rows coupled to patch
+// DoFs, whose residual does see x_B, are redone afterwards by k_cheb0_halo.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_cheb0_entry(int nitems, const PatchItem* __restrict__ items,
+                                                        const int32_t* __restrict__ pdofs,
+                                                        const double* __restrict__ inv, int n,
+                                                        const T* __restrict__ b, const T* __restrict__ dinv,
+                                                        T* __restrict__ x, T* __restrict__ d, T* __restrict__ xout,
+                                                        T cr) {
+  extern __shared__ double rs[];
+  if ((int)blockIdx.x < nitems) {  // block-uniform
+    patch_item<T>(items[blockIdx.x], pdofs, inv, nullptr, b, x, rs);
+    return;
+  }
+  const int i = ((int)blockIdx.x - nitems) * kBlock + threadIdx.x;
+  if (i >= n) return;
+  const T t = dinv[i] * b[i];
+  const T dn = cr * t;
+  d[i] = dn;
+  xout[i] = dn;
 }
 
 template <typename T>
@@ -810,6 +843,8 @@ void by_layout(int lanes, int unroll, int sub, bool c16, F&& f) {
         if (sub == 2) f(Lay<3, C>());
         else if (sub == 4) f(Lay<5, C>());
         else if (unroll == 2) f(Lay<2, C>());
+        else if (unroll == 3) f(Lay<6, C>());
+        else if (unroll == 4) f(Lay<7, C>());
         else f(Lay<1, C>());
         break;
       case 4: f(Lay<4, C>()); break;
@@ -908,7 +943,21 @@ void patch_solve_setup(int max_patch) {
   if (smem > 48 * 1024) {
     cudaFuncSetAttribute(k_patch_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(k_patch_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_cheb0_entry<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_cheb0_entry<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
+}
+
+template <typename T>
+void cheb_entry_local(int nitems, const PatchItem* items, const int32_t* pdofs, const double* inv, int max_patch,
+                      int n, const T* b, const T* dinv, T* x, T* d, T* xout, double cr, int nh, const int32_t* hrow,
+                      const int32_t* hrp, const int32_t* hci, const T* hv, cudaStream_t s) {
+  if (n == 0) return;
+  const size_t smem = (size_t)max_patch * sizeof(double);
+  launch(k_cheb0_entry<T>, nitems + grid_for(n, kBlock), kBlock, smem, s, nitems, items, pdofs, inv, n, b, dinv, x,
+         d, xout, (T)cr);
+  if (nh > 0)
+    launch(k_cheb0_halo<T>, grid_for(nh, kBlock / 32), kBlock, 0, s, nh, hrow, hrp, hci, hv, b, dinv, x, d, xout, (T)cr);
 }
 
 template <typename T>
@@ -991,6 +1040,9 @@ void dot_self(int n, const double* r, const Reduce& rd, cudaStream_t s) {
                                    double*, cudaStream_t);                                                \
   template void patch_solve<T>(int, const PatchItem*, const int32_t*, const double*, const double*, const T*, T*, \
                                 int, cudaStream_t);                                                      \
+  template void cheb_entry_local<T>(int, const PatchItem*, const int32_t*, const double*, int, int, const T*,     \
+                                    const T*, T*, T*, T*, double, int, const int32_t*, const int32_t*,           \
+                                    const int32_t*, const T*, cudaStream_t);                                     \
   template void dense_solve<T>(int, const double*, const T*, T*, double*, int, cudaStream_t);                    \
   template void axpy_from<T>(int, const T*, double*, cudaStream_t);                                              \
   template void cg_init<T>(int, const double*, double*, double*, T*, T*, const Reduce&, cudaStream_t);         \

@@ -25,7 +25,7 @@ struct SellMat {
   int32_t* perm = nullptr;  // [nrows] matrix row held by each slot, or null (identity)
   int32_t sigma = 1;        // window within which rows were sorted by length
   int32_t lanes = 1;        // 1: SELL-32 (off/col/val/perm); G > 1: CSR vector (rp/col/val)
-  int32_t unroll = 1;       // SELL-32 row loop: 1 = steps of 4 + scalar remainder, 2 = predicated steps
+  int32_t unroll = 1;       // SELL-32 row loop: 1 = steps of 4 + scalar remainder, 2 = predicated steps of 4, 3 = of 8, 4 = of 16
   int32_t pf = 0;           // SELL: slices ahead whose data a warp prefetches into L2 (0 = none)
   int32_t sub = 1;          // SELL: lanes per row (1, 2, 4); a slice holds 32/sub rows whose
                             // entries j of row r sit at lane r*sub + j%sub of step j/sub
@@ -109,6 +109,14 @@ void patch_solve_setup(int max_patch);
 template <typename T>
 void patch_solve(int nitems, const PatchItem* items, const int32_t* pdofs, const double* inv, const double* rbuf,
                  const T* b, T* x, int max_patch, cudaStream_t s);
+// Start of a sandwich pre-smoothing from a zero iterate in one launch (plus the halo rows):
+// x_B = (A^[d])^{-1} b_B on every patch, d = cr D^{-1} b and x_out = d on every row, then the
+// rows coupled to patch DoFs (hrow, with their rows of A in hrp/hci/hv) recomputed with
+// r = b - A x. x must be zero outside the patch DoFs on entry.
+template <typename T>
+void cheb_entry_local(int nitems, const PatchItem* items, const int32_t* pdofs, const double* inv, int max_patch,
+                      int n, const T* b, const T* dinv, T* x, T* d, T* xout, double cr, int nh, const int32_t* hrow,
+                      const int32_t* hrp, const int32_t* hci, const T* hv, cudaStream_t s);
 
 // ---- coarsest level: x = X b with X = A_L^{-1} dense symmetric (split-K, deterministic) ----
 template <typename T>
