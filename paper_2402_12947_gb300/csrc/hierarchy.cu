@@ -253,7 +253,7 @@ SellMat<T> make_layout(const Csr& A, DevMem& mem, Layout L) {
 
 std::string layout_name(const Layout& c) {
   if (c.lanes > 1) return "v" + std::to_string(c.lanes);
-  return "s" + std::to_string(c.sigma) + (c.sub > 1 ? "x" + std::to_string(c.sub) : "") + (c.unroll == 2 ? "p" : (c.unroll == 3 ? "q" : (c.unroll == 4 ? "r" : ""))) +
+  return "s" + std::to_string(c.sigma) + (c.sub > 1 ? "x" + std::to_string(c.sub) : "") + (c.unroll == 2 ? "p" : (c.unroll == 3 ? "q" : "")) +
          (c.pf > 0 ? "f" + std::to_string(c.pf) : "");
 }
 
@@ -308,11 +308,11 @@ void tune_store(const std::string& key, const Layout& L) {
 // Autotuner (sigma option 0): time y = A x on the device for each candidate layout and keep
 // the fastest. Candidates: SELL with one lane per row and windows 1, 256, 2048 (when sorting
 // removes padding), each with steps of four and a scalar or a predicated row remainder and
-// with predicated steps of eight and sixteen; SELL with 2 and
+// with predicated steps of eight; SELL with 2 and
 // 4 lanes per row at the best window; CSR vector with 4, 8, 16, 32 lanes per row up to
 // twice the longest row; then, on large operators whose best layout is SELL, bulk L2
 // prefetch distances of half, one and two waves of slices. Timing: one warm-up launch,
-// then the mean of 5 launches between CUDA events.
+// then the mean of 5 launches between CUDA events, the best of three rounds.
 template <typename T>
 SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log) {
   if (sigma != 0 || A.nrows == 0) return make_sell<T>(A, mem, std::max(sigma, 1));
@@ -333,7 +333,6 @@ SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log) {
     cand.push_back({1, c, 1, 1, 0});
     cand.push_back({1, c, 2, 1, 0});
     cand.push_back({1, c, 3, 1, 0});
-    cand.push_back({1, c, 4, 1, 0});
   }
   DevMem scratch;
   scratch.stream = mem.stream;
@@ -345,31 +344,42 @@ SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log) {
   CK(cudaEventCreate(&e1));
   Layout best = cand[0];
   float best_ms = -1.f;
+  // Candidates that share a storage (lanes, window, lanes per row) are built once and timed
+  // in three interleaved rounds; each keeps its fastest round, so that a slow moment of the
+  // device does not decide between layouts that differ only in the row loop.
   auto try_layouts = [&](const std::vector<Layout>& cs) {
     DevMem trial;
     trial.stream = st;
-    SellMat<T> S;
-    Layout built{0, 0, 0, 0, 0};
-    for (const Layout& c : cs) {
-      if (c.lanes != built.lanes || c.sigma != built.sigma || c.sub != built.sub) {
-        trial.release();
-        S = make_layout<T>(A, trial, c);
-        built = c;
+    for (size_t g0 = 0; g0 < cs.size();) {
+      size_t g1 = g0 + 1;
+      while (g1 < cs.size() && cs[g1].lanes == cs[g0].lanes && cs[g1].sigma == cs[g0].sigma && cs[g1].sub == cs[g0].sub)
+        ++g1;
+      trial.release();
+      SellMat<T> S = make_layout<T>(A, trial, cs[g0]);
+      std::vector<float> tbest(g1 - g0, -1.f);
+      for (int round = 0; round < 3; ++round)
+        for (size_t i = g0; i < g1; ++i) {
+          const Layout& c = cs[i];
+          S.unroll = c.unroll;
+          S.pf = c.lanes > 1 ? 0 : c.pf;
+          sell_spmv<T>(S, x, y, st);
+          CK(cudaEventRecord(e0, st));
+          for (int rep = 0; rep < 5; ++rep) sell_spmv<T>(S, x, y, st);
+          CK(cudaEventRecord(e1, st));
+          CK(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          CK(cudaEventElapsedTime(&ms, e0, e1));
+          if (tbest[i - g0] < 0 || ms < tbest[i - g0]) tbest[i - g0] = ms;
+        }
+      for (size_t i = g0; i < g1; ++i) {
+        const float ms = tbest[i - g0];
+        if (log) *log += " " + layout_name(cs[i]) + ":" + std::to_string((int)(ms / 5 * 1e3)) + "us";
+        if (best_ms < 0 || ms < best_ms) {
+          best_ms = ms;
+          best = cs[i];
+        }
       }
-      S.unroll = c.unroll;
-      S.pf = c.lanes > 1 ? 0 : c.pf;
-      sell_spmv<T>(S, x, y, st);
-      CK(cudaEventRecord(e0, st));
-      for (int rep = 0; rep < 5; ++rep) sell_spmv<T>(S, x, y, st);
-      CK(cudaEventRecord(e1, st));
-      CK(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, e0, e1));
-      if (log) *log += " " + layout_name(c) + ":" + std::to_string((int)(ms / 5 * 1e3)) + "us";
-      if (best_ms < 0 || ms < best_ms) {
-        best_ms = ms;
-        best = c;
-      }
+      g0 = g1;
     }
     trial.release();
   };
@@ -406,6 +416,10 @@ struct DevLevel {
   double* pv = nullptr;
   double *inv = nullptr, *rbuf = nullptr;
   PatchItem* items = nullptr;
+  // rows (A P)_{i,:} of the patch rows, ELL with apw entries each (the S_c after prolongation)
+  int apw = 0;
+  int32_t* apci = nullptr;
+  double* apv = nullptr;
   // rows coupled to patch DoFs, with their entries of A (first Chebyshev step after S_c)
   int nh = 0;
   int32_t *hrow = nullptr, *hrp = nullptr, *hci = nullptr;
@@ -473,14 +487,19 @@ struct Engine {
     if (sgs) sgs_sweep(l, s);
     else cheb(l, s, zero);
   }
-  void local(int l, cudaStream_t s, bool zero = false) {
+  // zero: the iterate is zero (residual b); rready: the patch residual is already in rbuf
+  void local(int l, cudaStream_t s, bool zero = false, bool rready = false) {
     DevLevel<T>& L = lv[l];
-    if (!zero) patch_residual<T>(L.nt, L.pw, L.pdofs, L.pci, L.pv, L.b, L.x, L.rbuf, s);
+    if (!zero && !rready) {
+      patch_residual<T>(L.nt, L.pw, L.pdofs, L.pci, L.pv, L.b, L.x, L.rbuf, s);
+      ++launches;
+    }
     patch_solve<T>(L.nitems, L.items, L.pdofs, L.inv, zero ? nullptr : L.rbuf, L.b, L.x, L.max_patch, s);
-    launches += zero ? 1 : 2;
+    ++launches;
   }
-  // zero: the iterate is zero on entry (first pre-smoothing on every level of a cycle)
-  void smooth(int l, bool post, cudaStream_t s, bool zero = false) {
+  // zero: the iterate is zero on entry (first pre-smoothing on every level of a cycle);
+  // rready: the residual of a leading S_c is already in rbuf (first post-smoothing)
+  void smooth(int l, bool post, cudaStream_t s, bool zero = false, bool rready = false) {
     if (!local_on(l)) {
       global(l, s, zero ? 1 : 0);
       return;
@@ -489,7 +508,7 @@ struct Engine {
       if (zero && !sgs) {
         cheb(l, s, 3);  // S_c from zero and the first Chebyshev step share a launch
       } else {
-        local(l, s, zero);
+        local(l, s, zero, rready);
         global(l, s, zero ? 2 : 0);
       }
       local(l, s);
@@ -497,7 +516,7 @@ struct Engine {
       global(l, s, zero ? 1 : 0);
       local(l, s);
     } else {
-      local(l, s);
+      local(l, s, false, rready);
       global(l, s);
     }
   }
@@ -517,6 +536,14 @@ struct Engine {
     sell_prolong<T>(lv[l].P, lv[l + 1].x, lv[l].x, s);
     ++launches;
   }
+  // Prolongation and, in the same launch, the residual of the first post-smoothing S_c
+  // (every post-smoothing order starts with S_c), from the residual kept by the restriction.
+  bool prolong_with_patch_residual(int l) const { return local_on(l) && lv[l].apw > 0; }
+  void prolong_pr(int l, cudaStream_t s) {
+    DevLevel<T>& L = lv[l];
+    sell_prolong_pr<T>(L.P, lv[l + 1].x, L.x, L.nt, L.apw, L.pdofs, L.apci, L.apv, L.res, L.rbuf, s);
+    ++launches;
+  }
   void cycle(int l, cudaStream_t s) {
     if (l == (int)lv.size() - 1) {
       coarse(s);
@@ -525,8 +552,10 @@ struct Engine {
     for (int k = 0; k < nu; ++k) smooth(l, false, s, k == 0);
     residual_restrict(l, s);
     cycle(l + 1, s);
-    prolong(l, s);
-    for (int k = 0; k < nu; ++k) smooth(l, true, s);
+    const bool pr = prolong_with_patch_residual(l);
+    if (pr) prolong_pr(l, s);
+    else prolong(l, s);
+    for (int k = 0; k < nu; ++k) smooth(l, true, s, false, pr && k == 0);
   }
 };
 
@@ -976,6 +1005,37 @@ void build_device(mg_hierarchy* h) {
                 halo[i] = 1;
                 break;
               }
+          // rows (A P)_{i,:} of the patch rows (columns sorted), ELL padded with (0, 0.0)
+          {
+            std::vector<std::vector<std::pair<int32_t, double>>> ap(D.nt);
+            std::vector<double> acc(H.P.ncols, 0.0);
+            std::vector<uint8_t> hit(H.P.ncols, 0);
+            std::vector<int32_t> cols;
+            int apw = 1;
+            for (int t = 0; t < D.nt; ++t) {
+              const int32_t i = H.patch_dofs[t];
+              cols.clear();
+              for (int32_t k = H.A.rp[i]; k < H.A.rp[i + 1]; ++k) {
+                const int32_t j = H.A.ci[k];
+                for (int32_t m = H.P.rp[j]; m < H.P.rp[j + 1]; ++m) {
+                  const int32_t c = H.P.ci[m];
+                  if (!hit[c]) hit[c] = 1, cols.push_back(c);
+                  acc[c] += H.A.v[k] * H.P.v[m];
+                }
+              }
+              std::sort(cols.begin(), cols.end());
+              for (int32_t c : cols) ap[t].push_back({c, acc[c]}), acc[c] = 0.0, hit[c] = 0;
+              apw = std::max(apw, (int)cols.size());
+            }
+            std::vector<int32_t> apci((size_t)D.nt * apw, 0);
+            std::vector<double> apv((size_t)D.nt * apw, 0.0);
+            for (int t = 0; t < D.nt; ++t)
+              for (size_t k = 0; k < ap[t].size(); ++k)
+                apci[(size_t)t * apw + k] = ap[t][k].first, apv[(size_t)t * apw + k] = ap[t][k].second;
+            D.apw = apw;
+            D.apci = mem.upload(apci);
+            D.apv = mem.upload(apv);
+          }
           std::vector<int32_t> hrow, hrp(1, 0), hci;
           std::vector<T> hv;
           for (int64_t i = 0; i < D.n; ++i)
@@ -1429,6 +1489,9 @@ int64_t estimate_device_bytes(const mg_hierarchy* h) {
       tot += 8 * m * m + 64 * m;
     }
     if (np > 0) tot += 16 * (int64_t)lv.A.nnz() / std::max<int64_t>(lv.A.nrows, 1) * (int64_t)lv.patch_dofs.size() * 4;
+    if (np > 0 && l + 1 < h->L)  // rows of A P on the patch rows
+      tot += 12 * (int64_t)lv.patch_dofs.size() * (lv.A.nnz() / std::max<int64_t>(lv.A.nrows, 1) + 1) *
+             (lv.P.nnz() / std::max<int64_t>(lv.P.nrows, 1) + 1);
   }
   const int64_t nc = h->host[h->L - 1].A.nrows;
   tot += 16 * nc * nc;  // coarse inverse and split-K partials

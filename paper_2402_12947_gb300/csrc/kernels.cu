@@ -89,7 +89,7 @@ struct Col32 {
 // Sum over the w padded entries of one SELL-32 lane starting at element k (stride 32).
 // PRED = false: four entries per step (their value and index loads together, then the x
 // gathers, then the FMAs), the remaining w % 4 entries one at a time. PRED = true: every
-// step takes STEP (4, 8 or 16) entries, the last one predicated: a wider step keeps more
+// step takes STEP (4 or 8) entries, the last one predicated: the wider step keeps twice the
 // loads in flight per thread at the cost of registers. All variants perform the same FMAs
 // in the same order (identical results); which is fastest depends on the operator and
 // precision.
@@ -178,12 +178,12 @@ __device__ __forceinline__ T csrv_lane(const T* __restrict__ val, int k, int k1,
 }
 
 // Kernel layout parameter G: 1 = SELL, one lane per row (steps of four, scalar remainder);
-// 2 = the same with predicated steps; 6 / 7 = predicated steps of 8 / 16; 3 = SELL with 2 lanes
+// 2 = the same with predicated steps; 6 = predicated steps of eight; 3 = SELL with 2 lanes
 // per row and 5 = SELL with 4 lanes per row (predicated steps; a row's partial sums are
 // combined by xor shuffles); G in {4, 8, 16, 32} = CSR vector with G lanes per row.
 template <int G>
 __host__ __device__ constexpr bool is_sell() {
-  return G == 1 || G == 2 || G == 3 || G == 5 || G == 6 || G == 7;
+  return G == 1 || G == 2 || G == 3 || G == 5 || G == 6;
 }
 template <int G>
 __host__ __device__ constexpr int sell_sub() {
@@ -199,7 +199,7 @@ __device__ __forceinline__ bool op_row(const OpView<T>& m, const T* __restrict__
   if constexpr (is_sell<G>() && sell_sub<G>() == 1) {
     if (tid >= m.nrows) return false;
     row = m.perm ? m.perm[tid] : tid;
-    acc = sell_row<T, C16, G != 1, G == 6 ? 8 : (G == 7 ? 16 : 4)>(m, x, tid);
+    acc = sell_row<T, C16, G != 1, G == 6 ? 8 : 4>(m, x, tid);
     return true;
   } else if constexpr (is_sell<G>()) {
     // one warp per slice (warp-uniform bounds), every lane runs the slice's steps and the
@@ -500,6 +500,34 @@ __global__ void __launch_bounds__(kBlock) k_patch_residual(int nt, int w, const 
   for (int k = lane; k < w; k += 32) s = fma(pv[r0 + k], (double)x[pci[r0 + k]], s);
   s = warp_sum(s);
   if (lane == 0) rbuf[t] = bt - s;
+}
+
+// Coarse-grid correction x += P x_c fused with the residual of the S_c that follows it: the
+// residual before the correction, res = b - A x (kept from the restriction), gives
+// r_B = res_B - (A P)_B x_c on the patch rows, with the rows (A P)_{i,:} of the patch rows
+// precomputed (ELL, w entries each, FP64). Blocks [0, nbp) run the prolongation, the others
+// one warp per patch row. Neither part reads what the other writes.
+template <typename T, int G, bool C16>
+__global__ void __launch_bounds__(kBlock) k_prolong_pr(OpView<T> m, const T* __restrict__ xc, T* __restrict__ x,
+                                                       int nbp, int nt, int w, const int32_t* __restrict__ pdofs,
+                                                       const int32_t* __restrict__ apci,
+                                                       const double* __restrict__ apv, const T* __restrict__ res,
+                                                       double* __restrict__ rbuf) {
+  if ((int)blockIdx.x >= nbp) {  // block-uniform
+    const int t = (((int)blockIdx.x - nbp) * kBlock + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (t >= nt) return;  // warp-uniform
+    const double rt = (double)res[pdofs[t]];
+    const int64_t r0 = (int64_t)t * w;
+    double acc = 0.0;
+    for (int k = lane; k < w; k += 32) acc = fma(apv[r0 + k], (double)xc[apci[r0 + k]], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) rbuf[t] = rt - acc;
+    return;
+  }
+  int row;
+  T ax;
+  if (!op_row<T, G, C16>(m, xc, row, ax) || !group_leader<G>()) return;
+  x[row] = x[row] + ax;
 }
 
 // S_c phase 2: e = (A^[d])^{-1} r_B and x_B += e, one launch over the work list. A work
@@ -844,7 +872,6 @@ void by_layout(int lanes, int unroll, int sub, bool c16, F&& f) {
         else if (sub == 4) f(Lay<5, C>());
         else if (unroll == 2) f(Lay<2, C>());
         else if (unroll == 3) f(Lay<6, C>());
-        else if (unroll == 4) f(Lay<7, C>());
         else f(Lay<1, C>());
         break;
       case 4: f(Lay<4, C>()); break;
@@ -887,6 +914,17 @@ void sell_cheb(const SellMat<T>& A, const T* xin, const T* b, const T* dinv, T* 
     else
       launch(k_cheb<T, G, L::c16, false>, op_blocks(A), kBlock, 0, s, view(A), xin, b, dinv, d, xout, (T)cd,
                                                                              (T)cr);
+  });
+}
+template <typename T>
+void sell_prolong_pr(const SellMat<T>& P, const T* xc, T* x, int nt, int w, const int32_t* pdofs, const int32_t* apci,
+                     const double* apv, const T* res, double* rbuf, cudaStream_t s) {
+  const int nbp = P.nrows == 0 ? 0 : op_blocks(P);
+  if (nbp + nt == 0) return;
+  by_layout(P.lanes, P.unroll, P.sub, P.col16 != nullptr, [&](auto g) {
+    using L = decltype(g);
+    launch(k_prolong_pr<T, L::lanes, L::c16>, nbp + grid_for(nt, kBlock / 32), kBlock, 0, s, view(P), xc, x, nbp, nt,
+           w, pdofs, apci, apv, res, rbuf);
   });
 }
 template <typename T>
@@ -1032,6 +1070,8 @@ void dot_self(int n, const double* r, const Reduce& rd, cudaStream_t s) {
   template void sell_cheb<T>(const SellMat<T>&, const T*, const T*, const T*, T*, T*, double, double, bool,      \
                              cudaStream_t);                                                                      \
   template void sell_prolong<T>(const SellMat<T>&, const T*, T*, cudaStream_t);                                  \
+  template void sell_prolong_pr<T>(const SellMat<T>&, const T*, T*, int, int, const int32_t*, const int32_t*,     \
+                                   const double*, const T*, double*, cudaStream_t);                             \
   template void sell_restrict<T>(const SellMat<T>&, const T*, T*, T*, cudaStream_t);                             \
   template void sell_gs<T>(const SellMat<T>&, const int32_t*, const T*, const T*, T*, cudaStream_t);             \
   template void cheb_first_from_zero<T>(int, const T*, const T*, const T*, T*, T*, double, int, const int32_t*, \

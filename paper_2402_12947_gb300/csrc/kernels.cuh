@@ -25,7 +25,7 @@ struct SellMat {
   int32_t* perm = nullptr;  // [nrows] matrix row held by each slot, or null (identity)
   int32_t sigma = 1;        // window within which rows were sorted by length
   int32_t lanes = 1;        // 1: SELL-32 (off/col/val/perm); G > 1: CSR vector (rp/col/val)
-  int32_t unroll = 1;       // SELL-32 row loop: 1 = steps of 4 + scalar remainder, 2 = predicated steps of 4, 3 = of 8, 4 = of 16
+  int32_t unroll = 1;       // SELL-32 row loop: 1 = steps of 4 + scalar remainder, 2 = predicated steps of 4, 3 = of 8
   int32_t pf = 0;           // SELL: slices ahead whose data a warp prefetches into L2 (0 = none)
   int32_t sub = 1;          // SELL: lanes per row (1, 2, 4); a slice holds 32/sub rows whose
                             // entries j of row r sit at lane r*sub + j%sub of step j/sub
@@ -85,6 +85,12 @@ void cheb_first_from_zero(int n, const T* b, const T* dinv, const T* xin, T* d, 
                           const int32_t* hrow, const int32_t* hrp, const int32_t* hci, const T* hv, cudaStream_t s);
 // x += P xc.
 template <typename T> void sell_prolong(const SellMat<T>& P, const T* xc, T* x, cudaStream_t s);
+// x += P x_c and, in the same launch, the residual of the S_c that follows on the nt patch
+// rows: rbuf[t] = res[pdofs[t]] - (A P)_{pdofs[t],:} x_c with res = b - A x before the
+// correction and the rows of A P in ELL form (apci/apv, w entries per row, FP64).
+template <typename T>
+void sell_prolong_pr(const SellMat<T>& P, const T* xc, T* x, int nt, int w, const int32_t* pdofs, const int32_t* apci,
+                     const double* apv, const T* res, double* rbuf, cudaStream_t s);
 // bc = R r and xc = 0 (xc has R.nrows entries).
 template <typename T> void sell_restrict(const SellMat<T>& R, const T* r, T* bc, T* xc, cudaStream_t s);
 // One colour of a multicolour Gauss-Seidel sweep: for each row r of M (the colour's rows,
