@@ -253,7 +253,8 @@ SellMat<T> make_layout(const Csr& A, DevMem& mem, Layout L) {
 
 std::string layout_name(const Layout& c) {
   if (c.lanes > 1) return "v" + std::to_string(c.lanes);
-  return "s" + std::to_string(c.sigma) + (c.sub > 1 ? "x" + std::to_string(c.sub) : "") + (c.unroll == 2 ? "p" : (c.unroll == 3 ? "q" : "")) +
+  const char* loop = c.unroll == 2 ? "p" : (c.unroll == 3 ? "q" : "");
+  return "s" + std::to_string(c.sigma) + (c.sub > 1 ? "x" + std::to_string(c.sub) : "") + loop +
          (c.pf > 0 ? "f" + std::to_string(c.pf) : "");
 }
 
