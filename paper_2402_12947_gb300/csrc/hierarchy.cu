@@ -149,7 +149,7 @@ void set_indices(SellMat<T>& S, DevMem& mem, const std::vector<int32_t>& col, st
 // sub lanes per row a slice holds 32/sub rows and entry j of its row r sits at step j/sub,
 // lane r*sub + j%sub; padding has value 0 and the slice's smallest column.
 template <typename T>
-SellMat<T> make_sell(const Csr& A, DevMem& mem, int sigma = 1, int sub = 1) {
+SellMat<T> make_sell(const Csr& A, DevMem& mem, int sigma = 1, int sub = 1, bool wide_only = false) {
   SellMat<T> S;
   const int R = 32 / sub;
   S.nrows = (int32_t)A.nrows;
@@ -205,10 +205,28 @@ SellMat<T> make_sell(const Csr& A, DevMem& mem, int sigma = 1, int sub = 1) {
     base[sl] = (int64_t)mx - mn <= 65535 ? mn : -1;
     if (base[sl] >= 0) narrow_nnz += snnz[sl];
   }
+  if (wide_only) narrow_nnz = 0;  // 32-bit indices only
   set_indices(S, mem, col, base, narrow_nnz, [&](int32_t sl, auto&& f) {
     for (int64_t k = off[sl]; k < off[sl + 1]; ++k) f(k);
   });
   if (sigma > 1) S.perm = mem.upload(ord);
+  // chunks of whole slices for the TMA-staged kernel (one lane per row, 32-bit indices, every
+  // slice within one shared-memory stage)
+  const int64_t E = tma_stage_entries<T>();
+  bool fits = sub == 1 && S.col16 == nullptr && S.nslices > 0;
+  for (int32_t sl = 0; fits && sl < S.nslices; ++sl) fits = off[sl + 1] - off[sl] <= E;
+  if (fits) {
+    std::vector<int32_t> ch(1, 0);
+    int64_t acc = 0;
+    for (int32_t sl = 0; sl < S.nslices; ++sl) {
+      const int64_t n = off[sl + 1] - off[sl];
+      if (acc + n > E) ch.push_back(sl), acc = 0;
+      acc += n;
+    }
+    ch.push_back(S.nslices);
+    S.nchunks = (int32_t)ch.size() - 1;
+    S.chunks = mem.upload(ch);
+  }
   return S;
 }
 
@@ -245,15 +263,17 @@ struct Layout {
 
 template <typename T>
 SellMat<T> make_layout(const Csr& A, DevMem& mem, Layout L) {
-  SellMat<T> S = L.lanes > 1 ? make_csrv<T>(A, mem, L.lanes) : make_sell<T>(A, mem, L.sigma, L.sub);
+  // the TMA-staged kernel (unroll 5) streams 32-bit indices
+  SellMat<T> S = L.lanes > 1 ? make_csrv<T>(A, mem, L.lanes) : make_sell<T>(A, mem, L.sigma, L.sub, L.unroll == 5);
   S.unroll = L.unroll;
   S.pf = L.lanes > 1 ? 0 : L.pf;
+  S.tma = L.lanes == 1 && L.unroll == 5 && S.chunks != nullptr;
   return S;
 }
 
 std::string layout_name(const Layout& c) {
   if (c.lanes > 1) return "v" + std::to_string(c.lanes);
-  const char* loop = c.unroll == 2 ? "p" : (c.unroll == 3 ? "q" : "");
+  const char* loop = c.unroll == 2 ? "p" : (c.unroll == 3 ? "q" : (c.unroll == 5 ? "t" : ""));
   return "s" + std::to_string(c.sigma) + (c.sub > 1 ? "x" + std::to_string(c.sub) : "") + loop +
          (c.pf > 0 ? "f" + std::to_string(c.pf) : "");
 }
@@ -315,8 +335,19 @@ void tune_store(const std::string& key, const Layout& L) {
 // prefetch distances of half, one and two waves of slices. Timing: one warm-up launch,
 // then the mean of 5 launches between CUDA events, the best of three rounds.
 template <typename T>
-SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log) {
+SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log, bool allow_tma = false) {
   if (sigma != 0 || A.nrows == 0) return make_sell<T>(A, mem, std::max(sigma, 1));
+  const char* force = std::getenv("NNMG_FORCE_LAYOUT");
+  if (allow_tma && force && std::string(force) == "tma") {  // test hook: the TMA-staged kernel wherever it fits
+    DevMem trial;
+    trial.stream = mem.stream;
+    const bool fits = make_layout<T>(A, trial, {1, 1, 5, 1, 0}).tma != 0;
+    trial.release();
+    if (fits) {
+      if (log) *log += " forced " + layout_name({1, 1, 5, 1, 0});
+      return make_layout<T>(A, mem, {1, 1, 5, 1, 0});
+    }
+  }
   const std::string key = tune_key(A, (int)sizeof(T));
   Layout cached{};
   if (tune_lookup(key, &cached)) {
@@ -334,6 +365,7 @@ SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log) {
     cand.push_back({1, c, 1, 1, 0});
     cand.push_back({1, c, 2, 1, 0});
     cand.push_back({1, c, 3, 1, 0});
+    if (allow_tma) cand.push_back({1, c, 5, 1, 0});
   }
   DevMem scratch;
   scratch.stream = mem.stream;
@@ -353,16 +385,23 @@ SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log) {
     trial.stream = st;
     for (size_t g0 = 0; g0 < cs.size();) {
       size_t g1 = g0 + 1;
-      while (g1 < cs.size() && cs[g1].lanes == cs[g0].lanes && cs[g1].sigma == cs[g0].sigma && cs[g1].sub == cs[g0].sub)
+      while (g1 < cs.size() && cs[g1].lanes == cs[g0].lanes && cs[g1].sigma == cs[g0].sigma && cs[g1].sub == cs[g0].sub &&
+             (cs[g1].unroll == 5) == (cs[g0].unroll == 5))
         ++g1;
       trial.release();
       SellMat<T> S = make_layout<T>(A, trial, cs[g0]);
       std::vector<float> tbest(g1 - g0, -1.f);
+      std::vector<char> bad(g1 - g0, 0);
       for (int round = 0; round < 3; ++round)
         for (size_t i = g0; i < g1; ++i) {
           const Layout& c = cs[i];
           S.unroll = c.unroll;
           S.pf = c.lanes > 1 ? 0 : c.pf;
+          S.tma = c.lanes == 1 && c.unroll == 5 && S.chunks != nullptr;
+          if ((c.unroll == 5 && !S.tma) || bad[i - g0]) {
+            bad[i - g0] = 1;  // no chunk table for this storage, or a bounded wait gave up
+            continue;
+          }
           sell_spmv<T>(S, x, y, st);
           CK(cudaEventRecord(e0, st));
           for (int rep = 0; rep < 5; ++rep) sell_spmv<T>(S, x, y, st);
@@ -370,9 +409,11 @@ SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log) {
           CK(cudaEventSynchronize(e1));
           float ms = 0.f;
           CK(cudaEventElapsedTime(&ms, e0, e1));
+          if (S.tma && take_wait_timeout(st)) bad[i - g0] = 1;
           if (tbest[i - g0] < 0 || ms < tbest[i - g0]) tbest[i - g0] = ms;
         }
       for (size_t i = g0; i < g1; ++i) {
+        if (bad[i - g0]) continue;
         const float ms = tbest[i - g0];
         if (log) *log += " " + layout_name(cs[i]) + ":" + std::to_string((int)(ms / 5 * 1e3)) + "us";
         if (best_ms < 0 || ms < best_ms) {
@@ -589,6 +630,7 @@ struct mg_hierarchy {
   cudaStream_t own_stream = nullptr;
   int launches_vcycle = 0, launches_iter = 0;
   int64_t dropped_dofs = 0;  // DoFs excluded as dependent by the dense direct solves
+  bool uses_tma = false;     // some operator runs the TMA-staged kernel (bounded waits)
 
   bool mixed() const { return opt.precision == MG_PREC_MIXED; }
   template <typename F>
@@ -804,6 +846,7 @@ void finish_setup_host(mg_hierarchy* h) {
 void build_device(mg_hierarchy* h) {
   const mg_options_t& o = h->opt;
   const int L = h->L;
+  tma_prepare();
   PhaseTimer tm;
   const int64_t ncoarse = h->host[L - 1].A.nrows;
 
@@ -945,7 +988,8 @@ void build_device(mg_hierarchy* h) {
       if (!perm[l].empty()) D.perm = mem.upload(perm[l]);
       D.n = (int)H.A.nrows;
       std::string tlog;
-      D.A = tuned_sell<T>(H.A, mem, o.sell_sigma, &tlog);
+      D.A = tuned_sell<T>(H.A, mem, o.sell_sigma, &tlog, true);
+      h->uses_tma |= D.A.tma != 0;
       if (l < L - 1) {
         D.P = tuned_sell<T>(H.P, mem, o.sell_sigma, &tlog);
         D.R = tuned_sell<T>(H.R, mem, o.sell_sigma, &tlog);
@@ -1830,6 +1874,10 @@ int mg_solve(mg_hierarchy_t* h, const double* b, double* x, double rtol, int32_t
   int rc = run_solve(h, rtol, maxit, info, s);
   scatter<double, double>(h->n0, h->perm0, h->cx, x, s);
   CK(cudaStreamSynchronize(s));
+  if (h->uses_tma && take_wait_timeout(s)) {
+    h->err = "a bounded wait in the TMA-staged SpMV gave up; the result is not valid";
+    return MG_ERR_TIMEOUT;
+  }
   if (rc != MG_OK) h->err = rc == MG_ERR_BREAKDOWN ? "CG breakdown" : "no convergence within maxit";
   return rc;
   API_END_H(h)

@@ -287,6 +287,183 @@ __global__ void __launch_bounds__(kBlock) k_restrict(OpView<T> m, const T* __res
   xc[row] = T(0);
 }
 
+// ---- TMA-staged SELL SpMV -------------------------------------------------------------
+// A persistent kernel (grid = SMs x resident CTAs) for SELL with one lane per row and 32-bit
+// indices. Chunk c (a run of whole slices, at most E padded entries) goes to CTA c mod grid.
+// One producer thread streams each chunk's values and column indices into a shared-memory
+// stage with two bulk copies (cp.async.bulk, completion counted on the stage's "full"
+// mbarrier, L2 evict-first: the matrix is read once per pass, the vectors stay in L2); 16
+// consumer warps take one slice each per step, read the slice's entries from shared memory,
+// gather x from global memory and apply the epilogue to their rows, then release the stage
+// on its "empty" mbarrier. The row sum has the same FMAs in the same order as the register
+// variants. Every wait is bounded (about a second): on expiry the thread sets
+// g_wait_timeout and stops; the producer still waits (bounded) for its copies in flight.
+constexpr int kTmaConsumers = 16;
+constexpr int kTmaThreads = 32 * (kTmaConsumers + 1);
+constexpr int kTmaStages = 3;
+constexpr int kTmaBarBytes = 128;
+
+__device__ int g_wait_timeout;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+// Wait until the phase of parity `parity` has completed, for at most ~2^31 SM clocks (about
+// a second); false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > (1ll << 31)) {
+      atomicExch(&g_wait_timeout, 1);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+// bytes: a multiple of 16, both addresses 16-byte aligned
+__device__ __forceinline__ void bulk_to_smem(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+      : "memory");
+}
+
+// Epilogues: load() reads the row's vector operands (issued before the row's gathers),
+// store() finishes the row with the same arithmetic as the register kernels.
+template <typename T, bool FIRST>
+struct EpiCheb {
+  const T *b, *dinv, *xin;
+  T *d, *xout;
+  T cd, cr;
+  struct Pre {
+    T b, dinv, d, xin;
+  };
+  __device__ __forceinline__ Pre load(int row) const {
+    return Pre{b[row], dinv[row], FIRST ? T(0) : d[row], xin[row]};
+  }
+  __device__ __forceinline__ void store(int row, T ax, const Pre& p) const {
+    const T r = p.b - ax;
+    const T t = p.dinv * r;
+    const T dn = FIRST ? cr * t : fma(cd, p.d, cr * t);
+    d[row] = dn;
+    xout[row] = p.xin + dn;
+  }
+};
+template <typename T>
+struct EpiResid {
+  const T* b;
+  T* r;
+  struct Pre {
+    T b;
+  };
+  __device__ __forceinline__ Pre load(int row) const { return Pre{b[row]}; }
+  __device__ __forceinline__ void store(int row, T ax, const Pre& p) const { r[row] = p.b - ax; }
+};
+template <typename T>
+struct EpiSpmv {
+  T* y;
+  struct Pre {};
+  __device__ __forceinline__ Pre load(int) const { return Pre{}; }
+  __device__ __forceinline__ void store(int row, T ax, const Pre&) const { y[row] = ax; }
+};
+
+template <typename T, typename Epi>
+__global__ void __launch_bounds__(kTmaThreads, 1) k_sell_tma(OpView<T> m, const int32_t* __restrict__ chunks,
+                                                             int nchunks, const T* __restrict__ x, Epi epi) {
+  constexpr int E = tma_stage_entries<T>();
+  extern __shared__ __align__(128) unsigned char tsm[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(tsm);
+  uint64_t* empty = full + kTmaStages;
+  T* sval = reinterpret_cast<T*>(tsm + kTmaBarBytes);
+  int32_t* scol = reinterpret_cast<int32_t*>(tsm + kTmaBarBytes + (size_t)kTmaStages * E * sizeof(T));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTmaStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kTmaConsumers);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (warp == kTmaConsumers) {  // producer
+    if (lane != 0) return;
+    const uint64_t pol = l2_evict_first();
+    int k = 0;
+    for (int c = blockIdx.x; c < nchunks; c += gridDim.x, ++k) {
+      const int s = k % kTmaStages;
+      const int use = k / kTmaStages;
+      if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) break;
+      const int64_t e0 = m.off[chunks[c]], e1 = m.off[chunks[c + 1]];
+      const uint32_t n = (uint32_t)(e1 - e0);
+      if (n == 0) {
+        mbar_arrive(&full[s]);
+        continue;
+      }
+      mbar_expect_tx(&full[s], n * (uint32_t)(sizeof(T) + sizeof(int32_t)));
+      bulk_to_smem(sval + (size_t)s * E, m.val + e0, n * (uint32_t)sizeof(T), &full[s], pol);
+      bulk_to_smem(scol + (size_t)s * E, m.col + e0, n * (uint32_t)sizeof(int32_t), &full[s], pol);
+    }
+    // copies still in flight (normally consumed already) complete before the CTA exits
+    for (int j = k > kTmaStages ? k - kTmaStages : 0; j < k; ++j) mbar_wait(&full[j % kTmaStages], (j / kTmaStages) & 1);
+    return;
+  }
+  int k = 0;
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x, ++k) {
+    const int s = k % kTmaStages;
+    if (!mbar_wait(&full[s], (k / kTmaStages) & 1)) return;
+    const int s0 = chunks[c], s1 = chunks[c + 1];
+    const int64_t cb = m.off[s0];
+    const T* vs = sval + (size_t)s * E;
+    const int32_t* cs = scol + (size_t)s * E;
+    for (int sl = s0 + warp; sl < s1; sl += kTmaConsumers) {
+      const int slot = sl * 32 + lane;
+      const bool live = slot < m.nrows;
+      const int row = live ? (m.perm ? m.perm[slot] : slot) : 0;
+      typename Epi::Pre pre{};
+      if (live) pre = epi.load(row);
+      const int64_t o = m.off[sl];
+      const int w = (int)((m.off[sl + 1] - o) >> 5);
+      const int b0 = (int)(o - cb) + lane;
+      T acc = T(0);
+      for (int j = 0; j < w; j += 8) {
+        T v[8], xv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const bool ok = j + u < w;
+          v[u] = ok ? vs[b0 + (j + u) * 32] : T(0);
+          xv[u] = ok ? __ldg(x + cs[b0 + (j + u) * 32]) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (j + u < w) acc = fma(v[u], xv[u], acc);
+      }
+      if (live) epi.store(row, acc, pre);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+}
+
 // One colour of a multicolour Gauss-Seidel sweep. m holds the colour's rows without their
 // diagonal and without couplings between rows of the colour; rows[] maps its rows to the
 // level's. x_i = dinv_i (b_i - sum_j a_ij x_j). The kernel reads x (through xr) only at
@@ -885,9 +1062,67 @@ void by_layout(int lanes, int unroll, int sub, bool c16, F&& f) {
   else go(std::false_type());
 }
 
+bool take_wait_timeout(cudaStream_t s) {
+  static const int zero = 0;
+  int v = 0;
+  cudaMemcpyFromSymbolAsync(&v, g_wait_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  if (v) {
+    cudaMemcpyToSymbolAsync(g_wait_timeout, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s);
+    cudaStreamSynchronize(s);
+  }
+  return v != 0;
+}
+
+template <typename T>
+constexpr size_t tma_smem() {
+  return kTmaBarBytes + (size_t)kTmaStages * tma_stage_entries<T>() * (sizeof(T) + sizeof(int32_t));
+}
+
+// One-time set-up per instantiation (shared-memory limit, resident CTAs): thread-safe, and
+// run by tma_prepare() before any graph capture.
+template <typename T, typename Epi>
+int tma_grid_cap() {
+  static const int cap = [] {
+    auto kernel = k_sell_tma<T, Epi>;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem<T>());
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kTmaThreads, tma_smem<T>());
+    return std::max(1, sms * std::max(per, 1));
+  }();
+  return cap;
+}
+
+// Persistent launch of the TMA-staged SpMV with epilogue `epi`: as many CTAs as fit on the
+// device at once (one per SM at this shared-memory size), at most one per chunk.
+template <typename T, typename Epi>
+void launch_tma(const SellMat<T>& A, const T* x, const Epi& epi, cudaStream_t s) {
+  const int cap = tma_grid_cap<T, Epi>();
+  auto kernel = k_sell_tma<T, Epi>;
+  const size_t smem = tma_smem<T>();
+  const int grid = std::min(cap, A.nchunks);
+  if (grid <= 0) return;
+  launch(kernel, grid, kTmaThreads, smem, s, view(A), A.chunks, A.nchunks, x, epi);
+}
+
+template <typename T>
+void tma_prepare_t() {
+  tma_grid_cap<T, EpiSpmv<T>>();
+  tma_grid_cap<T, EpiResid<T>>();
+  tma_grid_cap<T, EpiCheb<T, true>>();
+  tma_grid_cap<T, EpiCheb<T, false>>();
+}
+void tma_prepare() {
+  tma_prepare_t<float>();
+  tma_prepare_t<double>();
+}
+
 template <typename T>
 void sell_spmv(const SellMat<T>& A, const T* x, T* y, cudaStream_t s) {
   if (A.nrows == 0) return;
+  if (A.tma) return launch_tma<T>(A, x, EpiSpmv<T>{y}, s);
   by_layout(A.lanes, A.unroll, A.sub, A.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
     launch(k_spmv<T, L::lanes, L::c16>, op_blocks(A), kBlock, 0, s, view(A), x, y);
@@ -896,6 +1131,7 @@ void sell_spmv(const SellMat<T>& A, const T* x, T* y, cudaStream_t s) {
 template <typename T>
 void sell_resid(const SellMat<T>& A, const T* x, const T* b, T* r, cudaStream_t s) {
   if (A.nrows == 0) return;
+  if (A.tma) return launch_tma<T>(A, x, EpiResid<T>{b, r}, s);
   by_layout(A.lanes, A.unroll, A.sub, A.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
     launch(k_resid<T, L::lanes, L::c16>, op_blocks(A), kBlock, 0, s, view(A), x, b, r);
@@ -905,6 +1141,10 @@ template <typename T>
 void sell_cheb(const SellMat<T>& A, const T* xin, const T* b, const T* dinv, T* d, T* xout, double cd, double cr,
                bool first, cudaStream_t s) {
   if (A.nrows == 0) return;
+  if (A.tma) {
+    if (first) return launch_tma<T>(A, xin, EpiCheb<T, true>{b, dinv, xin, d, xout, (T)cd, (T)cr}, s);
+    return launch_tma<T>(A, xin, EpiCheb<T, false>{b, dinv, xin, d, xout, (T)cd, (T)cr}, s);
+  }
   by_layout(A.lanes, A.unroll, A.sub, A.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
     constexpr int G = L::lanes;

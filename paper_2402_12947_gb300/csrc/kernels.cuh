@@ -36,7 +36,24 @@ struct SellMat {
   uint16_t* col16 = nullptr;
   int32_t* cbase = nullptr; // [nslices] (SELL) or [nrows] (CSR vector)
   double idx_bytes = 0;     // index bytes of the nonzeros (2 or 4 each), for the roofline
+  // TMA-staged variant (SELL, one lane per row, 32-bit indices): chunks[c] .. chunks[c+1]
+  // are the slices of chunk c, at most tma_stage_entries<T>() padded entries; tma = 1 runs
+  // the persistent kernel that streams the chunks into shared memory with bulk copies.
+  int32_t* chunks = nullptr;
+  int32_t nchunks = 0;
+  int32_t tma = 0;
 };
+
+// Padded entries of one shared-memory stage of the TMA-staged SpMV (values and indices).
+template <typename T>
+__host__ __device__ constexpr int tma_stage_entries() {
+  return sizeof(T) == 4 ? 4096 : 2048;
+}
+// A bounded wait in a kernel gave up (the kernel set a device flag and returned): reads and
+// clears the flag through stream s (synchronises s).
+bool take_wait_timeout(cudaStream_t s);
+// One-time set-up of the TMA-staged kernels (call before capturing a graph that uses them).
+void tma_prepare();
 
 // Device-side state of the preconditioned CG recurrence (all FP64).
 struct CgState {

@@ -296,3 +296,35 @@ def test_time_vcycle_per_level(nnmg):
     assert t[0] > t[-1]
     with pytest.raises(nnmg.NnmgError):
         H.time_vcycle(H.num_levels, reps=1)
+
+
+@pytest.mark.parametrize("name", ["c1_p2", "c2_p2_128", "cube_p2"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_tma_staged_spmv(nnmg, name, precision, monkeypatch):
+    """Every level operator on the TMA-staged kernel (bulk copies of slice chunks into shared
+    memory; the test hook forces it wherever it fits): the same V-cycle and solve as the oracle
+    in FP64, and a converged mixed-precision solve."""
+    monkeypatch.setenv("NNMG_FORCE_LAYOUT", "tma")
+    meshes, Ho, degree, layers = case(name)
+    lam = [lv.lmax for lv in Ho.levels[:-1]]
+    n = Ho.levels[0].n
+    b, x0 = rng_vec(n, 170), rng_vec(n, 171)
+    with nnmg.Hierarchy.from_meshes(meshes, degree, 0.1, patch_layers=layers, lambda_override=lam,
+                                    precision=precision) as H:
+        n1 = Ho.levels[1].n  # level 0's apply goes through the FP64 CG operator; level 1's does not
+        v = rng_vec(n1, 172)
+        y = torch.zeros(n1, dtype=torch.float64, device="cuda")
+        H.apply_A(1, dev(v), y)
+        assert rel_err(host(y), Ho.levels[1].A @ v) < (TOL64 if precision == "fp64" else 1e-5)
+        xs = torch.zeros(n, dtype=torch.float64, device="cuda")
+        if precision == "fp64":
+            x = dev(x0)
+            H.vcycle(dev(b), x)
+            assert rel_err(host(x), x0 + mg.vcycle(Ho, b - Ho.levels[0].A @ x0)) < TOL64
+            xr, itr, _, _ = mg.pcg(Ho, b, 1e-10)
+            info = H.solve(dev(b), xs, rtol=1e-10)
+            assert info["iterations"] == itr and rel_err(host(xs), xr) < 1e-9
+        else:
+            _, itr, _, _ = mg.pcg(Ho, b, 1e-8)
+            info = H.solve(dev(b), xs, rtol=1e-8)
+            assert info["converged"] and info["iterations"] <= itr + 1 and info["true_rel_residual"] < 1.5e-8
