@@ -328,8 +328,9 @@ void tune_store(const std::string& key, const Layout& L) {
 
 // Autotuner (sigma option 0): time y = A x on the device for each candidate layout and keep
 // the fastest. Candidates: SELL with one lane per row and windows 1, 256, 2048 (when sorting
-// removes padding), each with steps of four and a scalar or a predicated row remainder and
-// with predicated steps of eight; SELL with 2 and
+// removes padding), each with steps of four and a scalar or a predicated row remainder, with
+// predicated steps of eight and (level operators with at least 2^22 nonzeros) the TMA-staged
+// kernel; SELL with 2 and
 // 4 lanes per row at the best window; CSR vector with 4, 8, 16, 32 lanes per row up to
 // twice the longest row; then, on large operators whose best layout is SELL, bulk L2
 // prefetch distances of half, one and two waves of slices. Timing: one warm-up launch,
@@ -365,7 +366,7 @@ SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log, bo
     cand.push_back({1, c, 1, 1, 0});
     cand.push_back({1, c, 2, 1, 0});
     cand.push_back({1, c, 3, 1, 0});
-    if (allow_tma) cand.push_back({1, c, 5, 1, 0});
+    if (allow_tma && A.nnz() >= (int64_t)1 << 22) cand.push_back({1, c, 5, 1, 0});  // bandwidth-bound sizes only
   }
   DevMem scratch;
   scratch.stream = mem.stream;
