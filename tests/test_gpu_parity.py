@@ -328,3 +328,31 @@ def test_tma_staged_spmv(nnmg, name, precision, monkeypatch):
             _, itr, _, _ = mg.pcg(Ho, b, 1e-8)
             info = H.solve(dev(b), xs, rtol=1e-8)
             assert info["converged"] and info["iterations"] <= itr + 1 and info["true_rel_residual"] < 1.5e-8
+
+
+@pytest.mark.parametrize("order,nu,k", [("global_then_local", 1, 2), ("global", 1, 2), ("sandwich", 2, 3),
+                                        ("sandwich", 1, 1), ("global_then_local", 2, 1)])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_vcycle_orders_nu_degree(nnmg, order, nu, k, precision):
+    """The whole V-cycle (with its folded launches: the S_c from zero fused with the first
+    Chebyshev step, the post-smoothing S_c residual fused with the prolongation) for every
+    smoother order, nu = 1, 2 and odd/even Chebyshev degrees, against the oracle cycle with
+    the same options."""
+    from oracle import hierarchy
+    meshes, _, degree, layers = case("c2_p2_128")
+    Ho = hierarchy.build(meshes, degree, layers=layers, order=order, nu=nu, cheb_degree=k)
+    lam = [lv.lmax for lv in Ho.levels[:-1]]
+    n = Ho.levels[0].n
+    b, x0 = rng_vec(n, 180), rng_vec(n, 181)
+    ref = x0 + mg.vcycle(Ho, b - Ho.levels[0].A @ x0)
+    with nnmg.Hierarchy.from_meshes(meshes, degree, 0.1, patch_layers=layers, lambda_override=lam, smoother=order,
+                                    nu=nu, cheb_degree=k, precision=precision) as H:
+        x = dev(x0)
+        H.vcycle(dev(b), x)
+        # FP32 cycle: rounding amplified by cancellation on the ill-conditioned levels
+        assert rel_err(host(x), ref) < (TOL64 if precision == "fp64" else 1e-3)
+        if precision == "fp64":
+            xr, itr, _, _ = mg.pcg(Ho, b, 1e-10)
+            xs = torch.zeros(n, dtype=torch.float64, device="cuda")
+            info = H.solve(dev(b), xs, rtol=1e-10)
+            assert info["iterations"] == itr and rel_err(host(xs), xr) < 1e-9
