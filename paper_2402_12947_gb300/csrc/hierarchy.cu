@@ -5,7 +5,11 @@
 //                  recurse, x_l += P_l x_{l+1}, nu x S (post)
 //   level L-1:     x = A^{-1} b with the dense inverse (FP64)
 // where S is the combined smoother of Sec. 4.2: S_c, cheb_degree fused Chebyshev steps,
-// S_c (sandwich), or the global-then-local / global-only variants.
+// S_c (sandwich), or the global-then-local / global-only variants. Two launches are folded
+// into neighbours without changing what is computed: the first pre-smoothing S_c (from
+// x = 0, residual b) shares a launch with the first Chebyshev step, and the residual of the
+// S_c that opens the post-smoothing, b - A(x + P x_c) = r_l - (A P) x_c, is formed in the
+// prolongation's launch from the r_l kept by the restriction.
 // MG-PCG (Sec. 6.2) keeps x, r, p, q, z and every scalar in FP64; in MIXED precision the
 // V-cycle runs on FP32 copies of the operators (int32 indices) and of r, while the patch
 // residuals and solves and the coarsest solve stay FP64.

@@ -5,9 +5,12 @@
 //                  residual, the Jacobi scaling and the three-term update
 //   sell_resid +   residual and restriction b_{l+1} = P_l^T (b_l - A_l u_l) (Eq. 4),
 //   sell_restrict  R = P^T stored explicitly so that both are row-wise gathers
-//   sell_prolong   coarse-grid correction u_l += P_l u_{l+1} (Alg. 1)
+//   sell_prolong   coarse-grid correction u_l += P_l u_{l+1} (Alg. 1); sell_prolong_pr
+//                  also forms the residual of the S_c that follows it
 //   patch_*        local correction S_c (Sec. 4.1, Alg. 2): patch residual, then the dense
 //                  FP64 solve with (A^[d])^{-1} and the scatter back
+//   cheb_entry_local  S_c from a zero iterate and the first Chebyshev step in one launch
+//   k_sell_tma     TMA-staged variant of the SpMV family (bulk copies into shared memory)
 //   dense_solve    direct solve on the coarsest level (Alg. 1)
 //   cg_*           CG preconditioned by one V-cycle (Sec. 6.2), deterministic reductions
 #include <cuda_runtime.h>
