@@ -240,7 +240,9 @@ int mg_vcycle(mg_hierarchy_t* h, const double* b_dev, double* x_dev, void* strea
 
 /* V-cycle-preconditioned CG (Sec. 6.2) from x = 0 until ||r||_2/||b||_2 <= rtol or maxit
  * iterations; x_dev receives the solution. Blocks until the solve has finished and fills
- * *info (may be NULL). Returns MG_OK, MG_ERR_NO_CONVERGENCE or MG_ERR_BREAKDOWN. */
+ * *info (may be NULL). Returns MG_OK, MG_ERR_NO_CONVERGENCE or MG_ERR_BREAKDOWN, or
+ * MG_ERR_TIMEOUT when the autotuner chose the TMA-staged SpMV for some operator and one of
+ * its bounded waits gave up during the solve (the result is then not valid). */
 int mg_solve(mg_hierarchy_t* h, const double* b_dev, double* x_dev, double rtol, int32_t maxit,
              mg_solve_info_t* info, void* stream);
 
