@@ -459,13 +459,15 @@ struct DevLevel {
   std::vector<double> cd, cr;
   // local correction
   int np = 0, nt = 0, nitems = 0, max_patch = 0, pw = 0;
-  int32_t *pdofs = nullptr, *pci = nullptr;   // patch rows of A, ELL with pw entries per row
+  int32_t *pdofs = nullptr, *pci = nullptr;   // patch rows of A, ELL with pw slots per row
+  int32_t* plen = nullptr;                     // entries of each patch row
   double* pv = nullptr;
   double *inv = nullptr, *rbuf = nullptr;
   PatchItem* items = nullptr;
-  // rows (A P)_{i,:} of the patch rows, ELL with apw entries each (the S_c after prolongation)
+  // rows (A P)_{i,:} of the patch rows, ELL with apw slots each and aplen entries (the S_c
+  // after prolongation)
   int apw = 0;
-  int32_t* apci = nullptr;
+  int32_t *apci = nullptr, *aplen = nullptr;
   double* apv = nullptr;
   // rows coupled to patch DoFs, with their entries of A (first Chebyshev step after S_c)
   int nh = 0;
@@ -538,7 +540,7 @@ struct Engine {
   void local(int l, cudaStream_t s, bool zero = false, bool rready = false) {
     DevLevel<T>& L = lv[l];
     if (!zero && !rready) {
-      patch_residual<T>(L.nt, L.pw, L.pdofs, L.pci, L.pv, L.b, L.x, L.rbuf, s);
+      patch_residual<T>(L.nt, L.pw, L.pdofs, L.plen, L.pci, L.pv, L.b, L.x, L.rbuf, s);
       ++launches;
     }
     patch_solve<T>(L.nitems, L.items, L.pdofs, L.inv, zero ? nullptr : L.rbuf, L.b, L.x, L.max_patch, s);
@@ -588,7 +590,7 @@ struct Engine {
   bool prolong_with_patch_residual(int l) const { return local_on(l) && lv[l].apw > 0; }
   void prolong_pr(int l, cudaStream_t s) {
     DevLevel<T>& L = lv[l];
-    sell_prolong_pr<T>(L.P, lv[l + 1].x, L.x, L.nt, L.apw, L.pdofs, L.apci, L.apv, L.res, L.rbuf, s);
+    sell_prolong_pr<T>(L.P, lv[l + 1].x, L.x, L.nt, L.apw, L.pdofs, L.aplen, L.apci, L.apv, L.res, L.rbuf, s);
     ++launches;
   }
   void cycle(int l, cudaStream_t s) {
@@ -1017,15 +1019,17 @@ void build_device(mg_hierarchy* h) {
             pw = std::max(pw, H.A.rp[r + 1] - H.A.rp[r]);
           }
           D.pw = pw;
-          std::vector<int32_t> pci((size_t)D.nt * pw);
+          std::vector<int32_t> pci((size_t)D.nt * pw), plen(D.nt);
           std::vector<double> pv((size_t)D.nt * pw, 0.0);
           for (int t = 0; t < D.nt; ++t) {
             const int32_t r = H.patch_dofs[t];
             const int64_t o = (int64_t)t * pw;
             int j = 0;
             for (int32_t k = H.A.rp[r]; k < H.A.rp[r + 1]; ++k, ++j) pci[o + j] = H.A.ci[k], pv[o + j] = H.A.v[k];
+            plen[t] = j;
             for (; j < pw; ++j) pci[o + j] = r;
           }
+          D.plen = mem.upload(plen);
           // work list: the patches' row blocks, largest patches first
           std::vector<int> porder(D.np);
           for (int p = 0; p < D.np; ++p) porder[p] = p;
@@ -1077,13 +1081,16 @@ void build_device(mg_hierarchy* h) {
               for (int32_t c : cols) ap[t].push_back({c, acc[c]}), acc[c] = 0.0, hit[c] = 0;
               apw = std::max(apw, (int)cols.size());
             }
-            std::vector<int32_t> apci((size_t)D.nt * apw, 0);
+            std::vector<int32_t> apci((size_t)D.nt * apw, 0), aplen(D.nt);
             std::vector<double> apv((size_t)D.nt * apw, 0.0);
-            for (int t = 0; t < D.nt; ++t)
+            for (int t = 0; t < D.nt; ++t) {
+              aplen[t] = (int32_t)ap[t].size();
               for (size_t k = 0; k < ap[t].size(); ++k)
                 apci[(size_t)t * apw + k] = ap[t][k].first, apv[(size_t)t * apw + k] = ap[t][k].second;
+            }
             D.apw = apw;
             D.apci = mem.upload(apci);
+            D.aplen = mem.upload(aplen);
             D.apv = mem.upload(apv);
           }
           std::vector<int32_t> hrow, hrp(1, 0), hci;

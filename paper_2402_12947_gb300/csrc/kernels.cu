@@ -666,19 +666,34 @@ __global__ void __launch_bounds__(kBlock) k_cheb0_halo(int nh, const int32_t* __
   xout[i] = xin[i] + dn;
 }
 
+// Sum of row t of an ELL block (w slots per row, the row's len entries first) against x,
+// one warp per row, lane l taking entries l, l + 32, ...: the first 32 slots are loaded
+// without waiting for the row length (padding slots hold value 0 and a valid column), the
+// rest only up to len, so padded slots cost neither bytes nor FP64 FMAs beyond the first 32.
+template <typename T>
+__device__ __forceinline__ double ell_row_sum(int64_t r0, int w, int len, const int32_t* __restrict__ ci,
+                                              const double* __restrict__ v, const T* __restrict__ x, int lane) {
+  double s = 0.0;
+  if (lane < w) {
+    const double a = v[r0 + lane];
+    const double xv = (double)x[ci[r0 + lane]];
+    if (lane < len) s = fma(a, xv, s);
+  }
+  for (int k = lane + 32; k < len; k += 32) s = fma(v[r0 + k], (double)x[ci[r0 + k]], s);
+  return warp_sum(s);
+}
+
 // S_c phase 1: r_B = b_B - (A x)_B for every patch row, one warp per row (FP64).
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_patch_residual(int nt, int w, const int32_t* __restrict__ pdofs,
+                                                           const int32_t* __restrict__ plen,
                                                            const int32_t* __restrict__ pci,
                                                            const double* __restrict__ pv, const T* __restrict__ b,
                                                            const T* __restrict__ x, double* __restrict__ rbuf) {
   const int t = (blockIdx.x * kBlock + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (t >= nt) return;  // warp-uniform
   const double bt = (double)b[pdofs[t]];
-  const int64_t r0 = (int64_t)t * w;
-  double s = 0.0;
-  for (int k = lane; k < w; k += 32) s = fma(pv[r0 + k], (double)x[pci[r0 + k]], s);
-  s = warp_sum(s);
+  const double s = ell_row_sum<T>((int64_t)t * w, w, plen[t], pci, pv, x, lane);
   if (lane == 0) rbuf[t] = bt - s;
 }
 
@@ -690,6 +705,7 @@ __global__ void __launch_bounds__(kBlock) k_patch_residual(int nt, int w, const 
 template <typename T, int G, bool C16>
 __global__ void __launch_bounds__(kBlock) k_prolong_pr(OpView<T> m, const T* __restrict__ xc, T* __restrict__ x,
                                                        int nbp, int nt, int w, const int32_t* __restrict__ pdofs,
+                                                       const int32_t* __restrict__ aplen,
                                                        const int32_t* __restrict__ apci,
                                                        const double* __restrict__ apv, const T* __restrict__ res,
                                                        double* __restrict__ rbuf) {
@@ -697,10 +713,7 @@ __global__ void __launch_bounds__(kBlock) k_prolong_pr(OpView<T> m, const T* __r
     const int t = (((int)blockIdx.x - nbp) * kBlock + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (t >= nt) return;  // warp-uniform
     const double rt = (double)res[pdofs[t]];
-    const int64_t r0 = (int64_t)t * w;
-    double acc = 0.0;
-    for (int k = lane; k < w; k += 32) acc = fma(apv[r0 + k], (double)xc[apci[r0 + k]], acc);
-    acc = warp_sum(acc);
+    const double acc = ell_row_sum<T>((int64_t)t * w, w, aplen[t], apci, apv, xc, lane);
     if (lane == 0) rbuf[t] = rt - acc;
     return;
   }
@@ -1160,14 +1173,14 @@ void sell_cheb(const SellMat<T>& A, const T* xin, const T* b, const T* dinv, T* 
   });
 }
 template <typename T>
-void sell_prolong_pr(const SellMat<T>& P, const T* xc, T* x, int nt, int w, const int32_t* pdofs, const int32_t* apci,
-                     const double* apv, const T* res, double* rbuf, cudaStream_t s) {
+void sell_prolong_pr(const SellMat<T>& P, const T* xc, T* x, int nt, int w, const int32_t* pdofs, const int32_t* aplen,
+                     const int32_t* apci, const double* apv, const T* res, double* rbuf, cudaStream_t s) {
   const int nbp = P.nrows == 0 ? 0 : op_blocks(P);
   if (nbp + nt == 0) return;
   by_layout(P.lanes, P.unroll, P.sub, P.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
     launch(k_prolong_pr<T, L::lanes, L::c16>, nbp + grid_for(nt, kBlock / 32), kBlock, 0, s, view(P), xc, x, nbp, nt,
-           w, pdofs, apci, apv, res, rbuf);
+           w, pdofs, aplen, apci, apv, res, rbuf);
   });
 }
 template <typename T>
@@ -1213,10 +1226,10 @@ void cheb_first_from_zero(int n, const T* b, const T* dinv, const T* xin, T* d, 
 }
 
 template <typename T>
-void patch_residual(int nt, int w, const int32_t* pdofs, const int32_t* pci, const double* pv, const T* b, const T* x,
-                    double* rbuf, cudaStream_t s) {
+void patch_residual(int nt, int w, const int32_t* pdofs, const int32_t* plen, const int32_t* pci, const double* pv,
+                    const T* b, const T* x, double* rbuf, cudaStream_t s) {
   if (nt == 0) return;
-  launch(k_patch_residual<T>, grid_for(nt, kBlock / 32), kBlock, 0, s, nt, w, pdofs, pci, pv, b, x, rbuf);
+  launch(k_patch_residual<T>, grid_for(nt, kBlock / 32), kBlock, 0, s, nt, w, pdofs, plen, pci, pv, b, x, rbuf);
 }
 
 void patch_solve_setup(int max_patch) {
@@ -1314,13 +1327,13 @@ void dot_self(int n, const double* r, const Reduce& rd, cudaStream_t s) {
                              cudaStream_t);                                                                      \
   template void sell_prolong<T>(const SellMat<T>&, const T*, T*, cudaStream_t);                                  \
   template void sell_prolong_pr<T>(const SellMat<T>&, const T*, T*, int, int, const int32_t*, const int32_t*,     \
-                                   const double*, const T*, double*, cudaStream_t);                             \
+                                   const int32_t*, const double*, const T*, double*, cudaStream_t);             \
   template void sell_restrict<T>(const SellMat<T>&, const T*, T*, T*, cudaStream_t);                             \
   template void sell_gs<T>(const SellMat<T>&, const int32_t*, const T*, const T*, T*, cudaStream_t);             \
   template void cheb_first_from_zero<T>(int, const T*, const T*, const T*, T*, T*, double, int, const int32_t*, \
                                         const int32_t*, const int32_t*, const T*, cudaStream_t);                 \
-  template void patch_residual<T>(int, int, const int32_t*, const int32_t*, const double*, const T*, const T*,   \
-                                   double*, cudaStream_t);                                                \
+  template void patch_residual<T>(int, int, const int32_t*, const int32_t*, const int32_t*, const double*,       \
+                                   const T*, const T*, double*, cudaStream_t);                            \
   template void patch_solve<T>(int, const PatchItem*, const int32_t*, const double*, const double*, const T*, T*, \
                                 int, cudaStream_t);                                                      \
   template void cheb_entry_local<T>(int, const PatchItem*, const int32_t*, const double*, int, int, const T*,     \

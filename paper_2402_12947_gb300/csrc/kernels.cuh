@@ -104,10 +104,10 @@ void cheb_first_from_zero(int n, const T* b, const T* dinv, const T* xin, T* d, 
 template <typename T> void sell_prolong(const SellMat<T>& P, const T* xc, T* x, cudaStream_t s);
 // x += P x_c and, in the same launch, the residual of the S_c that follows on the nt patch
 // rows: rbuf[t] = res[pdofs[t]] - (A P)_{pdofs[t],:} x_c with res = b - A x before the
-// correction and the rows of A P in ELL form (apci/apv, w entries per row, FP64).
+// correction and the rows of A P in ELL form (apci/apv, w slots per row, aplen[t] entries).
 template <typename T>
-void sell_prolong_pr(const SellMat<T>& P, const T* xc, T* x, int nt, int w, const int32_t* pdofs, const int32_t* apci,
-                     const double* apv, const T* res, double* rbuf, cudaStream_t s);
+void sell_prolong_pr(const SellMat<T>& P, const T* xc, T* x, int nt, int w, const int32_t* pdofs, const int32_t* aplen,
+                     const int32_t* apci, const double* apv, const T* res, double* rbuf, cudaStream_t s);
 // bc = R r and xc = 0 (xc has R.nrows entries).
 template <typename T> void sell_restrict(const SellMat<T>& R, const T* r, T* bc, T* xc, cudaStream_t s);
 // One colour of a multicolour Gauss-Seidel sweep: for each row r of M (the colour's rows,
@@ -121,10 +121,11 @@ int sell_blocks(int nrows, int lanes);
 
 // ---- local correction S_c (two phases) ----
 // S_c phase 1: rbuf[t] = b[pdofs[t]] - (A x)[pdofs[t]] for the nt patch rows, stored
-// ELL-style with w entries per row (pci/pv [nt*w], padding has value 0).
+// ELL-style with w slots per row (pci/pv [nt*w]), row t's plen[t] entries first, padding
+// with value 0 and a valid column.
 template <typename T>
-void patch_residual(int nt, int w, const int32_t* pdofs, const int32_t* pci, const double* pv, const T* b, const T* x,
-                    double* rbuf, cudaStream_t s);
+void patch_residual(int nt, int w, const int32_t* pdofs, const int32_t* plen, const int32_t* pci, const double* pv,
+                    const T* b, const T* x, double* rbuf, cudaStream_t s);
 // Raise the dynamic shared-memory limit of the solve kernel for patches of up to max_patch DoFs.
 void patch_solve_setup(int max_patch);
 // S_c phase 2, x_B += (A^[d])^{-1} r_B, one block per work item; rbuf == nullptr: the
