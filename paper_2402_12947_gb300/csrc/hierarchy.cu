@@ -1508,9 +1508,11 @@ mg_hierarchy* build_host_hierarchy(const mg_mesh_t* levels, int32_t L, int32_t d
     f.P = prolongation(dms[l - 1], meshes[l], dms[l]);
     if (elastic) f.P = kron_identity(f.P, meshes[0].dim);
     f.R = transpose(f.P);
+    tm.mark("transfer L" + std::to_string(l));
     Csr AP = spgemm(f.A, f.P);
+    tm.mark("A P L" + std::to_string(l));
     H->host[l].A = unit_diagonal_on_empty_rows(spgemm(f.R, AP));
-    tm.mark("transfer+galerkin L" + std::to_string(l));
+    tm.mark("galerkin L" + std::to_string(l));
   }
   meshes.clear();
   dms.clear();

@@ -12,6 +12,8 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <mutex>
+#include <thread>
 
 #include "internal.hpp"
 
@@ -214,45 +216,31 @@ Csr transpose(const Csr& A) {
   return T;
 }
 
+// C = A B (Gustavson, one pass): each thread computes a contiguous block of rows into its own
+// buffers (entries accumulated in the order of A's row then B's row, columns sorted), then
+// the blocks are copied into place behind the row pointers.
 Csr spgemm(const Csr& A, const Csr& B) {
-  Csr C;
-  C.nrows = A.nrows;
-  C.ncols = B.ncols;
-  std::vector<int32_t> len(A.nrows);
-  int nt = num_threads();
-  // pass 1: row lengths
+  struct Block {
+    int64_t lo = 0, hi = 0;
+    std::vector<int32_t> len, ci;
+    std::vector<double> v;
+  };
+  std::mutex mu;
+  std::vector<Block> blocks;
   parallel_for(A.nrows, [&](int64_t lo, int64_t hi) {
-    std::vector<int64_t> mark(B.ncols, -1);
-    for (int64_t i = lo; i < hi; ++i) {
-      int32_t n = 0;
-      for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
-        int32_t r = A.ci[k];
-        for (int32_t q = B.rp[r]; q < B.rp[r + 1]; ++q)
-          if (mark[B.ci[q]] != i) mark[B.ci[q]] = i, ++n;
-      }
-      len[i] = n;
-    }
-  });
-  (void)nt;
-  C.rp.assign(A.nrows + 1, 0);
-  for (int64_t i = 0; i < A.nrows; ++i) {
-    if ((int64_t)C.rp[i] + len[i] > INT32_MAX) throw Error(MG_ERR_INVALID_ARG, "product nnz exceeds 2^31");
-    C.rp[i + 1] = C.rp[i] + len[i];
-  }
-  C.ci.resize(C.rp[A.nrows]);
-  C.v.resize(C.rp[A.nrows]);
-  // pass 2: values, accumulated in the order of A's row then B's row
-  parallel_for(A.nrows, [&](int64_t lo, int64_t hi) {
+    Block blk;
+    blk.lo = lo, blk.hi = hi;
+    blk.len.resize(hi - lo);
     std::vector<int64_t> mark(B.ncols, -1);
     std::vector<double> acc(B.ncols, 0.0);
     std::vector<int32_t> cols;
     for (int64_t i = lo; i < hi; ++i) {
       cols.clear();
       for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
-        int32_t r = A.ci[k];
-        double a = A.v[k];
+        const int32_t r = A.ci[k];
+        const double a = A.v[k];
         for (int32_t q = B.rp[r]; q < B.rp[r + 1]; ++q) {
-          int32_t j = B.ci[q];
+          const int32_t j = B.ci[q];
           if (mark[j] != i) {
             mark[j] = i;
             acc[j] = 0.0;
@@ -262,10 +250,34 @@ Csr spgemm(const Csr& A, const Csr& B) {
         }
       }
       std::sort(cols.begin(), cols.end());
-      int32_t pos = C.rp[i];
-      for (int32_t j : cols) C.ci[pos] = j, C.v[pos++] = acc[j];
+      blk.len[i - lo] = (int32_t)cols.size();
+      for (int32_t j : cols) blk.ci.push_back(j), blk.v.push_back(acc[j]);
     }
+    std::lock_guard<std::mutex> lk(mu);
+    blocks.push_back(std::move(blk));
   });
+  std::sort(blocks.begin(), blocks.end(), [](const Block& a, const Block& b) { return a.lo < b.lo; });
+  Csr C;
+  C.nrows = A.nrows;
+  C.ncols = B.ncols;
+  C.rp.assign(A.nrows + 1, 0);
+  int64_t tot = 0;
+  for (const Block& blk : blocks)
+    for (int64_t i = blk.lo; i < blk.hi; ++i) {
+      tot += blk.len[i - blk.lo];
+      if (tot > INT32_MAX) throw Error(MG_ERR_INVALID_ARG, "product nnz exceeds 2^31");
+      C.rp[i + 1] = (int32_t)tot;
+    }
+  C.ci.resize(tot);
+  C.v.resize(tot);
+  std::vector<std::thread> th;
+  for (const Block& blk : blocks)
+    th.emplace_back([&C, &blk] {
+      if (blk.ci.empty()) return;
+      std::memcpy(C.ci.data() + C.rp[blk.lo], blk.ci.data(), blk.ci.size() * sizeof(int32_t));
+      std::memcpy(C.v.data() + C.rp[blk.lo], blk.v.data(), blk.v.size() * sizeof(double));
+    });
+  for (auto& t : th) t.join();
   return C;
 }
 

@@ -395,7 +395,6 @@ Csr assemble_stiffness(const MeshH& m, const DofMapH& dm) {
   Csr A;
   A.nrows = A.ncols = dm.nfree;
   A.rp.assign(dm.nfree + 1, 0);
-  std::vector<std::vector<int32_t>> cols_tmp;  // unused; rows are built in two passes
   // pass 1: row patterns (free columns sharing a cell)
   std::vector<int32_t> rowlen(dm.nfree);
   parallel_for(dm.nfree, [&](int64_t lo, int64_t hi) {
