@@ -1,10 +1,15 @@
 // Internal host-side data structures and set-up routines of the nnmg library.
 #pragma once
 
+#include <algorithm>
+#include <climits>
 #include <cstdint>
+#include <cstring>
 #include <functional>
+#include <mutex>
 #include <stdexcept>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda_runtime_api.h>
@@ -76,6 +81,58 @@ struct LevelH {
 int num_threads();
 void set_thread_budget(int k);
 void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& body);
+
+// A CSR matrix built row by row in one parallel pass: each parallel_for block creates its
+// scratch with make_state() and appends row i's sorted columns and values through
+// fill(state, i, ci, v); the blocks are then copied into place behind the row pointers.
+template <typename MakeState, typename Fill>
+Csr csr_from_rows(int64_t nrows, int64_t ncols, MakeState&& make_state, Fill&& fill) {
+  struct Block {
+    int64_t lo = 0, hi = 0;
+    std::vector<int64_t> end;  // running entry count after each row of the block
+    std::vector<int32_t> ci;
+    std::vector<double> v;
+  };
+  std::vector<Block> blocks;
+  std::mutex mu;
+  parallel_for(nrows, [&](int64_t lo, int64_t hi) {
+    Block blk;
+    blk.lo = lo, blk.hi = hi;
+    blk.end.resize(hi - lo);
+    auto st = make_state();
+    for (int64_t i = lo; i < hi; ++i) {
+      fill(st, i, blk.ci, blk.v);
+      blk.end[i - lo] = (int64_t)blk.ci.size();
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    blocks.push_back(std::move(blk));
+  });
+  std::sort(blocks.begin(), blocks.end(), [](const Block& a, const Block& b) { return a.lo < b.lo; });
+  Csr C;
+  C.nrows = nrows;
+  C.ncols = ncols;
+  C.rp.assign(nrows + 1, 0);
+  int64_t base = 0;
+  for (const Block& blk : blocks) {
+    for (int64_t i = blk.lo; i < blk.hi; ++i) {
+      const int64_t e = base + blk.end[i - blk.lo];
+      if (e > INT32_MAX) throw Error(MG_ERR_INVALID_ARG, "nnz exceeds 2^31");
+      C.rp[i + 1] = (int32_t)e;
+    }
+    base += (int64_t)blk.ci.size();
+  }
+  C.ci.resize(base);
+  C.v.resize(base);
+  std::vector<std::thread> th;
+  for (const Block& blk : blocks)
+    th.emplace_back([&C, &blk] {
+      if (blk.ci.empty()) return;
+      std::memcpy(C.ci.data() + C.rp[blk.lo], blk.ci.data(), blk.ci.size() * sizeof(int32_t));
+      std::memcpy(C.v.data() + C.rp[blk.lo], blk.v.data(), blk.v.size() * sizeof(double));
+    });
+  for (auto& t : th) t.join();
+  return C;
+}
 
 // ---- setup_fem.cpp: DoF maps, assembly, quality, patches ----
 DofMapH build_dofmap(const MeshH& m, int degree);

@@ -12,8 +12,6 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
-#include <mutex>
-#include <thread>
 
 #include "internal.hpp"
 
@@ -216,69 +214,34 @@ Csr transpose(const Csr& A) {
   return T;
 }
 
-// C = A B (Gustavson, one pass): each thread computes a contiguous block of rows into its own
-// buffers (entries accumulated in the order of A's row then B's row, columns sorted), then
-// the blocks are copied into place behind the row pointers.
+// C = A B (Gustavson, one pass): row i accumulates in the order of A's row then B's row
+// and stores its columns sorted.
 Csr spgemm(const Csr& A, const Csr& B) {
-  struct Block {
-    int64_t lo = 0, hi = 0;
-    std::vector<int32_t> len, ci;
-    std::vector<double> v;
-  };
-  std::mutex mu;
-  std::vector<Block> blocks;
-  parallel_for(A.nrows, [&](int64_t lo, int64_t hi) {
-    Block blk;
-    blk.lo = lo, blk.hi = hi;
-    blk.len.resize(hi - lo);
-    std::vector<int64_t> mark(B.ncols, -1);
-    std::vector<double> acc(B.ncols, 0.0);
+  struct State {
+    std::vector<int64_t> mark;
+    std::vector<double> acc;
     std::vector<int32_t> cols;
-    for (int64_t i = lo; i < hi; ++i) {
-      cols.clear();
-      for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
-        const int32_t r = A.ci[k];
-        const double a = A.v[k];
-        for (int32_t q = B.rp[r]; q < B.rp[r + 1]; ++q) {
-          const int32_t j = B.ci[q];
-          if (mark[j] != i) {
-            mark[j] = i;
-            acc[j] = 0.0;
-            cols.push_back(j);
+  };
+  return csr_from_rows(
+      A.nrows, B.ncols, [&] { return State{std::vector<int64_t>(B.ncols, -1), std::vector<double>(B.ncols, 0.0), {}}; },
+      [&](State& st, int64_t i, std::vector<int32_t>& ci, std::vector<double>& v) {
+        st.cols.clear();
+        for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+          const int32_t r = A.ci[k];
+          const double a = A.v[k];
+          for (int32_t q = B.rp[r]; q < B.rp[r + 1]; ++q) {
+            const int32_t j = B.ci[q];
+            if (st.mark[j] != i) {
+              st.mark[j] = i;
+              st.acc[j] = 0.0;
+              st.cols.push_back(j);
+            }
+            st.acc[j] += a * B.v[q];
           }
-          acc[j] += a * B.v[q];
         }
-      }
-      std::sort(cols.begin(), cols.end());
-      blk.len[i - lo] = (int32_t)cols.size();
-      for (int32_t j : cols) blk.ci.push_back(j), blk.v.push_back(acc[j]);
-    }
-    std::lock_guard<std::mutex> lk(mu);
-    blocks.push_back(std::move(blk));
-  });
-  std::sort(blocks.begin(), blocks.end(), [](const Block& a, const Block& b) { return a.lo < b.lo; });
-  Csr C;
-  C.nrows = A.nrows;
-  C.ncols = B.ncols;
-  C.rp.assign(A.nrows + 1, 0);
-  int64_t tot = 0;
-  for (const Block& blk : blocks)
-    for (int64_t i = blk.lo; i < blk.hi; ++i) {
-      tot += blk.len[i - blk.lo];
-      if (tot > INT32_MAX) throw Error(MG_ERR_INVALID_ARG, "product nnz exceeds 2^31");
-      C.rp[i + 1] = (int32_t)tot;
-    }
-  C.ci.resize(tot);
-  C.v.resize(tot);
-  std::vector<std::thread> th;
-  for (const Block& blk : blocks)
-    th.emplace_back([&C, &blk] {
-      if (blk.ci.empty()) return;
-      std::memcpy(C.ci.data() + C.rp[blk.lo], blk.ci.data(), blk.ci.size() * sizeof(int32_t));
-      std::memcpy(C.v.data() + C.rp[blk.lo], blk.v.data(), blk.v.size() * sizeof(double));
-    });
-  for (auto& t : th) t.join();
-  return C;
+        std::sort(st.cols.begin(), st.cols.end());
+        for (int32_t j : st.cols) ci.push_back(j), v.push_back(st.acc[j]);
+      });
 }
 
 std::vector<double> dense_submatrix(const Csr& A, const int32_t* idx, int64_t n) {

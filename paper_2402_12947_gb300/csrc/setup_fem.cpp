@@ -392,79 +392,53 @@ Csr assemble_stiffness(const MeshH& m, const DofMapH& dm) {
     if (!cell_geometry(m, c, G, &vol) || !(vol > 0))
       throw Error(MG_ERR_DEGENERATE_CELL, "cell " + std::to_string(c) + " has zero volume");
   }
-  Csr A;
-  A.nrows = A.ncols = dm.nfree;
-  A.rp.assign(dm.nfree + 1, 0);
-  // pass 1: row patterns (free columns sharing a cell)
-  std::vector<int32_t> rowlen(dm.nfree);
-  parallel_for(dm.nfree, [&](int64_t lo, int64_t hi) {
-    std::vector<int32_t> buf;
-    for (int64_t i = lo; i < hi; ++i) {
-      int64_t g = dm.free_list[i];
-      buf.clear();
-      for (int64_t k = dstart[g]; k < dstart[g + 1]; ++k) {
-        int64_t c = dcells[k];
-        for (int b = 0; b < nloc; ++b) {
-          int64_t fj = dm.free_index[dm.cell_dofs[c * nloc + b]];
-          if (fj >= 0) buf.push_back((int32_t)fj);
-        }
-      }
-      std::sort(buf.begin(), buf.end());
-      rowlen[i] = (int32_t)(std::unique(buf.begin(), buf.end()) - buf.begin());
-    }
-  });
-  for (int64_t i = 0; i < dm.nfree; ++i) {
-    if ((int64_t)A.rp[i] + rowlen[i] > INT32_MAX) throw Error(MG_ERR_INVALID_ARG, "nnz exceeds 2^31");
-    A.rp[i + 1] = A.rp[i] + rowlen[i];
-  }
-  A.ci.resize(A.rp[dm.nfree]);
-  A.v.assign(A.rp[dm.nfree], 0.0);
   GradTerm terms[10];
   for (int a = 0; a < nloc; ++a) terms[a] = basis_term(dm.degree, d, a);
-  // pass 2: columns and values; each row sums its cells in ascending cell order
-  parallel_for(dm.nfree, [&](int64_t lo, int64_t hi) {
-    std::vector<int32_t> buf;
-    for (int64_t i = lo; i < hi; ++i) {
-      int64_t g = dm.free_list[i];
-      buf.clear();
-      for (int64_t k = dstart[g]; k < dstart[g + 1]; ++k) {
-        int64_t c = dcells[k];
-        for (int b = 0; b < nloc; ++b) {
-          int64_t fj = dm.free_index[dm.cell_dofs[c * nloc + b]];
-          if (fj >= 0) buf.push_back((int32_t)fj);
-        }
-      }
-      std::sort(buf.begin(), buf.end());
-      buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
-      int32_t* rc = &A.ci[A.rp[i]];
-      double* rv = &A.v[A.rp[i]];
-      std::copy(buf.begin(), buf.end(), rc);
-      for (int64_t k = dstart[g]; k < dstart[g + 1]; ++k) {
-        int64_t c = dcells[k];
-        int a = dlocal[k];
-        double G[12], vol;
-        cell_geometry(m, c, G, &vol);
-        double GG[4][4];
-        for (int p = 0; p < d1; ++p)
-          for (int q = 0; q < d1; ++q) {
-            double s = 0;
-            for (int r = 0; r < d; ++r) s += G[p * d + r] * G[q * d + r];
-            GG[p][q] = s;
+  // one pass per row: its pattern (free columns sharing a cell, sorted), then its values,
+  // summed over its cells in ascending cell order
+  return csr_from_rows(
+      dm.nfree, dm.nfree, [] { return std::vector<int32_t>(); },
+      [&](std::vector<int32_t>& buf, int64_t i, std::vector<int32_t>& ci, std::vector<double>& v) {
+        const int64_t g = dm.free_list[i];
+        buf.clear();
+        for (int64_t k = dstart[g]; k < dstart[g + 1]; ++k) {
+          const int64_t c = dcells[k];
+          for (int b = 0; b < nloc; ++b) {
+            const int64_t fj = dm.free_index[dm.cell_dofs[c * nloc + b]];
+            if (fj >= 0) buf.push_back((int32_t)fj);
           }
-        for (int b = 0; b < nloc; ++b) {
-          int64_t fj = dm.free_index[dm.cell_dofs[c * nloc + b]];
-          if (fj < 0) continue;
-          double kab = 0;
-          for (int s = 0; s < terms[a].nterms; ++s)
-            for (int t = 0; t < terms[b].nterms; ++t)
-              kab += GG[terms[a].p[s]][terms[b].p[t]] * affine_product_mean(terms[a].f[s], terms[b].f[t], d);
-          int64_t pos = std::lower_bound(rc, rc + buf.size(), (int32_t)fj) - rc;
-          rv[pos] += vol * kab;
         }
-      }
-    }
-  });
-  return A;
+        std::sort(buf.begin(), buf.end());
+        buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
+        const size_t r0 = ci.size();
+        ci.insert(ci.end(), buf.begin(), buf.end());
+        v.resize(ci.size(), 0.0);
+        const int32_t* rc = ci.data() + r0;
+        double* rv = v.data() + r0;
+        for (int64_t k = dstart[g]; k < dstart[g + 1]; ++k) {
+          const int64_t c = dcells[k];
+          const int a = dlocal[k];
+          double G[12], vol;
+          cell_geometry(m, c, G, &vol);
+          double GG[4][4];
+          for (int p = 0; p < d1; ++p)
+            for (int q = 0; q < d1; ++q) {
+              double s = 0;
+              for (int r = 0; r < d; ++r) s += G[p * d + r] * G[q * d + r];
+              GG[p][q] = s;
+            }
+          for (int b = 0; b < nloc; ++b) {
+            const int64_t fj = dm.free_index[dm.cell_dofs[c * nloc + b]];
+            if (fj < 0) continue;
+            double kab = 0;
+            for (int s = 0; s < terms[a].nterms; ++s)
+              for (int t = 0; t < terms[b].nterms; ++t)
+                kab += GG[terms[a].p[s]][terms[b].p[t]] * affine_product_mean(terms[a].f[s], terms[b].f[t], d);
+            const int64_t pos = std::lower_bound(rc, rc + buf.size(), (int32_t)fj) - rc;
+            rv[pos] += vol * kab;
+          }
+        }
+      });
 }
 
 std::vector<double> load_constant(const MeshH& m, const DofMapH& dm, double f) {
