@@ -240,9 +240,12 @@ int mg_vcycle(mg_hierarchy_t* h, const double* b_dev, double* x_dev, void* strea
 
 /* V-cycle-preconditioned CG (Sec. 6.2) from x = 0 until ||r||_2/||b||_2 <= rtol or maxit
  * iterations; x_dev receives the solution. Blocks until the solve has finished and fills
- * *info (may be NULL). Returns MG_OK, MG_ERR_NO_CONVERGENCE or MG_ERR_BREAKDOWN, or
- * MG_ERR_TIMEOUT when the autotuner chose the TMA-staged SpMV for some operator and one of
- * its bounded waits gave up during the solve (the result is then not valid). */
+ * *info (may be NULL). Returns MG_OK, MG_ERR_NO_CONVERGENCE or MG_ERR_BREAKDOWN.
+ * Only for hierarchies built with the TMA-staged SpMV forced (environment variable
+ * NNMG_FORCE_LAYOUT=tma at set-up; the autotuner never picks it): MG_ERR_TIMEOUT when one of
+ * that kernel's bounded waits gave up (the result is then not valid); every entry point that
+ * runs operators of such a hierarchy (mg_vcycle, mg_solve*, the single steps, the server's
+ * requests) checks and clears the device's flag after its work and reports it this way. */
 int mg_solve(mg_hierarchy_t* h, const double* b_dev, double* x_dev, double rtol, int32_t maxit,
              mg_solve_info_t* info, void* stream);
 
@@ -374,7 +377,10 @@ void mg_server_destroy(mg_server_t* s);
  * path where cudaMalloc/cudaFree would stall or synchronise the device). The split-K
  * partial sums live in a static device array of 2^20 doubles (8 MiB per device, held until
  * the process exits) instead of allocated scratch; no allocation happens in the call.
- * Limits: 1 <= n <= 65536 (larger n: MG_ERR_INVALID_ARG, message in mg_last_error(NULL)).
+ * Limits: 1 <= n <= 65536, every such n admitted (at most 16 split-K chunks of at most 4096
+ * columns); larger n: MG_ERR_INVALID_ARG, message in mg_last_error(NULL). A failed launch of
+ * this call's own kernels: MG_ERR_CUDA (an earlier, unrelated sticky error is not reported
+ * as this call's).
  * The first call on a device looks up the array's address with that device current;
  * make it before any stream capture. All calls share the array (each call writes every
  * partial it reads, so nothing needs clearing): calls whose kernels overlap on the GPU

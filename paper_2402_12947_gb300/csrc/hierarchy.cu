@@ -20,6 +20,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cctype>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -330,27 +331,88 @@ void tune_store(const std::string& key, const Layout& L) {
   }
 }
 
+// Layout from its name (the inverse of layout_name): "v<G>" = CSR vector with G in {4, 8,
+// 16, 32} lanes per row; "s<sigma>[x<S>][p|q|t][f<pf>]" = SELL with rows sorted in windows of
+// sigma, S in {2, 4} lanes per row, row loop p = predicated steps of four, q = predicated
+// steps of eight, t = the TMA-staged kernel (default: steps of four with a scalar tail), and
+// an L2 prefetch distance of pf slices; "tma" = "s1t".
+bool parse_layout(const std::string& name, Layout* out) {
+  Layout L{1, 1, 1, 1, 0};
+  if (name == "tma") {
+    *out = {1, 1, 5, 1, 0};
+    return true;
+  }
+  size_t i = 0;
+  auto num = [&](int* v) {
+    size_t j = i;
+    while (j < name.size() && std::isdigit((unsigned char)name[j])) ++j;
+    if (j == i || j - i > 7) return false;
+    *v = std::atoi(name.substr(i, j - i).c_str());
+    i = j;
+    return true;
+  };
+  if (name.empty()) return false;
+  if (name[0] == 'v') {
+    ++i;
+    if (!num(&L.lanes) || i != name.size()) return false;
+    if (L.lanes != 4 && L.lanes != 8 && L.lanes != 16 && L.lanes != 32) return false;
+    *out = L;
+    return true;
+  }
+  if (name[0] != 's') return false;
+  ++i;
+  if (!num(&L.sigma) || L.sigma < 1) return false;
+  if (i < name.size() && name[i] == 'x') {
+    ++i;
+    if (!num(&L.sub) || (L.sub != 2 && L.sub != 4)) return false;
+    L.unroll = 2;
+  }
+  if (i < name.size() && (name[i] == 'p' || name[i] == 'q' || name[i] == 't')) {
+    L.unroll = name[i] == 'p' ? 2 : (name[i] == 'q' ? 3 : 5);
+    ++i;
+  }
+  if (L.unroll == 5 && L.sub != 1) return false;
+  if (i < name.size() && name[i] == 'f') {
+    ++i;
+    if (!num(&L.pf) || L.pf < 1) return false;
+  }
+  if (i != name.size()) return false;
+  *out = L;
+  return true;
+}
+
 // Autotuner (sigma option 0): time y = A x on the device for each candidate layout and keep
 // the fastest. Candidates: SELL with one lane per row and windows 1, 256, 2048 (when sorting
-// removes padding), each with steps of four and a scalar or a predicated row remainder, with
-// predicated steps of eight and (level operators with at least 2^22 nonzeros) the TMA-staged
-// kernel; SELL with 2 and
-// 4 lanes per row at the best window; CSR vector with 4, 8, 16, 32 lanes per row up to
-// twice the longest row; then, on large operators whose best layout is SELL, bulk L2
-// prefetch distances of half, one and two waves of slices. Timing: one warm-up launch,
-// then the mean of 5 launches between CUDA events, the best of three rounds.
+// removes padding), each with steps of four and a scalar or a predicated row remainder and
+// with predicated steps of eight; SELL with 2 and 4 lanes per row at the best window; CSR
+// vector with 4, 8, 16, 32 lanes per row up to twice the longest row; then, on large
+// operators whose best layout is SELL, bulk L2 prefetch distances of half, one and two
+// waves of slices. Timing: one warm-up launch, then the mean of 5 launches between CUDA
+// events, the best of three rounds.
+// The environment variable NNMG_FORCE_LAYOUT=<layout name> (parse_layout) skips the timing
+// and gives every operator that layout, so that tests can run each candidate's kernels; the
+// TMA-staged kernel ("tma", "s1t") exists only behind this switch and applies to the level
+// operators whose slices fit its shared-memory stages (allow_tma), the others are tuned.
 template <typename T>
 SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log, bool allow_tma = false) {
   if (sigma != 0 || A.nrows == 0) return make_sell<T>(A, mem, std::max(sigma, 1));
   const char* force = std::getenv("NNMG_FORCE_LAYOUT");
-  if (allow_tma && force && std::string(force) == "tma") {  // test hook: the TMA-staged kernel wherever it fits
-    DevMem trial;
-    trial.stream = mem.stream;
-    const bool fits = make_layout<T>(A, trial, {1, 1, 5, 1, 0}).tma != 0;
-    trial.release();
-    if (fits) {
-      if (log) *log += " forced " + layout_name({1, 1, 5, 1, 0});
-      return make_layout<T>(A, mem, {1, 1, 5, 1, 0});
+  if (force && *force) {
+    Layout F{};
+    if (!parse_layout(force, &F)) throw Error(MG_ERR_INVALID_ARG, std::string("NNMG_FORCE_LAYOUT: unknown layout ") + force);
+    bool use = true;
+    if (F.unroll == 5) {  // the TMA-staged kernel where its chunk table exists
+      use = false;
+      if (allow_tma) {
+        DevMem trial;
+        trial.stream = mem.stream;
+        use = make_layout<T>(A, trial, F).tma != 0;
+        trial.release();
+      }
+    }
+    if (use) {
+      if (log) *log += " forced " + layout_name(F);
+      return make_layout<T>(A, mem, F);
     }
   }
   const std::string key = tune_key(A, (int)sizeof(T));
@@ -370,7 +432,6 @@ SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log, bo
     cand.push_back({1, c, 1, 1, 0});
     cand.push_back({1, c, 2, 1, 0});
     cand.push_back({1, c, 3, 1, 0});
-    if (allow_tma && A.nnz() >= (int64_t)1 << 22) cand.push_back({1, c, 5, 1, 0});  // bandwidth-bound sizes only
   }
   DevMem scratch;
   scratch.stream = mem.stream;
@@ -1042,7 +1103,8 @@ void build_device(mg_hierarchy* h) {
             D.max_patch = std::max(D.max_patch, m);
             for (int r0 = 0; r0 < m; r0 += kPatchRowsPerItem) items.push_back({p0, m, r0, 0, level_inv_off[l][p]});
           }
-          if (D.max_patch > 27000) throw Error(MG_ERR_INVALID_ARG, "patch larger than 27000 DoFs");
+          if (D.max_patch > kMaxPatchDofs)
+            throw Error(MG_ERR_INVALID_ARG, "patch larger than " + std::to_string(kMaxPatchDofs) + " DoFs");
           max_patch = std::max(max_patch, D.max_patch);
           D.nitems = (int)items.size();
           D.pci = mem.upload(pci);
@@ -1345,6 +1407,15 @@ void check_level(const mg_hierarchy* h, int l, bool below_coarsest = false) {
     throw Error(MG_ERR_INVALID_ARG, "level index out of range");
 }
 
+// Hierarchies built with the TMA-staged SpMV forced (NNMG_FORCE_LAYOUT=tma): after the work
+// enqueued on s, read and clear the device's timeout flag of its bounded waits (synchronises
+// s) and report MG_ERR_TIMEOUT if one gave up. The flag is shared by every stream of the
+// device, so concurrent forced-TMA work elsewhere can also set it.
+void check_tma_timeout(mg_hierarchy* h, cudaStream_t s) {
+  if (h->uses_tma && take_wait_timeout(s))
+    throw Error(MG_ERR_TIMEOUT, "a bounded wait in the TMA-staged SpMV gave up; the result is not valid");
+}
+
 // A library-numbered FP64 vector into a level's internal order and type (perm: internal
 // index -> library index; null = same order), and back.
 template <typename T>
@@ -1397,6 +1468,7 @@ int level_step(mg_hierarchy_t* h, int32_t l, const double* b, double* x, void* s
     store<T>(x, L.x, L.n, L.perm, s);
   });
   check_launch("level step");
+  check_tma_timeout(h, s);
   return MG_OK;
 }
 }  // namespace
@@ -1584,7 +1656,11 @@ void enqueue_host_solve(mg_hierarchy* h, const double* b, double* x, double rtol
   CK(cudaEventRecord(done, s));
 }
 
-int collect_host_solve(const mg_hierarchy* h, mg_solve_info_t* info) { return collect_state(h, info); }
+int collect_host_solve(mg_hierarchy* h, mg_solve_info_t* info) {
+  const int rc = collect_state(h, info);
+  if (h->uses_tma && take_wait_timeout(h->own_stream)) return MG_ERR_TIMEOUT;  // forced TMA-staged SpMV only
+  return rc;
+}
 
 void destroy_hierarchy(mg_hierarchy* h) { delete h; }
 
@@ -1874,6 +1950,7 @@ int mg_vcycle(mg_hierarchy_t* h, const double* b, double* x, void* stream) {
   });
   scatter<double, double>(n, h->perm0, h->cp, x, s);
   check_launch("mg_vcycle");
+  check_tma_timeout(h, s);
   return MG_OK;
   API_END_H(h)
 }
@@ -1888,10 +1965,7 @@ int mg_solve(mg_hierarchy_t* h, const double* b, double* x, double rtol, int32_t
   int rc = run_solve(h, rtol, maxit, info, s);
   scatter<double, double>(h->n0, h->perm0, h->cx, x, s);
   CK(cudaStreamSynchronize(s));
-  if (h->uses_tma && take_wait_timeout(s)) {
-    h->err = "a bounded wait in the TMA-staged SpMV gave up; the result is not valid";
-    return MG_ERR_TIMEOUT;
-  }
+  check_tma_timeout(h, s);
   if (rc != MG_OK) h->err = rc == MG_ERR_BREAKDOWN ? "CG breakdown" : "no convergence within maxit";
   return rc;
   API_END_H(h)
@@ -1909,6 +1983,7 @@ int mg_solve_host(mg_hierarchy_t* h, const double* b, double* x, double rtol, in
   scatter<double, double>(h->n0, h->perm0, h->cx, h->cp, s);
   CK(cudaMemcpyAsync(x, h->cp, sizeof(double) * h->n0, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  check_tma_timeout(h, s);
   if (rc != MG_OK) h->err = rc == MG_ERR_BREAKDOWN ? "CG breakdown" : "no convergence within maxit";
   return rc;
   API_END_H(h)
@@ -1979,6 +2054,7 @@ int mg_solve_batch(mg_hierarchy_t* const* hs, const double* const* b, double* co
   for (int i = 0; i < n; ++i) {
     mg_hierarchy* hi = hs[i];
     CK(cudaStreamSynchronize(hi->own_stream));
+    check_tma_timeout(hi, hi->own_stream);
     int rc = collect_state(hi, info ? &info[i] : nullptr);
     if (rc_all == MG_OK) rc_all = rc;
   }
@@ -2007,6 +2083,7 @@ int mg_apply_A(mg_hierarchy_t* h, int32_t l, const double* x, double* y, void* s
     });
   }
   check_launch("mg_apply_A");
+  check_tma_timeout(h, s);
   return MG_OK;
   API_END_H(h)
 }
@@ -2060,6 +2137,7 @@ int mg_residual_restrict(mg_hierarchy_t* h, int32_t l, const double* b, const do
     store<T>(bc, C.b, C.n, C.perm, s);
   });
   check_launch("mg_residual_restrict");
+  check_tma_timeout(h, s);
   return MG_OK;
   API_END_H(h)
 }

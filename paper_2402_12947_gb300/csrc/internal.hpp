@@ -200,7 +200,7 @@ std::vector<double> hierarchy_unit_load(const mg_hierarchy* h);
 // solution to x (page-locked host) and the CG state out, then record `done`.
 void enqueue_host_solve(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit, cudaEvent_t done);
 // After `done` has completed: the solve's status and info.
-int collect_host_solve(const mg_hierarchy* h, mg_solve_info_t* info);
+int collect_host_solve(mg_hierarchy* h, mg_solve_info_t* info);
 void destroy_hierarchy(mg_hierarchy* h);
 // Message returned by mg_last_error(NULL) in the calling thread.
 void set_last_error(const std::string& msg);

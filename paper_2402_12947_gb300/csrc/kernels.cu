@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <type_traits>
@@ -45,15 +46,16 @@ __device__ __forceinline__ int32_t ld_stream(const int32_t* p) { return __ldcs(p
 //    CSR entries (coalesced) and combine their partial sums with xor shuffles.
 // Every vector access of an epilogue goes through the matrix row.
 // Launch on stream s (plain stream order).
+// Returns the launch's own status (callers that batch launches check check_launch later).
 template <typename... KArgs, typename... Args>
-void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+cudaError_t launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cfg.numAttrs = 0;
-  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 template <typename T>
@@ -1232,14 +1234,27 @@ void patch_residual(int nt, int w, const int32_t* pdofs, const int32_t* plen, co
   launch(k_patch_residual<T>, grid_for(nt, kBlock / 32), kBlock, 0, s, nt, w, pdofs, plen, pci, pv, b, x, rbuf);
 }
 
+// The limit is a per-function attribute of the device's context, shared by every hierarchy in
+// the process: it is raised once per device to the largest patch any hierarchy may have
+// (27000 DoFs, 216,000 bytes) and never lowered, so that a hierarchy set up later (possibly
+// on another thread) cannot shrink the limit under an earlier one's launches.
 void patch_solve_setup(int max_patch) {
-  size_t smem = (size_t)max_patch * sizeof(double);
-  if (smem > 48 * 1024) {
-    cudaFuncSetAttribute(k_patch_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_patch_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_cheb0_entry<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_cheb0_entry<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  }
+  static std::mutex mu;
+  static bool done[64] = {};
+  if ((size_t)max_patch * sizeof(double) <= 48 * 1024) return;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) throw Error(MG_ERR_CUDA, "no current device");
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return;
+  const int smem = kMaxPatchDofs * (int)sizeof(double);
+  const cudaError_t e[4] = {
+      cudaFuncSetAttribute(k_patch_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+      cudaFuncSetAttribute(k_patch_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+      cudaFuncSetAttribute(k_cheb0_entry<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+      cudaFuncSetAttribute(k_cheb0_entry<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)};
+  for (cudaError_t x : e)
+    if (x != cudaSuccess) throw Error(MG_ERR_CUDA, std::string("patch solve shared-memory limit: ") + cudaGetErrorString(x));
+  done[dev] = true;
 }
 
 template <typename T>
@@ -1265,11 +1280,12 @@ void patch_solve(int nitems, const PatchItem* items, const int32_t* pdofs, const
 int dense_chunks(int n, int kchunk) { return grid_for(n, kchunk); }
 
 template <typename T>
-void dense_solve(int n, const double* X, const T* b, T* x, double* part, int kchunk, cudaStream_t s) {
+cudaError_t dense_solve(int n, const double* X, const T* b, T* x, double* part, int kchunk, cudaStream_t s) {
   int nch = dense_chunks(n, kchunk);
   dim3 grid(grid_for(n, kBlock), nch);
-  launch(k_dense_partial<T>, grid, kBlock, kchunk * sizeof(double), s, n, kchunk, X, b, part);
-  launch(k_dense_reduce<T>, grid_for(n, kBlock / 32), kBlock, 0, s, n, nch, part, x);
+  cudaError_t e = launch(k_dense_partial<T>, grid, kBlock, kchunk * sizeof(double), s, n, kchunk, X, b, part);
+  if (e != cudaSuccess) return e;
+  return launch(k_dense_reduce<T>, grid_for(n, kBlock / 32), kBlock, 0, s, n, nch, part, x);
 }
 
 template <typename Src, typename Dst>
@@ -1339,7 +1355,7 @@ void dot_self(int n, const double* r, const Reduce& rd, cudaStream_t s) {
   template void cheb_entry_local<T>(int, const PatchItem*, const int32_t*, const double*, int, int, const T*,     \
                                     const T*, T*, T*, T*, double, int, const int32_t*, const int32_t*,           \
                                     const int32_t*, const T*, cudaStream_t);                                     \
-  template void dense_solve<T>(int, const double*, const T*, T*, double*, int, cudaStream_t);                    \
+  template cudaError_t dense_solve<T>(int, const double*, const T*, T*, double*, int, cudaStream_t);                    \
   template void axpy_from<T>(int, const T*, double*, cudaStream_t);                                              \
   template void cg_init<T>(int, const double*, double*, double*, T*, T*, const Reduce&, cudaStream_t);         \
   template void cg_update<T>(int, const CgState*, const double*, const double*, double*, double*, T*, T*,        \

@@ -86,6 +86,7 @@ struct PatchItem {
 
 constexpr int kBlock = 256;
 constexpr int kPatchRowsPerItem = 8;    // rows of one patch per S_c work item (one warp each)
+constexpr int kMaxPatchDofs = 27000;    // largest patch (its residual is staged in shared memory)
 
 // ---- SELL-32 SpMV family ----
 template <typename T> void sell_spmv(const SellMat<T>& A, const T* x, T* y, cudaStream_t s);
@@ -126,7 +127,8 @@ int sell_blocks(int nrows, int lanes);
 template <typename T>
 void patch_residual(int nt, int w, const int32_t* pdofs, const int32_t* plen, const int32_t* pci, const double* pv,
                     const T* b, const T* x, double* rbuf, cudaStream_t s);
-// Raise the dynamic shared-memory limit of the solve kernel for patches of up to max_patch DoFs.
+// Raise the dynamic shared-memory limit of the solve kernels (once, to kMaxPatchDofs) when a
+// hierarchy has a patch above 48 KB of residual.
 void patch_solve_setup(int max_patch);
 // S_c phase 2, x_B += (A^[d])^{-1} r_B, one block per work item; rbuf == nullptr: the
 // iterate is zero and the residual is b itself (phase 1 skipped).
@@ -143,8 +145,9 @@ void cheb_entry_local(int nitems, const PatchItem* items, const int32_t* pdofs, 
                       const int32_t* hrp, const int32_t* hci, const T* hv, cudaStream_t s);
 
 // ---- coarsest level: x = X b with X = A_L^{-1} dense symmetric (split-K, deterministic) ----
+// Returns the status of its own two launches.
 template <typename T>
-void dense_solve(int n, const double* X, const T* b, T* x, double* part, int kchunk, cudaStream_t s);
+cudaError_t dense_solve(int n, const double* X, const T* b, T* x, double* part, int kchunk, cudaStream_t s);
 int dense_chunks(int n, int kchunk);
 
 // ---- batched dense inversion (set-up): in-place Gauss-Jordan on symmetric positive

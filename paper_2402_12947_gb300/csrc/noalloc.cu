@@ -28,6 +28,7 @@ namespace {
 
 constexpr int64_t kStaticPartials = int64_t(1) << 20;   // doubles (8 MiB)
 constexpr int kStaticMaxChunk = 4096;                   // columns per split-K chunk (32 KiB of shared memory)
+constexpr int64_t kStaticMaxN = int64_t(1) << 16;       // largest n: 16 chunks of 4096 columns
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_static_partials[kStaticPartials];
@@ -69,25 +70,30 @@ int mg_dense_symv_static(const double* X, int64_t n, const double* b, double* x,
     set_last_error("mg_dense_symv_static: null pointer or n < 1");
     return MG_ERR_INVALID_ARG;
   }
-  // split-K: nchunks partial vectors of length n must fit the static array, with at most
-  // kStaticMaxChunk columns per chunk; this admits n <= 65536
+  if (n > kStaticMaxN) {
+    set_last_error("mg_dense_symv_static: n = " + std::to_string(n) + " exceeds the limit n <= " +
+                   std::to_string(kStaticMaxN) + " of the static scratch (2^20 partial sums)");
+    return MG_ERR_INVALID_ARG;
+  }
+  // split-K: about four blocks per SM (152 SMs) from the row blocks times the chunks, then
+  // at least ceil(n / kStaticMaxChunk) chunks so that no chunk exceeds kStaticMaxChunk
+  // columns; nchunks partial vectors of length n must fit the static array. For
+  // n <= kStaticMaxN = 2^16 the second rule gives at most 16 chunks, so n * nchunks <= 2^20.
   const int64_t rowblocks = (n + kBlock - 1) / kBlock;
   int64_t nchunks = std::max<int64_t>(1, (4 * 152 + rowblocks - 1) / rowblocks);
   nchunks = std::min<int64_t>(nchunks, kStaticPartials / n);
-  if (nchunks < 1) nchunks = 1;
-  int64_t kchunk = ((n + nchunks - 1) / nchunks + 31) / 32 * 32;
-  if (n * dense_chunks((int)std::min<int64_t>(n, INT32_MAX), (int)std::min<int64_t>(kchunk, INT32_MAX)) >
-          kStaticPartials ||
-      kchunk > kStaticMaxChunk) {
-    set_last_error("mg_dense_symv_static: n = " + std::to_string(n) +
-                   " exceeds the static scratch (n <= 65536, 2^20 partial sums)");
+  nchunks = std::max<int64_t>(nchunks, (n + kStaticMaxChunk - 1) / kStaticMaxChunk);
+  const int64_t kchunk = ((n + nchunks - 1) / nchunks + 31) / 32 * 32;
+  const int64_t used = n * dense_chunks((int)n, (int)kchunk);
+  if (used > kStaticPartials || kchunk > kStaticMaxChunk) {  // unreachable for n <= kStaticMaxN
+    set_last_error("mg_dense_symv_static: internal chunking error for n = " + std::to_string(n));
     return MG_ERR_INVALID_ARG;
   }
   int code = MG_OK;
   double* part = static_partials(&code);
   if (!part) return code;
-  dense_solve<double>((int)n, X, b, x, part, (int)kchunk, (cudaStream_t)stream);
-  cudaError_t e = cudaGetLastError();
+  // the status of this call's own launches (not a sticky error left by an earlier call)
+  cudaError_t e = dense_solve<double>((int)n, X, b, x, part, (int)kchunk, (cudaStream_t)stream);
   if (e != cudaSuccess) {
     set_last_error(std::string("mg_dense_symv_static: ") + cudaGetErrorString(e));
     return MG_ERR_CUDA;

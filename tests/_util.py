@@ -28,6 +28,9 @@ CASES = {
     "c2_p2_128": (lambda: inputs.config_c2(n_fine=128, levels=4, n_clusters=8), 2, 1),
     "cube_p1": (lambda: small_3d(n=12), 1, 1),
     "cube_p2": (lambda: small_3d(n=6), 2, 1),
+    # fine level 146,689 DoFs: its slices span more than 2^16 columns, so the operators there
+    # store 32-bit column indices (the kernels of the 1024^2 benchmark); coarser levels 16-bit
+    "c2_p2_192": (lambda: inputs.config_c2(n_fine=192, levels=4, n_clusters=8), 2, 1),
 }
 
 _cache = {}
@@ -54,3 +57,24 @@ def csr_arrays(H):
 
 def to_csr(rp, ci, v, shape):
     return sp.csr_matrix((v, ci, rp), shape=shape)
+
+
+_lmin = {}
+
+
+def lambda_min(A) -> float:
+    """Smallest eigenvalue of the SPD matrix A (shift-invert Lanczos about 0)."""
+    import scipy.sparse.linalg as sla
+    key = (A.shape, A.nnz, float(A.data[:64].sum()))
+    if key not in _lmin:
+        _lmin[key] = float(sla.eigsh(A.tocsc(), k=1, sigma=0.0, which="LM", return_eigenvectors=False)[0])
+    return _lmin[key]
+
+
+def solution_gap_bound(A, b, x1, x2) -> float:
+    """Bound on ||x1 - x2||_2 for two approximate solutions of A x = b:
+    A (x1 - x2) = (b - A x2) - (b - A x1), so ||x1 - x2|| <= (||b - A x1|| + ||b - A x2||) / lambda_min(A).
+    Two solves stopped at the same relative residual need not agree more closely than this."""
+    r1 = np.linalg.norm(b - A @ x1)
+    r2 = np.linalg.norm(b - A @ x2)
+    return (r1 + r2) / lambda_min(A)

@@ -1,21 +1,30 @@
 """Parity at the full 2D P2 workload (1024^2 grid, 4.19M DoFs, 6 non-nested levels, 32
 needle/flattened clusters per level), in the configuration the benchmark times.
 
-The oracle cannot run the whole hierarchy at this size, so it computes sampled outputs one
-by one: rows of A_0 from the element matrices of the cells around each sampled DoF, rows of
-P_0 by point location of the sampled fine DoF points, rows of the GPU SpMV; and properties
-that hold at any size: the FP64 and mixed solves reach rtol 1e-8 with the residual
-recomputed on the host from the exported operator.
+Set-up: the oracle's assembly and point location run too slowly at this size for the whole
+hierarchy, so it checks sampled rows of A_0 (element matrices of the cells around each
+sampled DoF) and of P_0 (point location of the sampled fine DoF points).
+Hot path: the oracle's V-cycle (Alg. 1, Sec. 4.2) runs at full size on the exported
+operators, patches and eigenvalues (oracle.hierarchy.from_matrices), so every step the
+benchmark times is compared element by element, with the operators in the layouts the
+autotuner picked for the benchmark (32-bit column indices on the fine level):
+  * FP64 hierarchy: Chebyshev, S_c, residual + restriction and prolongation on levels 0 and 1,
+    and a whole V-cycle, at 1e-10;
+  * mixed hierarchy (the benchmark's value): the same in FP32 within the first-order
+    rounding-error bound of the FP32 schedule (tests/_fp32_bound.py), checked at the
+    components with the largest error and at random ones;
+  * both solves reach rtol 1e-8 with the residual recomputed on the host.
 """
 import numpy as np
 import pytest
 
-from _util import rel_err
+from _fp32_bound import Fp32Schedule, check as check32
+from _util import TOL64, rel_err
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from oracle import fem, smoother, transfer  # noqa: E402
+from oracle import fem, hierarchy, mg, smoother, transfer  # noqa: E402
 from paper_2402_12947_gb300 import inputs  # noqa: E402
 
 
@@ -137,3 +146,113 @@ def test_sampled_local_correction(full):
             # they may differ by a small multiple of kappa * u
             tol = max(1e-10, 8.0 * np.linalg.cond(Ad) * 2.0 ** -53)
             assert rel_err(xh[p], ref) < tol, (l, k, len(p), tol)
+
+
+def _to_csr(rp, ci, v, shape):
+    import scipy.sparse as sp
+    return sp.csr_matrix((v, ci, rp), shape=shape)
+
+
+@pytest.fixture(scope="module")
+def oracle_full(full):
+    """The oracle hierarchy on the FP64 hierarchy's exported operators, patches and lambdas."""
+    _, H, _ = full
+    L = H.num_levels
+    As, Ps, patches = [], [], []
+    for l in range(L):
+        n = H.num_dofs(l)
+        As.append(_to_csr(*H.export_level(l), (n, n)))
+        patches.append(H.export_patches(l))
+        if l + 1 < L:
+            Ps.append(_to_csr(*H.export_transfer(l), (n, H.num_dofs(l + 1))))
+    lam = [H.eigs(l)[2] for l in range(L - 1)]
+    return hierarchy.from_matrices(As, Ps, patches, lam)
+
+
+_sched = {}
+
+
+def _schedule(Ho):
+    if "s" not in _sched:
+        _sched["s"] = Fp32Schedule(Ho)
+    return _sched["s"]
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def _host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+FEW = dict(k_worst=8, k_random=8)   # adjoint columns at 4.19M DoFs: memory of the bound
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("l", [0, 1])
+def test_fullsize_steps(full, oracle_full, precision, l):
+    """Chebyshev (S_g), S_c (Alg. 2), residual + restriction and prolongation of level l."""
+    _, H64, H32 = full
+    H = H64 if precision == "fp64" else H32
+    Ho = oracle_full
+    lo = Ho.levels[l]
+    rng = np.random.default_rng(300 + l)
+    b, x0 = rng.uniform(-1, 1, lo.n), rng.uniform(-1, 1, lo.n)
+    xc = rng.uniform(-1, 1, Ho.levels[l + 1].n)
+    x = _dev(x0)
+    H.chebyshev(l, _dev(b), x)
+    got_cheb = _host(x)
+    x = _dev(x0)
+    H.local_correction(l, _dev(b), x)
+    got_loc = _host(x)
+    r = torch.zeros(lo.n, dtype=torch.float64, device="cuda")
+    bc = torch.zeros(Ho.levels[l + 1].n, dtype=torch.float64, device="cuda")
+    H.residual_restrict(l, _dev(b), _dev(x0), r, bc)
+    got_r, got_bc = _host(r), _host(bc)
+    x = _dev(x0)
+    H.prolong_correct(l, _dev(xc), x)
+    got_p = _host(x)
+    if precision == "fp64":
+        assert rel_err(got_cheb, smoother.chebyshev(lo.A, lo.dinv, b, x0, lo.lmax, lo.lmin, Ho.cheb_degree)) < TOL64
+        assert rel_err(got_loc, lo.local.apply(lo.A, b, x0)) < TOL64
+        rr = b - lo.A @ x0
+        assert rel_err(got_r, rr) < TOL64
+        assert rel_err(got_bc, lo.R @ rr) < TOL64
+        assert rel_err(got_p, x0 + lo.P @ xc) < TOL64
+        return
+    sch = _schedule(Ho)
+    tape, var = sch.chebyshev(l, b, x0)
+    assert rel_err(tape.val[var], smoother.chebyshev(lo.A, lo.dinv, b, x0, lo.lmax, lo.lmin, Ho.cheb_degree)) < TOL64
+    check32(tape, var, got_cheb, ("cheb", l), **FEW)
+    tape, var = sch.local_correction(l, b, x0)
+    check32(tape, var, got_loc, ("local", l), **FEW)
+    tape, rv, bv = sch.residual_restrict(l, b, x0)
+    check32(tape, rv, got_r, ("res", l), **FEW)
+    check32(tape, bv, got_bc, ("restrict", l), **FEW)
+    tape, pv = sch.prolong_correct(l, xc, x0)
+    check32(tape, pv, got_p, ("prolong", l), **FEW)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fullsize_vcycle(full, oracle_full, precision):
+    """One whole V-cycle at 4.19M DoFs (every kernel of the benchmark's cycle, including the
+    S_c from zero fused with the first Chebyshev step and the post-smoothing S_c residual
+    fused with the prolongation)."""
+    _, H64, H32 = full
+    H = H64 if precision == "fp64" else H32
+    Ho = oracle_full
+    n = Ho.levels[0].n
+    rng = np.random.default_rng(320)
+    b, x0 = rng.uniform(-1, 1, n), rng.uniform(-1, 1, n)
+    x = _dev(x0)
+    H.vcycle(_dev(b), x)
+    got = _host(x)
+    ref = x0 + mg.vcycle(Ho, b - Ho.levels[0].A @ x0)
+    if precision == "fp64":
+        assert rel_err(got, ref) < TOL64
+    else:
+        tape, var = _schedule(Ho).vcycle(b, x0)
+        assert rel_err(tape.val[var], ref) < TOL64
+        check32(tape, var, got, "vcycle", **FEW)

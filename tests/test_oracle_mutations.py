@@ -9,7 +9,7 @@ import test_oracle_mg as t_mg
 import test_oracle_quality as t_q
 import test_oracle_smoother as t_sm
 import test_oracle_transfer as t_tr
-from oracle import eig, elasticity, fem, mg, smoother, transfer
+from oracle import eig, elasticity, fem, mg, patches, smoother, transfer
 
 
 def _cheb_first_step_by_lmax(orig):
@@ -76,6 +76,9 @@ CASES = [
      lambda r: t_tr.test_galerkin_spd_and_dense_triple_product(2, 1)),
     ("v-cycle without post-smoothing", mg, "vcycle", lambda o: _vcycle_no_post,
      lambda r: t_mg.test_vcycle_linear_and_symmetric(r.getfixturevalue("c1_meshes"))),
+    ("patch components all merged", patches, "connected_components",
+     lambda o: (lambda g, directed=False: (1, np.zeros(g.shape[0], dtype=np.int32))),
+     lambda r: t_sm.test_patch_components_are_vertex_connected_components(1)),
     ("elasticity lambda term dropped", elasticity, "element_elasticity",
      lambda o: (lambda c, cl, d, mu, lam: o(c, cl, d, mu, 0.0)), lambda r: t_el.test_affine_energies(2, 1)),
 ]

@@ -91,6 +91,60 @@ def test_patches_disjoint_spd_and_cover_bad_cells():
     assert sorted(expect[expect >= 0].tolist()) == sorted(allp.tolist())
 
 
+def _bfs_components(cells, region_cells):
+    """Connected components of a set of cells under shared-vertex adjacency, by breadth-first
+    search over pairs of cells (brute force)."""
+    left = set(int(c) for c in region_cells)
+    comps = []
+    while left:
+        start = left.pop()
+        comp, queue = {start}, [start]
+        while queue:
+            c = queue.pop()
+            vc = set(cells[c].tolist())
+            for o in list(left):
+                if vc & set(cells[o].tolist()):
+                    left.discard(o)
+                    comp.add(o)
+                    queue.append(o)
+        comps.append(sorted(comp))
+    return comps
+
+
+@pytest.mark.parametrize("layers", [1, 2])
+def test_patch_components_are_vertex_connected_components(layers):
+    """Sec. 4.1/4.4: the subdomains are the vertex-connected components of the extended
+    region. Bad cells are planted through gamma on a 14^2 P2 mesh: two far-apart cells (two
+    patches), and two cells that share only a vertex (one merged patch); every patch equals the
+    free DoFs of one brute-force component."""
+    m = inputs.jitter_mesh(inputs.structured_mesh(2, 14), 0.2, np.random.default_rng(7))
+    dm = fem.dof_map(m.coords, m.cells, 2)
+    cents = m.coords[m.cells].mean(axis=1)
+    far_a = int(np.argmin(np.linalg.norm(cents - [0.2, 0.2], axis=1)))
+    far_b = int(np.argmin(np.linalg.norm(cents - [0.8, 0.8], axis=1)))
+    # a cell touching far_b's region only through one vertex, two layers away from far_a
+    vb = set(m.cells[far_b].tolist())
+    touch = [c for c in range(len(m.cells)) if len(vb & set(m.cells[c].tolist())) == 1]
+    g = np.ones(len(m.cells))
+    for bad, expect in (([far_a, far_b], 2), ([far_b, touch[0]], 1)):
+        g[:] = 1.0
+        g[bad] = 1e-3
+        pt = patches.local_patches(m.cells, g, 0.1, layers, m.nv, dm.cell_dofs, dm.free_index)
+        # the extended region by its definition: cells sharing a vertex with the region, repeated
+        region = set(bad)
+        for _ in range(layers):
+            verts = set(m.cells[sorted(region)].ravel().tolist())
+            region = {c for c in range(len(m.cells)) if verts & set(m.cells[c].tolist())}
+        comps = _bfs_components(m.cells, sorted(region))
+        assert len(comps) == expect == len(pt), (bad, len(comps), len(pt))
+        want = []
+        for comp in comps:
+            f = dm.free_index[np.unique(dm.cell_dofs[comp].ravel())]
+            want.append(np.sort(f[f >= 0]))
+        want.sort(key=lambda p: int(p[0]))
+        assert all(np.array_equal(a, b) for a, b in zip(pt, want))
+
+
 def _dense_operator(fn, n):
     return np.stack([fn(np.eye(n)[i]) for i in range(n)], axis=1)
 
