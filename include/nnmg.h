@@ -149,7 +149,12 @@ typedef struct mg_options_t {
   int32_t pde;             /* enum mg_pde (POISSON); mg_setup only */
   double young;            /* Young's modulus E for MG_PDE_ELASTICITY (6.9e10, Sec. 6.3) */
   double poisson_ratio;    /* Poisson's ratio nu for MG_PDE_ELASTICITY (0.33, Sec. 6.3) */
-  int32_t reserved[4];
+  int32_t small_level_dofs; /* the first level with at most this many DoFs, and every level
+                              below it, run their part of each V-cycle inside one persistent
+                              cooperative launch (phases separated by grid barriers) instead of
+                              one launch per step; 0 = never (Chebyshev global smoother only)
+                              (100000) */
+  int32_t reserved[3];
 } mg_options_t;
 
 /* Result of a solve. */

@@ -538,6 +538,12 @@ struct DevLevel {
   // inside the colour, and the level rows they update
   std::vector<SellMat<T>> gs;
   std::vector<int32_t*> gs_rows;
+  // levels run inside the persistent launch: A, P, R as CSR (0, 1, 2) with G lanes per row,
+  // and one descriptor per patch row
+  int32_t *crp[3] = {nullptr, nullptr, nullptr}, *cci[3] = {nullptr, nullptr, nullptr};
+  T* cval[3] = {nullptr, nullptr, nullptr};
+  int cG[3] = {4, 4, 4};
+  PRow* prow = nullptr;
 };
 
 }  // namespace
@@ -553,6 +559,18 @@ struct Engine {
   int nc = 0, kchunk = 256;
   double *Xc = nullptr, *cpart = nullptr;
   int launches = 0;
+  // persistent launch of the cycle from level pers_from down (-1: none), its program
+  int pers_from = -1, pers_phases = 0;
+  PPhase* d_phases = nullptr;
+  PTask* d_tasks = nullptr;
+  PBarrier* bar = nullptr;
+  double* cb64 = nullptr;   // FP64 copy of the coarsest right-hand side (persistent launch)
+  // the FP64 level-0 operator as CSR for the CG product of a persistent solve (pers_from == 0)
+  int32_t *a0rp = nullptr, *a0ci = nullptr;
+  double* a0v = nullptr;
+  int a0G = 4;
+  std::vector<PTask> htasks;
+  std::vector<PPhase> hphases;
 
   bool local_on(int l) const {
     return lv[l].np > 0 && order != MG_SMOOTHER_GLOBAL && ((local_mask >> std::min(l, 31)) & 1u);
@@ -655,6 +673,11 @@ struct Engine {
     ++launches;
   }
   void cycle(int l, cudaStream_t s) {
+    if (l == pers_from) {
+      CK(persistent_launch<T>(d_phases, pers_phases, d_tasks, bar, s));
+      ++launches;
+      return;
+    }
     if (l == (int)lv.size() - 1) {
       coarse(s);
       return;
@@ -666,6 +689,264 @@ struct Engine {
     if (pr) prolong_pr(l, s);
     else prolong(l, s);
     for (int k = 0; k < nu; ++k) smooth(l, true, s, false, pr && k == 0);
+  }
+
+  // ---- persistent launch of the small levels: set-up ----
+  // Lanes per row of a CSR operator in the persistent kernel: about eight entries per lane
+  // (two steps of four loads), at least 4 and at most 32 lanes.
+  static int csr_lanes(const Csr& A) {
+    const double avg = A.nrows > 0 ? (double)A.nnz() / (double)A.nrows : 0.0;
+    int G = 4;
+    while (G < 32 && 8.0 * G < avg) G *= 2;
+    return G;
+  }
+  // The first level with at most thr DoFs such that every level below is smaller still (-1
+  // when none, or thr = 0, or the global smoother is SGS); its CSR operators and patch rows
+  // are uploaded and the cycle from it down is recorded and uploaded.
+  void build_persistent(const std::vector<LevelH>& dl, const std::vector<std::vector<int64_t>>& inv_off, int thr,
+                        DevMem& mem) {
+    pers_from = -1;
+    const int L = (int)lv.size();
+    if (thr <= 0 || sgs) return;
+    for (int l = L - 1; l >= 0 && lv[l].n <= thr; --l) pers_from = l;
+    if (pers_from < 0) return;
+    for (int l = pers_from; l + 1 < L; ++l) {
+      DevLevel<T>& D = lv[l];
+      const Csr* ops[3] = {&dl[l].A, &dl[l].P, &dl[l].R};
+      for (int k = 0; k < 3; ++k) {
+        const Csr& M = *ops[k];
+        D.crp[k] = mem.upload(M.rp);
+        D.cci[k] = mem.upload(M.ci);
+        std::vector<T> v(M.v.begin(), M.v.end());
+        D.cval[k] = mem.upload(v);
+        D.cG[k] = csr_lanes(M);
+      }
+      if (D.np > 0) {
+        const std::vector<int32_t>& ptr = dl[l].patch_ptr;
+        std::vector<PRow> rows;
+        rows.reserve(D.nt);
+        for (int p = 0; p + 1 < (int)ptr.size(); ++p) {
+          const int32_t m = ptr[p + 1] - ptr[p];
+          for (int32_t i = 0; i < m; ++i) rows.push_back(PRow{ptr[p], m, i, 0, inv_off[l][p] + (int64_t)i * m});
+        }
+        D.prow = mem.upload(rows);
+      }
+    }
+    if (pers_from == 0) {
+      a0rp = mem.upload(dl[0].A.rp);
+      a0ci = mem.upload(dl[0].A.ci);
+      a0v = mem.upload(dl[0].A.v);
+      a0G = csr_lanes(dl[0].A);
+    }
+    cb64 = mem.alloc<double>(nc);
+    htasks.clear();
+    hphases.clear();
+    rec_cycle(pers_from);
+    pers_phases = (int)hphases.size();
+    d_tasks = mem.upload(htasks);
+    d_phases = mem.upload(hphases);
+    bar = mem.alloc<PBarrier>(1);
+  }
+
+  // ---- the cycle from a level down, recorded as a persistent program ----
+  // Same schedule as cycle() and the functions it calls, step for step: every launch there is
+  // a phase here (rec_* mirrors the function of the same name), and the two launches that
+  // write disjoint arrays (S_c from zero with the first Chebyshev step; the prolongation with
+  // the patch residual of the next S_c) each share a phase.
+  void ph_open() { hphases.push_back(PPhase{(int)htasks.size(), (int)htasks.size(), 0, 0}); }
+  void ph_task(PTask t) {
+    if (t.n <= 0) return;
+    PPhase& ph = hphases.back();
+    t.u0 = ph.units;
+    ph.units += ptask_units(t);
+    htasks.push_back(t);
+    ph.t1 = (int)htasks.size();
+  }
+  void ph_close() {
+    if (hphases.back().units == 0) hphases.pop_back();
+  }
+  static PTask task(int kind, int n) {
+    PTask t;
+    std::memset(&t, 0, sizeof(t));
+    t.kind = kind;
+    t.n = n;
+    t.G = 4;
+    return t;
+  }
+  // A CSR task over operator op (0 = A, 1 = P, 2 = R) of level l.
+  PTask csr_task(int kind, int l, int op) {
+    DevLevel<T>& L = lv[l];
+    PTask t = task(kind, op == 2 ? lv[l + 1].n : L.n);
+    t.rp = L.crp[op];
+    t.ci = L.cci[op];
+    t.val = L.cval[op];
+    t.G = L.cG[op];
+    return t;
+  }
+  PTask halo_task(int l, const T* x, T* xout, double cr) {
+    DevLevel<T>& L = lv[l];
+    PTask t = task(PK_CHEB_FIRST, L.nh);
+    t.rows = L.hrow;
+    t.rp = L.hrp;
+    t.ci = L.hci;
+    t.val = L.hv;
+    t.G = 8;
+    t.x = x;
+    t.b = L.b;
+    t.dinv = L.dinv;
+    t.d = L.d;
+    t.y = xout;
+    t.c2 = cr;
+    return t;
+  }
+  PTask patch_solve_task(int l, bool zero) {
+    DevLevel<T>& L = lv[l];
+    PTask t = task(PK_PATCH_SOLVE, L.nt);
+    t.prow = L.prow;
+    t.inv = L.inv;
+    t.pdofs = L.pdofs;
+    t.rbuf = zero ? nullptr : L.rbuf;
+    t.b = L.b;
+    t.y = L.x;
+    return t;
+  }
+  void rec_cheb(int l, int zero) {
+    DevLevel<T>& L = lv[l];
+    T *xa = L.x, *xb = L.xt;
+    for (int j = 0; j < cheb_k; ++j) {
+      if (j == 0 && zero) {
+        ph_open();
+        if (zero == 3) ph_task(patch_solve_task(l, true));
+        PTask c = task(PK_CHEB0, L.n);
+        c.x = zero == 3 ? nullptr : xa;
+        c.b = L.b;
+        c.dinv = L.dinv;
+        c.d = L.d;
+        c.y = xb;
+        c.c2 = L.cr[0];
+        ph_task(c);
+        ph_close();
+        if ((zero == 3 || zero == 2) && L.nh > 0) {
+          ph_open();
+          ph_task(halo_task(l, xa, xb, L.cr[0]));
+          ph_close();
+        }
+      } else {
+        PTask c = csr_task(j == 0 ? PK_CHEB_FIRST : PK_CHEB, l, 0);
+        c.x = xa;
+        c.b = L.b;
+        c.dinv = L.dinv;
+        c.d = L.d;
+        c.y = xb;
+        c.c1 = L.cd[j];
+        c.c2 = L.cr[j];
+        ph_open();
+        ph_task(c);
+        ph_close();
+      }
+      std::swap(xa, xb);
+    }
+    if (xa != L.x) {
+      PTask c = task(PK_COPY, L.n);
+      c.x = xa;
+      c.y = L.x;
+      ph_open();
+      ph_task(c);
+      ph_close();
+    }
+  }
+  void rec_local(int l, bool zero = false, bool rready = false) {
+    DevLevel<T>& L = lv[l];
+    if (!zero && !rready) {
+      PTask r = task(PK_PATCH_RES, L.nt);
+      r.w = L.pw;
+      r.pdofs = L.pdofs;
+      r.plen = L.plen;
+      r.pci = L.pci;
+      r.pv = L.pv;
+      r.b = L.b;
+      r.x = L.x;
+      r.rbuf = L.rbuf;
+      ph_open();
+      ph_task(r);
+      ph_close();
+    }
+    ph_open();
+    ph_task(patch_solve_task(l, zero));
+    ph_close();
+  }
+  void rec_smooth(int l, bool post, bool zero = false, bool rready = false) {
+    if (!local_on(l)) {
+      rec_cheb(l, zero ? 1 : 0);
+      return;
+    }
+    if (order == MG_SMOOTHER_SANDWICH) {
+      if (zero) rec_cheb(l, 3);
+      else {
+        rec_local(l, false, rready);
+        rec_cheb(l, 0);
+      }
+      rec_local(l);
+    } else if (!post) {
+      rec_cheb(l, zero ? 1 : 0);
+      rec_local(l);
+    } else {
+      rec_local(l, false, rready);
+      rec_cheb(l, 0);
+    }
+  }
+  void rec_cycle(int l) {
+    if (l == (int)lv.size() - 1) {
+      DevLevel<T>& C = lv.back();
+      PTask t = task(PK_DENSE, nc);
+      t.inv = Xc;
+      t.b = C.b;
+      t.y = C.x;
+      if (l > pers_from) t.y64 = cb64;   // filled by the restriction in this launch
+      ph_open();
+      ph_task(t);
+      ph_close();
+      return;
+    }
+    DevLevel<T>& L = lv[l];
+    DevLevel<T>& C = lv[l + 1];
+    for (int k = 0; k < nu; ++k) rec_smooth(l, false, k == 0);
+    PTask r = csr_task(PK_RESID, l, 0);
+    r.x = L.x;
+    r.b = L.b;
+    r.y = L.res;
+    ph_open();
+    ph_task(r);
+    ph_close();
+    PTask q = csr_task(PK_RESTRICT, l, 2);
+    q.x = L.res;
+    q.y = C.b;
+    q.z = C.x;
+    if (l + 2 == (int)lv.size()) q.y64 = cb64;
+    ph_open();
+    ph_task(q);
+    ph_close();
+    rec_cycle(l + 1);
+    const bool pr = prolong_with_patch_residual(l);
+    PTask p = csr_task(PK_PROLONG, l, 1);
+    p.x = C.x;
+    p.y = L.x;
+    ph_open();
+    ph_task(p);
+    if (pr) {
+      PTask a = task(PK_PATCH_RES_AP, L.nt);
+      a.w = L.apw;
+      a.pdofs = L.pdofs;
+      a.plen = L.aplen;
+      a.pci = L.apci;
+      a.pv = L.apv;
+      a.b = L.res;
+      a.x = C.x;
+      a.rbuf = L.rbuf;
+      ph_task(a);
+    }
+    ph_close();
+    for (int k = 0; k < nu; ++k) rec_smooth(l, true, false, pr && k == 0);
   }
 };
 
@@ -699,6 +980,15 @@ struct mg_hierarchy {
   int launches_vcycle = 0, launches_iter = 0;
   int64_t dropped_dofs = 0;  // DoFs excluded as dependent by the dense direct solves
   bool uses_tma = false;     // some operator runs the TMA-staged kernel (bounded waits)
+  // the whole MG-PCG solve as one persistent launch (hierarchies whose whole cycle runs
+  // persistently, small_level_dofs >= n_0); empty otherwise
+  struct Solo {
+    PPhase* phases = nullptr;
+    PTask* tasks = nullptr;
+    CgState** states = nullptr;
+    PBarrier* bar = nullptr;
+    int nhead = 0, nbody = 0;
+  } solo;
 
   bool mixed() const { return opt.precision == MG_PREC_MIXED; }
   template <typename F>
@@ -733,6 +1023,7 @@ void validate_options(const mg_options_t& o) {
   if (o.global_smoother < 0 || o.global_smoother > 1) throw Error(MG_ERR_INVALID_ARG, "unknown global smoother");
   if (o.reorder < 0 || o.reorder > 2) throw Error(MG_ERR_INVALID_ARG, "unknown reorder mode");
   if (o.pde < 0 || o.pde > 1) throw Error(MG_ERR_INVALID_ARG, "unknown pde");
+  if (o.small_level_dofs < 0) throw Error(MG_ERR_INVALID_ARG, "small_level_dofs must be >= 0");
   if (o.pde == MG_PDE_ELASTICITY && !(o.young > 0 && o.poisson_ratio > -1.0 && o.poisson_ratio < 0.5))
     throw Error(MG_ERR_INVALID_ARG, "elasticity needs E > 0 and -1 < nu < 1/2");
 }
@@ -1219,6 +1510,8 @@ void build_device(mg_hierarchy* h) {
   {
     h->perm0 = h->e64 ? h->e64->lv[0].perm : h->e32->lv[0].perm;
   }
+  // the small levels in one persistent launch per cycle (after the level-0 vectors are final)
+  h->with_engine([&](auto& e) { e.build_persistent(dl, level_inv_off, o.small_level_dofs, mem); });
   if (max_patch > 0) patch_solve_setup(max_patch);
   CK(cudaStreamSynchronize(h->own_stream));
   tm.mark("device upload");
@@ -1351,9 +1644,183 @@ int collect_state(const mg_hierarchy* h, mg_solve_info_t* info) {
   return MG_OK;
 }
 
+// ---- MG-PCG of one or many hierarchies in one persistent launch ----
+// The program: per problem the CG steps of CgRunner as tasks and the recorded V-cycle; the
+// problems' phases are merged by index (phase k runs the k-th step of every problem), so one
+// grid barrier serves every problem's step. The body repeats until every problem has
+// stopped; a stopped problem's tasks do nothing (gated on its CG state). Each problem's
+// arithmetic does not depend on the others (every unit computes the same values whichever
+// warp runs it, and reductions sum per-unit partials in unit order), so a problem gives the
+// same bits alone and in any batch.
+struct PProgram {
+  std::vector<PTask> tasks;
+  std::vector<PPhase> phases;
+  void phase(const std::vector<PTask>& ts, int check = 0) {
+    PPhase ph{(int)tasks.size(), (int)tasks.size(), 0, check};
+    for (PTask t : ts) {
+      if (t.n <= 0) continue;
+      t.u0 = ph.units;
+      ph.units += ptask_units(t);
+      tasks.push_back(t);
+    }
+    ph.t1 = (int)tasks.size();
+    if (ph.units > 0 || check) phases.push_back(ph);
+  }
+};
+
+template <typename T>
+Engine<T>& engine_of(mg_hierarchy* h);
+template <>
+Engine<double>& engine_of<double>(mg_hierarchy* h) {
+  return *h->e64;
+}
+template <>
+Engine<float>& engine_of<float>(mg_hierarchy* h) {
+  return *h->e32;
+}
+
+bool persistent_solve_ok(const mg_hierarchy* h) {
+  return h->device && (h->e64 ? h->e64->pers_from == 0 : (h->e32 && h->e32->pers_from == 0));
+}
+
+// Records the program of the problems hs (same precision T, whole cycle persistent) into pg;
+// part[i]: a partial-sum buffer of problem i with at least ceil(n_0 / 8) entries.
+template <typename T>
+void assemble_pcg(const std::vector<mg_hierarchy*>& hs, const std::vector<double*>& part, PProgram& pg, int* nhead) {
+  const int K = (int)hs.size();
+  auto base = [](int kind, int n) {
+    PTask t;
+    std::memset(&t, 0, sizeof(t));
+    t.kind = kind;
+    t.n = n;
+    t.G = 4;
+    return t;
+  };
+  auto units32 = [](int n) { return (n + 31) / 32; };
+  auto per = [&](auto&& make) {
+    std::vector<PTask> v;
+    for (int i = 0; i < K; ++i) v.push_back(make(i, hs[i], engine_of<T>(hs[i])));
+    return v;
+  };
+  auto fin = [&](int op, bool ap, bool gated) {
+    return per([&, op, ap, gated](int i, mg_hierarchy* h, Engine<T>& e) {
+      PTask t = base(PK_FINISH, 1);
+      t.w = ap ? (h->n0 + 32 / e.a0G - 1) / (32 / e.a0G) : units32(h->n0);
+      t.part = part[i];
+      t.st = h->st;
+      t.op = op;
+      t.gate = gated ? h->st : nullptr;
+      return t;
+    });
+  };
+  auto vcycle = [&]() {
+    size_t len = 0;
+    for (mg_hierarchy* h : hs) len = std::max(len, engine_of<T>(h).hphases.size());
+    for (size_t k = 0; k < len; ++k) {
+      std::vector<PTask> ts;
+      for (mg_hierarchy* h : hs) {
+        Engine<T>& e = engine_of<T>(h);
+        if (k >= e.hphases.size()) continue;
+        for (int j = e.hphases[k].t0; j < e.hphases[k].t1; ++j) {
+          PTask t = e.htasks[j];
+          t.gate = h->st;
+          ts.push_back(t);
+        }
+      }
+      pg.phase(ts);
+    }
+  };
+  auto vec = [&](int kind, bool gated, int first = 0) {
+    return per([&, kind, gated, first](int i, mg_hierarchy* h, Engine<T>& e) {
+      PTask t = base(kind, h->n0);
+      t.cb = h->cb;
+      t.cx = h->cx;
+      t.cr = h->cr;
+      t.cp = h->cp;
+      t.cq = h->cq;
+      t.vb = e.lv[0].b;
+      t.vx = e.lv[0].x;
+      t.st = h->st;
+      t.part = part[i];
+      t.w = first;
+      t.gate = gated ? h->st : nullptr;
+      return t;
+    });
+  };
+  // head: r = b, x = 0; z = V r; p = z
+  pg.phase(vec(PK_CG_INIT, false));
+  pg.phase(fin(FIN_BB, false, false));
+  vcycle();
+  pg.phase(vec(PK_CG_DOTZ, true, 1));
+  pg.phase(fin(FIN_RZ0, false, true));
+  *nhead = (int)pg.phases.size();
+  // body: q = A p, alpha; x, r updated, convergence (check); z = V r; beta; p = z + beta p
+  pg.phase(per([&](int i, mg_hierarchy* h, Engine<T>& e) {
+    PTask t = base(PK_CG_AP, h->n0);
+    t.rp = e.a0rp;
+    t.ci = e.a0ci;
+    t.val = e.a0v;
+    t.G = e.a0G;
+    t.cp = h->cp;
+    t.cq = h->cq;
+    t.part = part[i];
+    t.gate = h->st;
+    return t;
+  }));
+  pg.phase(fin(FIN_PQ, true, true));
+  pg.phase(vec(PK_CG_UPDATE, true));
+  pg.phase(fin(FIN_RR, false, true), 1);
+  vcycle();
+  pg.phase(vec(PK_CG_DOTZ, true));
+  pg.phase(fin(FIN_RZ, false, true));
+  pg.phase(vec(PK_CG_PUPDATE, true));
+}
+
+// The program of one hierarchy, kept with it (device memory of the hierarchy).
+// Partial sums of one problem's reductions: one per unit of its largest reduction task.
+int64_t pcg_part_size(mg_hierarchy* h) {
+  const int G = h->e64 ? h->e64->a0G : h->e32->a0G;
+  return std::max<int64_t>((h->n0 + 31) / 32, ((int64_t)h->n0 * G + 31) / 32) + 1;
+}
+
+template <typename T>
+void build_solo(mg_hierarchy* h) {
+  std::vector<mg_hierarchy*> hs{h};
+  std::vector<double*> part{h->mem.alloc<double>(pcg_part_size(h))};
+  PProgram pg;
+  int nhead = 0;
+  assemble_pcg<T>(hs, part, pg, &nhead);
+  h->solo.tasks = h->mem.upload(pg.tasks);
+  h->solo.phases = h->mem.upload(pg.phases);
+  std::vector<CgState*> st{h->st};
+  h->solo.states = h->mem.upload(st);
+  h->solo.bar = h->mem.alloc<PBarrier>(1);
+  h->solo.nhead = nhead;
+  h->solo.nbody = (int)pg.phases.size() - nhead;
+}
+
+int pcg_iteration_cap(int maxit) { return std::min(maxit, 100000) + 1; }
+
+// The solve itself on s (state already enqueued): the persistent program, or the graph.
+void enqueue_solo_or_graph(mg_hierarchy* h, int maxit, cudaStream_t s) {
+  if (h->solo.tasks) {
+    auto go = [&](auto tag) {
+      using T = decltype(tag);
+      CK(persistent_launch<T>(h->solo.phases, h->solo.nhead, h->solo.tasks, h->solo.bar, s, h->solo.nbody,
+                              h->solo.states, 1, pcg_iteration_cap(maxit)));
+    };
+    if (h->e64) go(double());
+    else go(float());
+  } else {
+    CK(cudaGraphLaunch(h->graph, s));
+  }
+}
+
 int run_solve(mg_hierarchy* h, double rtol, int maxit, mg_solve_info_t* info, cudaStream_t s) {
   enqueue_state(h, rtol, maxit, s);
-  if (h->graph) {
+  if (h->solo.tasks) {
+    enqueue_solo_or_graph(h, maxit, s);
+  } else if (h->graph) {
     CK(cudaGraphLaunch(h->graph, s));
   } else {
     dispatch(h, [&](auto& r) { r.head(s, 0, 0); });
@@ -1407,11 +1874,30 @@ void check_level(const mg_hierarchy* h, int l, bool below_coarsest = false) {
     throw Error(MG_ERR_INVALID_ARG, "level index out of range");
 }
 
-// Hierarchies built with the TMA-staged SpMV forced (NNMG_FORCE_LAYOUT=tma): after the work
-// enqueued on s, read and clear the device's timeout flag of its bounded waits (synchronises
-// s) and report MG_ERR_TIMEOUT if one gave up. The flag is shared by every stream of the
-// device, so concurrent forced-TMA work elsewhere can also set it.
-void check_tma_timeout(mg_hierarchy* h, cudaStream_t s) {
+// After the work enqueued on s, the bounded device-side waits of that work (synchronises s
+// when the hierarchy has any): the grid barriers of the persistent small-level launch (the
+// hierarchy's own error word, cleared with its barrier state) and, for hierarchies built with
+// the TMA-staged SpMV forced (NNMG_FORCE_LAYOUT=tma), that kernel's device-wide flag, which
+// concurrent forced-TMA work elsewhere can also set. Either expiry: MG_ERR_TIMEOUT.
+bool take_persistent_error(mg_hierarchy* h, cudaStream_t s) {
+  PBarrier* bars[2] = {h->e64 ? h->e64->bar : (h->e32 ? h->e32->bar : nullptr), h->solo.bar};
+  bool any = false;
+  for (PBarrier* bar : bars) {
+    if (!bar) continue;
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, &bar->error, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (err) {
+      CK(cudaMemsetAsync(bar, 0, sizeof(PBarrier), s));
+      CK(cudaStreamSynchronize(s));
+      any = true;
+    }
+  }
+  return any;
+}
+void check_device_waits(mg_hierarchy* h, cudaStream_t s) {
+  if (take_persistent_error(h, s))
+    throw Error(MG_ERR_TIMEOUT, "a grid barrier of the persistent small-level launch gave up; the result is not valid");
   if (h->uses_tma && take_wait_timeout(s))
     throw Error(MG_ERR_TIMEOUT, "a bounded wait in the TMA-staged SpMV gave up; the result is not valid");
 }
@@ -1442,7 +1928,12 @@ void store(double* dst, const T* src, int n, const int32_t* perm, cudaStream_t s
 void device_phase(mg_hierarchy* h) {
   build_device(h);
   count_launches(h);
-  if (h->opt.use_graph) build_graph(h);
+  if (persistent_solve_ok(h)) {  // the whole solve in one persistent launch; no graph needed
+    if (h->e64) build_solo<double>(h);
+    else build_solo<float>(h);
+  } else if (h->opt.use_graph) {
+    build_graph(h);
+  }
   CK(cudaStreamSynchronize(h->own_stream));
 }
 
@@ -1468,7 +1959,7 @@ int level_step(mg_hierarchy_t* h, int32_t l, const double* b, double* x, void* s
     store<T>(x, L.x, L.n, L.perm, s);
   });
   check_launch("level step");
-  check_tma_timeout(h, s);
+  check_device_waits(h, s);
   return MG_OK;
 }
 }  // namespace
@@ -1498,6 +1989,7 @@ void mg_default_options(mg_options_t* o) {
   o->pde = MG_PDE_POISSON;
   o->young = 6.9e10;
   o->poisson_ratio = 0.33;
+  o->small_level_dofs = 0;
 }
 
 }  // extern "C"
@@ -1644,12 +2136,13 @@ std::vector<double> hierarchy_unit_load(const mg_hierarchy* h) {
 }
 
 void enqueue_host_solve(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit, cudaEvent_t done) {
-  if (!h->graph) throw Error(MG_ERR_INVALID_ARG, "the solve server needs hierarchies built with use_graph = 1");
+  if (!h->graph && !h->solo.tasks)
+    throw Error(MG_ERR_INVALID_ARG, "the solve server needs hierarchies built with use_graph = 1");
   cudaStream_t s = h->own_stream;
   CK(cudaMemcpyAsync(h->cq, b, sizeof(double) * h->n0, cudaMemcpyHostToDevice, s));
   gather<double, double>(h->n0, h->perm0, h->cq, h->cb, s);
   enqueue_state(h, rtol, maxit, s);
-  CK(cudaGraphLaunch(h->graph, s));
+  enqueue_solo_or_graph(h, maxit, s);
   enqueue_exit(h, s);
   scatter<double, double>(h->n0, h->perm0, h->cx, h->cq, s);
   CK(cudaMemcpyAsync(x, h->cq, sizeof(double) * h->n0, cudaMemcpyDeviceToHost, s));
@@ -1658,6 +2151,7 @@ void enqueue_host_solve(mg_hierarchy* h, const double* b, double* x, double rtol
 
 int collect_host_solve(mg_hierarchy* h, mg_solve_info_t* info) {
   const int rc = collect_state(h, info);
+  if (take_persistent_error(h, h->own_stream)) return MG_ERR_TIMEOUT;
   if (h->uses_tma && take_wait_timeout(h->own_stream)) return MG_ERR_TIMEOUT;  // forced TMA-staged SpMV only
   return rc;
 }
@@ -1950,7 +2444,7 @@ int mg_vcycle(mg_hierarchy_t* h, const double* b, double* x, void* stream) {
   });
   scatter<double, double>(n, h->perm0, h->cp, x, s);
   check_launch("mg_vcycle");
-  check_tma_timeout(h, s);
+  check_device_waits(h, s);
   return MG_OK;
   API_END_H(h)
 }
@@ -1965,7 +2459,7 @@ int mg_solve(mg_hierarchy_t* h, const double* b, double* x, double rtol, int32_t
   int rc = run_solve(h, rtol, maxit, info, s);
   scatter<double, double>(h->n0, h->perm0, h->cx, x, s);
   CK(cudaStreamSynchronize(s));
-  check_tma_timeout(h, s);
+  check_device_waits(h, s);
   if (rc != MG_OK) h->err = rc == MG_ERR_BREAKDOWN ? "CG breakdown" : "no convergence within maxit";
   return rc;
   API_END_H(h)
@@ -1983,7 +2477,7 @@ int mg_solve_host(mg_hierarchy_t* h, const double* b, double* x, double rtol, in
   scatter<double, double>(h->n0, h->perm0, h->cx, h->cp, s);
   CK(cudaMemcpyAsync(x, h->cp, sizeof(double) * h->n0, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  check_tma_timeout(h, s);
+  check_device_waits(h, s);
   if (rc != MG_OK) h->err = rc == MG_ERR_BREAKDOWN ? "CG breakdown" : "no convergence within maxit";
   return rc;
   API_END_H(h)
@@ -2032,29 +2526,74 @@ int mg_solve_batch(mg_hierarchy_t* const* hs, const double* const* b, double* co
   mg_hierarchy* h = nullptr;
   API_BEGIN
   if (n < 0 || (n > 0 && (!hs || !b || !x))) throw Error(MG_ERR_INVALID_ARG, "invalid batch arrays");
+  if (!(rtol >= 0) || maxit < 1) throw Error(MG_ERR_INVALID_ARG, "rtol must be >= 0 and maxit >= 1");
   cudaStream_t s = (cudaStream_t)stream;
+  // problems whose whole solve runs persistently: one launch per precision for all of them;
+  // the others: their graphs on their own streams, overlapping on the device
+  std::vector<int> g64, g32, rest;
+  for (int i = 0; i < n; ++i) {
+    mg_hierarchy* hi = checked(hs[i]);
+    if (persistent_solve_ok(hi)) (hi->e64 ? g64 : g32).push_back(i);
+    else rest.push_back(i);
+  }
   cudaEvent_t start;
   CK(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
   CK(cudaEventRecord(start, s));
-  // enqueue every problem on its own stream (graph launches overlap on the device)
-  for (int i = 0; i < n; ++i) {
-    mg_hierarchy* hi = checked(hs[i]);
-    CK(cudaStreamWaitEvent(hi->own_stream, start, 0));
-    std::memset(hi->hst, 0, sizeof(CgState));
-    hi->hst->rtol2 = rtol * rtol;
-    hi->hst->maxit = maxit;
-    gather<double, double>(hi->n0, hi->perm0, b[i], hi->cb, hi->own_stream);
-    CK(cudaMemcpyAsync(hi->st, hi->hst, sizeof(CgState), cudaMemcpyHostToDevice, hi->own_stream));
+  for (int i : rest) {
+    mg_hierarchy* hi = hs[i];
     if (!hi->graph) throw Error(MG_ERR_INVALID_ARG, "mg_solve_batch needs hierarchies built with use_graph = 1");
+    CK(cudaStreamWaitEvent(hi->own_stream, start, 0));
+    gather<double, double>(hi->n0, hi->perm0, b[i], hi->cb, hi->own_stream);
+    enqueue_state(hi, rtol, maxit, hi->own_stream);
     CK(cudaGraphLaunch(hi->graph, hi->own_stream));
     enqueue_exit(hi, hi->own_stream);
     scatter<double, double>(hi->n0, hi->perm0, hi->cx, x[i], hi->own_stream);
   }
+  DevMem tmp;
+  tmp.stream = s;
+  auto group = [&](const std::vector<int>& idx, auto tag) {
+    using T = decltype(tag);
+    if (idx.empty()) return;
+    std::vector<mg_hierarchy*> gh;
+    std::vector<double*> part;
+    std::vector<CgState*> states;
+    for (int i : idx) {
+      mg_hierarchy* hi = hs[i];
+      gh.push_back(hi);
+      part.push_back(tmp.alloc<double>(pcg_part_size(hi)));
+      states.push_back(hi->st);
+      gather<double, double>(hi->n0, hi->perm0, b[i], hi->cb, s);
+      enqueue_state(hi, rtol, maxit, s);
+    }
+    PProgram pg;
+    int nhead = 0;
+    assemble_pcg<T>(gh, part, pg, &nhead);
+    PTask* dt = tmp.upload(pg.tasks);
+    PPhase* dp = tmp.upload(pg.phases);
+    CgState** ds = tmp.upload(states);
+    PBarrier* bar = tmp.alloc<PBarrier>(1);
+    CK(persistent_launch<T>(dp, nhead, dt, bar, s, (int)pg.phases.size() - nhead, ds, (int)gh.size(),
+                            pcg_iteration_cap(maxit)));
+    for (int i : idx) {
+      enqueue_exit(hs[i], s);
+      scatter<double, double>(hs[i]->n0, hs[i]->perm0, hs[i]->cx, x[i], s);
+    }
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, &bar->error, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (err) throw Error(MG_ERR_TIMEOUT, "a grid barrier of the batched persistent solve gave up; results not valid");
+  };
+  group(g64, double());
+  group(g32, float());
+  CK(cudaStreamSynchronize(s));
+  tmp.release();
   int rc_all = MG_OK;
   for (int i = 0; i < n; ++i) {
     mg_hierarchy* hi = hs[i];
-    CK(cudaStreamSynchronize(hi->own_stream));
-    check_tma_timeout(hi, hi->own_stream);
+    if (std::find(rest.begin(), rest.end(), i) != rest.end()) {
+      CK(cudaStreamSynchronize(hi->own_stream));
+      check_device_waits(hi, hi->own_stream);
+    }
     int rc = collect_state(hi, info ? &info[i] : nullptr);
     if (rc_all == MG_OK) rc_all = rc;
   }
@@ -2083,7 +2622,7 @@ int mg_apply_A(mg_hierarchy_t* h, int32_t l, const double* x, double* y, void* s
     });
   }
   check_launch("mg_apply_A");
-  check_tma_timeout(h, s);
+  check_device_waits(h, s);
   return MG_OK;
   API_END_H(h)
 }
@@ -2137,7 +2676,7 @@ int mg_residual_restrict(mg_hierarchy_t* h, int32_t l, const double* b, const do
     store<T>(bc, C.b, C.n, C.perm, s);
   });
   check_launch("mg_residual_restrict");
-  check_tma_timeout(h, s);
+  check_device_waits(h, s);
   return MG_OK;
   API_END_H(h)
 }

@@ -507,62 +507,6 @@ __device__ __forceinline__ double block_sum(double v) {
 }
 
 constexpr int kCgBlocks = 152 * 4;
-// Absolute bound on CG iterations inside one graph launch, whatever maxit says.
-constexpr int kMaxCgIterations = 100000;
-
-__device__ void apply_finish(CgState* st, double s, int op, int use_cond, unsigned long long handle) {
-  switch (op) {
-    case FIN_BB:
-      st->bb = s;
-      st->it = 0;
-      st->status = 0;
-      st->cont = 1;
-      break;
-    case FIN_RZ0:
-      st->rz = s;
-      break;
-    case FIN_PQ:
-      if (st->bb == 0.0) {
-        st->alpha = 0.0;
-      } else if (!(s > 0.0) || !isfinite(s) || !isfinite(st->rz)) {
-        st->alpha = 0.0;
-        st->status = 3;
-      } else {
-        st->alpha = st->rz / s;
-      }
-      st->pq = s;
-      break;
-    case FIN_RR: {
-      st->rr = s;
-      int cont = 1;
-      if (st->bb == 0.0) {  // b = 0: x = 0 is exact, no iteration
-        st->status = 1;
-        st->cont = 0;
-        if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)handle, 0u);
-        break;
-      }
-      st->it += 1;
-      if (st->status == 3) cont = 0;
-      else if (s <= st->rtol2 * st->bb) st->status = 1, cont = 0;
-      else if (st->it >= st->maxit || st->it >= kMaxCgIterations) st->status = 2, cont = 0;
-      if (!isfinite(s)) st->status = 3, cont = 0;
-      st->cont = cont;
-      if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)handle, (unsigned)cont);
-      break;
-    }
-    case FIN_RZ:
-      st->beta = s / st->rz;
-      st->rz = s;
-      break;
-    case FIN_NORM:
-      st->rr = s;
-      break;
-    case FIN_TRUE:
-      st->rr_true = s;
-      break;
-  }
-}
-
 // Every thread of the block calls this with the block's partial s (valid in thread 0, as
 // block_sum returns it). The last block to arrive sums all partials in index order.
 __device__ void reduce_finish(double s, const Reduce& rd) {

@@ -64,6 +64,70 @@ struct CgState {
 // FIN_NORM: rr = the sum; FIN_TRUE: rr_true = the sum (|b - A x|^2 recomputed at exit)
 enum FinishOp { FIN_BB = 0, FIN_RZ0 = 1, FIN_PQ = 2, FIN_RR = 3, FIN_RZ = 4, FIN_NORM = 5, FIN_TRUE = 6 };
 
+// The CG state update that finishes a reduction with sum s (shared by the per-kernel solve and
+// the persistent batched solve): FIN_BB starts the recurrence, FIN_PQ sets alpha (breakdown on
+// a non-positive or non-finite p.q), FIN_RR counts the iteration and decides whether to go on
+// (converged, maxit, breakdown; inside a captured graph also the while-node condition),
+// FIN_RZ sets beta.
+#ifdef __CUDACC__
+// Absolute bound on CG iterations inside one solve, whatever maxit says.
+constexpr int kMaxCgIterations = 100000;
+
+__device__ inline void apply_finish(CgState* st, double s, int op, int use_cond, unsigned long long handle) {
+  switch (op) {
+    case FIN_BB:
+      st->bb = s;
+      st->it = 0;
+      st->status = 0;
+      st->cont = 1;
+      break;
+    case FIN_RZ0:
+      st->rz = s;
+      break;
+    case FIN_PQ:
+      if (st->bb == 0.0) {
+        st->alpha = 0.0;
+      } else if (!(s > 0.0) || !isfinite(s) || !isfinite(st->rz)) {
+        st->alpha = 0.0;
+        st->status = 3;
+      } else {
+        st->alpha = st->rz / s;
+      }
+      st->pq = s;
+      break;
+    case FIN_RR: {
+      st->rr = s;
+      int cont = 1;
+      if (st->bb == 0.0) {  // b = 0: x = 0 is exact, no iteration
+        st->status = 1;
+        st->cont = 0;
+        if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)handle, 0u);
+        break;
+      }
+      st->it += 1;
+      if (st->status == 3) cont = 0;
+      else if (s <= st->rtol2 * st->bb) st->status = 1, cont = 0;
+      else if (st->it >= st->maxit || st->it >= kMaxCgIterations) st->status = 2, cont = 0;
+      if (!isfinite(s)) st->status = 3, cont = 0;
+      st->cont = cont;
+      if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)handle, (unsigned)cont);
+      break;
+    }
+    case FIN_RZ:
+      st->beta = s / st->rz;
+      st->rz = s;
+      break;
+    case FIN_NORM:
+      st->rr = s;
+      break;
+    case FIN_TRUE:
+      st->rr_true = s;
+      break;
+  }
+}
+
+#endif
+
 // A reduction fused into the kernel that produces it: every block writes its partial sum to
 // part[block]; the last block to finish (an atomic ticket, reset by that block) sums the
 // partials in a fixed order and applies `op` to the CG state. With use_cond set (inside a
@@ -196,6 +260,86 @@ void cg_dotz(int n, const double* r, const T* vx, double* p, bool first, const R
 template <typename T> void cg_pupdate(int n, const CgState* st, const T* vx, double* p, cudaStream_t s);
 // reduction of |r|^2
 void dot_self(int n, const double* r, const Reduce& rd, cudaStream_t s);
+
+// ---- persistent execution of the lower V-cycle (persistent.cu) ----
+// Task kinds. CSR tasks (G lanes per row, 32/G rows per warp unit; rows != null maps task row
+// r to level row rows[r]): PK_CHEB_FIRST / PK_CHEB r = b - A x, d = c1 d + c2 D^-1 r (FIRST:
+// d = c2 D^-1 r), y = x + d; PK_RESID y = b - A x; PK_RESTRICT y = A x and z = 0; PK_PROLONG
+// y += A x; PK_SPMV y = A x. Elementwise (32 rows per unit): PK_CHEB0 d = c2 D^-1 b, y = x + d
+// (x null: y = d); PK_COPY y = x. One patch row per unit (FP64): PK_PATCH_RES / PK_PATCH_RES_AP
+// rbuf[r] = b[pdofs[r]] - (ELL row r of pv/pci, w slots, plen entries) . x; PK_PATCH_SOLVE
+// y[g] += X_i . r over the row's patch (r = rbuf, or b[pdofs] when rbuf is null). One row per
+// unit: PK_DENSE y_i = X_i . b (FP64, inv = row-major n x n; b from y64 when set, which the
+// restriction into the coarsest level fills, so that b is converted to FP64 once).
+// MG-PCG (FP64 recurrence, V-cycle vectors vb/vx of type T), 32 rows per unit unless CSR,
+// each unit writing its partial sum to part[unit]: PK_CG_INIT r = b, x = 0, vb = r, vx = 0,
+// partial b.b; PK_CG_AP (CSR, A_0 in FP64) q = A p, partial p.q; PK_CG_UPDATE x += alpha p,
+// r -= alpha q, vb = r, vx = 0, partial r.r; PK_CG_DOTZ partial r.z with z = vx (w = 1: also
+// p = z); PK_CG_PUPDATE p = z + beta p; PK_FINISH (one unit) sums part[0 .. w) in a fixed
+// order and applies FinishOp op to the CG state st. A task with gate set does nothing once
+// that CG state has stopped (gate->cont == 0).
+enum PKind {
+  PK_CHEB_FIRST = 1, PK_CHEB, PK_RESID, PK_RESTRICT, PK_PROLONG, PK_SPMV,
+  PK_CHEB0, PK_COPY, PK_PATCH_RES, PK_PATCH_RES_AP, PK_PATCH_SOLVE, PK_DENSE,
+  PK_CG_INIT, PK_CG_AP, PK_CG_UPDATE, PK_CG_DOTZ, PK_CG_PUPDATE, PK_FINISH
+};
+// One row of a patch solve: the patch's DoFs are pdofs[p0 .. p0 + n), this is its row i, whose
+// inverse row starts at element inv of the arena.
+struct PRow {
+  int32_t p0, n, i, pad;
+  int64_t inv;
+};
+struct PTask {
+  int32_t kind, n, G, u0;        // u0: the task's first unit within its phase
+  int32_t w, op;
+  const int32_t *rp, *ci, *rows;
+  const void* val;
+  const void *x, *b, *dinv;
+  void *d, *y, *z;
+  double c1, c2;
+  const int32_t *pdofs, *plen, *pci;
+  const double* pv;
+  double* rbuf;
+  const PRow* prow;
+  const double* inv;
+  double* y64;                  // PK_RESTRICT: also y64 = (double) y; PK_DENSE: b read from here
+  // MG-PCG
+  const CgState* gate;
+  CgState* st;
+  double* part;
+  const double* cb;
+  double *cx, *cr, *cp, *cq;
+  void *vb, *vx;
+};
+struct PPhase {
+  int32_t t0, t1, units, check;   // tasks [t0, t1) and their units in total; check: see below
+};
+// Barrier state of one hierarchy's persistent launches (zero-initialised; count returns to 0
+// after every complete barrier).
+struct PBarrier {
+  unsigned count, gen;
+  int error, abort;
+};
+constexpr int kPersistentThreads = 1024;
+constexpr int kPersistentBlocksPerSm = 1;
+// Units of a task: CSR kinds 32/G rows per unit, elementwise 32 rows, patch and dense kinds one row.
+inline int ptask_units(const PTask& t) {
+  switch (t.kind) {
+    case PK_CHEB0: case PK_COPY: case PK_CG_INIT: case PK_CG_UPDATE: case PK_CG_DOTZ: case PK_CG_PUPDATE:
+      return (t.n + 31) / 32;
+    case PK_PATCH_RES: case PK_PATCH_RES_AP: case PK_PATCH_SOLVE: case PK_DENSE: return t.n;
+    case PK_FINISH: return 1;
+    default: return (t.n + 32 / t.G - 1) / (32 / t.G);
+  }
+}
+template <typename T> int persistent_grid();
+// One cooperative launch walking phases[0 .. nhead) once with a grid barrier between phases;
+// then, when nbody > 0, the body phases[nhead .. nhead + nbody) repeatedly: after the barrier
+// that follows a body phase with check set, the loop ends unless some CG state of
+// states[0 .. nstates) still has cont set (at most max_iter passes).
+template <typename T>
+cudaError_t persistent_launch(const PPhase* phases, int nhead, const PTask* tasks, PBarrier* bar, cudaStream_t s,
+                              int nbody = 0, CgState* const* states = nullptr, int nstates = 0, int max_iter = 0);
 
 void check_launch(const char* what);
 

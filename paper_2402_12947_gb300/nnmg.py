@@ -42,7 +42,7 @@ class MgOptions(C.Structure):
                 ("use_graph", C.c_int32), ("local_levels_mask", C.c_int32), ("quality_threshold", C.c_double),
                 ("sell_sigma", C.c_int32), ("reorder", C.c_int32), ("global_smoother", C.c_int32),
                 ("pde", C.c_int32), ("young", C.c_double), ("poisson_ratio", C.c_double),
-                ("reserved", C.c_int32 * 4)]
+                ("small_level_dofs", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 class MgSolveInfo(C.Structure):

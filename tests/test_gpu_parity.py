@@ -413,3 +413,77 @@ def test_large_patch_limit_survives_a_later_smaller_hierarchy(nnmg):
     finally:
         H1.close()
         H2.close()
+
+
+@pytest.mark.parametrize("name", ["c1_p2", "c2_p2_128", "cube_p2"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_persistent_small_levels(nnmg, name, precision):
+    """The cycle from the first level with at most small_level_dofs DoFs down runs in one
+    persistent launch (phases and grid barriers instead of one launch per step): for every
+    split point (0 = off, so each level in turn, up to the whole cycle) the V-cycle matches the
+    oracle and the solve takes the oracle's iteration count."""
+    meshes, Ho, degree, layers = case(name)
+    lam = [lv.lmax for lv in Ho.levels[:-1]]
+    n = Ho.levels[0].n
+    b, x0 = rng_vec(n, 195), rng_vec(n, 196)
+    ref = x0 + mg.vcycle(Ho, b - Ho.levels[0].A @ x0)
+    rtol = 1e-10 if precision == "fp64" else 1e-8
+    xr, itr, _, _ = mg.pcg(Ho, b, rtol)
+    sizes = [lv.n for lv in Ho.levels]
+    for thr in [0] + sizes[::-1]:
+        with nnmg.Hierarchy.from_meshes(meshes, degree, 0.1, patch_layers=layers, lambda_override=lam,
+                                        precision=precision, small_level_dofs=thr) as H:
+            x = dev(x0)
+            H.vcycle(dev(b), x)
+            if precision == "fp64":
+                assert rel_err(host(x), ref) < TOL64, thr
+            else:
+                tape, var = Fp32Schedule(Ho).vcycle(b, x0)
+                check32(tape, var, host(x), thr)
+            xs = torch.zeros(n, dtype=torch.float64, device="cuda")
+            info = H.solve(dev(b), xs, rtol=rtol)
+            ok = info["iterations"] == itr if precision == "fp64" else info["iterations"] <= itr + 1
+            assert info["converged"] and ok, (thr, info, itr)
+            xh = host(xs)
+            assert np.linalg.norm(xh - xr) <= solution_gap_bound(Ho.levels[0].A, b, xh, xr)
+
+
+def test_persistent_batch_matches_alone_and_oracle(nnmg):
+    """mg_solve_batch with hierarchies whose whole solve runs persistently (small_level_dofs
+    >= n_0): one cooperative launch per precision iterates every problem's MG-PCG (phases of
+    all problems merged, a stopped problem idle) and the others run their graphs meanwhile.
+    Each result is bitwise the one of the same hierarchy solved alone, whatever else is in
+    the batch, and matches the oracle (FP64: the oracle's iteration count)."""
+    names = ["c1_p1", "c1_p2", "cube_p1", "cube_p2", "c2_p2_128"]
+    hs, bs, refs = [], [], []
+    big = 1 << 30
+    for k, nm in enumerate(names):
+        meshes, Ho, degree, layers = case(nm)
+        lam = [lv.lmax for lv in Ho.levels[:-1]]
+        prec = "fp64" if k % 2 == 0 else "mixed"
+        hs.append(nnmg.Hierarchy.from_meshes(meshes, degree, 0.1, patch_layers=layers, lambda_override=lam,
+                                             precision=prec, small_level_dofs=big))
+        b = rng_vec(Ho.levels[0].n, 500 + k)
+        bs.append(dev(b))
+        refs.append((Ho, b, prec))
+    hs.append(lib_geo(nnmg, "c1_p1"))   # a graph-path hierarchy in the same call
+    bs.append(dev(rng_vec(case("c1_p1")[1].levels[0].n, 510)))
+    try:
+        alone = []
+        for h, b in zip(hs, bs):
+            x = torch.zeros_like(b)
+            h.solve(b, x, rtol=1e-9)
+            alone.append(x)
+        for order in (list(range(len(hs))), list(range(len(hs)))[::-1], [0, 2]):
+            xs = [torch.zeros_like(bs[i]) for i in order]
+            infos = nnmg.solve_batch([hs[i] for i in order], [bs[i] for i in order], xs, rtol=1e-9)
+            for i, x, inf in zip(order, xs, infos):
+                assert inf["converged"]
+                assert torch.equal(alone[i], x), (i, order)
+        for (Ho, b, prec), x in zip(refs, alone):
+            xr, itr, _, _ = mg.pcg(Ho, b, 1e-9)
+            xh = host(x)
+            assert np.linalg.norm(xh - xr) <= solution_gap_bound(Ho.levels[0].A, b, xh, xr)
+    finally:
+        for h in hs[:-1]:
+            h.close()
