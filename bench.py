@@ -52,13 +52,16 @@ def parse():
     ap.add_argument("--n-fine", type=int, default=1024)
     ap.add_argument("--levels", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle-check", action="store_true",
+                    help="skip the oracle's solve of the same problem (error of each GPU solution against it)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the bounded serving stream of the default line")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every kernel individually instead of one CUDA graph per solve (profilers "
                          "cannot see kernel nodes of graphs with conditional nodes)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "serve", "paper", "lattice", "dumbbell"],
                     help="'serve': the mixed request stream through the continuous-batching server; "
                          "'paper': the Case A/B comparison and the residual history of the paper's examples")
-    ap.add_argument("--reorder", default=None, choices=["none", "rcm", "spatial"],
+    ap.add_argument("--reorder", default=None, choices=["none", "rcm", "spatial", "spatial-coarse"],
                     help="device-internal DoF order (default: the library's default)")
     ap.add_argument("--global-smoother", default="chebyshev", choices=["chebyshev", "sgs"],
                     help="S_g of the combined smoother (c2/c3/c4)")
@@ -151,8 +154,9 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline_subprocess(n_fine: int, steps: int = 1) -> dict:
-    """Time the CPU oracle's MG-PCG solve (setup excluded) in a fresh single-threaded process."""
+def cpu_baseline_subprocess(n_fine: int, steps: int = 1, single_thread: bool = True) -> dict:
+    """Time the CPU oracle's MG-PCG solve (setup excluded) in a fresh process, single-threaded
+    or with the thread settings left to the libraries (all host cores)."""
     code = f"""
 import json, time, os, sys
 sys.path.insert(0, {ROOT!r})
@@ -174,7 +178,10 @@ print(json.dumps({{"n": H.levels[0].n, "levels": levels, "setup_s": setup, "time
 """
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[k] = "1"
+        if single_thread:
+            env[k] = "1"
+        else:
+            env.pop(k, None)
     env.pop("CUDA_VISIBLE_DEVICES", None)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
@@ -182,11 +189,95 @@ print(json.dumps({{"n": H.levels[0].n, "levels": levels, "setup_s": setup, "time
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def export_for_oracle(H, b, path):
+    """The FP64 hierarchy's operators, transfers, patches and eigenvalues (library numbering)
+    and the right-hand side, for the oracle's V-cycle on the same data."""
+    import numpy as np
+    L = H.num_levels
+    arrs = {"L": np.array(L), "b": b}
+    for l in range(L):
+        rp, ci, v = H.export_level(l)
+        arrs.update({f"Ar{l}": rp, f"Ac{l}": ci, f"Av{l}": v})
+        pt = H.export_patches(l)
+        arrs[f"pp{l}"] = np.concatenate([[0], np.cumsum([len(p) for p in pt])]).astype(np.int64)
+        arrs[f"pd{l}"] = np.concatenate(pt).astype(np.int32) if pt else np.zeros(0, np.int32)
+        if l + 1 < L:
+            rp, ci, v = H.export_transfer(l)
+            arrs.update({f"Pr{l}": rp, f"Pc{l}": ci, f"Pv{l}": v})
+    arrs["lam"] = np.array([H.eigs(l)[2] for l in range(L - 1)])
+    np.savez(path, **arrs)
+
+
+ORACLE_SOLVE = """
+import json, sys, time
+import numpy as np, scipy.sparse as sp
+sys.path.insert(0, {root!r})
+from oracle import hierarchy, mg
+d = np.load({path!r})
+L = int(d["L"])
+n = [len(d[f"Ar{{l}}"]) - 1 for l in range(L)]
+As = [sp.csr_matrix((d[f"Av{{l}}"], d[f"Ac{{l}}"], d[f"Ar{{l}}"]), shape=(n[l], n[l])) for l in range(L)]
+Ps = [sp.csr_matrix((d[f"Pv{{l}}"], d[f"Pc{{l}}"], d[f"Pr{{l}}"]), shape=(n[l], n[l + 1])) for l in range(L - 1)]
+pats = []
+for l in range(L):
+    pp, pd = d[f"pp{{l}}"], d[f"pd{{l}}"]
+    pats.append([pd[pp[i]:pp[i + 1]] for i in range(len(pp) - 1)])
+t0 = time.perf_counter()
+H = hierarchy.from_matrices(As, Ps, pats, d["lam"])
+t1 = time.perf_counter()
+x, it, hist, tr = mg.pcg(H, d["b"], {rtol!r})
+t2 = time.perf_counter()
+np.save({out!r}, x)
+print(json.dumps({{"iterations": it, "true_rel_residual": tr, "setup_s": t1 - t0, "solve_s": t2 - t1}}))
+"""
+
+
+def start_oracle_solve(H, b):
+    """The oracle's MG-PCG on the exported FP64 hierarchy, started in the background
+    (single-threaded SciPy); returns (process, output path, directory)."""
+    tmp = tempfile.mkdtemp(prefix="nnmg_oracle_")
+    path, out = os.path.join(tmp, "h.npz"), os.path.join(tmp, "x.npy")
+    export_for_oracle(H, b, path)
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    env.pop("CUDA_VISIBLE_DEVICES", None)
+    code = ORACLE_SOLVE.format(root=ROOT, path=path, out=out, rtol=RTOL)
+    proc = subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                            text=True, env=env)
+    return proc, out, tmp
+
+
+def finish_oracle_solve(handle, solutions, timeout=900):
+    """Waits for the oracle; relative 2-norm errors of the GPU solutions against its solution."""
+    import numpy as np
+    import shutil
+    proc, out, tmp = handle
+    try:
+        so, se = proc.communicate(timeout=timeout)
+        if proc.returncode != 0:
+            return {"error": se[-500:]}
+        info = json.loads(so.strip().splitlines()[-1])
+        xo = np.load(out)
+        res = {k: float(np.linalg.norm(v - xo) / np.linalg.norm(xo)) for k, v in solutions.items()}
+        res.update({"oracle_iterations": info["iterations"], "oracle_true_rel_residual": info["true_rel_residual"],
+                    "oracle_solve_s": info["solve_s"],
+                    "note": "relative 2-norm difference to the oracle's MG-PCG solution (FP64, rtol 1e-8) on the "
+                            "exported operators; both solutions meet the residual test, so they may differ by up "
+                            "to (||r_gpu|| + ||r_oracle||) / lambda_min(A)"})
+        return res
+    except subprocess.TimeoutExpired:
+        proc.kill()
+        return {"error": "oracle solve timed out"}
+    finally:
+        shutil.rmtree(tmp, ignore_errors=True)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    d = cpu_baseline_subprocess(SAMPLE_N, steps=args.warmup + args.steps)
+    d = cpu_baseline_subprocess(SAMPLE_N, steps=args.warmup + args.steps, single_thread=False)
     t = d["times"][args.warmup:]
     mean = sum(t) / len(t)
     value = d["n"] / mean
@@ -196,7 +287,9 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": sample},
-            "cpu_baseline": {"value": value, "unit": "DoFs/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "DoFs/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample + " (thread settings left to NumPy/SciPy on all host cores; the sparse "
+                                                "products run on one of them)", "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "DoFs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -258,7 +351,7 @@ def run_ours(args):
     graph = 0 if args.no_graph else 1
     opts = dict(use_graph=graph, global_smoother=args.global_smoother)
     if args.reorder is not None:
-        opts["reorder"] = {"none": 0, "rcm": 1, "spatial": 2}[args.reorder]
+        opts["reorder"] = {"none": 0, "rcm": 1, "spatial": 2, "spatial-coarse": 3}[args.reorder]
     sgs = args.global_smoother == "sgs"
     H64 = nnmg.Hierarchy.from_meshes(meshes, degree, 0.1, **opts) if both else None
     setup64 = time.perf_counter() - t0
@@ -269,6 +362,7 @@ def run_ours(args):
     n = H32.num_dofs(0)
     b_host = inputs.uniform_rhs(n, replicas.rhs_seed(2, rank))
     b = torch.from_numpy(b_host).cuda()
+
     x = torch.zeros_like(b)
     stream = torch.cuda.current_stream()
 
@@ -326,8 +420,11 @@ def run_ours(args):
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
     e2e_ms = replicas.max_over_ranks([e2e_ms], device="cuda")[0]
 
+    x64 = x.clone()
     # the dominant kernel: fine-level fused Chebyshev SpMV of the FP32 V-cycle
     kms, kbytes = H32.time_smoother_kernel(reps=50)
+    # the second: the FP64 CG product q = A p with its p.q reduction
+    ap_ms, ap_bytes = H32.time_cg_product(reps=50)
     kms64, kbytes64 = H64.time_smoother_kernel(reps=50) if both else (float("nan"), float("nan"))
     peak, peak_src = measured_peak()
     traffic, rev = profiled_traffic()
@@ -340,11 +437,23 @@ def run_ours(args):
         return 0
     cpu = None
     if not args.no_cpu_baseline and args.workload == "c2":
-        d = cpu_baseline_subprocess(SAMPLE_N, steps=1)
-        cpu = {"value": d["n"] / d["times"][0], "unit": "DoFs/s", "cores": 1, "kind": "oracle",
-               "sample": f"oracle MG-PCG solve (setup excluded) on the same family at {SAMPLE_N}^2 "
-                         f"({d['n']} DoFs, {d['levels']} levels, {d['iterations'][0]} iterations, "
-                         f"{d['times'][0]:.1f} s), single-threaded NumPy/SciPy"}
+        ncores = os.cpu_count()
+        d1 = cpu_baseline_subprocess(SAMPLE_N, steps=1, single_thread=True)
+        dn = cpu_baseline_subprocess(SAMPLE_N, steps=1, single_thread=False)
+        sample = (f"oracle MG-PCG solve (setup excluded) on the same family at {SAMPLE_N}^2 ({dn['n']} DoFs, "
+                  f"{dn['levels']} levels, {dn['iterations'][0]} iterations)")
+        cpu = {"value": dn["n"] / dn["times"][0], "unit": "DoFs/s", "cores": ncores, "kind": "oracle",
+               "sample": sample + f", {dn['times'][0]:.1f} s with the thread settings left to NumPy/SciPy on "
+                         f"all {ncores} host cores (the sparse products run on one of them, BLAS on all)",
+               "cpu_model": cpu_model(),
+               "single_thread": {"value": d1["n"] / d1["times"][0], "cores": 1,
+                                 "sample": sample + f", {d1['times'][0]:.1f} s single-threaded"}}
+    serve = None if (args.no_serve or world > 1 or args.workload != "c2") else serve_bounded(nnmg, inputs)
+    # the oracle solves the same problem on the exported operators (after every GPU timing)
+    oracle_check = None
+    if both and not args.no_oracle_check and not sgs:
+        oracle_check = finish_oracle_solve(start_oracle_solve(H64, b_host),
+                                           {"mixed": x32.cpu().numpy(), "fp64": x64.cpu().numpy()})
     value = replicas.job_throughput(n, world, ms32)
     bpi32 = solve_bytes_per_iteration(H32, nnmg, 4)
     ideal32 = bpi32 * info32["iterations"] / (peak * 1e9) * 1e3
@@ -387,7 +496,13 @@ def run_ours(args):
                      "kernel": kernel_name,
                      "bytes_per_launch": kbytes, "ms_per_launch": kms, "peak_source": peak_src,
                      "fp64_kernel": {"achieved": kbytes64 / (kms64 * 1e-3) / 1e9, "ms_per_launch": kms64,
-                                     "bytes_per_launch": kbytes64}},
+                                     "bytes_per_launch": kbytes64},
+                     "cg_product": {"kernel": "FP64 CG product q = A_0 p with its p.q reduction (k_ap + k_finish)",
+                                    "bound": "hbm", "achieved": ap_bytes / (ap_ms * 1e-3) / 1e9, "peak": peak,
+                                    "frac": ap_bytes / (ap_ms * 1e-3) / 1e9 / peak, "ms_per_launch": ap_ms,
+                                    "bytes_per_launch": ap_bytes}},
+        "rel_error_vs_oracle": oracle_check,
+        "serve": serve,
         "cpu_baseline": cpu,
         "clocks": clk,
         "setup_s": {"fp64": setup64 if both else None, "mixed": setup32},
@@ -415,9 +530,71 @@ def serve_stream(n_requests: int, seed: int = 5):
     return out
 
 
+def serve_once(nnmg, stream, prec, rate, budget, max_active=16, setup_threads=12, arrival_seed=7):
+    """One pass of a request stream through the continuous-batching server: Poisson arrivals
+    at `rate` per second; per-request latency (submit to done) and device time (admission to
+    done), throughput over the wall time of the pass."""
+    import numpy as np
+    arrivals = np.cumsum(np.random.default_rng(arrival_seed).exponential(1.0 / rate, len(stream)))
+    with nnmg.Server(hbm_budget_bytes=budget, max_active=max_active, setup_threads=setup_threads) as srv:
+        t0 = time.perf_counter()
+        ids = []
+        for (meshes, degree, b, _), ta in zip(stream, arrivals):
+            now = time.perf_counter() - t0
+            if ta > now:
+                time.sleep(ta - now)
+            ids.append(srv.submit(meshes, degree, b=b, rtol=RTOL, precision=prec))
+        res = [srv.wait(i, timeout=3600) for i in ids]
+        wall = time.perf_counter() - t0
+        for i, r in zip(ids, res):
+            srv.fetch(i, r["n"])
+        st = srv.stats()
+    lat = np.array([r["t_total_ms"] for r in res])
+    dev = np.array([r["t_device_ms"] for r in res])
+    sol = np.array([r["t_solve_ms"] for r in res])
+    ok = [r for r in res if r["status"] == 0]
+    dofs = sum(r["n"] for r in ok)
+    return {"throughput_dofs_per_s": dofs / wall, "requests_per_s": len(ok) / wall,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "p50_device_ms": float(np.percentile(dev, 50)), "p99_device_ms": float(np.percentile(dev, 99)),
+            "mean_device_ms": float(dev.mean()),
+            "p50_solve_ms": float(np.percentile(sol, 50)), "p99_solve_ms": float(np.percentile(sol, 99)),
+            "sum_solve_ms": float(sol.sum()),
+            "failed": len(res) - len(ok), "peak_active": st["peak_active"],
+            "peak_bytes": st["peak_bytes"],
+            "max_true_rel_residual": max(r["true_rel_residual"] for r in ok) if ok else None,
+            "mean_iterations": float(np.mean([r["iterations"] for r in ok])) if ok else None}
+
+
+def serve_bounded(nnmg, inputs, n_requests=64, rate=32.0):
+    """The default line's serving measurement: a bounded seeded stream of the serving family
+    (2D P1/P2 32^2-256^2, 3D P1 16^3-32^3, 0-16 clusters each, random right-hand sides,
+    rtol 1e-8) at one Poisson arrival rate, mixed precision and FP64 on the same GPU."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(11)
+    stream, k = [], 0
+    while len(stream) < n_requests:
+        meshes, degree, label = inputs.serving_request(rng, 700000 + k)
+        k += 1
+        n = meshes[0].n
+        if (meshes[0].dim == 2 and n > 256) or (meshes[0].dim == 3 and n > 32):
+            continue
+        nfree = (n - 1) ** meshes[0].dim if degree == 1 else (2 * n - 1) ** meshes[0].dim
+        stream.append((meshes, degree, inputs.uniform_rhs(nfree, 700000 + k), label))
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.25 * free)
+    out = {"requests": n_requests, "arrival_rate_per_s": rate, "hbm_budget_bytes": budget, "max_active": 16,
+           "mix": "2D P1/P2 32^2-256^2 and 3D P1 16^3-32^3, 0-16 clusters, RHS U[-1,1], rtol 1e-8",
+           "dofs_total": int(sum((m[0].n - 1) ** m[0].dim if d == 1 else (2 * m[0].n - 1) ** m[0].dim
+                                 for m, d, _, _ in stream))}
+    for prec in ("mixed", "fp64"):
+        out[prec] = serve_once(nnmg, stream, prec, rate, budget)
+    return out
+
+
 def run_serve(args):
     """Continuous-batching server on the mixed stream at several Poisson arrival rates."""
-    import numpy as np
     import torch
     from paper_2402_12947_gb300 import build, nnmg
     build.build()
@@ -428,30 +605,7 @@ def run_serve(args):
     results = {}
     for prec in ("mixed", "fp64"):
         for rate in [float(r) for r in args.rates.split(",")]:
-            arrivals = np.cumsum(np.random.default_rng(7).exponential(1.0 / rate, len(stream)))
-            with nnmg.Server(hbm_budget_bytes=budget, max_active=16, setup_threads=12) as srv:
-                t0 = time.perf_counter()
-                ids = []
-                for (meshes, degree, b, _), ta in zip(stream, arrivals):
-                    now = time.perf_counter() - t0
-                    if ta > now:
-                        time.sleep(ta - now)
-                    ids.append(srv.submit(meshes, degree, b=b, rtol=RTOL, precision=prec))
-                res = [srv.wait(i, timeout=3600) for i in ids]
-                wall = time.perf_counter() - t0
-                for i, r in zip(ids, res):
-                    srv.fetch(i, r["n"])
-                st = srv.stats()
-            lat = np.array([r["t_total_ms"] for r in res])
-            ok = [r for r in res if r["status"] == 0]
-            dofs = sum(r["n"] for r in ok)
-            results[f"{prec}@{rate:g}/s"] = {
-                "throughput_dofs_per_s": dofs / wall, "requests_per_s": len(ok) / wall,
-                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "p50_device_ms": float(np.percentile([r["t_device_ms"] for r in res], 50)),
-                "failed": len(res) - len(ok), "peak_active": st["peak_active"], "peak_bytes": st["peak_bytes"],
-                "max_true_rel_residual": max(r["true_rel_residual"] for r in ok) if ok else None,
-                "mean_iterations": float(np.mean([r["iterations"] for r in ok])) if ok else None}
+            results[f"{prec}@{rate:g}/s"] = serve_once(nnmg, stream, prec, rate, budget)
     best = max(results.values(), key=lambda d: d["throughput_dofs_per_s"])
     line = {"metric": METRIC, "value": best["throughput_dofs_per_s"], "unit": "DoFs/s", "n_gpus": 1,
             "steps": args.requests, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
@@ -462,6 +616,17 @@ def run_serve(args):
             "serve": results}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def run_paper(args):

@@ -92,9 +92,11 @@ enum mg_pde {
 enum mg_reorder {
   MG_REORDER_NONE = 0,    /* the library numbering */
   MG_REORDER_RCM = 1,     /* reverse Cuthill-McKee of the matrix graph */
-  MG_REORDER_SPATIAL = 2  /* Z-order (Morton) of the DoF points, vertex and edge DoFs
+  MG_REORDER_SPATIAL = 2, /* Z-order (Morton) of the DoF points, vertex and edge DoFs
                              interleaved; the library numbering where a level has no points
                              (mg_setup_csr) */
+  MG_REORDER_SPATIAL_COARSE = 3  /* MG_REORDER_SPATIAL on every level but the finest, which
+                                    keeps the library numbering */
 };
 
 /* Arithmetic of the V-cycle (option `precision`). */
@@ -153,8 +155,13 @@ typedef struct mg_options_t {
                               below it, run their part of each V-cycle inside one persistent
                               cooperative launch (phases separated by grid barriers) instead of
                               one launch per step; 0 = never (Chebyshev global smoother only)
-                              (100000) */
-  int32_t reserved[3];
+                              (0) */
+  int32_t fp32_patch_kappa; /* MIXED precision: a patch whose block has condition number
+                              kappa_1 = ||A[B,B]||_1 ||A[B,B]^-1||_1 at most this value applies its
+                              inverse in FP32 (FP32 copy of the inverse, FP32 products); the
+                              ill-conditioned ones, and every patch in FP64 precision, stay FP64;
+                              0 = all FP64 (10000) */
+  int32_t reserved[2];
 } mg_options_t;
 
 /* Result of a solve. */
@@ -221,6 +228,10 @@ int mg_export_level(const mg_hierarchy_t* h, int32_t level, int32_t* rowptr, int
 int mg_export_transfer(const mg_hierarchy_t* h, int32_t level, int32_t* rowptr, int32_t* colidx, double* values);
 /* Patches of a level: ptr[num+1], dofs[total] (free DoF ids). */
 int mg_export_patches(const mg_hierarchy_t* h, int32_t level, int32_t* ptr, int32_t* dofs);
+/* Per patch of level l (the order of mg_export_patches): 1 if the local correction (Alg. 2)
+ * applies its inverse in FP32 (MIXED precision, option fp32_patch_kappa), else 0, into
+ * flags[num_patches] (host). Needs the device phase (INVALID_ARG for host-only hierarchies). */
+int mg_export_patch_precision(const mg_hierarchy_t* h, int32_t level, int32_t* flags);
 /* The multicolour SGS colouring of level l (library numbering): *ncolours, and colour[n]
  * (nullable) with each DoF's colour. INVALID_ARG unless global_smoother = MG_GLOBAL_SGS
  * and l is below the coarsest level. Works for host-only hierarchies. */
@@ -350,6 +361,8 @@ typedef struct mg_request_result_t {
   double t_wait_ms;            /* host set-up done -> admitted to the device */
   double t_device_ms;          /* admitted -> solution on the host (device set-up + solve) */
   double t_total_ms;           /* submission -> done */
+  double t_solve_ms;           /* GPU time of the solve itself (CUDA events on the request's
+                                  stream around the copies in and out and the MG-PCG) */
 } mg_request_result_t;
 
 typedef struct mg_server_stats_t {
@@ -392,6 +405,12 @@ void mg_server_destroy(mg_server_t* s);
  * race. X_dev, b_dev [n], x_dev [n] are caller-owned device pointers; asynchronous on
  * `stream`. */
 int mg_dense_symv_static(const double* X_dev, int64_t n, const double* b_dev, double* x_dev, void* stream);
+
+/* Mean device time of the FP64 CG product q = A_0 p with its p.q reduction (the k_ap kernel
+ * and its one-block finish) over reps back-to-back launches on `stream` (CUDA events; blocks),
+ * and its algorithmic bytes per launch (values and indices once, p and q once, metadata).
+ * Overwrites the hierarchy's CG work vectors; measurement helper. */
+int mg_time_cg_product(mg_hierarchy_t* h, int32_t reps, void* stream, double* ms, double* bytes);
 
 /* Device bytes held by the hierarchy. */
 int64_t mg_device_bytes(const mg_hierarchy_t* h);

@@ -524,6 +524,8 @@ struct DevLevel {
   int32_t* plen = nullptr;                     // entries of each patch row
   double* pv = nullptr;
   double *inv = nullptr, *rbuf = nullptr;
+  float* inv32 = nullptr;            // FP32 arena of the well-conditioned patches' inverses
+  std::vector<int32_t> pfp32;        // per patch: 1 if applied in FP32
   PatchItem* items = nullptr;
   // rows (A P)_{i,:} of the patch rows, ELL with apw slots each and aplen entries (the S_c
   // after prolongation)
@@ -582,8 +584,8 @@ struct Engine {
     T *xa = L.x, *xb = L.xt;
     for (int j = 0; j < cheb_k; ++j) {
       if (j == 0 && zero == 3) {
-        cheb_entry_local<T>(L.nitems, L.items, L.pdofs, L.inv, L.max_patch, L.n, L.b, L.dinv, xa, L.d, xb, L.cr[0],
-                            L.nh, L.hrow, L.hrp, L.hci, L.hv, s);
+        cheb_entry_local<T>(L.nitems, L.items, L.pdofs, L.inv, L.inv32, L.max_patch, L.n, L.b, L.dinv, xa, L.d, xb,
+                            L.cr[0], L.nh, L.hrow, L.hrp, L.hci, L.hv, s);
         launches += L.nh > 0 ? 2 : 1;
       } else if (j == 0 && zero) {
         const int nh = zero == 2 ? L.nh : 0;
@@ -622,7 +624,7 @@ struct Engine {
       patch_residual<T>(L.nt, L.pw, L.pdofs, L.plen, L.pci, L.pv, L.b, L.x, L.rbuf, s);
       ++launches;
     }
-    patch_solve<T>(L.nitems, L.items, L.pdofs, L.inv, zero ? nullptr : L.rbuf, L.b, L.x, L.max_patch, s);
+    patch_solve<T>(L.nitems, L.items, L.pdofs, L.inv, L.inv32, zero ? nullptr : L.rbuf, L.b, L.x, L.max_patch, s);
     ++launches;
   }
   // zero: the iterate is zero on entry (first pre-smoothing on every level of a cycle);
@@ -1021,9 +1023,10 @@ void validate_options(const mg_options_t& o) {
   if (!(o.lmax_safety > 0)) throw Error(MG_ERR_INVALID_ARG, "lmax_safety must be positive");
   if (o.sell_sigma < 0 || o.sell_sigma > (1 << 20)) throw Error(MG_ERR_INVALID_ARG, "sell_sigma must be in [0, 2^20]");
   if (o.global_smoother < 0 || o.global_smoother > 1) throw Error(MG_ERR_INVALID_ARG, "unknown global smoother");
-  if (o.reorder < 0 || o.reorder > 2) throw Error(MG_ERR_INVALID_ARG, "unknown reorder mode");
+  if (o.reorder < 0 || o.reorder > 3) throw Error(MG_ERR_INVALID_ARG, "unknown reorder mode");
   if (o.pde < 0 || o.pde > 1) throw Error(MG_ERR_INVALID_ARG, "unknown pde");
   if (o.small_level_dofs < 0) throw Error(MG_ERR_INVALID_ARG, "small_level_dofs must be >= 0");
+  if (o.fp32_patch_kappa < 0) throw Error(MG_ERR_INVALID_ARG, "fp32_patch_kappa must be >= 0");
   if (o.pde == MG_PDE_ELASTICITY && !(o.young > 0 && o.poisson_ratio > -1.0 && o.poisson_ratio < 0.5))
     throw Error(MG_ERR_INVALID_ARG, "elasticity needs E > 0 and -1 < nu < 1/2");
 }
@@ -1227,7 +1230,9 @@ void build_device(mg_hierarchy* h) {
     if (l + 1 == L) continue;
     const LevelH& H = h->host[l];
     if (o.reorder == MG_REORDER_RCM) perm[l] = rcm_order(H.A);
-    else if (o.reorder == MG_REORDER_SPATIAL && !H.dof_points.empty()) perm[l] = morton_order(H.dof_points, H.dim);
+    else if ((o.reorder == MG_REORDER_SPATIAL || (o.reorder == MG_REORDER_SPATIAL_COARSE && l > 0)) &&
+             !H.dof_points.empty())
+      perm[l] = morton_order(H.dof_points, H.dim);
     if (!perm[l].empty()) iperm[l] = inverse_perm(perm[l]);
   }
   for (int l = 0; l < L; ++l) {
@@ -1266,6 +1271,7 @@ void build_device(mg_hierarchy* h) {
   for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return blks[a].n > blks[b].n; });
   GjBatch gj;
+  std::vector<double> anorm;   // ||A_block||_1 by block id
   gj.nmat = (int)blks.size();
   std::vector<int64_t> boff(blks.size()), bvoff(blks.size());  // by block id
   std::vector<int64_t> soff, svoff;                              // by sorted position
@@ -1282,6 +1288,7 @@ void build_device(mg_hierarchy* h) {
   gj.max_n = gj.hn.empty() ? 0 : gj.hn[0];
   {
     std::vector<double> Mh(mtot), d0(vtot);
+    anorm.assign(blks.size(), 0.0);
     parallel_for((int64_t)blks.size(), [&](int64_t lo, int64_t hi) {
       for (int64_t id = lo; id < hi; ++id) {
         const Blk& bk = blks[id];
@@ -1298,6 +1305,13 @@ void build_device(mg_hierarchy* h) {
         std::vector<double> D = dense_submatrix(lv.A, idx, bk.n);
         std::copy(D.begin(), D.end(), Mh.begin() + boff[id]);
         for (int32_t i = 0; i < bk.n; ++i) d0[bvoff[id] + i] = D[(int64_t)i * bk.n + i];
+        double nrm = 0.0;   // ||A[B,B]||_1 (symmetric: the largest row sum of |a_ij|)
+        for (int32_t i = 0; i < bk.n; ++i) {
+          double rs = 0.0;
+          for (int32_t j = 0; j < bk.n; ++j) rs += std::fabs(D[(int64_t)i * bk.n + j]);
+          nrm = std::max(nrm, rs);
+        }
+        anorm[id] = nrm;
       }
     });
     gj.M = mem.upload(Mh);
@@ -1333,6 +1347,45 @@ void build_device(mg_hierarchy* h) {
   for (size_t id = 0; id < blks.size(); ++id)
     if (blks[id].patch >= 0) level_inv_off[blks[id].level].push_back(boff[id]);
   const double* coarse_inv = gj.M + boff[blks.size() - 1];
+  // Mixed precision: patches with kappa_1 = ||A_BB||_1 ||A_BB^-1||_1 <= fp32_patch_kappa apply an
+  // FP32 copy of their inverse (an FP32 arena); the others, and the coarsest block, stay FP64.
+  std::vector<std::vector<int32_t>> level_fp32(L);
+  std::vector<std::vector<int64_t>> level_inv32_off(L);
+  float* inv32 = nullptr;
+  if (h->mixed() && o.fp32_patch_kappa > 0 && blks.size() > 1) {
+    double* dn = mem.alloc<double>(gj.nmat);
+    batched_norm1(gj, dn, mem.stream);
+    std::vector<double> xn(gj.nmat);
+    CK(cudaMemcpyAsync(xn.data(), dn, sizeof(double) * gj.nmat, cudaMemcpyDeviceToHost, mem.stream));
+    CK(cudaStreamSynchronize(mem.stream));
+    int64_t tot32 = 0;
+    std::vector<int64_t> off32(blks.size(), -1);
+    for (int sp = 0; sp < gj.nmat; ++sp) {
+      const int id = order[sp];
+      if (blks[id].patch < 0) continue;
+      const double kappa = anorm[id] * xn[sp];
+      if (kappa <= (double)o.fp32_patch_kappa && std::isfinite(kappa)) {
+        off32[id] = tot32;
+        tot32 += (int64_t)blks[id].n * blks[id].n;
+      }
+    }
+    if (tot32 > 0) inv32 = mem.alloc<float>(tot32);
+    for (size_t id = 0; id < blks.size(); ++id) {
+      if (blks[id].patch < 0) continue;
+      const int l = blks[id].level;
+      level_fp32[l].push_back(off32[id] >= 0 ? 1 : 0);
+      level_inv32_off[l].push_back(off32[id]);
+      if (off32[id] >= 0)
+        convert<double, float>(blks[id].n * blks[id].n, gj.M + boff[id], inv32 + off32[id], mem.stream);
+    }
+    check_launch("FP32 patch inverses");
+  } else {
+    for (size_t id = 0; id < blks.size(); ++id)
+      if (blks[id].patch >= 0) {
+        level_fp32[blks[id].level].push_back(0);
+        level_inv32_off[blks[id].level].push_back(-1);
+      }
+  }
   auto upload_engine = [&](auto* eng, auto tag) {
     using T = decltype(tag);
     eng->cheb_k = o.cheb_degree;
@@ -1389,10 +1442,13 @@ void build_device(mg_hierarchy* h) {
             return H.patch_ptr[a + 1] - H.patch_ptr[a] > H.patch_ptr[b + 1] - H.patch_ptr[b];
           });
           std::vector<PatchItem> items;
+          D.pfp32 = level_fp32[l];
           for (int p : porder) {
             const int32_t p0 = H.patch_ptr[p], m = H.patch_ptr[p + 1] - p0;
             D.max_patch = std::max(D.max_patch, m);
-            for (int r0 = 0; r0 < m; r0 += kPatchRowsPerItem) items.push_back({p0, m, r0, 0, level_inv_off[l][p]});
+            const bool f32 = std::is_same<T, float>::value && level_fp32[l][p];
+            const int64_t off = f32 ? level_inv32_off[l][p] : level_inv_off[l][p];
+            for (int r0 = 0; r0 < m; r0 += kPatchRowsPerItem) items.push_back({p0, m, r0, f32 ? 1 : 0, off});
           }
           if (D.max_patch > kMaxPatchDofs)
             throw Error(MG_ERR_INVALID_ARG, "patch larger than " + std::to_string(kMaxPatchDofs) + " DoFs");
@@ -1401,6 +1457,7 @@ void build_device(mg_hierarchy* h) {
           D.pci = mem.upload(pci);
           D.pv = mem.upload(pv);
           D.inv = gj.M;
+          D.inv32 = inv32;
           D.rbuf = mem.alloc<double>(D.nt);
           D.items = mem.upload(items);
           // rows of A with an entry in a patch column (A is symmetric: patch DoFs and neighbours)
@@ -1990,6 +2047,7 @@ void mg_default_options(mg_options_t* o) {
   o->young = 6.9e10;
   o->poisson_ratio = 0.33;
   o->small_level_dofs = 0;
+  o->fp32_patch_kappa = 10000;
 }
 
 }  // extern "C"
@@ -2109,7 +2167,7 @@ int64_t estimate_device_bytes(const mg_hierarchy* h) {
     const int64_t np = (int64_t)lv.patch_ptr.size() - 1;
     for (int64_t p = 0; p < np; ++p) {
       int64_t m = lv.patch_ptr[p + 1] - lv.patch_ptr[p];
-      tot += 8 * m * m + 64 * m;
+      tot += (vbytes == 4 ? 12 : 8) * m * m + 64 * m;   // FP64 inverse (+ its FP32 copy, mixed)
     }
     if (np > 0) tot += 16 * (int64_t)lv.A.nnz() / std::max<int64_t>(lv.A.nrows, 1) * (int64_t)lv.patch_dofs.size() * 4;
     if (np > 0 && l + 1 < h->L)  // rows of A P on the patch rows
@@ -2135,10 +2193,12 @@ std::vector<double> hierarchy_unit_load(const mg_hierarchy* h) {
   return b;
 }
 
-void enqueue_host_solve(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit, cudaEvent_t done) {
+void enqueue_host_solve(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit, cudaEvent_t done,
+                        cudaEvent_t start) {
   if (!h->graph && !h->solo.tasks)
     throw Error(MG_ERR_INVALID_ARG, "the solve server needs hierarchies built with use_graph = 1");
   cudaStream_t s = h->own_stream;
+  if (start) CK(cudaEventRecord(start, s));
   CK(cudaMemcpyAsync(h->cq, b, sizeof(double) * h->n0, cudaMemcpyHostToDevice, s));
   gather<double, double>(h->n0, h->perm0, h->cq, h->cb, s);
   enqueue_state(h, rtol, maxit, s);
@@ -2327,6 +2387,21 @@ int mg_export_patches(const mg_hierarchy_t* hc, int32_t l, int32_t* ptr, int32_t
   const LevelH& lv = h->host[l];
   if (ptr) std::copy(lv.patch_ptr.begin(), lv.patch_ptr.end(), ptr);
   if (dofs) std::copy(lv.patch_dofs.begin(), lv.patch_dofs.end(), dofs);
+  return MG_OK;
+  API_END_H(h)
+}
+
+int mg_export_patch_precision(const mg_hierarchy_t* hc, int32_t l, int32_t* flags) {
+  mg_hierarchy* h = const_cast<mg_hierarchy*>(hc);
+  API_BEGIN
+  checked(h);
+  check_level(h, l);
+  const int64_t np = (int64_t)h->host[l].patch_ptr.size() - 1;
+  if (np > 0 && !flags) throw Error(MG_ERR_INVALID_ARG, "null flags");
+  h->with_engine([&](auto& e) {
+    const auto& v = e.lv[l].pfp32;
+    for (int64_t p = 0; p < np; ++p) flags[p] = (size_t)p < v.size() ? v[p] : 0;
+  });
   return MG_OK;
   API_END_H(h)
 }
@@ -2796,6 +2871,38 @@ int mg_time_smoother_kernel(mg_hierarchy_t* h, int32_t reps, void* stream, doubl
   cudaEventDestroy(e1);
   if (ms) *ms = (double)t / reps;
   if (bytes) *bytes = nbytes;
+  return MG_OK;
+  API_END_H(h)
+}
+
+int mg_time_cg_product(mg_hierarchy_t* h, int32_t reps, void* stream, double* ms, double* bytes) {
+  API_BEGIN
+  checked(h);
+  if (reps < 1) throw Error(MG_ERR_INVALID_ARG, "reps must be >= 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  // q = A p with the p.q reduction (into the CG state, which the next solve re-initialises)
+  CgState* st = h->st;
+  sell_ap(h->A0, h->cp, h->cq, h->part, st, FIN_NORM, s);  // warm-up
+  CK(cudaEventRecord(e0, s));
+  for (int i = 0; i < reps; ++i) sell_ap(h->A0, h->cp, h->cq, h->part, st, FIN_NORM, s);
+  CK(cudaEventRecord(e1, s));
+  check_launch("mg_time_cg_product");
+  CK(cudaEventSynchronize(e1));
+  float t = 0;
+  CK(cudaEventElapsedTime(&t, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const SellMat<double>& M = h->A0;
+  const double meta = M.lanes > 1 ? 4.0 * (M.nrows + 1) + (M.col16 ? 4.0 * M.nrows : 0.0)
+                                  : 8.0 * (M.nslices + 1) + (M.col16 ? 4.0 * M.nslices : 0.0) +
+                                        (M.perm ? 4.0 * M.nrows : 0.0);
+  if (ms) *ms = (double)t / reps;
+  // algorithmic bytes: each nonzero's value and index once, p read (gathered) and q written
+  // once, the slice/row metadata
+  if (bytes) *bytes = 8.0 * (double)M.nnz + M.idx_bytes + 16.0 * (double)M.nrows + meta;
   return MG_OK;
   API_END_H(h)
 }

@@ -198,7 +198,9 @@ int64_t hierarchy_dofs(const mg_hierarchy* h);
 std::vector<double> hierarchy_unit_load(const mg_hierarchy* h);
 // Enqueue one MG-PCG solve on the hierarchy's own stream: b (page-locked host, n_0) in, the
 // solution to x (page-locked host) and the CG state out, then record `done`.
-void enqueue_host_solve(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit, cudaEvent_t done);
+// `start` (nullable) is recorded before the copy in.
+void enqueue_host_solve(mg_hierarchy* h, const double* b, double* x, double rtol, int maxit, cudaEvent_t done,
+                        cudaEvent_t start = nullptr);
 // After `done` has completed: the solve's status and info.
 int collect_host_solve(mg_hierarchy* h, mg_solve_info_t* info);
 void destroy_hierarchy(mg_hierarchy* h);

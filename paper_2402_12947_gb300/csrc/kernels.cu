@@ -669,55 +669,68 @@ __global__ void __launch_bounds__(kBlock) k_prolong_pr(OpView<T> m, const T* __r
   x[row] = x[row] + ax;
 }
 
-// S_c phase 2: e = (A^[d])^{-1} r_B and x_B += e, one launch over the work list. A work
-// item is kPatchRowsPerItem (8) consecutive rows of one patch, one block per item and one
-// warp per row; lane l accumulates entries l, l + 32, ... of row i of the symmetric inverse
-// (contiguous), then the warp sums. The items are sorted by patch size, largest first, so
-// the longest items start first. Every load that does not need the residual (the row's DoF
-// id and current value, its first 256 inverse entries) is issued before the block barrier
-// that stages the patch residual in shared memory. With rbuf == nullptr the iterate is zero
-// and the residual is b itself.
-template <typename T>
-__device__ __forceinline__ void patch_item(const PatchItem it, const int32_t* __restrict__ pdofs,
-                                           const double* __restrict__ inv, const double* rbuf,
-                                           const T* __restrict__ b, T* __restrict__ x, double* rs) {
-  constexpr int K = 8;  // inverse entries per lane loaded ahead of the barrier (256 per row)
+// S_c phase 2: e = (A^[d])^{-1} r_B and x_B += e, one launch over the work list. A work item
+// is kPatchRowsPerItem (32) consecutive rows of one patch, one block per item: lane l owns row
+// i = row0 + l, and the block's eight warps split the columns, warp w taking j = w, w + 8, ...
+// The inverse X is symmetric, so row i's entry j is read as X[j][i]: for each j the warp reads
+// X[j][row0 .. row0 + 31], 256 contiguous bytes, and every FMA of a warp instruction is one of
+// the product's (no per-row warp reduction). The eight partial sums of a row are added in
+// warp order through shared memory. The patch residual is staged in shared memory first (b
+// itself when the iterate is zero, rbuf == nullptr). Items sorted by patch size, largest first.
+// FP32 items (mixed form, well-conditioned patches): X and the staged residual in FP32, FP32
+// FMAs, the result added to x in FP64 and rounded to T.
+constexpr int kPatchWarps = kBlock / 32;
+
+template <typename T, typename V>
+__device__ __forceinline__ void patch_item_rows(const PatchItem it, const int32_t* __restrict__ pdofs,
+                                                const V* __restrict__ X, const double* rbuf,
+                                                const T* __restrict__ b, T* __restrict__ x, V* rs) {
+  __shared__ V red[kPatchWarps][32];
   const int p0 = it.p0, n = it.n;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = it.row0 + warp;
+  const int i = it.row0 + lane;
   const bool ok = i < n;
-  const double* Xi = inv + it.inv + (int64_t)(ok ? i : 0) * n;
-  const int g = ok ? pdofs[p0 + i] : 0;
-  const T xg = ok ? x[g] : T(0);
-  double xr[K];
-#pragma unroll
-  for (int u = 0; u < K; ++u) xr[u] = ok && lane + 32 * u < n ? Xi[lane + 32 * u] : 0.0;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) rs[j] = rbuf ? rbuf[p0 + j] : (double)b[pdofs[p0 + j]];
+  const int g = warp == 0 && ok ? pdofs[p0 + i] : 0;
+  const T xg = warp == 0 && ok ? x[g] : T(0);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) rs[j] = (V)(rbuf ? rbuf[p0 + j] : (double)b[pdofs[p0 + j]]);
   __syncthreads();
-  if (!ok) return;  // warp-uniform; no block barrier follows
-  double e = 0.0;
+  const V* Xc = X + it.row0 + lane;
+  V e[2] = {V(0), V(0)};
+  int j = warp;
+  for (; j + 7 * kPatchWarps < n; j += 8 * kPatchWarps) {   // eight rows of X in flight per lane
+    V v[8];
 #pragma unroll
-  for (int u = 0; u < K; ++u)
-    if (lane + 32 * u < n) e = fma(xr[u], rs[lane + 32 * u], e);
-  for (int j0 = 32 * K; j0 < n; j0 += 32 * K) {  // rows longer than 256: K loads per lane at a time
-    double v[K];
+    for (int u = 0; u < 8; ++u) v[u] = ok ? Xc[(int64_t)(j + u * kPatchWarps) * n] : V(0);
 #pragma unroll
-    for (int u = 0; u < K; ++u) v[u] = j0 + lane + 32 * u < n ? Xi[j0 + lane + 32 * u] : 0.0;
-#pragma unroll
-    for (int u = 0; u < K; ++u)
-      if (j0 + lane + 32 * u < n) e = fma(v[u], rs[j0 + lane + 32 * u], e);
+    for (int u = 0; u < 8; ++u) e[u & 1] = fma(v[u], rs[j + u * kPatchWarps], e[u & 1]);
   }
-  e = warp_sum(e);
-  if (lane == 0) x[g] = (T)((double)xg + e);
+  for (; j < n; j += kPatchWarps) e[0] = fma(ok ? Xc[(int64_t)j * n] : V(0), rs[j], e[0]);
+  red[warp][lane] = e[0] + e[1];
+  __syncthreads();
+  if (warp != 0 || !ok) return;
+  double s = 0.0;
+#pragma unroll
+  for (int w = 0; w < kPatchWarps; ++w) s += (double)red[w][lane];
+  x[g] = (T)((double)xg + s);
+}
+
+template <typename T>
+__device__ __forceinline__ void patch_item(const PatchItem it, const int32_t* __restrict__ pdofs,
+                                           const double* __restrict__ inv, const float* __restrict__ inv32,
+                                           const double* rbuf, const T* __restrict__ b, T* __restrict__ x,
+                                           double* rs) {
+  if (it.fp32) patch_item_rows<T, float>(it, pdofs, inv32 + it.inv, rbuf, b, x, reinterpret_cast<float*>(rs));
+  else patch_item_rows<T, double>(it, pdofs, inv + it.inv, rbuf, b, x, rs);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_patch_solve(const PatchItem* __restrict__ items,
                                                         const int32_t* __restrict__ pdofs,
-                                                        const double* __restrict__ inv, const double* rbuf,
+                                                        const double* __restrict__ inv,
+                                                        const float* __restrict__ inv32, const double* rbuf,
                                                         const T* __restrict__ b, T* __restrict__ x) {
   extern __shared__ double rs[];
-  patch_item<T>(items[blockIdx.x], pdofs, inv, rbuf, b, x, rs);
+  patch_item<T>(items[blockIdx.x], pdofs, inv, inv32, rbuf, b, x, rs);
 }
 
 // Start of a pre-smoothing S_c, S_g, ... from a zero iterate, in one launch: blocks
@@ -728,13 +741,14 @@ __global__ void __launch_bounds__(kBlock) k_patch_solve(const PatchItem* __restr
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_cheb0_entry(int nitems, const PatchItem* __restrict__ items,
                                                         const int32_t* __restrict__ pdofs,
-                                                        const double* __restrict__ inv, int n,
+                                                        const double* __restrict__ inv,
+                                                        const float* __restrict__ inv32, int n,
                                                         const T* __restrict__ b, const T* __restrict__ dinv,
                                                         T* __restrict__ x, T* __restrict__ d, T* __restrict__ xout,
                                                         T cr) {
   extern __shared__ double rs[];
   if ((int)blockIdx.x < nitems) {  // block-uniform
-    patch_item<T>(items[blockIdx.x], pdofs, inv, nullptr, b, x, rs);
+    patch_item<T>(items[blockIdx.x], pdofs, inv, inv32, nullptr, b, x, rs);
     return;
   }
   const int i = ((int)blockIdx.x - nitems) * kBlock + threadIdx.x;
@@ -953,6 +967,28 @@ __global__ void k_gj_update(GjBatch g, int k) {
   }
 }
 
+// max_i sum_j |M_ij| of matrix blockIdx.x of the batch (column sums: M is symmetric, so
+// thread i reads column i, coalesced across the block).
+__global__ void __launch_bounds__(kBlock) k_gj_norm1(GjBatch g, double* __restrict__ out) {
+  __shared__ double best[kBlock];
+  const int b = blockIdx.x;
+  const int n = g.n[b];
+  const double* M = g.M + g.off[b];
+  double m = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double sum = 0.0;
+    for (int j = 0; j < n; ++j) sum += fabs(M[(int64_t)j * n + i]);
+    m = fmax(m, sum);
+  }
+  best[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = kBlock / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) best[threadIdx.x] = fmax(best[threadIdx.x], best[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[b] = best[0];
+}
+
 }  // namespace
 
 void lanczos_dot(int n, const double* w, const double* v, double* part, double* out, cudaStream_t s) {
@@ -978,6 +1014,10 @@ void batched_spsd_inverse(const GjBatch& g, cudaStream_t s) {
     k_gj_prep<<<active, kBlock, 0, s>>>(g, k);
     k_gj_update<<<dim3(bx, active), kBlock, 0, s>>>(g, k);
   }
+}
+
+void batched_norm1(const GjBatch& g, double* out, cudaStream_t s) {
+  if (g.nmat > 0) k_gj_norm1<<<g.nmat, kBlock, 0, s>>>(g, out);
 }
 
 int sell_blocks(int nrows, int lanes) { return grid_for((int)std::min<int64_t>((int64_t)nrows * lanes, INT32_MAX), kBlock); }
@@ -1202,23 +1242,23 @@ void patch_solve_setup(int max_patch) {
 }
 
 template <typename T>
-void cheb_entry_local(int nitems, const PatchItem* items, const int32_t* pdofs, const double* inv, int max_patch,
-                      int n, const T* b, const T* dinv, T* x, T* d, T* xout, double cr, int nh, const int32_t* hrow,
-                      const int32_t* hrp, const int32_t* hci, const T* hv, cudaStream_t s) {
+void cheb_entry_local(int nitems, const PatchItem* items, const int32_t* pdofs, const double* inv, const float* inv32,
+                      int max_patch, int n, const T* b, const T* dinv, T* x, T* d, T* xout, double cr, int nh,
+                      const int32_t* hrow, const int32_t* hrp, const int32_t* hci, const T* hv, cudaStream_t s) {
   if (n == 0) return;
   const size_t smem = (size_t)max_patch * sizeof(double);
-  launch(k_cheb0_entry<T>, nitems + grid_for(n, kBlock), kBlock, smem, s, nitems, items, pdofs, inv, n, b, dinv, x,
-         d, xout, (T)cr);
+  launch(k_cheb0_entry<T>, nitems + grid_for(n, kBlock), kBlock, smem, s, nitems, items, pdofs, inv, inv32, n, b,
+         dinv, x, d, xout, (T)cr);
   if (nh > 0)
     launch(k_cheb0_halo<T>, grid_for(nh, kBlock / 32), kBlock, 0, s, nh, hrow, hrp, hci, hv, b, dinv, x, d, xout, (T)cr);
 }
 
 template <typename T>
-void patch_solve(int nitems, const PatchItem* items, const int32_t* pdofs, const double* inv, const double* rbuf,
-                 const T* b, T* x, int max_patch, cudaStream_t s) {
+void patch_solve(int nitems, const PatchItem* items, const int32_t* pdofs, const double* inv, const float* inv32,
+                 const double* rbuf, const T* b, T* x, int max_patch, cudaStream_t s) {
   if (nitems == 0) return;
   size_t smem = (size_t)max_patch * sizeof(double);
-  launch(k_patch_solve<T>, nitems, kBlock, smem, s, items, pdofs, inv, rbuf, b, x);
+  launch(k_patch_solve<T>, nitems, kBlock, smem, s, items, pdofs, inv, inv32, rbuf, b, x);
 }
 
 int dense_chunks(int n, int kchunk) { return grid_for(n, kchunk); }
@@ -1294,10 +1334,10 @@ void dot_self(int n, const double* r, const Reduce& rd, cudaStream_t s) {
                                         const int32_t*, const int32_t*, const T*, cudaStream_t);                 \
   template void patch_residual<T>(int, int, const int32_t*, const int32_t*, const int32_t*, const double*,       \
                                    const T*, const T*, double*, cudaStream_t);                            \
-  template void patch_solve<T>(int, const PatchItem*, const int32_t*, const double*, const double*, const T*, T*, \
-                                int, cudaStream_t);                                                      \
-  template void cheb_entry_local<T>(int, const PatchItem*, const int32_t*, const double*, int, int, const T*,     \
-                                    const T*, T*, T*, T*, double, int, const int32_t*, const int32_t*,           \
+  template void patch_solve<T>(int, const PatchItem*, const int32_t*, const double*, const float*, const double*, \
+                                const T*, T*, int, cudaStream_t);                                         \
+  template void cheb_entry_local<T>(int, const PatchItem*, const int32_t*, const double*, const float*, int, int,  \
+                                    const T*, const T*, T*, T*, T*, double, int, const int32_t*, const int32_t*, \
                                     const int32_t*, const T*, cudaStream_t);                                     \
   template cudaError_t dense_solve<T>(int, const double*, const T*, T*, double*, int, cudaStream_t);                    \
   template void axpy_from<T>(int, const T*, double*, cudaStream_t);                                              \

@@ -142,14 +142,15 @@ struct Reduce {
 };
 
 // One S_c work item: rows row0 .. row0 + kPatchRowsPerItem - 1 of a patch whose DoFs are
-// pdofs[p0 .. p0 + n) and whose dense inverse starts at element inv of the arena.
+// pdofs[p0 .. p0 + n) and whose dense inverse starts at element inv of the FP64 arena, or,
+// with fp32 set (well-conditioned patches of the mixed form), of the FP32 arena.
 struct PatchItem {
-  int32_t p0, n, row0, pad;
+  int32_t p0, n, row0, fp32;
   int64_t inv;
 };
 
 constexpr int kBlock = 256;
-constexpr int kPatchRowsPerItem = 8;    // rows of one patch per S_c work item (one warp each)
+constexpr int kPatchRowsPerItem = 32;   // rows of one patch per S_c work item (one lane each)
 constexpr int kMaxPatchDofs = 27000;    // largest patch (its residual is staged in shared memory)
 
 // ---- SELL-32 SpMV family ----
@@ -197,16 +198,16 @@ void patch_solve_setup(int max_patch);
 // S_c phase 2, x_B += (A^[d])^{-1} r_B, one block per work item; rbuf == nullptr: the
 // iterate is zero and the residual is b itself (phase 1 skipped).
 template <typename T>
-void patch_solve(int nitems, const PatchItem* items, const int32_t* pdofs, const double* inv, const double* rbuf,
-                 const T* b, T* x, int max_patch, cudaStream_t s);
+void patch_solve(int nitems, const PatchItem* items, const int32_t* pdofs, const double* inv, const float* inv32,
+                 const double* rbuf, const T* b, T* x, int max_patch, cudaStream_t s);
 // Start of a sandwich pre-smoothing from a zero iterate in one launch (plus the halo rows):
 // x_B = (A^[d])^{-1} b_B on every patch, d = cr D^{-1} b and x_out = d on every row, then the
 // rows coupled to patch DoFs (hrow, with their rows of A in hrp/hci/hv) recomputed with
 // r = b - A x. x must be zero outside the patch DoFs on entry.
 template <typename T>
-void cheb_entry_local(int nitems, const PatchItem* items, const int32_t* pdofs, const double* inv, int max_patch,
-                      int n, const T* b, const T* dinv, T* x, T* d, T* xout, double cr, int nh, const int32_t* hrow,
-                      const int32_t* hrp, const int32_t* hci, const T* hv, cudaStream_t s);
+void cheb_entry_local(int nitems, const PatchItem* items, const int32_t* pdofs, const double* inv, const float* inv32,
+                      int max_patch, int n, const T* b, const T* dinv, T* x, T* d, T* xout, double cr, int nh,
+                      const int32_t* hrow, const int32_t* hrp, const int32_t* hci, const T* hv, cudaStream_t s);
 
 // ---- coarsest level: x = X b with X = A_L^{-1} dense symmetric (split-K, deterministic) ----
 // Returns the status of its own two launches.
@@ -230,6 +231,8 @@ struct GjBatch {
   int32_t *drop = nullptr, *bad = nullptr, *ndrop = nullptr;
 };
 void batched_spsd_inverse(const GjBatch& g, cudaStream_t s);
+// max_i sum_j |M_ij| of each matrix of a batch (its 1-norm, M symmetric) into out[b].
+void batched_norm1(const GjBatch& g, double* out, cudaStream_t s);
 
 // ---- Lanczos (set-up): out = w.v; w -= alpha v + beta vprev with out = |w|^2; v, vprev
 // advanced with v = w / beta. Reductions in a fixed order. ----

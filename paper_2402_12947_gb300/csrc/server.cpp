@@ -54,7 +54,8 @@ struct Request {
   mg_hierarchy* h = nullptr;
   int64_t est = 0, bytes = 0, n = 0;
   double *pin_b = nullptr, *pin_x = nullptr;
-  cudaEvent_t ev = nullptr;
+  cudaEvent_t ev = nullptr, ev0 = nullptr;   // solve done; solve start (timing)
+  double t_solve_ms = 0.0;
   std::vector<double> x;
   mg_solve_info_t info{};
   Clock::time_point t_submit, t_setup0, t_setup1, t_admit, t_done;
@@ -157,9 +158,9 @@ struct mg_server {
         r->pin_b = nnmg::pinned_acquire(r->n);
         r->pin_x = nnmg::pinned_acquire(r->n);
         std::memcpy(r->pin_b, r->b.data(), sizeof(double) * r->n);
-        if (cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess)
+        if (cudaEventCreate(&r->ev) != cudaSuccess || cudaEventCreate(&r->ev0) != cudaSuccess)
           throw nnmg::Error(MG_ERR_CUDA, "cudaEventCreate failed");
-        nnmg::enqueue_host_solve(r->h, r->pin_b, r->pin_x, r->rtol, r->maxit, r->ev);
+        nnmg::enqueue_host_solve(r->h, r->pin_b, r->pin_x, r->rtol, r->maxit, r->ev, r->ev0);
       } catch (const nnmg::Error& e) {
         std::lock_guard<std::mutex> lk(mu);
         release_locked(r);
@@ -187,7 +188,8 @@ struct mg_server {
     nnmg::pinned_release(r->pin_x);
     r->pin_b = r->pin_x = nullptr;
     if (r->ev) cudaEventDestroy(r->ev);
-    r->ev = nullptr;
+    if (r->ev0) cudaEventDestroy(r->ev0);
+    r->ev = r->ev0 = nullptr;
     in_use -= r->est;
     --n_active;
     cv_admit.notify_all();
@@ -214,6 +216,8 @@ struct mg_server {
       if (finished.empty()) std::this_thread::sleep_for(std::chrono::microseconds(50));
       for (Request* r : finished) {
         int st = nnmg::collect_host_solve(r->h, &r->info);
+        float ms = 0.f;
+        if (r->ev0 && cudaEventElapsedTime(&ms, r->ev0, r->ev) == cudaSuccess) r->t_solve_ms = ms;
         r->x.assign(r->pin_x, r->pin_x + r->n);
         std::lock_guard<std::mutex> lk(mu);
         release_locked(r);
@@ -243,6 +247,7 @@ void fill_result(const Request* r, mg_request_result_t* out) {
   out->t_wait_ms = nnmg::ms_between(setup1, admit);
   out->t_device_ms = nnmg::ms_between(admit, r->t_done);
   out->t_total_ms = nnmg::ms_between(r->t_submit, r->t_done);
+  out->t_solve_ms = r->t_solve_ms;
 }
 }  // namespace
 

@@ -42,7 +42,7 @@ class MgOptions(C.Structure):
                 ("use_graph", C.c_int32), ("local_levels_mask", C.c_int32), ("quality_threshold", C.c_double),
                 ("sell_sigma", C.c_int32), ("reorder", C.c_int32), ("global_smoother", C.c_int32),
                 ("pde", C.c_int32), ("young", C.c_double), ("poisson_ratio", C.c_double),
-                ("small_level_dofs", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("small_level_dofs", C.c_int32), ("fp32_patch_kappa", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class MgSolveInfo(C.Structure):
@@ -69,7 +69,7 @@ class MgRequestResult(C.Structure):
     _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("rel_residual", C.c_double),
                 ("true_rel_residual", C.c_double), ("n", C.c_int64), ("device_bytes", C.c_int64),
                 ("t_queue_ms", C.c_double), ("t_setup_ms", C.c_double), ("t_wait_ms", C.c_double),
-                ("t_device_ms", C.c_double), ("t_total_ms", C.c_double)]
+                ("t_device_ms", C.c_double), ("t_total_ms", C.c_double), ("t_solve_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -100,6 +100,7 @@ _SIGS = {
     "mg_export_level": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "mg_export_transfer": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "mg_export_patches": (C.c_int, [_P, C.c_int32, _P, _P]),
+    "mg_export_patch_precision": (C.c_int, [_P, C.c_int32, _P]),
     "mg_export_colouring": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int32), _P]),
     "mg_eigs": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mg_dof_coords": (C.c_int, [_P, C.c_int32, _P]),
@@ -123,6 +124,7 @@ _SIGS = {
     "mg_coarse_solve": (C.c_int, [_P, _P, _P, _P]),
     "mg_time_smoother_kernel": (C.c_int, [_P, C.c_int32, _P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mg_device_bytes": (C.c_int64, [_P]),
+    "mg_time_cg_product": (C.c_int, [_P, C.c_int32, _P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mg_server_create": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.POINTER(_P)]),
     "mg_server_submit": (C.c_int, [_P, C.POINTER(MgRequest), C.POINTER(C.c_int64)]),
     "mg_server_poll": (C.c_int, [_P, C.c_int64, C.POINTER(MgRequestResult)]),
@@ -324,6 +326,15 @@ class Hierarchy:
         _check(lib.mg_export_patches(self._h, l, ptr.ctypes.data, dofs.ctypes.data), self._h)
         return [dofs[ptr[i]:ptr[i + 1]].copy() for i in range(num.value)]
 
+    def export_patch_precision(self, l: int):
+        """1 per patch whose inverse is applied in FP32, else 0 (order of export_patches)."""
+        num = C.c_int32()
+        tot = C.c_int64()
+        _check(lib.mg_num_patches(self._h, l, C.byref(num), C.byref(tot)), self._h)
+        flags = np.zeros(max(num.value, 1), dtype=np.int32)
+        _check(lib.mg_export_patch_precision(self._h, l, flags.ctypes.data), self._h)
+        return flags[:num.value]
+
     def export_colouring(self, l: int):
         num = C.c_int32()
         _check(lib.mg_export_colouring(self._h, l, C.byref(num), None), self._h)
@@ -443,6 +454,12 @@ class Hierarchy:
     def coarse_solve(self, b, x, stream=None):
         n = self.num_dofs(self.num_levels - 1)
         _check(lib.mg_coarse_solve(self._h, _dev_ptr(b, n), _dev_ptr(x, n), _stream(stream)), self._h)
+
+    def time_cg_product(self, reps=20, stream=None):
+        """(ms per launch, algorithmic bytes per launch) of the FP64 CG product q = A p."""
+        ms, by = C.c_double(), C.c_double()
+        _check(lib.mg_time_cg_product(self._h, reps, _stream(stream), C.byref(ms), C.byref(by)), self._h)
+        return ms.value, by.value
 
     def time_smoother_kernel(self, reps=20, stream=None):
         ms, nbytes = C.c_double(), C.c_double()

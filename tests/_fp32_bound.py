@@ -99,15 +99,19 @@ class Tape:
 
 class _Patches:
     """S_c data of one level: K = sum_d E_d X_d E_d^T (block-diagonal, X_d = A[B_d, B_d]^{-1}
-    with zero rows and columns on dependent DoFs) and the FP64 rounding scale of each block."""
+    with zero rows and columns on dependent DoFs), the FP64 rounding scale of each block and,
+    for the patches applied in FP32 (fp32[d] = 1: FP32 copy of X_d, residual staged in FP32,
+    FP32 products and sums), their rows' FP32 scale n_B + 3 (X_d and the residual rounded, n_B
+    sums; the result is added in FP64 and rounded as for an FP64 patch)."""
 
-    def __init__(self, A, patches):
+    def __init__(self, A, patches, fp32=None):
         n = A.shape[0]
         rows, cols, vals = [], [], []
         self.mask = np.zeros(n, dtype=bool)
         self.scale = np.zeros(n)       # n_B * kappa_B on the rows of B
+        self.scale32 = np.zeros(n)     # n_B + 3 on the rows of an FP32 patch
         blocks = []
-        for B in patches:
+        for d, B in enumerate(patches):
             B = np.asarray(B)
             Abb = A[B][:, B].toarray()
             keep = ~smoother.dependent_dofs(Abb)
@@ -121,6 +125,8 @@ class _Patches:
             vals.append(X.ravel())
             self.mask[B] = True
             self.scale[B] = len(B) * kappa
+            if fp32 is not None and fp32[d]:
+                self.scale32[B] = len(B) + 3
             blocks.append((B, X))
         self.K = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n)) \
             if patches else sp.csr_matrix((n, n))
@@ -128,7 +134,7 @@ class _Patches:
 
 
 class _Level:
-    def __init__(self, lev, cheb_degree):
+    def __init__(self, lev, cheb_degree, fp32=None):
         self.A = lev.A.tocsr()
         self.absA = _abs(self.A)
         self.m = np.diff(self.A.indptr).astype(np.float64)
@@ -145,7 +151,7 @@ class _Level:
             self.R = lev.R.tocsr()
             self.absR = _abs(self.R)
             self.mR = np.diff(self.R.indptr).astype(np.float64)
-        self.pt = _Patches(self.A, lev.patches) if lev.patches else None
+        self.pt = _Patches(self.A, lev.patches, fp32) if lev.patches else None
         if self.pt is not None:
             self.KA = (self.pt.K @ self.A).tocsr()          # non-zero on the patch rows only
             if self.P is not None:
@@ -156,10 +162,12 @@ class Fp32Schedule:
     """Replays the library's FP32 V-cycle schedule (orders sandwich / global_then_local /
     global, nu, Chebyshev degree of the oracle hierarchy H) on a tape."""
 
-    def __init__(self, H, u=U32):
+    def __init__(self, H, u=U32, fp32=None):
+        """fp32: per level, per patch 1 where the library applies the inverse in FP32
+        (Hierarchy.export_patch_precision), or None (every patch FP64)."""
         self.H = H
         self.u = u
-        self.lv = [_Level(lev, H.cheb_degree) for lev in H.levels]
+        self.lv = [_Level(lev, H.cheb_degree, None if fp32 is None else fp32[l]) for l, lev in enumerate(H.levels)]
         Ac = H.levels[-1].A.toarray()
         keep = ~smoother.dependent_dofs(Ac)
         Xk = np.linalg.inv(Ac[np.ix_(keep, keep)])
@@ -201,6 +209,7 @@ class Fp32Schedule:
         pt = L.pt
         xv, bv = t.val[x], t.val[b]
         fp64 = U64 * pt.scale * (pt.absK @ (np.abs(bv) + L.absA @ np.abs(xv)))
+        fp64 = fp64 + u * pt.scale32 * (pt.absK @ np.abs(bv - L.A @ xv))
         return t.op([(x, None), (x, L.KA, -1.0), (b, pt.K)],
                      lambda v: np.where(pt.mask, u * np.abs(v), 0.0) + fp64)
 
@@ -232,6 +241,7 @@ class Fp32Schedule:
         pt = L.pt
         xv, bv = t.val[xhat], t.val[b]
         fp64 = U64 * pt.scale * (pt.absK @ (np.abs(bv) + L.absA @ np.abs(xv)))
+        fp64 = fp64 + u * pt.scale32 * (pt.absK @ np.abs(bv - L.A @ xv))
         return t.op([(xhat, None), (res, pt.K), (xc, -L.KAP)],
                     lambda v: np.where(pt.mask, u * np.abs(v), 0.0) + fp64)
 

@@ -78,3 +78,8 @@ def solution_gap_bound(A, b, x1, x2) -> float:
     r1 = np.linalg.norm(b - A @ x1)
     r2 = np.linalg.norm(b - A @ x2)
     return (r1 + r2) / lambda_min(A)
+
+
+def fp32_flags(H):
+    """Per level, per patch: 1 where the library hierarchy H applies the inverse in FP32."""
+    return [H.export_patch_precision(l) for l in range(H.num_levels)]

@@ -22,10 +22,12 @@ from oracle import hierarchy, mg, smoother
 f32 = np.float32
 
 
-def emulate_vcycle(H, b, x0, plant=None):
+def emulate_vcycle(H, b, x0, plant=None, fp32_patches=False):
     """mg_vcycle's arithmetic in float32 with FP64 patch/coarse solves (the library's mixed form).
     plant: None, "skip_patch" (level 0's first patch gets no correction) or "drop_last" (the
-    Chebyshev SpMV of level 1 skips the last entry of every row, a loop-bound mistake)."""
+    Chebyshev SpMV of level 1 skips the last entry of every row, a loop-bound mistake).
+    fp32_patches: every patch applies an FP32 copy of its inverse to the FP32-rounded residual
+    in FP32 arithmetic, the result added in FP64 and rounded to FP32."""
     L = len(H.levels)
     A32 = [lv.A.astype(f32) for lv in H.levels]
     Acheb = list(A32)
@@ -44,6 +46,14 @@ def emulate_vcycle(H, b, x0, plant=None):
             Ainv[key] = smoother.DirectSolver(H.levels[l].A[B][:, B].toarray())
         return Ainv[key]
 
+    def solve(l, B, r):
+        if not fp32_patches:
+            return X(l, B).solve(r)
+        key = ("32", l, tuple(B))
+        if key not in Ainv:
+            Ainv[key] = np.linalg.inv(H.levels[l].A[B][:, B].toarray()).astype(f32)
+        return (Ainv[key] @ r.astype(f32)).astype(np.float64)
+
     def patches(l):
         ps = H.levels[l].patches
         return ps[1:] if (plant == "skip_patch" and l == 0) else ps
@@ -52,7 +62,7 @@ def emulate_vcycle(H, b, x0, plant=None):
         r = b.astype(np.float64) - H.levels[l].A @ x.astype(np.float64)
         x = x.copy()
         for B in patches(l):
-            x[B] = (x[B].astype(np.float64) + X(l, B).solve(r[B])).astype(f32)
+            x[B] = (x[B].astype(np.float64) + solve(l, B, r[B])).astype(f32)
         return x
 
     def cheb(l, x, b):
@@ -90,7 +100,7 @@ def emulate_vcycle(H, b, x0, plant=None):
                 rb = res.astype(np.float64) - (H.levels[l].A @ H.levels[l].P) @ xc.astype(np.float64)
                 xh = xh.copy()
                 for B in patches(l):
-                    xh[B] = (xh[B].astype(np.float64) + X(l, B).solve(rb[B])).astype(f32)
+                    xh[B] = (xh[B].astype(np.float64) + solve(l, B, rb[B])).astype(f32)
                 xh = cheb(l, xh, b)
                 if H.order == "sandwich":
                     xh = local(l, xh, b)
@@ -119,6 +129,19 @@ def test_fp32_emulation_within_bounds(name, order):
     assert ratio > 1e-3          # the emulation's error is a visible fraction of the bound
     comps = np.arange(0, n, max(1, n // 64))
     assert np.max(tape.bound(var, comps)) < 5e-2 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("name", ["c1_p2", "c2_p2_128", "cube_p2"])
+def test_fp32_patch_inverses_within_bounds(name):
+    """Every patch applied in FP32 (the mixed form's well-conditioned patches): the emulation
+    within the bound of the schedule told so (n_B + 3 roundings of |X| |r| per patch row)."""
+    _, Ho, _, _ = case(name)
+    n = Ho.levels[0].n
+    b = np.random.default_rng(6).uniform(-1, 1, n)
+    x0 = np.zeros(n)
+    flags = [np.ones(len(lv.patches), dtype=np.int32) for lv in Ho.levels]
+    tape, var = Fp32Schedule(Ho, fp32=flags).vcycle(b, x0)
+    check(tape, var, emulate_vcycle(Ho, b, x0, fp32_patches=True), name)
 
 
 def test_fp32_bounds_nu2_degree3():

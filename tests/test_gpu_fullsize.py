@@ -19,7 +19,7 @@ import numpy as np
 import pytest
 
 from _fp32_bound import Fp32Schedule, check as check32
-from _util import TOL64, rel_err
+from _util import TOL64, fp32_flags, rel_err
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -172,9 +172,9 @@ def oracle_full(full):
 _sched = {}
 
 
-def _schedule(Ho):
+def _schedule(Ho, H):
     if "s" not in _sched:
-        _sched["s"] = Fp32Schedule(Ho)
+        _sched["s"] = Fp32Schedule(Ho, fp32=fp32_flags(H))
     return _sched["s"]
 
 
@@ -222,7 +222,7 @@ def test_fullsize_steps(full, oracle_full, precision, l):
         assert rel_err(got_bc, lo.R @ rr) < TOL64
         assert rel_err(got_p, x0 + lo.P @ xc) < TOL64
         return
-    sch = _schedule(Ho)
+    sch = _schedule(Ho, H)
     tape, var = sch.chebyshev(l, b, x0)
     assert rel_err(tape.val[var], smoother.chebyshev(lo.A, lo.dinv, b, x0, lo.lmax, lo.lmin, Ho.cheb_degree)) < TOL64
     check32(tape, var, got_cheb, ("cheb", l), **FEW)
@@ -253,6 +253,6 @@ def test_fullsize_vcycle(full, oracle_full, precision):
     if precision == "fp64":
         assert rel_err(got, ref) < TOL64
     else:
-        tape, var = _schedule(Ho).vcycle(b, x0)
+        tape, var = _schedule(Ho, H).vcycle(b, x0)
         assert rel_err(tape.val[var], ref) < TOL64
         check32(tape, var, got, "vcycle", **FEW)

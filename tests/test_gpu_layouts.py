@@ -18,7 +18,7 @@ import numpy as np
 import pytest
 
 from _fp32_bound import Fp32Schedule, check as check32
-from _util import TOL64, case, rel_err, solution_gap_bound
+from _util import TOL64, case, fp32_flags, rel_err, solution_gap_bound
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -57,10 +57,14 @@ def reference():
 _sched = {}
 
 
-def schedule():
-    if "s" not in _sched:
-        _sched["s"] = Fp32Schedule(reference()["Ho"])
-    return _sched["s"]
+def schedule(H):
+    """The FP32 schedule with the library's per-patch precision (identical in every forced
+    layout: it depends on the patch blocks only)."""
+    flags = fp32_flags(H)
+    key = tuple(tuple(f.tolist()) for f in flags)
+    if key not in _sched:
+        _sched[key] = Fp32Schedule(reference()["Ho"], fp32=flags)
+    return _sched[key]
 
 
 def dev(a):
@@ -102,7 +106,7 @@ def test_forced_layout(nnmg, layout, precision, monkeypatch):
             if precision == "fp64" or l == 0:
                 assert rel_err(host(y), lo.A @ v) < TOL64, (layout, l)
             else:
-                tape, var = schedule().apply(l, v)
+                tape, var = schedule(H).apply(l, v)
                 check32(tape, var, host(y), (layout, l))
         # one V-cycle from x0 (every smoothing, transfer and correction kernel of the layout)
         x = dev(x0)
@@ -110,7 +114,7 @@ def test_forced_layout(nnmg, layout, precision, monkeypatch):
         if precision == "fp64":
             assert rel_err(host(x), R["vc"]) < TOL64, layout
         else:
-            tape, var = schedule().vcycle(b, x0)
+            tape, var = schedule(H).vcycle(b, x0)
             check32(tape, var, host(x), layout)
         # the solve (the CG product q = A p and its reduction run on the forced layout too)
         rtol = 1e-10 if precision == "fp64" else 1e-8

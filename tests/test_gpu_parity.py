@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 
 from _fp32_bound import Fp32Schedule, check as check32
-from _util import TOL64, case, csr_arrays, rel_err, solution_gap_bound
+from _util import TOL64, case, csr_arrays, fp32_flags, rel_err, solution_gap_bound
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -192,7 +192,7 @@ def test_mixed_precision_solve(nnmg, name):
     # one FP32 V-cycle against its rounding-error bound around the exact (oracle) cycle
     z = torch.zeros(n, dtype=torch.float64, device="cuda")
     H.vcycle(dev(b), z)
-    tape, var = Fp32Schedule(Ho).vcycle(b, np.zeros(n))
+    tape, var = Fp32Schedule(Ho, fp32=fp32_flags(H)).vcycle(b, np.zeros(n))
     assert rel_err(tape.val[var], mg.vcycle(Ho, b)) < TOL64
     check32(tape, var, host(z), name)
 
@@ -333,7 +333,7 @@ def test_tma_staged_spmv(nnmg, name, precision, monkeypatch):
         if precision == "fp64":
             assert rel_err(host(y), Ho.levels[1].A @ v) < TOL64
         else:
-            tape, var = Fp32Schedule(Ho).apply(1, v)
+            tape, var = Fp32Schedule(Ho, fp32=fp32_flags(H)).apply(1, v)
             check32(tape, var, host(y), "apply")
         xs = torch.zeros(n, dtype=torch.float64, device="cuda")
         if precision == "fp64":
@@ -350,7 +350,7 @@ def test_tma_staged_spmv(nnmg, name, precision, monkeypatch):
             assert info["converged"] and info["iterations"] <= itr + 1 and info["true_rel_residual"] < 1.5e-8
             x = dev(x0)
             H.vcycle(dev(b), x)
-            tape, var = Fp32Schedule(Ho).vcycle(b, x0)
+            tape, var = Fp32Schedule(Ho, fp32=fp32_flags(H)).vcycle(b, x0)
             check32(tape, var, host(x), "tma vcycle")
 
 
@@ -376,7 +376,7 @@ def test_vcycle_orders_nu_degree(nnmg, order, nu, k, precision):
         if precision == "fp64":
             assert rel_err(host(x), ref) < TOL64
         else:   # the FP32 cycle within its rounding-error bound
-            tape, var = Fp32Schedule(Ho).vcycle(b, x0)
+            tape, var = Fp32Schedule(Ho, fp32=fp32_flags(H)).vcycle(b, x0)
             check32(tape, var, host(x), (order, nu, k))
         # the solve as well where the local correction is on (without it CG needs a few hundred
         # iterations on these low-quality cells, and rounding moves the count by a few)
@@ -438,7 +438,7 @@ def test_persistent_small_levels(nnmg, name, precision):
             if precision == "fp64":
                 assert rel_err(host(x), ref) < TOL64, thr
             else:
-                tape, var = Fp32Schedule(Ho).vcycle(b, x0)
+                tape, var = Fp32Schedule(Ho, fp32=fp32_flags(H)).vcycle(b, x0)
                 check32(tape, var, host(x), thr)
             xs = torch.zeros(n, dtype=torch.float64, device="cuda")
             info = H.solve(dev(b), xs, rtol=rtol)
