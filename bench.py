@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every kernel individually instead of one CUDA graph per solve (profilers "
                          "cannot see kernel nodes of graphs with conditional nodes)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "serve", "paper", "lattice", "dumbbell"],
+    ap.add_argument("--workload", default="c2",
+                    choices=["c2", "c3", "c4", "serve", "paper", "lattice", "dumbbell", "persistent"],
                     help="'serve': the mixed request stream through the continuous-batching server; "
                          "'paper': the Case A/B comparison and the residual history of the paper's examples")
     ap.add_argument("--reorder", default=None, choices=["none", "rcm", "spatial", "spatial-coarse"],
@@ -425,6 +426,11 @@ def run_ours(args):
     kms, kbytes = H32.time_smoother_kernel(reps=50)
     # the second: the FP64 CG product q = A p with its p.q reduction
     ap_ms, ap_bytes = H32.time_cg_product(reps=50)
+    # the local correction's solve launch on the fine level (FP64-ALU bound where FP64) and the
+    # device's FP64 FMA rate
+    fp64_fma = nnmg.measure_fp64_fma()
+    ps32 = H32.time_patch_solve(0, reps=20)
+    ps64 = H64.time_patch_solve(0, reps=20) if both else None
     kms64, kbytes64 = H64.time_smoother_kernel(reps=50) if both else (float("nan"), float("nan"))
     peak, peak_src = measured_peak()
     traffic, rev = profiled_traffic()
@@ -501,6 +507,15 @@ def run_ours(args):
                                     "bound": "hbm", "achieved": ap_bytes / (ap_ms * 1e-3) / 1e9, "peak": peak,
                                     "frac": ap_bytes / (ap_ms * 1e-3) / 1e9 / peak, "ms_per_launch": ap_ms,
                                     "bytes_per_launch": ap_bytes}},
+        "patch_solve": {
+            "kernel": "S_c solve launch on level 0 (k_patch_solve: lane per row, columns split over 8 warps)",
+            "bound": "alu (FP64 FMA) where the inverses are FP64", "fp64_fma_per_s_measured": fp64_fma,
+            "mixed": {"ms_per_launch": ps32[0], "fma_fp64": ps32[1], "fma_fp32": ps32[2], "bytes": ps32[3],
+                      "frac_fp64_alu": (ps32[1] / (ps32[0] * 1e-3)) / fp64_fma if ps32[0] > 0 else None,
+                      "hbm_gbs": ps32[3] / (ps32[0] * 1e-3) / 1e9 if ps32[0] > 0 else None},
+            "fp64": {"ms_per_launch": ps64[0], "fma_fp64": ps64[1], "bytes": ps64[3],
+                     "frac_fp64_alu": (ps64[1] / (ps64[0] * 1e-3)) / fp64_fma if ps64[0] > 0 else None,
+                     "hbm_gbs": ps64[3] / (ps64[0] * 1e-3) / 1e9 if ps64[0] > 0 else None} if ps64 else None},
         "rel_error_vs_oracle": oracle_check,
         "serve": serve,
         "cpu_baseline": cpu,
@@ -615,6 +630,67 @@ def run_serve(args):
                        "hbm_budget_bytes": budget, "max_active": 16},
             "serve": results}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_persistent(args):
+    """The persistent cooperative path against the default launches: (1) the C2 solve with the
+    cycle from the first level of at most small_level_dofs DoFs down in one persistent launch
+    per cycle, for several split points (0 = off), with the V-cycle time from each level;
+    (2) 16 small requests of the serving family solved one by one and as one batch, with CUDA
+    graphs on their own streams (small_level_dofs = 0) and as one persistent launch
+    (small_level_dofs >= n_0)."""
+    import numpy as np
+    import torch
+    from paper_2402_12947_gb300 import build
+    build.build()
+    from paper_2402_12947_gb300 import inputs, nnmg
+    torch.cuda.set_device(0)
+
+    def timed(f, reps):
+        f()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            f()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {"workload": "persistent", "c2": [], "batch": {}}
+    meshes = inputs.config_c2()
+    b = torch.from_numpy(inputs.uniform_rhs(2047 ** 2, 2)).cuda()
+    lam = None
+    for thr in (0, 20000, 100000):
+        H = nnmg.Hierarchy.from_meshes(meshes, 2, 0.1, precision="mixed", small_level_dofs=thr, lambda_override=lam)
+        if lam is None:
+            lam = [H.eigs(l)[2] for l in range(H.num_levels - 1)]
+        x = torch.zeros_like(b)
+        info = H.solve(b, x, rtol=RTOL)
+        ms = timed(lambda: H.solve(b, x, rtol=RTOL), 5)
+        out["c2"].append({"small_level_dofs": thr, "ms_per_solve": ms, "iterations": info["iterations"],
+                          "vcycle_us_from_level": [round(H.time_vcycle(l, reps=30) * 1e3, 1)
+                                                   for l in range(H.num_levels)]})
+        H.close()
+    rng = np.random.default_rng(5)
+    specs, k = [], 0
+    while len(specs) < 16:
+        m, degree, label = inputs.serving_request(rng, 1000 + k)
+        k += 1
+        if (m[0].dim == 2 and m[0].n <= 128) or (m[0].dim == 3 and m[0].n <= 32):
+            specs.append((m, degree, label))
+    for mode, thr in (("graphs", 0), ("persistent", 1 << 30)):
+        hs = [nnmg.Hierarchy.from_meshes(m, d, 0.1, precision="mixed", small_level_dofs=thr) for m, d, _ in specs]
+        bs = [torch.from_numpy(inputs.uniform_rhs(h.num_dofs(0), 3)).cuda() for h in hs]
+        xs = [torch.zeros_like(v) for v in bs]
+        seq = timed(lambda: [h.solve(v, x, rtol=RTOL) for h, v, x in zip(hs, bs, xs)], 3)
+        bat = timed(lambda: nnmg.solve_batch(hs, bs, xs, rtol=RTOL), 3)
+        out["batch"][mode] = {"sequential_ms": seq, "batch_ms": bat}
+        for h in hs:
+            h.close()
+    out["batch"]["requests"] = [lab for _, _, lab in specs]
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -801,6 +877,8 @@ def run_dumbbell(args):
 
 def main():
     args = parse()
+    if args.workload == "persistent":
+        return run_persistent(args)
     if args.workload == "paper":
         return run_paper(args)
     if args.workload == "lattice":

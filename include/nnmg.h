@@ -412,6 +412,18 @@ int mg_dense_symv_static(const double* X_dev, int64_t n, const double* b_dev, do
  * Overwrites the hierarchy's CG work vectors; measurement helper. */
 int mg_time_cg_product(mg_hierarchy_t* h, int32_t reps, void* stream, double* ms, double* bytes);
 
+/* Mean device time of one S_c solve launch on level l (the patch GEMVs of Alg. 2 over the
+ * work list, on whatever residual the hierarchy holds; overwrites the level's iterate) over
+ * reps launches on `stream` (blocks), with its algorithmic work: FMAs with FP64 inverses
+ * (sum of n_d^2), FMAs with FP32 inverses, and the inverses' bytes. Measurement helper. */
+int mg_time_patch_solve(mg_hierarchy_t* h, int32_t level, int32_t reps, void* stream, double* ms, double* fma64,
+                        double* fma32, double* bytes);
+
+/* FP64 FMA throughput of the current device (FMAs per second): independent FMA chains on
+ * every SM, timed with CUDA events on `stream` (blocks; allocates and frees a small buffer).
+ * The denominator of the FP64-ALU roofline of the patch solves and the coarsest solve. */
+int mg_measure_fp64_fma(void* stream, double* fma_per_s);
+
 /* Device bytes held by the hierarchy. */
 int64_t mg_device_bytes(const mg_hierarchy_t* h);
 /* Number of kernel launches of one V-cycle, and of one CG iteration (V-cycle included). */

@@ -1448,7 +1448,11 @@ void build_device(mg_hierarchy* h) {
             D.max_patch = std::max(D.max_patch, m);
             const bool f32 = std::is_same<T, float>::value && level_fp32[l][p];
             const int64_t off = f32 ? level_inv32_off[l][p] : level_inv_off[l][p];
-            for (int r0 = 0; r0 < m; r0 += kPatchRowsPerItem) items.push_back({p0, m, r0, f32 ? 1 : 0, off});
+            // small patches: warp-per-row items (8 rows); larger: lane-per-row items (32 rows)
+            const bool small = m <= kSmallPatch;
+            const int mode = (f32 ? PI_FP32 : 0) | (small ? PI_WARP_ROWS : 0);
+            const int step = small ? kPatchRowsPerWarpItem : kPatchRowsPerItem;
+            for (int r0 = 0; r0 < m; r0 += step) items.push_back({p0, m, r0, mode, off});
           }
           if (D.max_patch > kMaxPatchDofs)
             throw Error(MG_ERR_INVALID_ARG, "patch larger than " + std::to_string(kMaxPatchDofs) + " DoFs");
@@ -1546,7 +1550,7 @@ void build_device(mg_hierarchy* h) {
   h->cq = mem.alloc<double>(n0);
   h->cz = mem.alloc<double>(n0);
   h->nparts = cg_parts(n0);
-  h->ap_parts = sell_blocks(n0, 32);  // partials of k_ap for any layout
+  h->ap_parts = sell_blocks(n0, 32);  // at least the block partials of k_ap for any layout
   h->part = mem.alloc<double>(std::max(h->nparts, h->ap_parts));
   h->ticket = mem.alloc<unsigned>(1);
   h->st = mem.alloc<CgState>(1);
@@ -1594,9 +1598,9 @@ struct CgRunner {
     return Reduce{h->part, h->ticket, h->st, op, use_cond, cond};
   }
   void tail(cudaStream_t s, int use_cond, unsigned long long cond) {
-    sell_ap(h->A0, h->cp, h->cq, h->part, h->st, FIN_PQ, s);
+    sell_ap(h->A0, h->cp, h->cq, red(FIN_PQ), s);
     cg_update<T>(h->n0, h->st, h->cp, h->cq, h->cx, h->cr, vb(), vx(), red(FIN_RR, use_cond, cond), s);
-    launches += 3;
+    launches += 2;
   }
   void head(cudaStream_t s, int use_cond, unsigned long long cond) {
     CK(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned), s));
@@ -2885,9 +2889,10 @@ int mg_time_cg_product(mg_hierarchy_t* h, int32_t reps, void* stream, double* ms
   CK(cudaEventCreate(&e1));
   // q = A p with the p.q reduction (into the CG state, which the next solve re-initialises)
   CgState* st = h->st;
-  sell_ap(h->A0, h->cp, h->cq, h->part, st, FIN_NORM, s);  // warm-up
+  const Reduce rd{h->part, h->ticket, st, FIN_NORM, 0, 0};
+  sell_ap(h->A0, h->cp, h->cq, rd, s);  // warm-up
   CK(cudaEventRecord(e0, s));
-  for (int i = 0; i < reps; ++i) sell_ap(h->A0, h->cp, h->cq, h->part, st, FIN_NORM, s);
+  for (int i = 0; i < reps; ++i) sell_ap(h->A0, h->cp, h->cq, rd, s);
   CK(cudaEventRecord(e1, s));
   check_launch("mg_time_cg_product");
   CK(cudaEventSynchronize(e1));
@@ -2903,6 +2908,56 @@ int mg_time_cg_product(mg_hierarchy_t* h, int32_t reps, void* stream, double* ms
   // algorithmic bytes: each nonzero's value and index once, p read (gathered) and q written
   // once, the slice/row metadata
   if (bytes) *bytes = 8.0 * (double)M.nnz + M.idx_bytes + 16.0 * (double)M.nrows + meta;
+  return MG_OK;
+  API_END_H(h)
+}
+
+int mg_time_patch_solve(mg_hierarchy_t* h, int32_t l, int32_t reps, void* stream, double* ms, double* fma64,
+                        double* fma32, double* bytes) {
+  API_BEGIN
+  checked(h);
+  check_level(h, l, true);
+  if (reps < 1) throw Error(MG_ERR_INVALID_ARG, "reps must be >= 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  double f64 = 0.0, f32 = 0.0;
+  float t = 0.f;
+  h->with_engine([&](auto& e) {
+    using T = typename std::remove_pointer<decltype(e.lv[0].b)>::type;
+    auto& L = e.lv[l];
+    const LevelH& H = h->host[l];
+    for (size_t p = 0; p + 1 < H.patch_ptr.size(); ++p) {
+      const double m = (double)(H.patch_ptr[p + 1] - H.patch_ptr[p]);
+      const bool lo = std::is_same<T, float>::value && p < L.pfp32.size() && L.pfp32[p];
+      (lo ? f32 : f64) += m * m;
+    }
+    if (L.nitems == 0) return;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    patch_solve<T>(L.nitems, L.items, L.pdofs, L.inv, L.inv32, L.rbuf, L.b, L.x, L.max_patch, s);  // warm-up
+    CK(cudaEventRecord(e0, s));
+    for (int i = 0; i < reps; ++i) patch_solve<T>(L.nitems, L.items, L.pdofs, L.inv, L.inv32, L.rbuf, L.b, L.x, L.max_patch, s);
+    CK(cudaEventRecord(e1, s));
+    check_launch("mg_time_patch_solve");
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(&t, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  });
+  if (ms) *ms = (double)t / reps;
+  if (fma64) *fma64 = f64;
+  if (fma32) *fma32 = f32;
+  if (bytes) *bytes = 8.0 * f64 + 4.0 * f32;
+  return MG_OK;
+  API_END_H(h)
+}
+
+int mg_measure_fp64_fma(void* stream, double* fma_per_s) {
+  mg_hierarchy* h = nullptr;
+  API_BEGIN
+  if (!fma_per_s) throw Error(MG_ERR_INVALID_ARG, "null output");
+  cudaStream_t s = (cudaStream_t)stream;
+  *fma_per_s = measure_fp64_fma(s);
   return MG_OK;
   API_END_H(h)
 }

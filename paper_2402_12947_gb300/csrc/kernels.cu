@@ -199,8 +199,10 @@ __host__ __device__ constexpr int sell_sub() {
 // CSR vector every lane of a group receives the group's total (all lanes take part in the
 // shuffles, so no lane leaves early).
 template <typename T, int G, bool C16>
-__device__ __forceinline__ bool op_row(const OpView<T>& m, const T* __restrict__ x, int& row, T& acc) {
-  const int tid = blockIdx.x * kBlock + threadIdx.x;
+__device__ __forceinline__ bool op_row(const OpView<T>& m, const T* __restrict__ x, int& row, T& acc,
+                                       int vblock = -1) {
+  // vblock: the (virtual) block whose rows this thread serves (grid-stride kernels), else blockIdx.x
+  const int tid = (vblock < 0 ? (int)blockIdx.x : vblock) * kBlock + threadIdx.x;
   if constexpr (is_sell<G>() && sell_sub<G>() == 1) {
     if (tid >= m.nrows) return false;
     row = m.perm ? m.perm[tid] : tid;
@@ -540,39 +542,25 @@ __device__ void reduce_finish(double s, const Reduce& rd) {
   }
 }
 
-// q = A p and per-block partial sums of p.q. Its grid has one block per 256 rows (16k
-// blocks on the fine level), too many for one arrival counter, so the partials are summed
-// by k_finish.
+// q = A p with the p.q reduction in the same launch. The grid (about eight blocks per SM) walks
+// the operator's blocks of rows (`nvb` virtual blocks, grid-stride, a fixed assignment), each
+// thread accumulating p_i q_i of its rows in a register; one block reduction per block, then
+// the last block to finish sums the block partials in order and applies the reduction's op
+// (reduce_finish). On GB300 this operator pass is bound by the FP64 pipe (one FMA per nonzero):
+// a block reduction for every 256 rows added about 30 % more FP64 instructions.
 template <int G, bool C16>
-__global__ void __launch_bounds__(kBlock) k_ap(OpView<double> m, const double* __restrict__ p, double* __restrict__ q,
-                                               double* __restrict__ part) {
-  int row;
-  double ap;
+__global__ void __launch_bounds__(kBlock) k_ap(OpView<double> m, int nvb, const double* __restrict__ p,
+                                               double* __restrict__ q, Reduce rd) {
   double v = 0.0;
-  if (op_row<double, G, C16>(m, p, row, ap) && group_leader<G>()) {
-    q[row] = ap;
-    v = p[row] * ap;
+  for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) {   // block-uniform loop
+    int row;
+    double ap;
+    if (op_row<double, G, C16>(m, p, row, ap, vb) && group_leader<G>()) {
+      q[row] = ap;
+      v = fma(p[row], ap, v);
+    }
   }
-  v = block_sum(v);
-  if (threadIdx.x == 0) part[blockIdx.x] = v;
-}
-
-// One block: the sum of part[0..nparts) in a fixed order (eight loads in flight per
-// thread), then op applied to the CG state.
-__global__ void __launch_bounds__(1024) k_finish(int nparts, const double* __restrict__ part, CgState* st, int op) {
-  double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  int i = threadIdx.x;
-  for (; i + 7 * 1024 < nparts; i += 8 * 1024) {
-    double v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = part[i + u * 1024];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) acc[u] += v[u];
-  }
-  for (; i < nparts; i += 1024) acc[0] += part[i];
-  double t = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
-  t = block_sum(t);
-  if (threadIdx.x == 0) apply_finish(st, t, op, 0, 0);
+  reduce_finish(block_sum(v), rd);
 }
 
 // First Chebyshev step from a zero iterate: r = b, d = cr D^{-1} b, x_out = x_in + d for
@@ -714,13 +702,50 @@ __device__ __forceinline__ void patch_item_rows(const PatchItem it, const int32_
   x[g] = (T)((double)xg + s);
 }
 
+// Small patches (n <= kSmallPatch): one warp per output row, lane l accumulating entries
+// l, l + 32, ... of row i of X (contiguous), then the warp sums; the row's first 256 entries
+// and its DoF id and value are loaded before the barrier that stages the residual, so an item
+// costs about two dependent memory round trips.
+template <typename T, typename V>
+__device__ __forceinline__ void patch_item_warp(const PatchItem it, const int32_t* __restrict__ pdofs,
+                                                const V* __restrict__ X, const double* rbuf,
+                                                const T* __restrict__ b, T* __restrict__ x, V* rs) {
+  constexpr int K = 8;
+  const int p0 = it.p0, n = it.n;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = it.row0 + warp;
+  const bool ok = i < n;
+  const V* Xi = X + (int64_t)(ok ? i : 0) * n;
+  const int g = ok ? pdofs[p0 + i] : 0;
+  const T xg = ok ? x[g] : T(0);
+  V xr[K];
+#pragma unroll
+  for (int u = 0; u < K; ++u) xr[u] = ok && lane + 32 * u < n ? Xi[lane + 32 * u] : V(0);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) rs[j] = (V)(rbuf ? rbuf[p0 + j] : (double)b[pdofs[p0 + j]]);
+  __syncthreads();
+  if (!ok) return;  // warp-uniform; no block barrier follows
+  V e = V(0);
+#pragma unroll
+  for (int u = 0; u < K; ++u)
+    if (lane + 32 * u < n) e = fma(xr[u], rs[lane + 32 * u], e);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+  if (lane == 0) x[g] = (T)((double)xg + (double)e);
+}
+
 template <typename T>
 __device__ __forceinline__ void patch_item(const PatchItem it, const int32_t* __restrict__ pdofs,
                                            const double* __restrict__ inv, const float* __restrict__ inv32,
                                            const double* rbuf, const T* __restrict__ b, T* __restrict__ x,
                                            double* rs) {
-  if (it.fp32) patch_item_rows<T, float>(it, pdofs, inv32 + it.inv, rbuf, b, x, reinterpret_cast<float*>(rs));
-  else patch_item_rows<T, double>(it, pdofs, inv + it.inv, rbuf, b, x, rs);
+  const bool lo = (it.mode & PI_FP32) != 0;
+  if (it.mode & PI_WARP_ROWS) {
+    if (lo) patch_item_warp<T, float>(it, pdofs, inv32 + it.inv, rbuf, b, x, reinterpret_cast<float*>(rs));
+    else patch_item_warp<T, double>(it, pdofs, inv + it.inv, rbuf, b, x, rs);
+  } else {
+    if (lo) patch_item_rows<T, float>(it, pdofs, inv32 + it.inv, rbuf, b, x, reinterpret_cast<float*>(rs));
+    else patch_item_rows<T, double>(it, pdofs, inv + it.inv, rbuf, b, x, rs);
+  }
 }
 
 template <typename T>
@@ -989,6 +1014,22 @@ __global__ void __launch_bounds__(kBlock) k_gj_norm1(GjBatch g, double* __restri
   if (threadIdx.x == 0) out[b] = best[0];
 }
 
+// FP64 FMA throughput: every thread runs 8 independent FMA chains of `iters` steps on values
+// that stay bounded (a = a * c + d with |c| < 1), then writes their sum (so nothing is elided).
+__global__ void __launch_bounds__(kBlock) k_fp64_fma(int iters, double c, double d, double* __restrict__ out) {
+  double a[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) a[u] = (double)(threadIdx.x + u);
+  for (int k = 0; k < iters; ++k) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] = fma(a[u], c, d);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) s += a[u];
+  out[blockIdx.x * kBlock + threadIdx.x] = s;
+}
+
 }  // namespace
 
 void lanczos_dot(int n, const double* w, const double* v, double* part, double* out, cudaStream_t s) {
@@ -1014,6 +1055,30 @@ void batched_spsd_inverse(const GjBatch& g, cudaStream_t s) {
     k_gj_prep<<<active, kBlock, 0, s>>>(g, k);
     k_gj_update<<<dim3(bx, active), kBlock, 0, s>>>(g, k);
   }
+}
+
+double measure_fp64_fma(cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = sms * 8, iters = 4096;
+  double* out = nullptr;
+  if (cudaMallocAsync(&out, sizeof(double) * blocks * kBlock, s) != cudaSuccess) throw Error(MG_ERR_OOM, "probe buffer");
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  k_fp64_fma<<<blocks, kBlock, 0, s>>>(iters, 0.999999, 1e-3, out);   // warm-up
+  cudaEventRecord(e0, s);
+  k_fp64_fma<<<blocks, kBlock, 0, s>>>(iters, 0.999999, 1e-3, out);
+  cudaEventRecord(e1, s);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(out, s);
+  check_launch("FP64 FMA probe");
+  return (double)blocks * kBlock * 8.0 * iters / (ms * 1e-3);   // FMAs per second
 }
 
 void batched_norm1(const GjBatch& g, double* out, cudaStream_t s) {
@@ -1193,13 +1258,23 @@ void sell_gs(const SellMat<T>& M, const int32_t* rows, const T* b, const T* dinv
     launch(k_gs<T, L::lanes, L::c16>, op_blocks(M), kBlock, 0, s, view(M), rows, x, b, dinv, x);
   });
 }
-void sell_ap(const SellMat<double>& A, const double* p, double* q, double* part, CgState* st, int op, cudaStream_t s) {
-  int nb = op_blocks(A);
+int ap_parts(const SellMat<double>& A) {
+  static const int cap = [] {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return std::max(1, sms * 8);
+  }();
+  return std::max(1, std::min(op_blocks(A), cap));
+}
+
+void sell_ap(const SellMat<double>& A, const double* p, double* q, const Reduce& rd, cudaStream_t s) {
+  const int nvb = op_blocks(A);
+  const int grid = ap_parts(A);
   by_layout(A.lanes, A.unroll, A.sub, A.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
-    launch(k_ap<L::lanes, L::c16>, nb, kBlock, 0, s, view(A), p, q, part);
+    launch(k_ap<L::lanes, L::c16>, grid, kBlock, 0, s, view(A), nvb, p, q, rd);
   });
-  launch(k_finish, 1, 1024, 0, s, nb, (const double*)part, st, op);
 }
 
 template <typename T>

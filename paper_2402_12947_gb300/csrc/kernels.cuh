@@ -141,16 +141,20 @@ struct Reduce {
   unsigned long long handle;
 };
 
-// One S_c work item: rows row0 .. row0 + kPatchRowsPerItem - 1 of a patch whose DoFs are
-// pdofs[p0 .. p0 + n) and whose dense inverse starts at element inv of the FP64 arena, or,
-// with fp32 set (well-conditioned patches of the mixed form), of the FP32 arena.
+// One S_c work item: rows row0 .. row0 + (kPatchRowsPerItem or, with PI_WARP_ROWS,
+// kPatchRowsPerWarpItem) - 1 of a patch whose DoFs are pdofs[p0 .. p0 + n) and whose dense
+// inverse starts at element inv of the FP64 arena, or, with PI_FP32 (well-conditioned patches
+// of the mixed form), of the FP32 arena.
+enum PatchItemMode { PI_FP32 = 1, PI_WARP_ROWS = 2 };
 struct PatchItem {
-  int32_t p0, n, row0, fp32;
+  int32_t p0, n, row0, mode;
   int64_t inv;
 };
 
 constexpr int kBlock = 256;
 constexpr int kPatchRowsPerItem = 32;   // rows of one patch per S_c work item (one lane each)
+constexpr int kPatchRowsPerWarpItem = 8; // rows per item of a small patch (one warp each)
+constexpr int kSmallPatch = 256;         // patches up to this size take warp-per-row items
 constexpr int kMaxPatchDofs = 27000;    // largest patch (its residual is staged in shared memory)
 
 // ---- SELL-32 SpMV family ----
@@ -182,7 +186,10 @@ template <typename T> void sell_restrict(const SellMat<T>& R, const T* r, T* bc,
 template <typename T>
 void sell_gs(const SellMat<T>& M, const int32_t* rows, const T* b, const T* dinv, T* x, cudaStream_t s);
 // q = A p, then p.q summed by one finishing block that applies `op` to the CG state (FP64).
-void sell_ap(const SellMat<double>& A, const double* p, double* q, double* part, CgState* st, int op, cudaStream_t s);
+// q = A p and p.q, reduced in the same launch (grid-stride blocks, the last block to finish sums
+// the partials in order and applies rd.op); rd.part needs ap_parts(A) entries.
+void sell_ap(const SellMat<double>& A, const double* p, double* q, const Reduce& rd, cudaStream_t s);
+int ap_parts(const SellMat<double>& A);
 int sell_blocks(int nrows, int lanes);
 
 // ---- local correction S_c (two phases) ----
@@ -345,5 +352,7 @@ cudaError_t persistent_launch(const PPhase* phases, int nhead, const PTask* task
                               int nbody = 0, CgState* const* states = nullptr, int nstates = 0, int max_iter = 0);
 
 void check_launch(const char* what);
+// FP64 FMAs per second of the device (independent FMA chains on every SM, CUDA events).
+double measure_fp64_fma(cudaStream_t s);
 
 }  // namespace nnmg

@@ -125,6 +125,9 @@ _SIGS = {
     "mg_time_smoother_kernel": (C.c_int, [_P, C.c_int32, _P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mg_device_bytes": (C.c_int64, [_P]),
     "mg_time_cg_product": (C.c_int, [_P, C.c_int32, _P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "mg_measure_fp64_fma": (C.c_int, [_P, C.POINTER(C.c_double)]),
+    "mg_time_patch_solve": (C.c_int, [_P, C.c_int32, C.c_int32, _P, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mg_server_create": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.POINTER(_P)]),
     "mg_server_submit": (C.c_int, [_P, C.POINTER(MgRequest), C.POINTER(C.c_int64)]),
     "mg_server_poll": (C.c_int, [_P, C.c_int64, C.POINTER(MgRequestResult)]),
@@ -455,6 +458,13 @@ class Hierarchy:
         n = self.num_dofs(self.num_levels - 1)
         _check(lib.mg_coarse_solve(self._h, _dev_ptr(b, n), _dev_ptr(x, n), _stream(stream)), self._h)
 
+    def time_patch_solve(self, l=0, reps=20, stream=None):
+        """(ms per launch, FMAs with FP64 inverses, FMAs with FP32 inverses, inverse bytes) of
+        one S_c solve launch on level l."""
+        v = [C.c_double() for _ in range(4)]
+        _check(lib.mg_time_patch_solve(self._h, l, reps, _stream(stream), *[C.byref(x) for x in v]), self._h)
+        return tuple(x.value for x in v)
+
     def time_cg_product(self, reps=20, stream=None):
         """(ms per launch, algorithmic bytes per launch) of the FP64 CG product q = A p."""
         ms, by = C.c_double(), C.c_double()
@@ -465,6 +475,13 @@ class Hierarchy:
         ms, nbytes = C.c_double(), C.c_double()
         _check(lib.mg_time_smoother_kernel(self._h, reps, _stream(stream), C.byref(ms), C.byref(nbytes)), self._h)
         return ms.value, nbytes.value
+
+
+def measure_fp64_fma(stream=None) -> float:
+    """FP64 FMAs per second of the current device (see mg_measure_fp64_fma)."""
+    v = C.c_double()
+    _check(lib.mg_measure_fp64_fma(_stream(stream), C.byref(v)))
+    return v.value
 
 
 def dense_symv_static(X, b, x, stream=None):
