@@ -251,17 +251,23 @@ int mg_load_constant(const mg_hierarchy_t* h, double f, double* out_host);
 
 /* One V-cycle of Alg. 1 in place: x_dev (initial guess in, new iterate out) for
  * A_0 x = b, b_dev/x_dev [n_0] FP64. In MIXED precision the cycle computes the correction
- * for the residual in FP32 (x += V(b - A x)). */
+ * for the residual in FP32 (x += V(b - A x)). Asynchronous on `stream`, except for
+ * hierarchies with a bounded device-side wait (small_level_dofs > 0, or the TMA-staged SpMV
+ * forced), where it blocks to read the wait flags (MG_ERR_TIMEOUT as for mg_solve). */
 int mg_vcycle(mg_hierarchy_t* h, const double* b_dev, double* x_dev, void* stream);
 
 /* V-cycle-preconditioned CG (Sec. 6.2) from x = 0 until ||r||_2/||b||_2 <= rtol or maxit
  * iterations; x_dev receives the solution. Blocks until the solve has finished and fills
  * *info (may be NULL). Returns MG_OK, MG_ERR_NO_CONVERGENCE or MG_ERR_BREAKDOWN.
- * Only for hierarchies built with the TMA-staged SpMV forced (environment variable
- * NNMG_FORCE_LAYOUT=tma at set-up; the autotuner never picks it): MG_ERR_TIMEOUT when one of
- * that kernel's bounded waits gave up (the result is then not valid); every entry point that
- * runs operators of such a hierarchy (mg_vcycle, mg_solve*, the single steps, the server's
- * requests) checks and clears the device's flag after its work and reports it this way. */
+ * The solve runs as one CUDA graph (use_graph = 1) or per-kernel launches; with
+ * small_level_dofs >= n_0 the whole solve is one persistent cooperative launch, and with a
+ * smaller nonzero small_level_dofs each V-cycle's lower levels are.
+ * MG_ERR_TIMEOUT (the result is then not valid) only where a bounded device-side wait can
+ * run: a grid barrier of the persistent launch (small_level_dofs > 0) or the TMA-staged SpMV
+ * (only with the environment variable NNMG_FORCE_LAYOUT=tma at set-up; the autotuner never
+ * picks it). Every entry point that runs such work (mg_vcycle, mg_solve*, the single steps,
+ * the server's requests) checks and clears the flag after its work and reports it this way;
+ * the TMA flag is shared by every stream of the device. */
 int mg_solve(mg_hierarchy_t* h, const double* b_dev, double* x_dev, double rtol, int32_t maxit,
              mg_solve_info_t* info, void* stream);
 
@@ -274,9 +280,14 @@ int mg_solve_host(mg_hierarchy_t* h, const double* b_host, double* x_host, doubl
 int mg_solve_stationary(mg_hierarchy_t* h, const double* b_dev, double* x_dev, double rtol,
                         int32_t maxit, mg_solve_info_t* info, void* stream);
 
-/* Solve n independent problems (their own hierarchies, all FP64 at the boundary) with the
- * V-cycles of all problems interleaved on the device (one stream per problem, joined
- * back to `stream`). Blocks; info[n] may be NULL. Returns the first non-OK status. */
+/* Solve n independent problems (their own hierarchies, all FP64 at the boundary). The
+ * problems whose whole solve runs persistently (small_level_dofs >= n_0) are iterated
+ * together in one persistent cooperative launch per precision on `stream` (their steps
+ * merged phase by phase; a problem's result is bitwise the same as solved alone); the others
+ * run their solve graphs on their own streams, overlapping on the device, joined back to
+ * `stream`. The persistent group allocates (and frees) its program and partial sums on
+ * `stream` during the call. Blocks; info[n] may be NULL. Returns the first non-OK status
+ * (MG_ERR_TIMEOUT as for mg_solve). */
 int mg_solve_batch(mg_hierarchy_t* const* hs, const double* const* b_dev, double* const* x_dev,
                    int32_t n, double rtol, int32_t maxit, mg_solve_info_t* info, void* stream);
 
