@@ -161,7 +161,15 @@ typedef struct mg_options_t {
                               inverse in FP32 (FP32 copy of the inverse, FP32 products); the
                               ill-conditioned ones, and every patch in FP64 precision, stay FP64;
                               0 = all FP64 (10000) */
-  int32_t reserved[2];
+  int32_t tune_min_nnz;    /* with sell_sigma = 0: operators with fewer nonzeros than this take
+                              a fixed rule instead of device timing (CSR vector, lanes per row
+                              the smallest power of two >= half the mean row length, 4..32, at
+                              most one device wave of threads; SELL with one lane per row for
+                              operators of more than 155,648 rows);
+                              below about a million nonzeros every candidate runs in a few
+                              microseconds, bound by launch and memory latency, and timing
+                              cannot separate them. 0 = time every operator (1 << 20) */
+  int32_t reserved[1];
 } mg_options_t;
 
 /* Result of a solve. */
@@ -357,7 +365,10 @@ typedef struct mg_request_t {
   int64_t n_b;
   double rtol;
   int32_t maxit;
-  int32_t reserved;
+  int32_t tune;                /* 0: every operator of the request takes the rule layout of
+                                  tune_min_nnz whatever opt says (a request is solved once, so
+                                  device timing runs at set-up would cost more than they save);
+                                  1: opt's tune_min_nnz applies */
 } mg_request_t;
 
 typedef struct mg_request_result_t {

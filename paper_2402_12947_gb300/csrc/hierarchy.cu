@@ -331,6 +331,20 @@ void tune_store(const std::string& key, const Layout& L) {
   }
 }
 
+// Layout of an operator too small for timing to separate the candidates: CSR vector with G
+// lanes per row, G the smallest power of two >= half the mean row length, within [4, 32], so
+// that a row takes about two dependent load steps, but with no more threads than one wave of
+// the device (152 SMs x 2048); an operator with rows enough for two waves at four lanes takes
+// SELL with one lane per row (predicated steps of eight) instead.
+Layout rule_layout(const Csr& A) {
+  constexpr int64_t kWave = 152 * 2048;
+  const double mean = A.nrows > 0 ? (double)A.nnz() / (double)A.nrows : 0.0;
+  if (A.nrows * 4 > 2 * kWave) return Layout{1, 1, 3, 1, 0};
+  int g = 4;
+  while (g < 32 && 2.0 * g < mean && A.nrows * 2 * g <= kWave) g *= 2;
+  return Layout{g, 1, 1, 1, 0};
+}
+
 // Layout from its name (the inverse of layout_name): "v<G>" = CSR vector with G in {4, 8,
 // 16, 32} lanes per row; "s<sigma>[x<S>][p|q|t][f<pf>]" = SELL with rows sorted in windows of
 // sigma, S in {2, 4} lanes per row, row loop p = predicated steps of four, q = predicated
@@ -394,7 +408,8 @@ bool parse_layout(const std::string& name, Layout* out) {
 // TMA-staged kernel ("tma", "s1t") exists only behind this switch and applies to the level
 // operators whose slices fit its shared-memory stages (allow_tma), the others are tuned.
 template <typename T>
-SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log, bool allow_tma = false) {
+SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, int64_t rule_below, std::string* log,
+                      bool allow_tma = false) {
   if (sigma != 0 || A.nrows == 0) return make_sell<T>(A, mem, std::max(sigma, 1));
   const char* force = std::getenv("NNMG_FORCE_LAYOUT");
   if (force && *force) {
@@ -414,6 +429,11 @@ SellMat<T> tuned_sell(const Csr& A, DevMem& mem, int sigma, std::string* log, bo
       if (log) *log += " forced " + layout_name(F);
       return make_layout<T>(A, mem, F);
     }
+  }
+  if (A.nnz() < rule_below) {
+    const Layout R = rule_layout(A);
+    if (log) *log += " rule " + layout_name(R);
+    return make_layout<T>(A, mem, R);
   }
   const std::string key = tune_key(A, (int)sizeof(T));
   Layout cached{};
@@ -1027,6 +1047,7 @@ void validate_options(const mg_options_t& o) {
   if (o.pde < 0 || o.pde > 1) throw Error(MG_ERR_INVALID_ARG, "unknown pde");
   if (o.small_level_dofs < 0) throw Error(MG_ERR_INVALID_ARG, "small_level_dofs must be >= 0");
   if (o.fp32_patch_kappa < 0) throw Error(MG_ERR_INVALID_ARG, "fp32_patch_kappa must be >= 0");
+  if (o.tune_min_nnz < 0) throw Error(MG_ERR_INVALID_ARG, "tune_min_nnz must be >= 0");
   if (o.pde == MG_PDE_ELASTICITY && !(o.young > 0 && o.poisson_ratio > -1.0 && o.poisson_ratio < 0.5))
     throw Error(MG_ERR_INVALID_ARG, "elasticity needs E > 0 and -1 < nu < 1/2");
 }
@@ -1051,7 +1072,7 @@ void cheb_coefficients(double lmax, double lmin, int k, std::vector<double>& cd,
 // one launch can update the whole colour in place.
 template <typename T>
 void build_sgs_ops(const LevelH& Hl, const LevelH& Hd, const std::vector<int32_t>& perm, DevLevel<T>& D, DevMem& mem,
-                   int sigma) {
+                   int sigma, int64_t rule_below) {
   const int64_t n = Hd.A.nrows;
   std::vector<int32_t> col(n);
   for (int64_t i = 0; i < n; ++i) col[i] = Hl.colour[perm.empty() ? i : perm[i]];
@@ -1072,74 +1093,109 @@ void build_sgs_ops(const LevelH& Hl, const LevelH& Hd, const std::vector<int32_t
       }
       M.rp[r + 1] = (int32_t)M.ci.size();
     }
-    D.gs.push_back(tuned_sell<T>(M, mem, sigma, nullptr));
+    D.gs.push_back(tuned_sell<T>(M, mem, sigma, rule_below, nullptr));
     D.gs_rows.push_back(mem.upload(rows[c]));
   }
 }
 
 // Everything after the operators are known: diagonals, patch inverses, eigenvalues,
 // coarsest inverse, then (unless host_only) the device upload and the solve graph.
-// lambda_max of D^{-1/2} A D^{-1/2} restricted to keep (NULL: all) by Lanczos on the device:
-// the scaled operator is uploaded once as a SELL-32 FP64 matrix, every step is an SpMV and
-// two fixed-order reductions, and the host solves the tridiagonal Ritz problem. Same start
-// vector and stopping rule as lanczos_lmax (residual |beta s_last| <= tol theta).
-double device_lanczos(const Csr& A, const uint8_t* keep, double tol, int maxit, int* iters, cudaStream_t s) {
-  const int64_t n = A.nrows;
-  std::vector<double> sc = lanczos_scaling(A, keep);
-  int64_t nk = 0;
-  for (double x : sc) nk += x != 0.0;
-  if (nk == 0) {
-    if (iters) *iters = 0;
-    return 0.0;
-  }
-  Csr S;
-  S.nrows = S.ncols = n;
-  S.rp.assign(n + 1, 0);
-  for (int64_t i = 0; i < n; ++i) {
-    if (sc[i] != 0.0)
-      for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k)
-        if (sc[A.ci[k]] != 0.0) {
-          S.ci.push_back(A.ci[k]);
-          S.v.push_back(sc[i] * A.v[k] * sc[A.ci[k]]);
-        }
-    S.rp[i + 1] = (int32_t)S.ci.size();
-  }
+// lambda_max of D^{-1/2} A D^{-1/2}, and of its restriction to the rows and columns keep
+// marks, by Lanczos on the device. The scaled operator (all rows, entries s_i a_ij s_j in CSR
+// order) is built once per level and uploaded as a SELL-32 FP64 matrix; both runs use it. The
+// restricted run starts from a vector that is zero outside keep and zeroes w outside keep in
+// every update, so its SpMV adds only exact zeros for the dropped columns and it computes the
+// same numbers as a run on the restricted operator. Every step is an SpMV and two fixed-order
+// reductions; the host solves the tridiagonal Ritz problem. Same start vector and stopping
+// rule as lanczos_lmax (residual |beta s_last| <= tol theta).
+struct DeviceLanczos {
+  int64_t n = 0;
+  std::vector<double> sc;   // s_i = a_ii^{-1/2}
   DevMem mem;
-  mem.stream = s;
-  SellMat<double> M = make_sell<double>(S, mem, 1);
-  double* v = mem.upload(lanczos_start(sc));
-  double* vprev = mem.alloc<double>(n);
-  double* w = mem.alloc<double>(n);
-  double* part = mem.alloc<double>(cg_parts((int)n));
-  double* ab = mem.alloc<double>(2);
-  double* hab = pinned_acquire(2);
-  std::vector<double> al, be(1, 0.0);
-  double theta = 0.0;
-  int k = 0;
-  for (k = 0; k < std::min<int64_t>(maxit, nk); ++k) {
-    sell_spmv<double>(M, v, w, s);
-    lanczos_dot((int)n, w, v, part, ab, s);
-    lanczos_update((int)n, w, v, vprev, ab, be[k], part, ab + 1, s);
-    CK(cudaMemcpyAsync(hab, ab, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    const double alpha = hab[0], beta = std::sqrt(hab[1]);
-    al.push_back(alpha);
-    be.push_back(beta);
-    double sl;
-    tridiag_top(al, be, k + 1, &theta, &sl);
-    if (beta * sl <= tol * std::fabs(theta) || beta <= 1e-14 * std::fabs(theta)) {
-      ++k;
-      break;
-    }
-    lanczos_next((int)n, w, v, vprev, 1.0 / beta, s);
+  SellMat<double> M;
+  cudaStream_t s = nullptr;
+
+  DeviceLanczos(const Csr& A, cudaStream_t stream) : n(A.nrows), s(stream) {
+    sc = lanczos_scaling(A, nullptr);
+    Csr S;
+    S.nrows = S.ncols = n;
+    S.rp = A.rp;
+    S.ci = A.ci;
+    S.v.resize(A.v.size());
+    parallel_for(n, [&](int64_t lo, int64_t hi) {
+      for (int64_t i = lo; i < hi; ++i)
+        for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) S.v[k] = sc[i] * A.v[k] * sc[A.ci[k]];
+    });
+    mem.stream = s;
+    M = make_sell<double>(S, mem, 1);
   }
-  check_launch("device Lanczos");
-  pinned_release(hab);
-  mem.release();
-  CK(cudaStreamSynchronize(s));
-  if (iters) *iters = k;
-  return theta;
-}
+  ~DeviceLanczos() { mem.release(); }
+
+  double run(const uint8_t* keep, double tol, int maxit, int* iters) {
+    std::vector<double> sk = sc;
+    int64_t nk = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      if (keep && !keep[i]) sk[i] = 0.0;
+      nk += sk[i] != 0.0;
+    }
+    if (nk == 0) {
+      if (iters) *iters = 0;
+      return 0.0;
+    }
+    DevMem run;
+    run.stream = s;
+    double* v = run.upload(lanczos_start(sk));
+    double* vprev = run.alloc<double>(n);
+    double* w = run.alloc<double>(n);
+    double* part = run.alloc<double>(cg_parts((int)n));
+    const uint8_t* kd = nullptr;
+    if (keep) kd = run.upload(std::vector<uint8_t>(keep, keep + n));
+    // step k leaves alpha_k in hist[2k] and beta_{k+1}^2 in hist[2k+1]; the host reads them
+    // back every kLanczosBatch steps and replays the stopping rule step by step, so the
+    // result (theta and the step count) is that of a loop which tested after every step; the
+    // steps queued past the stopping point are discarded
+    constexpr int kLanczosBatch = 16;
+    const int kmax = (int)std::min<int64_t>(maxit, nk);
+    double* hist = run.alloc<double>(2 * (size_t)std::max(kmax, 1));
+    double* hh = pinned_acquire(2 * (int64_t)std::max(kmax, 1));
+    std::vector<double> al, be(1, 0.0);
+    double theta = 0.0;
+    int k = 0, queued = 0;
+    bool done = false;
+    while (!done && queued < kmax) {
+      const int q1 = std::min(kmax, queued + kLanczosBatch);
+      for (int j = queued; j < q1; ++j) {
+        if (j > 0) lanczos_next((int)n, w, v, vprev, hist + 2 * j - 1, s);
+        sell_spmv<double>(M, v, w, s);
+        lanczos_dot((int)n, w, v, part, hist + 2 * j, s);
+        lanczos_update((int)n, w, v, vprev, hist + 2 * j, j > 0 ? hist + 2 * j - 1 : nullptr, kd, part,
+                       hist + 2 * j + 1, s);
+      }
+      CK(cudaMemcpyAsync(hh + 2 * queued, hist + 2 * queued, 2 * sizeof(double) * (q1 - queued),
+                         cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (; k < q1; ++k) {
+        const double alpha = hh[2 * k], beta = std::sqrt(hh[2 * k + 1]);
+        al.push_back(alpha);
+        be.push_back(beta);
+        double sl;
+        tridiag_top(al, be, k + 1, &theta, &sl);
+        if (beta * sl <= tol * std::fabs(theta) || beta <= 1e-14 * std::fabs(theta)) {
+          ++k;
+          done = true;
+          break;
+        }
+      }
+      queued = q1;
+    }
+    check_launch("device Lanczos");
+    pinned_release(hh);
+    CK(cudaStreamSynchronize(s));
+    run.release();
+    if (iters) *iters = k;
+    return theta;
+  }
+};
 
 // lambda_max (unadjusted and adjusted) of every smoothed level, on the host or the device.
 void compute_eigenvalues(mg_hierarchy* h, bool on_device) {
@@ -1152,8 +1208,10 @@ void compute_eigenvalues(mg_hierarchy* h, bool on_device) {
       lv.lmax = o.lambda_override[l];
       if (!(lv.lmax > 0)) throw Error(MG_ERR_INVALID_ARG, "lambda_override must be positive");
     } else {
+      std::unique_ptr<DeviceLanczos> dlz;
+      if (on_device) dlz.reset(new DeviceLanczos(lv.A, h->own_stream));
       auto lanczos = [&](const uint8_t* keep, int* it) {
-        return on_device ? device_lanczos(lv.A, keep, o.eig_tol, o.eig_maxit, it, h->own_stream)
+        return on_device ? dlz->run(keep, o.eig_tol, o.eig_maxit, it)
                          : lanczos_lmax(lv.A, keep, o.eig_tol, o.eig_maxit, it);
       };
       int it = 0;
@@ -1322,8 +1380,8 @@ void build_device(mg_hierarchy* h) {
   gj.voff = mem.upload(svoff);
   gj.rowk = mem.alloc<double>(vtot);
   gj.colk = mem.alloc<double>(vtot);
-  gj.pinv = mem.alloc<double>(gj.nmat);
-  gj.drop = mem.alloc<int32_t>(gj.nmat);
+  gj.rowk2 = mem.alloc<double>(vtot);
+  gj.colk2 = mem.alloc<double>(vtot);
   gj.bad = mem.alloc<int32_t>(gj.nmat);
   gj.ndrop = mem.alloc<int32_t>(gj.nmat);
   batched_spsd_inverse(gj, mem.stream);
@@ -1400,15 +1458,15 @@ void build_device(mg_hierarchy* h) {
       if (!perm[l].empty()) D.perm = mem.upload(perm[l]);
       D.n = (int)H.A.nrows;
       std::string tlog;
-      D.A = tuned_sell<T>(H.A, mem, o.sell_sigma, &tlog, true);
+      D.A = tuned_sell<T>(H.A, mem, o.sell_sigma, o.tune_min_nnz, &tlog, true);
       h->uses_tma |= D.A.tma != 0;
       if (l < L - 1) {
-        D.P = tuned_sell<T>(H.P, mem, o.sell_sigma, &tlog);
-        D.R = tuned_sell<T>(H.R, mem, o.sell_sigma, &tlog);
+        D.P = tuned_sell<T>(H.P, mem, o.sell_sigma, o.tune_min_nnz, &tlog);
+        D.R = tuned_sell<T>(H.R, mem, o.sell_sigma, o.tune_min_nnz, &tlog);
         std::vector<T> dv(H.dinv.begin(), H.dinv.end());
         D.dinv = mem.upload(dv);
         if (!eng->sgs) cheb_coefficients(H.lmax, H.lmin, o.cheb_degree, D.cd, D.cr);
-        else build_sgs_ops(h->host[l], H, perm[l], D, mem, o.sell_sigma);
+        else build_sgs_ops(h->host[l], H, perm[l], D, mem, o.sell_sigma, o.tune_min_nnz);
         D.xt = mem.alloc<T>(D.n);
         D.d = mem.alloc<T>(D.n);
         D.res = mem.alloc<T>(D.n);
@@ -1560,7 +1618,7 @@ void build_device(mg_hierarchy* h) {
     h->e32.reset(new Engine<float>());
     upload_engine(h->e32.get(), float());
     std::string tlog;
-    h->A0 = tuned_sell<double>(dl[0].A, mem, o.sell_sigma, &tlog);
+    h->A0 = tuned_sell<double>(dl[0].A, mem, o.sell_sigma, o.tune_min_nnz, &tlog);
   } else {
     h->e64.reset(new Engine<double>());
     upload_engine(h->e64.get(), double());
@@ -2052,6 +2110,7 @@ void mg_default_options(mg_options_t* o) {
   o->poisson_ratio = 0.33;
   o->small_level_dofs = 0;
   o->fp32_patch_kappa = 10000;
+  o->tune_min_nnz = 1 << 20;
 }
 
 }  // extern "C"

@@ -910,14 +910,17 @@ __global__ void __launch_bounds__(kBlock) k_lz_dot(int n, const double* __restri
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-// w -= alpha v + beta vprev, partial sums of |w|^2
+// w -= alpha v + beta vprev with beta = sqrt(beta2) (beta2 null: beta = 0), and w = 0 where
+// keep (if given) is 0; partial sums of |w|^2
 __global__ void __launch_bounds__(kBlock) k_lz_update(int n, double* __restrict__ w, const double* __restrict__ v,
                                                       const double* __restrict__ vprev, const double* __restrict__ alpha,
-                                                      double beta, double* __restrict__ part) {
+                                                      const double* __restrict__ beta2, const uint8_t* __restrict__ keep,
+                                                      double* __restrict__ part) {
   const double a = *alpha;
+  const double beta = beta2 ? sqrt(*beta2) : 0.0;
   double s = 0.0;
   for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
-    const double wi = w[i] - (a * v[i] + beta * vprev[i]);
+    const double wi = keep && !keep[i] ? 0.0 : w[i] - (a * v[i] + beta * vprev[i]);
     w[i] = wi;
     s = fma(wi, wi, s);
   }
@@ -925,8 +928,10 @@ __global__ void __launch_bounds__(kBlock) k_lz_update(int n, double* __restrict_
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
+// v_{k+1} = w / beta with beta = sqrt(beta2); vprev = v_k
 __global__ void __launch_bounds__(kBlock) k_lz_next(int n, const double* __restrict__ w, double* __restrict__ v,
-                                                    double* __restrict__ vprev, double inv_beta) {
+                                                    double* __restrict__ vprev, const double* __restrict__ beta2) {
+  const double inv_beta = 1.0 / sqrt(*beta2);
   for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
     vprev[i] = v[i];
     v[i] = w[i] * inv_beta;
@@ -943,53 +948,136 @@ __global__ void __launch_bounds__(1024) k_reduce_sum(int nparts, const double* _
 
 constexpr double kGjDrop = 1e-10;
 
-__global__ void k_gj_prep(GjBatch g, int k) {
+// Pivot rule of the batched sweep (semi-definite blocks): pivot k of a matrix is dropped when
+// its current value p is at most kGjDrop times the original diagonal d0 (row and column k of
+// the result are then zero); p below -kGjDrop d0, a non-positive d0 or a non-finite p marks the
+// matrix as not positive semi-definite. Otherwise the step is the Gauss-Jordan update with
+// pinv = 1/p: M[k][k] = pinv, M[k][j] = M[k][j] pinv, M[i][k] = -M[i][k] pinv and
+// M[i][j] = fma(-M[i][k] pinv, M[k][j], M[i][j]) with row and column k taken before the step.
+
+// The large matrices' sweep, one launch per pivot. rowk / colk hold row k and column k of
+// every active matrix as they are before pivot k (written by the previous step, or by
+// k_gj_snap0 for k = 0). Step k decides the pivot's drop from that snapshot, applies the
+// update to every element in place (element (i, j) reads only M[i][j] and the snapshot), and
+// writes the updated row and column k + 1 into the other snapshot buffers for the next step.
+// Tiles of 32 x 32 elements, 4 per thread.
+__global__ void k_gj_snap0(GjBatch g) {
   const int b = blockIdx.x;
   const int n = g.n[b];
-  if (k >= n) return;
   const double* M = g.M + g.off[b];
-  const double p = M[(int64_t)k * n + k];
-  const double d0 = g.diag0[g.voff[b] + k];
-  const bool bad = !(d0 > 0.0) || !isfinite(p) || p < -kGjDrop * d0;
-  const bool drop = bad || p <= kGjDrop * d0;
   double* rk = g.rowk + g.voff[b];
   double* ck = g.colk + g.voff[b];
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    rk[j] = drop ? 0.0 : M[(int64_t)k * n + j];
-    ck[j] = drop ? 0.0 : M[(int64_t)j * n + k];
-  }
-  if (threadIdx.x == 0) {
-    g.pinv[b] = drop ? 0.0 : 1.0 / p;
-    g.drop[b] = drop ? 1 : 0;
-    if (bad) g.bad[b] = 1;
-    if (drop) g.ndrop[b] += 1;
+    rk[j] = M[j];
+    ck[j] = M[(int64_t)j * n];
   }
 }
 
-__global__ void k_gj_update(GjBatch g, int k) {
+__global__ void __launch_bounds__(kBlock) k_gj_step(GjBatch g, int k, int tiles_x, const double* __restrict__ rk_all,
+                                                    const double* __restrict__ ck_all, double* __restrict__ rk_next,
+                                                    double* __restrict__ ck_next) {
   const int b = blockIdx.y;
   const int n = g.n[b];
   if (k >= n) return;
+  const int ti = blockIdx.x / tiles_x, tj = blockIdx.x - ti * tiles_x;
+  const int j = tj * 32 + (threadIdx.x & 31);
+  const int i0 = ti * 32 + (threadIdx.x >> 5) * 4;
+  if (ti * 32 >= n || j >= n) return;
   double* M = g.M + g.off[b];
-  const double* rk = g.rowk + g.voff[b];
-  const double* ck = g.colk + g.voff[b];
-  const double pinv = g.pinv[b];
-  const bool drop = g.drop[b] != 0;
-  const int64_t nn = (int64_t)n * n;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / n), j = (int)(e - (int64_t)i * n);
-    if (drop) {
-      if (i == k || j == k) M[e] = 0.0;
-    } else if (i == k && j == k) {
-      M[e] = pinv;
-    } else if (i == k) {
-      M[e] = rk[j] * pinv;
-    } else if (j == k) {
-      M[e] = -ck[i] * pinv;
-    } else {
-      M[e] = fma(-ck[i] * pinv, rk[j], M[e]);
-    }
+  const double* rk = rk_all + g.voff[b];
+  const double* ck = ck_all + g.voff[b];
+  const double p = rk[k];
+  const double d0 = g.diag0[g.voff[b] + k];
+  const bool bad = !(d0 > 0.0) || !isfinite(p) || p < -kGjDrop * d0;
+  const bool drop = bad || p <= kGjDrop * d0;
+  const double pinv = drop ? 0.0 : 1.0 / p;
+  if (j == k && i0 <= k && k < i0 + 4) {   // the thread holding element (k, k)
+    if (bad) g.bad[b] = 1;
+    if (drop) g.ndrop[b] += 1;
   }
+  const double rkj = drop ? 0.0 : rk[j];
+  double* rn = rk_next + g.voff[b];
+  double* cn = ck_next + g.voff[b];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = i0 + u;
+    if (i >= n) break;
+    const int64_t e = (int64_t)i * n + j;
+    double m;
+    if (drop) {
+      m = (i == k || j == k) ? 0.0 : M[e];
+    } else if (i == k && j == k) {
+      m = pinv;
+    } else if (i == k) {
+      m = rkj * pinv;
+    } else if (j == k) {
+      m = -ck[i] * pinv;
+    } else {
+      m = fma(-ck[i] * pinv, rkj, M[e]);
+    }
+    if (!drop || i == k || j == k) M[e] = m;
+    if (i == k + 1) rn[j] = m;
+    if (j == k + 1) cn[i] = m;
+  }
+}
+
+// The whole sweep of one small matrix (n <= kGjSmallN) in one block, the matrix held in shared
+// memory: matrix first + blockIdx.x of the batch. Every pivot step is the one k_gj_step
+// performs (same drop rule, same operations in the same order, so the same result), with
+// block barriers in place of launch boundaries.
+constexpr int kGjSmallN = 128;
+constexpr size_t kGjSmallSmem = ((size_t)kGjSmallN * kGjSmallN + 2 * kGjSmallN) * sizeof(double);
+
+__global__ void __launch_bounds__(kBlock) k_gj_small(GjBatch g, int first) {
+  extern __shared__ double gs[];
+  const int b = first + blockIdx.x;
+  const int n = g.n[b];
+  const int nn = n * n;
+  double* S = gs;
+  double* rk = gs + nn;
+  double* ck = rk + n;
+  __shared__ double pinv_s;
+  __shared__ int drop_s;
+  double* M = g.M + g.off[b];
+  const double* d0v = g.diag0 + g.voff[b];
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) S[e] = M[e];
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      const double p = S[k * n + k];
+      const double d0 = d0v[k];
+      const bool bad = !(d0 > 0.0) || !isfinite(p) || p < -kGjDrop * d0;
+      const bool drop = bad || p <= kGjDrop * d0;
+      pinv_s = drop ? 0.0 : 1.0 / p;
+      drop_s = drop ? 1 : 0;
+      if (bad) g.bad[b] = 1;
+      if (drop) g.ndrop[b] += 1;
+    }
+    __syncthreads();
+    const bool drop = drop_s != 0;
+    const double pinv = pinv_s;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      rk[j] = drop ? 0.0 : S[k * n + j];
+      ck[j] = drop ? 0.0 : S[j * n + k];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+      const int i = e / n, j = e - i * n;
+      if (drop) {
+        if (i == k || j == k) S[e] = 0.0;
+      } else if (i == k && j == k) {
+        S[e] = pinv;
+      } else if (i == k) {
+        S[e] = rk[j] * pinv;
+      } else if (j == k) {
+        S[e] = -ck[i] * pinv;
+      } else {
+        S[e] = fma(-ck[i] * pinv, rk[j], S[e]);
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) M[e] = S[e];
 }
 
 // max_i sum_j |M_ij| of matrix blockIdx.x of the batch (column sums: M is symmetric, so
@@ -1036,24 +1124,37 @@ void lanczos_dot(int n, const double* w, const double* v, double* part, double* 
   k_lz_dot<<<cg_parts(n), kBlock, 0, s>>>(n, w, v, part);
   k_reduce_sum<<<1, 1024, 0, s>>>(cg_parts(n), part, out);
 }
-void lanczos_update(int n, double* w, const double* v, const double* vprev, const double* alpha, double beta,
-                    double* part, double* out, cudaStream_t s) {
-  k_lz_update<<<cg_parts(n), kBlock, 0, s>>>(n, w, v, vprev, alpha, beta, part);
+void lanczos_update(int n, double* w, const double* v, const double* vprev, const double* alpha, const double* beta2,
+                    const uint8_t* keep, double* part, double* out, cudaStream_t s) {
+  k_lz_update<<<cg_parts(n), kBlock, 0, s>>>(n, w, v, vprev, alpha, beta2, keep, part);
   k_reduce_sum<<<1, 1024, 0, s>>>(cg_parts(n), part, out);
 }
-void lanczos_next(int n, const double* w, double* v, double* vprev, double inv_beta, cudaStream_t s) {
-  k_lz_next<<<cg_parts(n), kBlock, 0, s>>>(n, w, v, vprev, inv_beta);
+void lanczos_next(int n, const double* w, double* v, double* vprev, const double* beta2, cudaStream_t s) {
+  k_lz_next<<<cg_parts(n), kBlock, 0, s>>>(n, w, v, vprev, beta2);
 }
 
 void batched_spsd_inverse(const GjBatch& g, cudaStream_t s) {
-  int active = g.nmat;
-  for (int k = 0; k < g.max_n; ++k) {
+  // matrices are sorted by size, largest first: the small ones take one block each for the
+  // whole sweep (shared memory), the others one prep and one update launch per pivot
+  int nlarge = 0;
+  while (nlarge < g.nmat && g.hn[nlarge] > kGjSmallN) ++nlarge;
+  if (nlarge < g.nmat) {
+    const int ns = g.hn[nlarge];
+    cudaFuncSetAttribute(k_gj_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGjSmallSmem);
+    k_gj_small<<<g.nmat - nlarge, kBlock, ((size_t)ns * ns + 2 * ns) * sizeof(double), s>>>(g, nlarge);
+  }
+  if (nlarge == 0) return;
+  // snapshots of row and column k: rowk/colk for even k, rowk2/colk2 for odd k
+  k_gj_snap0<<<nlarge, kBlock, 0, s>>>(g);
+  const int tiles_x = (g.hn[0] + 31) / 32;
+  int active = nlarge;
+  for (int k = 0; k < g.max_n && active > 0; ++k) {
     while (active > 0 && g.hn[active - 1] <= k) --active;
     if (active == 0) break;
-    const int64_t nn = (int64_t)g.hn[0] * g.hn[0];
-    const int bx = (int)std::min<int64_t>((nn + kBlock - 1) / kBlock, 4096);
-    k_gj_prep<<<active, kBlock, 0, s>>>(g, k);
-    k_gj_update<<<dim3(bx, active), kBlock, 0, s>>>(g, k);
+    const bool even = (k & 1) == 0;
+    k_gj_step<<<dim3(tiles_x * tiles_x, active), kBlock, 0, s>>>(g, k, tiles_x, even ? g.rowk : g.rowk2,
+                                                                  even ? g.colk : g.colk2, even ? g.rowk2 : g.rowk,
+                                                                  even ? g.colk2 : g.colk);
   }
 }
 

@@ -234,19 +234,23 @@ struct GjBatch {
   int64_t* voff = nullptr;     // [nmat] offset of matrix b in the per-DoF vectors
   double* M = nullptr;         // matrices, overwritten by their inverses
   double* diag0 = nullptr;     // original diagonals
-  double *rowk = nullptr, *colk = nullptr, *pinv = nullptr;
-  int32_t *drop = nullptr, *bad = nullptr, *ndrop = nullptr;
+  double *rowk = nullptr, *colk = nullptr;     // row and column k before pivot k (even k)
+  double *rowk2 = nullptr, *colk2 = nullptr;   // the same for odd k
+  int32_t *bad = nullptr, *ndrop = nullptr;
 };
 void batched_spsd_inverse(const GjBatch& g, cudaStream_t s);
 // max_i sum_j |M_ij| of each matrix of a batch (its 1-norm, M symmetric) into out[b].
 void batched_norm1(const GjBatch& g, double* out, cudaStream_t s);
 
 // ---- Lanczos (set-up): out = w.v; w -= alpha v + beta vprev with out = |w|^2; v, vprev
-// advanced with v = w / beta. Reductions in a fixed order. ----
+// advanced with v = w / beta. The scalars stay on the device (alpha and beta^2 as the
+// reductions left them; beta = sqrt(beta^2) taken where it is used, a null beta2 meaning
+// beta = 0), so that several steps can be queued without a host round trip. With keep
+// (nullable), the update also sets w = 0 where keep is 0. Reductions in a fixed order. ----
 void lanczos_dot(int n, const double* w, const double* v, double* part, double* out, cudaStream_t s);
-void lanczos_update(int n, double* w, const double* v, const double* vprev, const double* alpha, double beta,
-                    double* part, double* out, cudaStream_t s);
-void lanczos_next(int n, const double* w, double* v, double* vprev, double inv_beta, cudaStream_t s);
+void lanczos_update(int n, double* w, const double* v, const double* vprev, const double* alpha, const double* beta2,
+                    const uint8_t* keep, double* part, double* out, cudaStream_t s);
+void lanczos_next(int n, const double* w, double* v, double* vprev, const double* beta2, cudaStream_t s);
 
 // ---- vectors ----
 template <typename Src, typename Dst> void convert(int n, const Src* a, Dst* b, cudaStream_t s);

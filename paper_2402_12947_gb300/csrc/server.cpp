@@ -13,6 +13,7 @@
 // only its own buffers (with fixed layouts, sell_sigma >= 1, the result is bitwise the same
 // alone and in the mix).
 #include <algorithm>
+#include <climits>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -283,6 +284,7 @@ int mg_server_submit(mg_server_t* s, const mg_request_t* q, int64_t* id) {
   else mg_default_options(&r->opt);
   r->opt.host_only = 0;
   r->opt.use_graph = 1;
+  if (!q->tune) r->opt.tune_min_nnz = INT32_MAX;
   r->meshes.resize(q->L);
   r->coords.resize(q->L);
   r->cells.resize(q->L);

@@ -42,7 +42,8 @@ class MgOptions(C.Structure):
                 ("use_graph", C.c_int32), ("local_levels_mask", C.c_int32), ("quality_threshold", C.c_double),
                 ("sell_sigma", C.c_int32), ("reorder", C.c_int32), ("global_smoother", C.c_int32),
                 ("pde", C.c_int32), ("young", C.c_double), ("poisson_ratio", C.c_double),
-                ("small_level_dofs", C.c_int32), ("fp32_patch_kappa", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("small_level_dofs", C.c_int32), ("fp32_patch_kappa", C.c_int32), ("tune_min_nnz", C.c_int32),
+                ("reserved", C.c_int32 * 1)]
 
 
 class MgSolveInfo(C.Structure):
@@ -62,7 +63,7 @@ class MgCsr(C.Structure):
 class MgRequest(C.Structure):
     _fields_ = [("levels", C.c_void_p), ("L", C.c_int32), ("degree", C.c_int32), ("quality_threshold", C.c_double),
                 ("opt", C.c_void_p), ("b", C.c_void_p), ("n_b", C.c_int64), ("rtol", C.c_double),
-                ("maxit", C.c_int32), ("reserved", C.c_int32)]
+                ("maxit", C.c_int32), ("tune", C.c_int32)]
 
 
 class MgRequestResult(C.Structure):
@@ -513,7 +514,8 @@ class Server:
         if code != OK:
             raise NnmgError(code, lib.mg_server_last_error().decode())
 
-    def submit(self, meshes, degree, b=None, rtol=1e-8, maxit=500, quality_threshold=0.1, **opts) -> int:
+    def submit(self, meshes, degree, b=None, rtol=1e-8, maxit=500, quality_threshold=0.1, tune=False,
+               **opts) -> int:
         arr = (MgMesh * len(meshes))()
         keep = []
         for i, m in enumerate(meshes):
@@ -531,7 +533,7 @@ class Server:
             bb = _np(b, np.float64)
             keep.append(bb)
             q.b, q.n_b = bb.ctypes.data, bb.size
-        q.rtol, q.maxit = rtol, maxit
+        q.rtol, q.maxit, q.tune = rtol, maxit, int(bool(tune))
         rid = C.c_int64()
         code = lib.mg_server_submit(self._s, C.byref(q), C.byref(rid))
         if code != OK:

@@ -33,17 +33,23 @@ def requests():
 OPTS = dict(sell_sigma=1)   # fixed layouts: no timing-dependent choice
 
 
-def test_results_identical_alone_and_in_the_mix(nnmg):
+# Server requests lay out every operator by the deterministic rule (tune = 0); the same
+# hierarchy solved alone gets the rule everywhere from tune_min_nnz = 2^31 - 1.
+RULE = dict(tune_min_nnz=2 ** 31 - 1)
+
+
+@pytest.mark.parametrize("opts,alone_opts", [(OPTS, OPTS), ({}, RULE)], ids=["fixed-sell", "rule"])
+def test_results_identical_alone_and_in_the_mix(nnmg, opts, alone_opts):
     reqs = requests()
     alone = []
     for meshes, degree, b in reqs:
-        with nnmg.Hierarchy.from_meshes(meshes, degree, 0.1, **OPTS) as H:
+        with nnmg.Hierarchy.from_meshes(meshes, degree, 0.1, **alone_opts) as H:
             x = torch.zeros(b.size, dtype=torch.float64, device="cuda")
             info = H.solve(torch.from_numpy(b).cuda(), x, rtol=1e-8)
             assert info["converged"]
             alone.append(x.cpu().numpy())
     with nnmg.Server(hbm_budget_bytes=8 << 30, max_active=4, setup_threads=4) as srv:
-        ids = [srv.submit(m, d, b=b, rtol=1e-8, **OPTS) for m, d, b in reqs]
+        ids = [srv.submit(m, d, b=b, rtol=1e-8, **opts) for m, d, b in reqs]
         res = [srv.wait(i) for i in ids]
         xs = [srv.fetch(i, r["n"]) for i, r in zip(ids, res)]
         st = srv.stats()

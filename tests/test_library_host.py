@@ -131,7 +131,8 @@ def test_setup_errors(nnmg):
 def test_options_validation(nnmg):
     from paper_2402_12947_gb300 import inputs
     meshes = inputs.config_c1()
-    for kw in (dict(cheb_degree=0), dict(nu=0), dict(smoother=7), dict(precision=5), dict(lmin_ratio=1.5)):
+    for kw in (dict(cheb_degree=0), dict(nu=0), dict(smoother=7), dict(precision=5), dict(lmin_ratio=1.5),
+               dict(tune_min_nnz=-1)):
         with pytest.raises(nnmg.NnmgError) as e:
             nnmg.Hierarchy.from_meshes(meshes, 1, 0.1, host_only=1, **kw)
         assert e.value.code == nnmg.ERR_INVALID_ARG
@@ -225,3 +226,32 @@ def test_elasticity_options_validated(nnmg):
     with nnmg.Hierarchy.from_meshes(meshes, degree, 0.1, host_only=1) as H:
         with pytest.raises(nnmg.NnmgError):
             H.load_traction(0, 1.0, [1.0, 0.0])
+
+
+def test_binding_structs_match_the_header(nnmg, tmp_path):
+    """The ctypes mirrors of the ABI structs have the C header's size and field offsets
+    (compiled with the host C compiler against include/nnmg.h)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"mg_options_t": nnmg.MgOptions, "mg_request_t": nnmg.MgRequest,
+               "mg_request_result_t": nnmg.MgRequestResult, "mg_solve_info_t": nnmg.MgSolveInfo,
+               "mg_mesh_t": nnmg.MgMesh, "mg_csr_t": nnmg.MgCsr, "mg_server_stats_t": nnmg.MgServerStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "nnmg.h"', 'int main(void) {']
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ['  return 0;', '}']
+    src = tmp_path / "abi.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "abi"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
