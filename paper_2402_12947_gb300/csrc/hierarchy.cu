@@ -1147,7 +1147,9 @@ struct DeviceLanczos {
     double* v = run.upload(lanczos_start(sk));
     double* vprev = run.alloc<double>(n);
     double* w = run.alloc<double>(n);
-    double* part = run.alloc<double>(cg_parts((int)n));
+    // block partials of both reductions (the SpMV's grid covers the 32-row slices of n rows)
+    double* part = run.alloc<double>((n + 31) / 32 * 32 / kBlock + 1);
+    unsigned* ticket = run.alloc<unsigned>(1);
     const uint8_t* kd = nullptr;
     if (keep) kd = run.upload(std::vector<uint8_t>(keep, keep + n));
     // step k leaves alpha_k in hist[2k] and beta_{k+1}^2 in hist[2k+1]; the host reads them
@@ -1166,9 +1168,8 @@ struct DeviceLanczos {
       const int q1 = std::min(kmax, queued + kLanczosBatch);
       for (int j = queued; j < q1; ++j) {
         if (j > 0) lanczos_next((int)n, w, v, vprev, hist + 2 * j - 1, s);
-        sell_spmv<double>(M, v, w, s);
-        lanczos_dot((int)n, w, v, part, hist + 2 * j, s);
-        lanczos_update((int)n, w, v, vprev, hist + 2 * j, j > 0 ? hist + 2 * j - 1 : nullptr, kd, part,
+        lanczos_spmv_dot(M, v, w, part, ticket, hist + 2 * j, s);
+        lanczos_update((int)n, w, v, vprev, hist + 2 * j, j > 0 ? hist + 2 * j - 1 : nullptr, kd, part, ticket,
                        hist + 2 * j + 1, s);
       }
       CK(cudaMemcpyAsync(hh + 2 * queued, hist + 2 * queued, 2 * sizeof(double) * (q1 - queued),
@@ -1382,8 +1383,14 @@ void build_device(mg_hierarchy* h) {
   gj.colk = mem.alloc<double>(vtot);
   gj.rowk2 = mem.alloc<double>(vtot);
   gj.colk2 = mem.alloc<double>(vtot);
+  gj.piv = mem.alloc<double>(2 * (size_t)gj.nmat);
+  gj.pdrop = mem.alloc<int32_t>(2 * (size_t)gj.nmat);
   gj.bad = mem.alloc<int32_t>(gj.nmat);
   gj.ndrop = mem.alloc<int32_t>(gj.nmat);
+  if (tm.on) {
+    CK(cudaStreamSynchronize(mem.stream));
+    tm.mark("dense blocks (host + upload)");
+  }
   batched_spsd_inverse(gj, mem.stream);
   check_launch("batched dense inverse");
   {

@@ -542,6 +542,41 @@ __device__ void reduce_finish(double s, const Reduce& rd) {
   }
 }
 
+// Every thread of the block calls this with the block's partial s (valid in thread 0); the last
+// block to arrive sums the partials in index order into *out and resets the ticket.
+__device__ void reduce_to(double s, double* part, unsigned* ticket, double* out) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;  // block-uniform
+  __threadfence();
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) acc += __ldcg(part + i);
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) {
+    *out = acc;
+    *ticket = 0u;
+  }
+}
+
+// Lanczos step on the scaled operator: w = S v and alpha = w.v in one launch.
+template <int G, bool C16>
+__global__ void __launch_bounds__(kBlock) k_lz_spmv_dot(OpView<double> m, const double* __restrict__ v,
+                                                        double* __restrict__ w, double* part, unsigned* ticket,
+                                                        double* alpha) {
+  int row;
+  double ax, s = 0.0;
+  if (op_row<double, G, C16>(m, v, row, ax) && group_leader<G>()) {
+    w[row] = ax;
+    s = ax * v[row];
+  }
+  reduce_to(block_sum(s), part, ticket, alpha);
+}
+
 // q = A p with the p.q reduction in the same launch. The grid (about eight blocks per SM) walks
 // the operator's blocks of rows (`nvb` virtual blocks, grid-stride, a fixed assignment), each
 // thread accumulating p_i q_i of its rows in a register; one block reduction per block, then
@@ -901,21 +936,13 @@ __global__ void __launch_bounds__(kBlock) k_dot_self(int n, const double* __rest
 
 inline int grid_for(int n, int per) { return (n + per - 1) / per; }
 
-// ---- Lanczos on the scaled operator S (set-up): w = S v is a plain SpMV ----
-__global__ void __launch_bounds__(kBlock) k_lz_dot(int n, const double* __restrict__ w, const double* __restrict__ v,
-                                                   double* __restrict__ part) {
-  double s = 0.0;
-  for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) s = fma(w[i], v[i], s);
-  s = block_sum(s);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
+// ---- Lanczos on the scaled operator S (set-up) ----
 // w -= alpha v + beta vprev with beta = sqrt(beta2) (beta2 null: beta = 0), and w = 0 where
-// keep (if given) is 0; partial sums of |w|^2
+// keep (if given) is 0; |w|^2 into *out (last block)
 __global__ void __launch_bounds__(kBlock) k_lz_update(int n, double* __restrict__ w, const double* __restrict__ v,
                                                       const double* __restrict__ vprev, const double* __restrict__ alpha,
                                                       const double* __restrict__ beta2, const uint8_t* __restrict__ keep,
-                                                      double* __restrict__ part) {
+                                                      double* part, unsigned* ticket, double* out) {
   const double a = *alpha;
   const double beta = beta2 ? sqrt(*beta2) : 0.0;
   double s = 0.0;
@@ -924,8 +951,7 @@ __global__ void __launch_bounds__(kBlock) k_lz_update(int n, double* __restrict_
     w[i] = wi;
     s = fma(wi, wi, s);
   }
-  s = block_sum(s);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  reduce_to(block_sum(s), part, ticket, out);
 }
 
 // v_{k+1} = w / beta with beta = sqrt(beta2); vprev = v_k
@@ -938,14 +964,6 @@ __global__ void __launch_bounds__(kBlock) k_lz_next(int n, const double* __restr
   }
 }
 
-__global__ void __launch_bounds__(1024) k_reduce_sum(int nparts, const double* __restrict__ part,
-                                                     double* __restrict__ out) {
-  double s = 0.0;
-  for (int i = threadIdx.x; i < nparts; i += 1024) s += part[i];
-  s = block_sum(s);
-  if (threadIdx.x == 0) *out = s;
-}
-
 constexpr double kGjDrop = 1e-10;
 
 // Pivot rule of the batched sweep (semi-definite blocks): pivot k of a matrix is dropped when
@@ -956,11 +974,23 @@ constexpr double kGjDrop = 1e-10;
 // M[i][j] = fma(-M[i][k] pinv, M[k][j], M[i][j]) with row and column k taken before the step.
 
 // The large matrices' sweep, one launch per pivot. rowk / colk hold row k and column k of
-// every active matrix as they are before pivot k (written by the previous step, or by
-// k_gj_snap0 for k = 0). Step k decides the pivot's drop from that snapshot, applies the
-// update to every element in place (element (i, j) reads only M[i][j] and the snapshot), and
-// writes the updated row and column k + 1 into the other snapshot buffers for the next step.
-// Tiles of 32 x 32 elements, 4 per thread.
+// every active matrix as they are before pivot k, and piv / pdrop the pivot's 1/p and drop
+// decision (written by the previous step, or by k_gj_snap0 for k = 0; the buffers alternate
+// with the parity of k). Step k applies the update to every element in place (element (i, j)
+// reads only M[i][j] and the snapshot), writes the updated row and column k + 1 into the other
+// snapshot buffers, and the thread that computes the new M[k+1][k+1] decides pivot k + 1. The
+// kernel is bound by the FP64 pipe: one division per pivot instead of one per thread, and the
+// row factor -M[i][k]/p formed once per row of a thread's 8 x 2 elements (64 x 64 tiles).
+__device__ __forceinline__ void gj_decide(const GjBatch& g, int b, int k, double p, double* piv, int32_t* pdrop) {
+  const double d0 = g.diag0[g.voff[b] + k];
+  const bool bad = !(d0 > 0.0) || !isfinite(p) || p < -kGjDrop * d0;
+  const bool drop = bad || p <= kGjDrop * d0;
+  piv[b] = drop ? 0.0 : 1.0 / p;
+  pdrop[b] = drop ? 1 : 0;
+  if (bad) g.bad[b] = 1;
+  if (drop) g.ndrop[b] += 1;
+}
+
 __global__ void k_gj_snap0(GjBatch g) {
   const int b = blockIdx.x;
   const int n = g.n[b];
@@ -971,53 +1001,85 @@ __global__ void k_gj_snap0(GjBatch g) {
     rk[j] = M[j];
     ck[j] = M[(int64_t)j * n];
   }
+  if (threadIdx.x == 0 && n > 0) gj_decide(g, b, 0, M[0], g.piv, g.pdrop);
 }
+
+constexpr int kGjTile = 64;   // rows and columns of a k_gj_step tile (8 rows x 2 columns per thread)
 
 __global__ void __launch_bounds__(kBlock) k_gj_step(GjBatch g, int k, int tiles_x, const double* __restrict__ rk_all,
                                                     const double* __restrict__ ck_all, double* __restrict__ rk_next,
-                                                    double* __restrict__ ck_next) {
+                                                    double* __restrict__ ck_next, const double* __restrict__ piv,
+                                                    const int32_t* __restrict__ pdrop, double* piv_next,
+                                                    int32_t* pdrop_next) {
   const int b = blockIdx.y;
   const int n = g.n[b];
   if (k >= n) return;
   const int ti = blockIdx.x / tiles_x, tj = blockIdx.x - ti * tiles_x;
-  const int j = tj * 32 + (threadIdx.x & 31);
-  const int i0 = ti * 32 + (threadIdx.x >> 5) * 4;
-  if (ti * 32 >= n || j >= n) return;
+  if (ti * kGjTile >= n || tj * kGjTile >= n) return;   // block-uniform
+  const int lane = threadIdx.x & 31;
+  const int i0 = ti * kGjTile + (threadIdx.x >> 5) * 8;
+  const int j0 = tj * kGjTile + lane;
   double* M = g.M + g.off[b];
   const double* rk = rk_all + g.voff[b];
   const double* ck = ck_all + g.voff[b];
-  const double p = rk[k];
-  const double d0 = g.diag0[g.voff[b] + k];
-  const bool bad = !(d0 > 0.0) || !isfinite(p) || p < -kGjDrop * d0;
-  const bool drop = bad || p <= kGjDrop * d0;
-  const double pinv = drop ? 0.0 : 1.0 / p;
-  if (j == k && i0 <= k && k < i0 + 4) {   // the thread holding element (k, k)
-    if (bad) g.bad[b] = 1;
-    if (drop) g.ndrop[b] += 1;
-  }
-  const double rkj = drop ? 0.0 : rk[j];
   double* rn = rk_next + g.voff[b];
   double* cn = ck_next + g.voff[b];
+  const double pinv = piv[b];
+  const bool drop = pdrop[b] != 0;
+  double rkj[2], f[8], m[8][2];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int i = i0 + u;
-    if (i >= n) break;
-    const int64_t e = (int64_t)i * n + j;
-    double m;
-    if (drop) {
-      m = (i == k || j == k) ? 0.0 : M[e];
-    } else if (i == k && j == k) {
-      m = pinv;
-    } else if (i == k) {
-      m = rkj * pinv;
-    } else if (j == k) {
-      m = -ck[i] * pinv;
-    } else {
-      m = fma(-ck[i] * pinv, rkj, M[e]);
+  for (int c = 0; c < 2; ++c) {
+    const int j = j0 + 32 * c;
+    rkj[c] = j < n && !drop ? rk[j] : 0.0;
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int i = i0 + r;
+    f[r] = i < n ? -ck[i] * pinv : 0.0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int j = j0 + 32 * c;
+      m[r][c] = i < n && j < n ? M[(int64_t)i * n + j] : 0.0;
     }
-    if (!drop || i == k || j == k) M[e] = m;
-    if (i == k + 1) rn[j] = m;
-    if (j == k + 1) cn[i] = m;
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int i = i0 + r;
+    if (i >= n) break;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int j = j0 + 32 * c;
+      if (j >= n) continue;
+      double v;
+      if (drop) {
+        if (i != k && j != k) continue;   // unchanged, and neither snapshot nor pivot k + 1 is here
+        v = 0.0;
+      } else if (i == k && j == k) {
+        v = pinv;
+      } else if (i == k) {
+        v = rkj[c] * pinv;
+      } else if (j == k) {
+        v = f[r];
+      } else {
+        v = fma(f[r], rkj[c], m[r][c]);
+      }
+      M[(int64_t)i * n + j] = v;
+      m[r][c] = v;
+    }
+  }
+  // row and column k + 1 after this step, and the decision on pivot k + 1
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int i = i0 + r;
+    if (i >= n) break;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int j = j0 + 32 * c;
+      if (j >= n) continue;
+      if (i == k + 1) rn[j] = m[r][c];
+      if (j == k + 1) cn[i] = m[r][c];
+      if (i == k + 1 && j == k + 1) gj_decide(g, b, k + 1, m[r][c], piv_next, pdrop_next);
+    }
   }
 }
 
@@ -1034,8 +1096,8 @@ __global__ void __launch_bounds__(kBlock) k_gj_small(GjBatch g, int first) {
   const int n = g.n[b];
   const int nn = n * n;
   double* S = gs;
-  double* rk = gs + nn;
-  double* ck = rk + n;
+  double* rk = gs + nn;   // row k before the pivot step
+  double* fk = rk + n;    // row factors -M[i][k] / p of the current pivot
   __shared__ double pinv_s;
   __shared__ int drop_s;
   double* M = g.M + g.off[b];
@@ -1058,7 +1120,7 @@ __global__ void __launch_bounds__(kBlock) k_gj_small(GjBatch g, int first) {
     const double pinv = pinv_s;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
       rk[j] = drop ? 0.0 : S[k * n + j];
-      ck[j] = drop ? 0.0 : S[j * n + k];
+      fk[j] = drop ? 0.0 : -S[j * n + k] * pinv;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < nn; e += blockDim.x) {
@@ -1070,9 +1132,9 @@ __global__ void __launch_bounds__(kBlock) k_gj_small(GjBatch g, int first) {
       } else if (i == k) {
         S[e] = rk[j] * pinv;
       } else if (j == k) {
-        S[e] = -ck[i] * pinv;
+        S[e] = fk[i];
       } else {
-        S[e] = fma(-ck[i] * pinv, rk[j], S[e]);
+        S[e] = fma(fk[i], rk[j], S[e]);
       }
     }
     __syncthreads();
@@ -1120,14 +1182,9 @@ __global__ void __launch_bounds__(kBlock) k_fp64_fma(int iters, double c, double
 
 }  // namespace
 
-void lanczos_dot(int n, const double* w, const double* v, double* part, double* out, cudaStream_t s) {
-  k_lz_dot<<<cg_parts(n), kBlock, 0, s>>>(n, w, v, part);
-  k_reduce_sum<<<1, 1024, 0, s>>>(cg_parts(n), part, out);
-}
 void lanczos_update(int n, double* w, const double* v, const double* vprev, const double* alpha, const double* beta2,
-                    const uint8_t* keep, double* part, double* out, cudaStream_t s) {
-  k_lz_update<<<cg_parts(n), kBlock, 0, s>>>(n, w, v, vprev, alpha, beta2, keep, part);
-  k_reduce_sum<<<1, 1024, 0, s>>>(cg_parts(n), part, out);
+                    const uint8_t* keep, double* part, unsigned* ticket, double* out, cudaStream_t s) {
+  k_lz_update<<<cg_parts(n), kBlock, 0, s>>>(n, w, v, vprev, alpha, beta2, keep, part, ticket, out);
 }
 void lanczos_next(int n, const double* w, double* v, double* vprev, const double* beta2, cudaStream_t s) {
   k_lz_next<<<cg_parts(n), kBlock, 0, s>>>(n, w, v, vprev, beta2);
@@ -1144,17 +1201,22 @@ void batched_spsd_inverse(const GjBatch& g, cudaStream_t s) {
     k_gj_small<<<g.nmat - nlarge, kBlock, ((size_t)ns * ns + 2 * ns) * sizeof(double), s>>>(g, nlarge);
   }
   if (nlarge == 0) return;
-  // snapshots of row and column k: rowk/colk for even k, rowk2/colk2 for odd k
+  // row/column snapshots and pivot decisions: rowk/colk/piv/pdrop for even k, the second
+  // buffers (rowk2/colk2, piv + nmat, pdrop + nmat) for odd k
   k_gj_snap0<<<nlarge, kBlock, 0, s>>>(g);
-  const int tiles_x = (g.hn[0] + 31) / 32;
+  const int tiles_x = (g.hn[0] + kGjTile - 1) / kGjTile;
   int active = nlarge;
   for (int k = 0; k < g.max_n && active > 0; ++k) {
     while (active > 0 && g.hn[active - 1] <= k) --active;
     if (active == 0) break;
     const bool even = (k & 1) == 0;
-    k_gj_step<<<dim3(tiles_x * tiles_x, active), kBlock, 0, s>>>(g, k, tiles_x, even ? g.rowk : g.rowk2,
-                                                                  even ? g.colk : g.colk2, even ? g.rowk2 : g.rowk,
-                                                                  even ? g.colk2 : g.colk);
+    double* pv0 = g.piv + (even ? 0 : g.nmat);
+    double* pv1 = g.piv + (even ? g.nmat : 0);
+    int32_t* pd0 = g.pdrop + (even ? 0 : g.nmat);
+    int32_t* pd1 = g.pdrop + (even ? g.nmat : 0);
+    k_gj_step<<<dim3(tiles_x * tiles_x, active), kBlock, 0, s>>>(
+        g, k, tiles_x, even ? g.rowk : g.rowk2, even ? g.colk : g.colk2, even ? g.rowk2 : g.rowk,
+        even ? g.colk2 : g.colk, pv0, pd0, pv1, pd1);
   }
 }
 
@@ -1357,6 +1419,13 @@ void sell_gs(const SellMat<T>& M, const int32_t* rows, const T* b, const T* dinv
   by_layout(M.lanes, M.unroll, M.sub, M.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
     launch(k_gs<T, L::lanes, L::c16>, op_blocks(M), kBlock, 0, s, view(M), rows, x, b, dinv, x);
+  });
+}
+void lanczos_spmv_dot(const SellMat<double>& M, const double* v, double* w, double* part, unsigned* ticket,
+                      double* alpha, cudaStream_t s) {
+  by_layout(M.lanes, M.unroll, M.sub, M.col16 != nullptr, [&](auto g) {
+    using L = decltype(g);
+    launch(k_lz_spmv_dot<L::lanes, L::c16>, op_blocks(M), kBlock, 0, s, view(M), v, w, part, ticket, alpha);
   });
 }
 int ap_parts(const SellMat<double>& A) {

@@ -236,20 +236,25 @@ struct GjBatch {
   double* diag0 = nullptr;     // original diagonals
   double *rowk = nullptr, *colk = nullptr;     // row and column k before pivot k (even k)
   double *rowk2 = nullptr, *colk2 = nullptr;   // the same for odd k
+  double* piv = nullptr;       // [2 nmat] 1/p of the current pivot (0 if dropped), by parity of k
+  int32_t* pdrop = nullptr;    // [2 nmat] the current pivot is dropped, by parity of k
   int32_t *bad = nullptr, *ndrop = nullptr;
 };
 void batched_spsd_inverse(const GjBatch& g, cudaStream_t s);
 // max_i sum_j |M_ij| of each matrix of a batch (its 1-norm, M symmetric) into out[b].
 void batched_norm1(const GjBatch& g, double* out, cudaStream_t s);
 
-// ---- Lanczos (set-up): out = w.v; w -= alpha v + beta vprev with out = |w|^2; v, vprev
-// advanced with v = w / beta. The scalars stay on the device (alpha and beta^2 as the
+// ---- Lanczos (set-up): w = S v with alpha = w.v; w -= alpha v + beta vprev with out = |w|^2;
+// v, vprev advanced with v = w / beta. The scalars stay on the device (alpha and beta^2 as the
 // reductions left them; beta = sqrt(beta^2) taken where it is used, a null beta2 meaning
 // beta = 0), so that several steps can be queued without a host round trip. With keep
-// (nullable), the update also sets w = 0 where keep is 0. Reductions in a fixed order. ----
-void lanczos_dot(int n, const double* w, const double* v, double* part, double* out, cudaStream_t s);
+// (nullable), the update also sets w = 0 where keep is 0. Each reduction is finished by the
+// last block of the kernel that produces it (fixed order; part holds the block partials,
+// ticket a zeroed counter). ----
+void lanczos_spmv_dot(const SellMat<double>& M, const double* v, double* w, double* part, unsigned* ticket,
+                      double* alpha, cudaStream_t s);
 void lanczos_update(int n, double* w, const double* v, const double* vprev, const double* alpha, const double* beta2,
-                    const uint8_t* keep, double* part, double* out, cudaStream_t s);
+                    const uint8_t* keep, double* part, unsigned* ticket, double* out, cudaStream_t s);
 void lanczos_next(int n, const double* w, double* v, double* vprev, const double* beta2, cudaStream_t s);
 
 // ---- vectors ----
