@@ -874,16 +874,37 @@ __global__ void k_axpy_from(int n, const T* __restrict__ z, double* __restrict__
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] += (double)z[i];
 }
 
+// The CG vector kernels walk the vectors grid-stride (608 blocks) four strides per step: the
+// step issues the loads of all four elements first, so that each thread keeps four times the
+// bytes in flight (at 4 blocks of 256 threads per SM a single element per step left these
+// kernels at about 0.6 of the HBM rate). Each thread's partial sum is accumulated in element
+// order, so the reductions stay deterministic.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_cg_init(int n, const double* __restrict__ b, double* __restrict__ r,
                                                     double* __restrict__ x, T* __restrict__ vb, T* __restrict__ vx,
                                                     Reduce rd) {
   double s = 0.0;
-  for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
+  const int st = gridDim.x * kBlock;
+  int i = blockIdx.x * kBlock + threadIdx.x;
+  for (; i + 3 * st < n; i += 4 * st) {
+    double bv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) bv[u] = b[i + u * st];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int k = i + u * st;
+      r[k] = bv[u];
+      x[k] = 0.0;
+      if constexpr (!std::is_same<T, double>::value) vb[k] = (T)bv[u];  // FP64: vb is r itself
+      vx[k] = T(0);
+      s = fma(bv[u], bv[u], s);
+    }
+  }
+  for (; i < n; i += st) {
     const double bi = b[i];
     r[i] = bi;
     x[i] = 0.0;
-    if constexpr (!std::is_same<T, double>::value) vb[i] = (T)bi;  // FP64: vb is r itself
+    if constexpr (!std::is_same<T, double>::value) vb[i] = (T)bi;
     vx[i] = T(0);
     s = fma(bi, bi, s);
   }
@@ -891,17 +912,39 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(int n, const double* __restr
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_cg_update(int n, const CgState* __restrict__ st, const double* __restrict__ p,
+__global__ void __launch_bounds__(kBlock) k_cg_update(int n, const CgState* __restrict__ stt, const double* __restrict__ p,
                                                       const double* __restrict__ q, double* __restrict__ x,
                                                       double* __restrict__ r, T* __restrict__ vb, T* __restrict__ vx,
                                                       Reduce rd) {
-  const double a = st->alpha;
+  const double a = stt->alpha;
   double s = 0.0;
-  for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
+  const int st = gridDim.x * kBlock;
+  int i = blockIdx.x * kBlock + threadIdx.x;
+  for (; i + 3 * st < n; i += 4 * st) {
+    double pv[4], qv[4], xv[4], rv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      pv[u] = p[i + u * st];
+      qv[u] = q[i + u * st];
+      xv[u] = x[i + u * st];
+      rv[u] = r[i + u * st];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int k = i + u * st;
+      x[k] = fma(a, pv[u], xv[u]);
+      const double ri = fma(-a, qv[u], rv[u]);
+      r[k] = ri;
+      if constexpr (!std::is_same<T, double>::value) vb[k] = (T)ri;  // FP64: vb is r itself
+      vx[k] = T(0);
+      s = fma(ri, ri, s);
+    }
+  }
+  for (; i < n; i += st) {
     x[i] = fma(a, p[i], x[i]);
     const double ri = fma(-a, q[i], r[i]);
     r[i] = ri;
-    if constexpr (!std::is_same<T, double>::value) vb[i] = (T)ri;  // FP64: vb is r itself
+    if constexpr (!std::is_same<T, double>::value) vb[i] = (T)ri;
     vx[i] = T(0);
     s = fma(ri, ri, s);
   }
@@ -912,7 +955,22 @@ template <typename T, bool FIRST>
 __global__ void __launch_bounds__(kBlock) k_cg_dotz(int n, const double* __restrict__ r, const T* __restrict__ vx,
                                                     double* __restrict__ p, Reduce rd) {
   double s = 0.0;
-  for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
+  const int st = gridDim.x * kBlock;
+  int i = blockIdx.x * kBlock + threadIdx.x;
+  for (; i + 3 * st < n; i += 4 * st) {
+    double zv[4], rv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      zv[u] = (double)vx[i + u * st];
+      rv[u] = r[i + u * st];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (FIRST) p[i + u * st] = zv[u];
+      s = fma(rv[u], zv[u], s);
+    }
+  }
+  for (; i < n; i += st) {
     const double zi = (double)vx[i];
     if (FIRST) p[i] = zi;
     s = fma(r[i], zi, s);
@@ -921,16 +979,36 @@ __global__ void __launch_bounds__(kBlock) k_cg_dotz(int n, const double* __restr
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_cg_pupdate(int n, const CgState* __restrict__ st, const T* __restrict__ vx,
+__global__ void __launch_bounds__(kBlock) k_cg_pupdate(int n, const CgState* __restrict__ stt, const T* __restrict__ vx,
                                                        double* __restrict__ p) {
-  const double beta = st->beta;
-  for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock)
-    p[i] = fma(beta, p[i], (double)vx[i]);
+  const double beta = stt->beta;
+  const int st = gridDim.x * kBlock;
+  int i = blockIdx.x * kBlock + threadIdx.x;
+  for (; i + 3 * st < n; i += 4 * st) {
+    double zv[4], pv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      zv[u] = (double)vx[i + u * st];
+      pv[u] = p[i + u * st];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) p[i + u * st] = fma(beta, pv[u], zv[u]);
+  }
+  for (; i < n; i += st) p[i] = fma(beta, p[i], (double)vx[i]);
 }
 
 __global__ void __launch_bounds__(kBlock) k_dot_self(int n, const double* __restrict__ r, Reduce rd) {
   double s = 0.0;
-  for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) s = fma(r[i], r[i], s);
+  const int st = gridDim.x * kBlock;
+  int i = blockIdx.x * kBlock + threadIdx.x;
+  for (; i + 3 * st < n; i += 4 * st) {
+    double rv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) rv[u] = r[i + u * st];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s = fma(rv[u], rv[u], s);
+  }
+  for (; i < n; i += st) s = fma(r[i], r[i], s);
   reduce_finish(block_sum(s), rd);
 }
 
