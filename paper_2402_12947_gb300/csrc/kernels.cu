@@ -577,7 +577,7 @@ __global__ void __launch_bounds__(kBlock) k_lz_spmv_dot(OpView<double> m, const 
   reduce_to(block_sum(s), part, ticket, alpha);
 }
 
-// q = A p with the p.q reduction in the same launch. The grid (about eight blocks per SM) walks
+// q = A p with the p.q reduction in the same launch. The grid (one resident wave) walks
 // the operator's blocks of rows (`nvb` virtual blocks, grid-stride, a fixed assignment), each
 // thread accumulating p_i q_i of its rows in a register; one block reduction per block, then
 // the last block to finish sums the block partials in order and applies the reduction's op
@@ -1506,22 +1506,24 @@ void lanczos_spmv_dot(const SellMat<double>& M, const double* v, double* w, doub
     launch(k_lz_spmv_dot<L::lanes, L::c16>, op_blocks(M), kBlock, 0, s, view(M), v, w, part, ticket, alpha);
   });
 }
-int ap_parts(const SellMat<double>& A) {
-  static const int cap = [] {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return std::max(1, sms * 8);
-  }();
-  return std::max(1, std::min(op_blocks(A), cap));
+// Blocks of one k_ap launch: one resident wave (SMs x the blocks of this instantiation that fit
+// on an SM: four at its 60-62 registers), at most one per row block. With two waves (8 blocks
+// per SM requested) the C2 product took 125.1 vs 122.2 us.
+template <typename K>
+int ap_wave(K kernel) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kBlock, 0);
+  return std::max(1, sms * std::max(per, 1));
 }
 
 void sell_ap(const SellMat<double>& A, const double* p, double* q, const Reduce& rd, cudaStream_t s) {
   const int nvb = op_blocks(A);
-  const int grid = ap_parts(A);
   by_layout(A.lanes, A.unroll, A.sub, A.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
-    launch(k_ap<L::lanes, L::c16>, grid, kBlock, 0, s, view(A), nvb, p, q, rd);
+    static const int wave = ap_wave(k_ap<L::lanes, L::c16>);
+    launch(k_ap<L::lanes, L::c16>, std::max(1, std::min(nvb, wave)), kBlock, 0, s, view(A), nvb, p, q, rd);
   });
 }
 

@@ -185,11 +185,10 @@ template <typename T> void sell_restrict(const SellMat<T>& R, const T* r, T* bc,
 // x_i = dinv_i (b_i - (M x)_r).
 template <typename T>
 void sell_gs(const SellMat<T>& M, const int32_t* rows, const T* b, const T* dinv, T* x, cudaStream_t s);
-// q = A p, then p.q summed by one finishing block that applies `op` to the CG state (FP64).
-// q = A p and p.q, reduced in the same launch (grid-stride blocks, the last block to finish sums
-// the partials in order and applies rd.op); rd.part needs ap_parts(A) entries.
+// q = A p and p.q (FP64), reduced in the same launch: one resident wave of blocks walks the
+// row blocks grid-stride, the last block to finish sums the block partials in order and
+// applies rd.op to the CG state; rd.part needs an entry per block (at most one per row block).
 void sell_ap(const SellMat<double>& A, const double* p, double* q, const Reduce& rd, cudaStream_t s);
-int ap_parts(const SellMat<double>& A);
 int sell_blocks(int nrows, int lanes);
 
 // ---- local correction S_c (two phases) ----
