@@ -1144,6 +1144,18 @@ struct DeviceLanczos {
     }
     DevMem run;
     run.stream = s;
+    double* hh = nullptr;
+    struct Release {   // this run's buffers also on an error path (stream-ordered frees)
+      DevMem& m;
+      double*& h;
+      ~Release() {
+        m.release();
+        if (h) {
+          cudaStreamSynchronize(m.stream);   // no copy into the staging buffer still in flight
+          pinned_release(h);
+        }
+      }
+    } release{run, hh};
     double* v = run.upload(lanczos_start(sk));
     double* vprev = run.alloc<double>(n);
     double* w = run.alloc<double>(n);
@@ -1159,7 +1171,7 @@ struct DeviceLanczos {
     constexpr int kLanczosBatch = 16;
     const int kmax = (int)std::min<int64_t>(maxit, nk);
     double* hist = run.alloc<double>(2 * (size_t)std::max(kmax, 1));
-    double* hh = pinned_acquire(2 * (int64_t)std::max(kmax, 1));
+    hh = pinned_acquire(2 * (int64_t)std::max(kmax, 1));
     std::vector<double> al, be(1, 0.0);
     double theta = 0.0;
     int k = 0, queued = 0;
@@ -1190,9 +1202,7 @@ struct DeviceLanczos {
       queued = q1;
     }
     check_launch("device Lanczos");
-    pinned_release(hh);
     CK(cudaStreamSynchronize(s));
-    run.release();
     if (iters) *iters = k;
     return theta;
   }

@@ -874,11 +874,10 @@ __global__ void k_axpy_from(int n, const T* __restrict__ z, double* __restrict__
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] += (double)z[i];
 }
 
-// The CG vector kernels walk the vectors grid-stride (608 blocks) four strides per step: the
-// step issues the loads of all four elements first, so that each thread keeps four times the
-// bytes in flight (at 4 blocks of 256 threads per SM a single element per step left these
-// kernels at about 0.6 of the HBM rate). Each thread's partial sum is accumulated in element
-// order, so the reductions stay deterministic.
+// The CG vector kernels walk the vectors grid-stride (608 blocks, 4 of 256 threads per SM)
+// four strides per step: the step issues the loads of all four elements before their
+// arithmetic, so that a thread has four elements' bytes in flight. Each thread's partial sum is
+// accumulated in element order, so the reductions stay deterministic.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_cg_init(int n, const double* __restrict__ b, double* __restrict__ r,
                                                     double* __restrict__ x, T* __restrict__ vb, T* __restrict__ vx,
