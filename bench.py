@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true",
                     help="skip the oracle's solve of the same problem (error of each GPU solution against it)")
-    ap.add_argument("--no-serve", action="store_true", help="skip the bounded serving stream of the default line")
+    ap.add_argument("--no-serve", action="store_true", help="skip the bounded serving stream and the batched solve of the default line")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every kernel individually instead of one CUDA graph per solve (profilers "
                          "cannot see kernel nodes of graphs with conditional nodes)")
@@ -455,6 +455,7 @@ def run_ours(args):
                "single_thread": {"value": d1["n"] / d1["times"][0], "cores": 1,
                                  "sample": sample + f", {d1['times'][0]:.1f} s single-threaded"}}
     serve = None if (args.no_serve or world > 1 or args.workload != "c2") else serve_bounded(nnmg, inputs)
+    batch = None if (args.no_serve or world > 1 or args.workload != "c2") else batch_bounded(nnmg, inputs)
     # the oracle solves the same problem on the exported operators (after every GPU timing)
     oracle_check = None
     if both and not args.no_oracle_check and not sgs:
@@ -518,6 +519,7 @@ def run_ours(args):
                      "hbm_gbs": ps64[3] / (ps64[0] * 1e-3) / 1e9 if ps64[0] > 0 else None} if ps64 else None},
         "rel_error_vs_oracle": oracle_check,
         "serve": serve,
+        "batch": batch,
         "cpu_baseline": cpu,
         "clocks": clk,
         "setup_s": {"fp64": setup64 if both else None, "mixed": setup32},
@@ -579,6 +581,51 @@ def serve_once(nnmg, stream, prec, rate, budget, max_active=16, setup_threads=12
             "peak_bytes": st["peak_bytes"],
             "max_true_rel_residual": max(r["true_rel_residual"] for r in ok) if ok else None,
             "mean_iterations": float(np.mean([r["iterations"] for r in ok])) if ok else None}
+
+
+def batch_bounded(nnmg, inputs, n_problems=16, reps=5):
+    """The default line's batch measurement: n_problems requests of the serving family (2D
+    P1/P2 32^2-128^2, 3D P1 16^3-32^3, 0-16 clusters, random right-hand sides, rtol 1e-8) set
+    up once, then solved together by mg_solve_batch (each problem's solve graph on its own
+    stream, overlapping on the device), mixed precision vs FP64 on the same GPU: GPU time per
+    batch (CUDA events on the calling stream, best of reps after one warm-up batch) and the
+    largest true relative residual."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(5)
+    specs, k = [], 0
+    while len(specs) < n_problems:
+        m, degree, label = inputs.serving_request(rng, 1000 + k)
+        k += 1
+        if (m[0].dim == 2 and m[0].n <= 128) or (m[0].dim == 3 and m[0].n <= 32):
+            specs.append((m, degree, label))
+    out = {"problems": n_problems, "mix": "2D P1/P2 32^2-128^2 and 3D P1 16^3-32^3, 0-16 clusters, RHS U[-1,1], "
+           "rtol 1e-8", "launch": "mg_solve_batch: one solve graph per problem on its own stream"}
+    for prec in ("mixed", "fp64"):
+        hs = [nnmg.Hierarchy.from_meshes(m, d, 0.1, precision=prec) for m, d, _ in specs]
+        try:
+            bs = [torch.from_numpy(inputs.uniform_rhs(h.num_dofs(0), 3)).cuda() for h in hs]
+            xs = [torch.zeros_like(v) for v in bs]
+            infos = nnmg.solve_batch(hs, bs, xs, rtol=RTOL)
+            torch.cuda.synchronize()
+            best = None
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                infos = nnmg.solve_batch(hs, bs, xs, rtol=RTOL)
+                e1.record()
+                torch.cuda.synchronize()
+                t = e0.elapsed_time(e1)
+                best = t if best is None else min(best, t)
+            dofs = sum(h.num_dofs(0) for h in hs)
+            out[prec] = {"ms_per_batch": best, "dofs_per_s": dofs / (best * 1e-3), "dofs": dofs,
+                         "iterations": [i["iterations"] for i in infos],
+                         "max_true_rel_residual": max(i["true_rel_residual"] for i in infos),
+                         "converged": all(i["converged"] for i in infos)}
+        finally:
+            for h in hs:
+                h.close()
+    return out
 
 
 def serve_bounded(nnmg, inputs, n_requests=64, rate=32.0):
