@@ -394,7 +394,9 @@ typedef struct mg_server_stats_t {
 } mg_server_stats_t;
 
 /* Create a server with an HBM budget (bytes), max_active concurrent requests on the device
- * and setup_threads host set-up workers. */
+ * and setup_threads host set-up workers. A request's host set-up runs its parallel loops on
+ * a share of the host cores fixed when it starts: all of them when no other request is in host
+ * set-up, a 1/(k+1) share beside k others (results do not depend on the share). */
 int mg_server_create(int64_t hbm_budget_bytes, int32_t max_active, int32_t setup_threads, mg_server_t** out);
 /* Queue a request (inputs copied); *id identifies it. Never blocks on the device. */
 int mg_server_submit(mg_server_t* s, const mg_request_t* req, int64_t* id);

@@ -80,9 +80,9 @@ struct mg_server {
   int64_t next_id = 1, in_use = 0, peak_bytes = 0;
   int64_t submitted = 0, completed = 0, failed = 0;
   int n_active = 0, peak_active = 0;
+  int n_setup = 0;                       // requests in host set-up on a worker
   bool stop = false;
   std::vector<std::thread> workers;
-  size_t workers_n = 1;
   std::thread poller;
 
   void finish_locked(Request* r, int status, const std::string& err) {
@@ -95,17 +95,32 @@ struct mg_server {
   }
 
   void worker() {
-    // the set-up workers share the host cores instead of each using all of them
-    nnmg::set_thread_budget(std::max(1, (int)std::thread::hardware_concurrency() / (int)workers_n));
     for (;;) {
       Request* r = nullptr;
+      int busy = 1;
       {
         std::unique_lock<std::mutex> lk(mu);
         cv_work.wait(lk, [&] { return stop || !pending.empty(); });
         if (stop && pending.empty()) return;
         r = pending.front();
         pending.pop_front();
+        busy = ++n_setup;
       }
+      // the host cores are shared among the requests in set-up when this one starts: alone it
+      // may use all of them, with k others a 1/(k+1) share (the set-up arithmetic does not
+      // depend on the number of threads)
+      nnmg::set_thread_budget(std::max(1, (int)std::thread::hardware_concurrency() / busy));
+      struct SetupDone {   // leaves the count when the host set-up ends, on every path
+        mg_server* s;
+        bool in = true;
+        void leave() {
+          if (!in) return;
+          in = false;
+          std::lock_guard<std::mutex> lk(s->mu);
+          --s->n_setup;
+        }
+        ~SetupDone() { leave(); }
+      } setup_done{this};
       r->t_setup0 = Clock::now();
       try {
         r->h = nnmg::build_host_hierarchy(r->meshes.data(), r->L, r->degree, r->thr, &r->opt);
@@ -125,6 +140,7 @@ struct mg_server {
         continue;
       }
       r->t_setup1 = Clock::now();
+      setup_done.leave();
       // admission: first in line, a free slot, and room under the budget
       {
         std::unique_lock<std::mutex> lk(mu);
@@ -262,7 +278,6 @@ int mg_server_create(int64_t hbm_budget_bytes, int32_t max_active, int32_t setup
   mg_server* s = new mg_server();
   s->budget = hbm_budget_bytes;
   s->max_active = max_active;
-  s->workers_n = (size_t)setup_threads;
   for (int i = 0; i < setup_threads; ++i) s->workers.emplace_back(&mg_server::worker, s);
   s->poller = std::thread(&mg_server::poll, s);
   *out = s;
