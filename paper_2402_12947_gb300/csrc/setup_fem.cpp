@@ -386,14 +386,37 @@ Csr assemble_stiffness(const MeshH& m, const DofMapH& dm) {
       dlocal[fill[g]] = (int8_t)a;
       dcells[fill[g]++] = c;
     }
-  // degenerate cells are an error
-  for (int64_t c = 0; c < m.nc; ++c) {
-    double G[12], vol;
-    if (!cell_geometry(m, c, G, &vol) || !(vol > 0))
-      throw Error(MG_ERR_DEGENERATE_CELL, "cell " + std::to_string(c) + " has zero volume");
-  }
+  // per cell: |K| and the Gram matrix G G^T of the barycentric gradients (rows of G), computed
+  // once instead of once per row of the cell; degenerate cells are an error (the first one)
+  std::vector<double> cvol(m.nc), cgg((size_t)m.nc * d1 * d1);
+  std::vector<uint8_t> bad(m.nc, 0);
+  parallel_for(m.nc, [&](int64_t lo, int64_t hi) {
+    for (int64_t c = lo; c < hi; ++c) {
+      double G[12], vol;
+      if (!cell_geometry(m, c, G, &vol) || !(vol > 0)) {
+        bad[c] = 1;
+        continue;
+      }
+      cvol[c] = vol;
+      double* gg = &cgg[(size_t)c * d1 * d1];
+      for (int p = 0; p < d1; ++p)
+        for (int q = 0; q < d1; ++q) {
+          double s = 0;
+          for (int r = 0; r < d; ++r) s += G[p * d + r] * G[q * d + r];
+          gg[p * d1 + q] = s;
+        }
+    }
+  });
+  for (int64_t c = 0; c < m.nc; ++c)
+    if (bad[c]) throw Error(MG_ERR_DEGENERATE_CELL, "cell " + std::to_string(c) + " has zero volume");
   GradTerm terms[10];
   for (int a = 0; a < nloc; ++a) terms[a] = basis_term(dm.degree, d, a);
+  // the means of the products of the basis gradients' affine factors, per (a, s, b, t)
+  double pm[10][2][10][2];
+  for (int a = 0; a < nloc; ++a)
+    for (int s = 0; s < terms[a].nterms; ++s)
+      for (int b = 0; b < nloc; ++b)
+        for (int t = 0; t < terms[b].nterms; ++t) pm[a][s][b][t] = affine_product_mean(terms[a].f[s], terms[b].f[t], d);
   // one pass per row: its pattern (free columns sharing a cell, sorted), then its values,
   // summed over its cells in ascending cell order
   return csr_from_rows(
@@ -418,22 +441,14 @@ Csr assemble_stiffness(const MeshH& m, const DofMapH& dm) {
         for (int64_t k = dstart[g]; k < dstart[g + 1]; ++k) {
           const int64_t c = dcells[k];
           const int a = dlocal[k];
-          double G[12], vol;
-          cell_geometry(m, c, G, &vol);
-          double GG[4][4];
-          for (int p = 0; p < d1; ++p)
-            for (int q = 0; q < d1; ++q) {
-              double s = 0;
-              for (int r = 0; r < d; ++r) s += G[p * d + r] * G[q * d + r];
-              GG[p][q] = s;
-            }
+          const double vol = cvol[c];
+          const double* gg = &cgg[(size_t)c * d1 * d1];
           for (int b = 0; b < nloc; ++b) {
             const int64_t fj = dm.free_index[dm.cell_dofs[c * nloc + b]];
             if (fj < 0) continue;
             double kab = 0;
             for (int s = 0; s < terms[a].nterms; ++s)
-              for (int t = 0; t < terms[b].nterms; ++t)
-                kab += GG[terms[a].p[s]][terms[b].p[t]] * affine_product_mean(terms[a].f[s], terms[b].f[t], d);
+              for (int t = 0; t < terms[b].nterms; ++t) kab += gg[terms[a].p[s] * d1 + terms[b].p[t]] * pm[a][s][b][t];
             const int64_t pos = std::lower_bound(rc, rc + buf.size(), (int32_t)fj) - rc;
             rv[pos] += vol * kab;
           }
@@ -577,6 +592,11 @@ Csr assemble_elasticity(const MeshH& m, const DofMapH& dm, double mu, double lam
   A.v.assign(A.rp[A.nrows], 0.0);
   GradTerm terms[10];
   for (int a = 0; a < nloc; ++a) terms[a] = basis_term(dm.degree, d, a);
+  double pm[10][2][10][2];   // means of the products of the gradients' affine factors
+  for (int a = 0; a < nloc; ++a)
+    for (int s1 = 0; s1 < terms[a].nterms; ++s1)
+      for (int b = 0; b < nloc; ++b)
+        for (int t1 = 0; t1 < terms[b].nterms; ++t1) pm[a][s1][b][t1] = affine_product_mean(terms[a].f[s1], terms[b].f[t1], d);
   parallel_for(nf, [&](int64_t lo, int64_t hi) {
     for (int64_t i = lo; i < hi; ++i) {
       const std::vector<int32_t>& cols = pat[i];
@@ -599,7 +619,7 @@ Csr assemble_elasticity(const MeshH& m, const DofMapH& dm, double mu, double lam
           double M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
           for (int s1 = 0; s1 < terms[a].nterms; ++s1)
             for (int t1 = 0; t1 < terms[b].nterms; ++t1) {
-              const double w = affine_product_mean(terms[a].f[s1], terms[b].f[t1], d);
+              const double w = pm[a][s1][b][t1];
               const double* ga = &G[terms[a].p[s1] * d];
               const double* gb = &G[terms[b].p[t1] * d];
               for (int r = 0; r < d; ++r)
