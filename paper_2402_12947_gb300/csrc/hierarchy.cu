@@ -1131,80 +1131,88 @@ struct DeviceLanczos {
   }
   ~DeviceLanczos() { mem.release(); }
 
-  double run(const uint8_t* keep, double tol, int maxit, int* iters) {
-    std::vector<double> sk = sc;
-    int64_t nk = 0;
-    for (int64_t i = 0; i < n; ++i) {
-      if (keep && !keep[i]) sk[i] = 0.0;
-      nk += sk[i] != 0.0;
-    }
-    if (nk == 0) {
-      if (iters) *iters = 0;
-      return 0.0;
-    }
+  // lambda_max of each of nv <= 2 runs (run r restricted to the rows keeps[r] marks, null: all),
+  // advanced together through the same launches; iters[r] and the result theta[r] are those of
+  // run r alone.
+  void run(int nv, const uint8_t* const* keeps, double tol, int maxit, int* iters, double* theta) {
+    // step k of run r leaves alpha_k in hist[r][2k] and beta_{k+1}^2 in hist[r][2k+1]; the host
+    // reads them back every kLanczosBatch steps and replays each run's stopping rule step by
+    // step, so every result (theta and the step count) is that of a loop which tested after
+    // every step; the steps queued past a run's stopping point are discarded
+    constexpr int kLanczosBatch = 16;
     DevMem run;
     run.stream = s;
-    double* hh = nullptr;
-    struct Release {   // this run's buffers also on an error path (stream-ordered frees)
+    double* hh[2] = {nullptr, nullptr};
+    struct Release {   // the runs' buffers also on an error path (stream-ordered frees)
       DevMem& m;
-      double*& h;
+      double** h;
       ~Release() {
         m.release();
-        if (h) {
-          cudaStreamSynchronize(m.stream);   // no copy into the staging buffer still in flight
-          pinned_release(h);
-        }
+        if (h[0] || h[1]) cudaStreamSynchronize(m.stream);   // no copy into a staging buffer in flight
+        for (int r = 0; r < 2; ++r)
+          if (h[r]) pinned_release(h[r]);
       }
     } release{run, hh};
-    double* v = run.upload(lanczos_start(sk));
-    double* vprev = run.alloc<double>(n);
-    double* w = run.alloc<double>(n);
-    // block partials of both reductions (the SpMV's grid covers the 32-row slices of n rows)
-    double* part = run.alloc<double>((n + 31) / 32 * 32 / kBlock + 1);
-    unsigned* ticket = run.alloc<unsigned>(1);
-    const uint8_t* kd = nullptr;
-    if (keep) kd = run.upload(std::vector<uint8_t>(keep, keep + n));
-    // step k leaves alpha_k in hist[2k] and beta_{k+1}^2 in hist[2k+1]; the host reads them
-    // back every kLanczosBatch steps and replays the stopping rule step by step, so the
-    // result (theta and the step count) is that of a loop which tested after every step; the
-    // steps queued past the stopping point are discarded
-    constexpr int kLanczosBatch = 16;
-    const int kmax = (int)std::min<int64_t>(maxit, nk);
-    double* hist = run.alloc<double>(2 * (size_t)std::max(kmax, 1));
-    hh = pinned_acquire(2 * (int64_t)std::max(kmax, 1));
-    std::vector<double> al, be(1, 0.0);
-    double theta = 0.0;
-    int k = 0, queued = 0;
-    bool done = false;
-    while (!done && queued < kmax) {
-      const int q1 = std::min(kmax, queued + kLanczosBatch);
-      for (int j = queued; j < q1; ++j) {
-        if (j > 0) lanczos_next((int)n, w, v, vprev, hist + 2 * j - 1, s);
-        lanczos_spmv_dot(M, v, w, part, ticket, hist + 2 * j, s);
-        lanczos_update((int)n, w, v, vprev, hist + 2 * j, j > 0 ? hist + 2 * j - 1 : nullptr, kd, part, ticket,
-                       hist + 2 * j + 1, s);
+    double *v[2], *w[2], *vprev[2], *hist[2];
+    const uint8_t* kd[2] = {nullptr, nullptr};
+    int kmax[2] = {0, 0}, k[2] = {0, 0}, kall = 0;
+    bool done[2] = {false, false};
+    for (int r = 0; r < nv; ++r) {
+      std::vector<double> sk = sc;
+      int64_t nk = 0;
+      for (int64_t i = 0; i < n; ++i) {
+        if (keeps[r] && !keeps[r][i]) sk[i] = 0.0;
+        nk += sk[i] != 0.0;
       }
-      CK(cudaMemcpyAsync(hh + 2 * queued, hist + 2 * queued, 2 * sizeof(double) * (q1 - queued),
-                         cudaMemcpyDeviceToHost, s));
+      kmax[r] = (int)std::min<int64_t>(maxit, nk);
+      kall = std::max(kall, kmax[r]);
+      theta[r] = 0.0;
+      if (iters) iters[r] = 0;
+      done[r] = kmax[r] == 0;
+      v[r] = run.upload(lanczos_start(sk));
+      vprev[r] = run.alloc<double>(n);
+      w[r] = run.alloc<double>(n);
+      if (keeps[r]) kd[r] = run.upload(std::vector<uint8_t>(keeps[r], keeps[r] + n));
+    }
+    if (kall == 0) return;
+    for (int r = 0; r < nv; ++r) {
+      hist[r] = run.alloc<double>(2 * (size_t)kall);
+      hh[r] = pinned_acquire(2 * (int64_t)kall);
+    }
+    // block partials of the reductions, per run (the SpMV's grid covers the 32-row slices)
+    double* part = run.alloc<double>(2 * ((n + 31) / 32 * 32 / kBlock + 1));
+    unsigned* ticket = run.alloc<unsigned>(1);
+    std::vector<double> al[2], be[2];
+    for (int r = 0; r < nv; ++r) be[r].assign(1, 0.0);
+    int queued = 0;
+    while (!(done[0] && (nv < 2 || done[1])) && queued < kall) {
+      const int q1 = std::min(kall, queued + kLanczosBatch);
+      for (int j = queued; j < q1; ++j) lanczos_step(M, nv, v, w, vprev, kd, hist, j, part, ticket, s);
+      for (int r = 0; r < nv; ++r)
+        CK(cudaMemcpyAsync(hh[r] + 2 * queued, hist[r] + 2 * queued, 2 * sizeof(double) * (q1 - queued),
+                           cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
-      for (; k < q1; ++k) {
-        const double alpha = hh[2 * k], beta = std::sqrt(hh[2 * k + 1]);
-        al.push_back(alpha);
-        be.push_back(beta);
-        double sl;
-        tridiag_top(al, be, k + 1, &theta, &sl);
-        if (beta * sl <= tol * std::fabs(theta) || beta <= 1e-14 * std::fabs(theta)) {
-          ++k;
-          done = true;
-          break;
+      for (int r = 0; r < nv; ++r) {
+        for (; !done[r] && k[r] < std::min(q1, kmax[r]); ++k[r]) {
+          const double alpha = hh[r][2 * k[r]], beta = std::sqrt(hh[r][2 * k[r] + 1]);
+          al[r].push_back(alpha);
+          be[r].push_back(beta);
+          double sl;
+          tridiag_top(al[r], be[r], k[r] + 1, &theta[r], &sl);
+          if (beta * sl <= tol * std::fabs(theta[r]) || beta <= 1e-14 * std::fabs(theta[r])) {
+            ++k[r];
+            done[r] = true;
+            break;
+          }
         }
+        if (k[r] >= kmax[r]) done[r] = true;
       }
       queued = q1;
     }
     check_launch("device Lanczos");
     CK(cudaStreamSynchronize(s));
-    if (iters) *iters = k;
-    return theta;
+    if (iters)
+      for (int r = 0; r < nv; ++r) iters[r] = k[r];
   }
 };
 
@@ -1219,23 +1227,27 @@ void compute_eigenvalues(mg_hierarchy* h, bool on_device) {
       lv.lmax = o.lambda_override[l];
       if (!(lv.lmax > 0)) throw Error(MG_ERR_INVALID_ARG, "lambda_override must be positive");
     } else {
-      std::unique_ptr<DeviceLanczos> dlz;
-      if (on_device) dlz.reset(new DeviceLanczos(lv.A, h->own_stream));
-      auto lanczos = [&](const uint8_t* keep, int* it) {
-        return on_device ? dlz->run(keep, o.eig_tol, o.eig_maxit, it)
-                         : lanczos_lmax(lv.A, keep, o.eig_tol, o.eig_maxit, it);
-      };
-      int it = 0;
-      lv.lmax_unadj = lanczos(nullptr, &it);
-      lv.lanczos_iters = it;
-      if (lv.patch_ptr.size() > 1) {
-        std::vector<uint8_t> keep(lv.A.nrows, 1);
+      // the unadjusted run and, with patches, the run restricted to the complement of the patch
+      // DoFs (adjusted lambda, Sec. 5); on the device both advance through the same launches
+      const bool adj = lv.patch_ptr.size() > 1;
+      std::vector<uint8_t> keep;
+      if (adj) {
+        keep.assign(lv.A.nrows, 1);
         for (int32_t f : lv.patch_dofs) keep[f] = 0;
-        lv.lmax_adj = lanczos(keep.data(), &it);
-        lv.lanczos_iters += it;
-      } else {
-        lv.lmax_adj = lv.lmax_unadj;
       }
+      int it[2] = {0, 0};
+      double th[2] = {0.0, 0.0};
+      if (on_device) {
+        DeviceLanczos dlz(lv.A, h->own_stream);
+        const uint8_t* keeps[2] = {nullptr, adj ? keep.data() : nullptr};
+        dlz.run(adj ? 2 : 1, keeps, o.eig_tol, o.eig_maxit, it, th);
+      } else {
+        th[0] = lanczos_lmax(lv.A, nullptr, o.eig_tol, o.eig_maxit, &it[0]);
+        if (adj) th[1] = lanczos_lmax(lv.A, keep.data(), o.eig_tol, o.eig_maxit, &it[1]);
+      }
+      lv.lmax_unadj = th[0];
+      lv.lmax_adj = adj ? th[1] : th[0];
+      lv.lanczos_iters = it[0] + (adj ? it[1] : 0);
       lv.lmax = (o.adjusted_lambda ? lv.lmax_adj : lv.lmax_unadj) * o.lmax_safety;
       tm.mark(std::string(on_device ? "device" : "host") + " lanczos L" + std::to_string(l) + " (" +
               std::to_string(lv.lanczos_iters) + " it)");

@@ -542,39 +542,60 @@ __device__ void reduce_finish(double s, const Reduce& rd) {
   }
 }
 
-// Every thread of the block calls this with the block's partial s (valid in thread 0); the last
-// block to arrive sums the partials in index order into *out and resets the ticket.
-__device__ void reduce_to(double s, double* part, unsigned* ticket, double* out) {
+// Every thread of the block calls this with the block's partials s[0 .. nv) (valid in thread 0),
+// nv <= 2; the last block to arrive sums each run's partials in index order into *out[r] and
+// resets the ticket. part holds gridDim.x entries per run.
+__device__ void reduce_to2(int nv, const double* s, double* part, unsigned* ticket, double* const* out) {
   __shared__ bool last;
   if (threadIdx.x == 0) {
-    part[blockIdx.x] = s;
+    for (int r = 0; r < nv; ++r) part[r * gridDim.x + blockIdx.x] = s[r];
     __threadfence();
     last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
   if (!last) return;  // block-uniform
   __threadfence();
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) acc += __ldcg(part + i);
-  acc = block_sum(acc);
-  if (threadIdx.x == 0) {
-    *out = acc;
-    *ticket = 0u;
+  for (int r = 0; r < nv; ++r) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) acc += __ldcg(part + r * gridDim.x + i);
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) *out[r] = acc;
+    __syncthreads();   // block_sum's shared words are reused by the next run
   }
+  if (threadIdx.x == 0) *ticket = 0u;
 }
 
-// Lanczos step on the scaled operator: w = S v and alpha = w.v in one launch.
+// One or two Lanczos runs on the same scaled operator S (set-up), advanced together: run r has
+// its vectors v, w, vprev, the rows it keeps (null: all) and its scalar history (alpha_k at 2k,
+// beta_{k+1}^2 at 2k + 1). Each run's arithmetic is that of a run alone.
+struct LzRuns {
+  int nv;
+  double* v[2];
+  double* w[2];
+  double* vprev[2];
+  const uint8_t* keep[2];
+  double* hist[2];
+};
+
+// Step j: w = S v and alpha = w.v for every run in one launch (the operator's rows are read by
+// the first run and found in cache by the second).
 template <int G, bool C16>
-__global__ void __launch_bounds__(kBlock) k_lz_spmv_dot(OpView<double> m, const double* __restrict__ v,
-                                                        double* __restrict__ w, double* part, unsigned* ticket,
-                                                        double* alpha) {
-  int row;
-  double ax, s = 0.0;
-  if (op_row<double, G, C16>(m, v, row, ax) && group_leader<G>()) {
-    w[row] = ax;
-    s = ax * v[row];
+__global__ void __launch_bounds__(kBlock) k_lz_spmv_dot(OpView<double> m, LzRuns z, int j, double* part,
+                                                        unsigned* ticket) {
+  double s[2] = {0.0, 0.0};
+  double* out[2];
+  for (int r = 0; r < z.nv; ++r) {
+    int row;
+    double ax;
+    if (op_row<double, G, C16>(m, z.v[r], row, ax) && group_leader<G>()) {
+      z.w[r][row] = ax;
+      s[r] = ax * z.v[r][row];
+    }
+    s[r] = block_sum(s[r]);
+    __syncthreads();
+    out[r] = z.hist[r] + 2 * j;
   }
-  reduce_to(block_sum(s), part, ticket, alpha);
+  reduce_to2(z.nv, s, part, ticket, out);
 }
 
 // q = A p with the p.q reduction in the same launch. The grid (one resident wave) walks
@@ -1014,30 +1035,39 @@ __global__ void __launch_bounds__(kBlock) k_dot_self(int n, const double* __rest
 inline int grid_for(int n, int per) { return (n + per - 1) / per; }
 
 // ---- Lanczos on the scaled operator S (set-up) ----
-// w -= alpha v + beta vprev with beta = sqrt(beta2) (beta2 null: beta = 0), and w = 0 where
-// keep (if given) is 0; |w|^2 into *out (last block)
-__global__ void __launch_bounds__(kBlock) k_lz_update(int n, double* __restrict__ w, const double* __restrict__ v,
-                                                      const double* __restrict__ vprev, const double* __restrict__ alpha,
-                                                      const double* __restrict__ beta2, const uint8_t* __restrict__ keep,
-                                                      double* part, unsigned* ticket, double* out) {
-  const double a = *alpha;
-  const double beta = beta2 ? sqrt(*beta2) : 0.0;
-  double s = 0.0;
-  for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
-    const double wi = keep && !keep[i] ? 0.0 : w[i] - (a * v[i] + beta * vprev[i]);
-    w[i] = wi;
-    s = fma(wi, wi, s);
+// Step j: w -= alpha v + beta vprev with beta = sqrt(beta_j^2) (0 at j = 0), and w = 0 outside
+// the run's kept rows; |w|^2 = beta_{j+1}^2 into the history (last block), for every run.
+__global__ void __launch_bounds__(kBlock) k_lz_update(int n, LzRuns z, int j, double* part, unsigned* ticket) {
+  double s[2] = {0.0, 0.0};
+  double* out[2];
+  for (int r = 0; r < z.nv; ++r) {
+    const double a = z.hist[r][2 * j];
+    const double beta = j > 0 ? sqrt(z.hist[r][2 * j - 1]) : 0.0;
+    const double* __restrict__ v = z.v[r];
+    const double* __restrict__ vp = z.vprev[r];
+    const uint8_t* __restrict__ keep = z.keep[r];
+    double* __restrict__ w = z.w[r];
+    double acc = 0.0;
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
+      const double wi = keep && !keep[i] ? 0.0 : w[i] - (a * v[i] + beta * vp[i]);
+      w[i] = wi;
+      acc = fma(wi, wi, acc);
+    }
+    s[r] = block_sum(acc);
+    __syncthreads();
+    out[r] = z.hist[r] + 2 * j + 1;
   }
-  reduce_to(block_sum(s), part, ticket, out);
+  reduce_to2(z.nv, s, part, ticket, out);
 }
 
-// v_{k+1} = w / beta with beta = sqrt(beta2); vprev = v_k
-__global__ void __launch_bounds__(kBlock) k_lz_next(int n, const double* __restrict__ w, double* __restrict__ v,
-                                                    double* __restrict__ vprev, const double* __restrict__ beta2) {
-  const double inv_beta = 1.0 / sqrt(*beta2);
-  for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
-    vprev[i] = v[i];
-    v[i] = w[i] * inv_beta;
+// Step j > 0: vprev = v, v = w / beta with beta = sqrt(beta_j^2), for every run.
+__global__ void __launch_bounds__(kBlock) k_lz_next(int n, LzRuns z, int j) {
+  for (int r = 0; r < z.nv; ++r) {
+    const double inv_beta = 1.0 / sqrt(z.hist[r][2 * j - 1]);
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
+      z.vprev[r][i] = z.v[r][i];
+      z.v[r][i] = z.w[r][i] * inv_beta;
+    }
   }
 }
 
@@ -1259,13 +1289,7 @@ __global__ void __launch_bounds__(kBlock) k_fp64_fma(int iters, double c, double
 
 }  // namespace
 
-void lanczos_update(int n, double* w, const double* v, const double* vprev, const double* alpha, const double* beta2,
-                    const uint8_t* keep, double* part, unsigned* ticket, double* out, cudaStream_t s) {
-  k_lz_update<<<cg_parts(n), kBlock, 0, s>>>(n, w, v, vprev, alpha, beta2, keep, part, ticket, out);
-}
-void lanczos_next(int n, const double* w, double* v, double* vprev, const double* beta2, cudaStream_t s) {
-  k_lz_next<<<cg_parts(n), kBlock, 0, s>>>(n, w, v, vprev, beta2);
-}
+
 
 void batched_spsd_inverse(const GjBatch& g, cudaStream_t s) {
   // matrices are sorted by size, largest first: the small ones take one block each for the
@@ -1498,12 +1522,25 @@ void sell_gs(const SellMat<T>& M, const int32_t* rows, const T* b, const T* dinv
     launch(k_gs<T, L::lanes, L::c16>, op_blocks(M), kBlock, 0, s, view(M), rows, x, b, dinv, x);
   });
 }
-void lanczos_spmv_dot(const SellMat<double>& M, const double* v, double* w, double* part, unsigned* ticket,
-                      double* alpha, cudaStream_t s) {
+void lanczos_step(const SellMat<double>& M, int nv, double* const* v, double* const* w, double* const* vprev,
+                  const uint8_t* const* keep, double* const* hist, int j, double* part, unsigned* ticket,
+                  cudaStream_t s) {
+  LzRuns z{};
+  z.nv = nv;
+  for (int r = 0; r < nv; ++r) {
+    z.v[r] = v[r];
+    z.w[r] = w[r];
+    z.vprev[r] = vprev[r];
+    z.keep[r] = keep[r];
+    z.hist[r] = hist[r];
+  }
+  const int n = M.nrows;
+  if (j > 0) k_lz_next<<<cg_parts(n), kBlock, 0, s>>>(n, z, j);
   by_layout(M.lanes, M.unroll, M.sub, M.col16 != nullptr, [&](auto g) {
     using L = decltype(g);
-    launch(k_lz_spmv_dot<L::lanes, L::c16>, op_blocks(M), kBlock, 0, s, view(M), v, w, part, ticket, alpha);
+    launch(k_lz_spmv_dot<L::lanes, L::c16>, op_blocks(M), kBlock, 0, s, view(M), z, j, part, ticket);
   });
+  k_lz_update<<<cg_parts(n), kBlock, 0, s>>>(n, z, j, part, ticket);
 }
 // Blocks of one k_ap launch: one resident wave (SMs x the blocks of this instantiation that fit
 // on an SM: four at its 60-62 registers), at most one per row block. With two waves (8 blocks

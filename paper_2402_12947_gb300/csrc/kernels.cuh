@@ -243,18 +243,17 @@ void batched_spsd_inverse(const GjBatch& g, cudaStream_t s);
 // max_i sum_j |M_ij| of each matrix of a batch (its 1-norm, M symmetric) into out[b].
 void batched_norm1(const GjBatch& g, double* out, cudaStream_t s);
 
-// ---- Lanczos (set-up): w = S v with alpha = w.v; w -= alpha v + beta vprev with out = |w|^2;
-// v, vprev advanced with v = w / beta. The scalars stay on the device (alpha and beta^2 as the
-// reductions left them; beta = sqrt(beta^2) taken where it is used, a null beta2 meaning
-// beta = 0), so that several steps can be queued without a host round trip. With keep
-// (nullable), the update also sets w = 0 where keep is 0. Each reduction is finished by the
-// last block of the kernel that produces it (fixed order; part holds the block partials,
-// ticket a zeroed counter). ----
-void lanczos_spmv_dot(const SellMat<double>& M, const double* v, double* w, double* part, unsigned* ticket,
-                      double* alpha, cudaStream_t s);
-void lanczos_update(int n, double* w, const double* v, const double* vprev, const double* alpha, const double* beta2,
-                    const uint8_t* keep, double* part, unsigned* ticket, double* out, cudaStream_t s);
-void lanczos_next(int n, const double* w, double* v, double* vprev, const double* beta2, cudaStream_t s);
+// ---- Lanczos (set-up): step j of nv <= 2 runs on the same scaled operator M (SELL-32, one
+// lane per row), run r with vectors v[r], w[r], vprev[r] (length M.nrows), the rows it keeps
+// keep[r] (null: all) and its scalar history hist[r] (alpha_k at 2k, beta_{k+1}^2 at 2k + 1):
+// for j > 0 v = w / beta_j (vprev = the old v), then w = M v with alpha_j = w.v, then
+// w -= alpha_j v + beta_j vprev (w = 0 outside keep) with beta_{j+1}^2 = |w|^2. The scalars
+// stay on the device, so that several steps can be queued without a host round trip; each
+// reduction is finished by the last block of the kernel that produces it (fixed order; part
+// holds 2 x the blocks of one launch, ticket is a zeroed counter). ----
+void lanczos_step(const SellMat<double>& M, int nv, double* const* v, double* const* w, double* const* vprev,
+                  const uint8_t* const* keep, double* const* hist, int j, double* part, unsigned* ticket,
+                  cudaStream_t s);
 
 // ---- vectors ----
 template <typename Src, typename Dst> void convert(int n, const Src* a, Dst* b, cudaStream_t s);
